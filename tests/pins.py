@@ -1,0 +1,378 @@
+"""Checks that pin the CPU oracle to facts outside itself.
+
+Each pin_* function raises AssertionError when the oracle disagrees with what
+the paper, a closed form, a textbook bound or an independent library fixes.
+They are called by the oracle tests and, against deliberately broken copies
+of the oracle, by the mutation tests (which expect them to fail).
+"""
+import ctypes
+import ctypes.util
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox and the Gaussian test matrix
+# --------------------------------------------------------------------------
+def _curand_lib():
+    cands = ["/usr/local/cuda/lib64/libcurand.so", ctypes.util.find_library("curand")]
+    for c in cands:
+        if c and os.path.exists(c) or (c and not c.startswith("/")):
+            try:
+                return ctypes.CDLL(c)
+            except OSError:
+                continue
+    return None
+
+
+def curand_host_philox_words(seed, n_words):
+    """Words from cuRAND's host-side Philox4x32-10 generator (an independent
+    library implementation of the same published generator)."""
+    lib = _curand_lib()
+    if lib is None:
+        return None
+    gen = ctypes.c_void_p()
+    CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
+    if lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) != 0:
+        return None
+    try:
+        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        buf = (ctypes.c_uint * n_words)()
+        assert lib.curandGenerate(gen, buf, ctypes.c_size_t(n_words)) == 0
+        return np.frombuffer(buf, dtype=np.uint32).copy()
+    finally:
+        lib.curandDestroyGenerator(gen)
+
+
+# cuRAND's host generator emits Philox block (counter n, subsequence s) at
+# output position n * 65536 + s (ordering observed and fixed by this test).
+CURAND_SUBSEQ_STRIDE = 65536
+
+
+def pin_philox_curand(philox):
+    """Oracle Philox words == cuRAND host Philox words for several counters,
+    streams (subsequences) and 64-bit seeds."""
+    checked = 0
+    for seed in (0, 7, 0x123456789ABCDEF, 0xFFFFFFFF00000001):
+        ref = curand_host_philox_words(seed, 4 * (3 * CURAND_SUBSEQ_STRIDE))
+        if ref is None:
+            raise RuntimeError("cuRAND host generator unavailable")
+        ref = ref.reshape(-1, 4)
+        for stream in (0, 1, 2, 5, 300, 65535):
+            mine = philox.philox_words(seed, stream, 3)
+            for n in range(3):
+                got = ref[n * CURAND_SUBSEQ_STRIDE + stream]
+                assert np.array_equal(mine[n], got), (seed, stream, n, mine[n], got)
+                checked += 1
+    return checked
+
+
+def pin_gaussian_stats(philox, n=400_000):
+    """Omega entries are N(0,1): KS test, moments, and the Box-Muller radius
+    z0^2 + z1^2 ~ chi^2(2) (mean 2); pairs uncorrelated; streams independent."""
+    from scipy import stats
+
+    Om = philox.gaussian_matrix(12345, 0, n // 400, 400).astype(np.float64).ravel()
+    assert abs(Om.mean()) < 5.0 / np.sqrt(Om.size), Om.mean()
+    assert abs(Om.var() - 1.0) < 0.01, Om.var()
+    assert stats.kstest(Om, "norm").pvalue > 1e-4
+    z = Om.reshape(-1, 2)
+    assert abs((z ** 2).sum(1).mean() - 2.0) < 0.03
+    assert abs(np.corrcoef(z[:, 0], z[:, 1])[0, 1]) < 0.01
+    Om2 = philox.gaussian_matrix(12345, 1, n // 400, 400).astype(np.float64).ravel()
+    assert abs(np.corrcoef(Om, Om2)[0, 1]) < 0.01
+    # the fourth moment of N(0,1) is 3
+    assert abs((Om ** 4).mean() - 3.0) < 0.08
+
+
+def pin_box_muller_special(philox):
+    """Closed forms of the transform: u1 = 1 gives z = 0; u2 near 1/4 puts the
+    whole radius into z1; u2 near 1/2 gives z0 = -radius."""
+    x = np.array([0xFFFFFFFF], dtype=np.uint32)          # u1 = 2^24 * 2^-24 = 1
+    z0, z1 = philox.box_muller(x, np.array([12345], dtype=np.uint32))
+    assert z0[0] == 0.0 and z1[0] == 0.0
+    # x = 0 -> u1 = 2^-24 -> radius sqrt(48 ln 2)
+    rad = np.sqrt(48.0 * np.log(2.0))
+    y_quarter = np.array([((1 << 21) << 9)], dtype=np.uint32)          # y>>9 = 2^21 -> u2 = (2^22+1)/2^24
+    z0, z1 = philox.box_muller(np.array([0], dtype=np.uint32), y_quarter)
+    assert abs(z1[0] - rad) < 1e-5 and abs(z0[0]) < 1e-5
+    y_half = np.array([((1 << 22) << 9)], dtype=np.uint32)             # u2 = (2^23+1)/2^24
+    z0, z1 = philox.box_muller(np.array([0], dtype=np.uint32), y_half)
+    assert abs(z0[0] + rad) < 1e-5 and abs(z1[0]) < 1e-5
+
+
+# --------------------------------------------------------------------------
+# Quantiser, e4m3 and QM
+# --------------------------------------------------------------------------
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append([p.strip() for p in line.split("|")])
+    return rows
+
+
+def pin_quant_golden(quant):
+    """Hand-worked examples of Eqs. (get_lambda) and (Quantization)."""
+    for bits, xs, codes in _read_golden("quant_worked_example.txt"):
+        prec = quant.PREC_INT8 if int(bits) == 8 else quant.PREC_INT4
+        x = np.array([[float(v) for v in xs.split()]], dtype=np.float32)
+        want = np.array([[float(v) for v in codes.split()]])
+        got, lam, s = quant.quantize(x, prec, 1)
+        assert np.array_equal(got, want), (bits, xs, got, want)
+
+
+def e4m3_decode_all():
+    """All finite e4m3 values from the bit-field definition (OCP OFP8)."""
+    vals = []
+    for code in range(256):
+        sgn = -1.0 if code & 0x80 else 1.0
+        e = (code >> 3) & 0xF
+        m = code & 0x7
+        if e == 15 and m == 7:
+            continue                                    # NaN
+        v = (m / 8.0) * 2.0 ** -6 if e == 0 else (1.0 + m / 8.0) * 2.0 ** (e - 7)
+        vals.append(sgn * v)
+    return np.array(sorted(set(vals)))
+
+
+def pin_e4m3(quant):
+    """Golden roundings, every representable value maps to itself, every
+    midpoint of two neighbours goes to the one with even mantissa."""
+    for x, want in _read_golden("e4m3_rounding.txt"):
+        got = quant.round_e4m3(np.float32(float(x)))
+        assert float(got) == float(want), (x, got, want)
+    grid = e4m3_decode_all()
+    assert grid.max() == 448.0 and np.min(grid[grid > 0]) == 2.0 ** -9
+    assert np.array_equal(quant.round_e4m3(grid.astype(np.float32)), grid)
+    pos = grid[grid >= 0]
+    mids = (pos[:-1] + pos[1:]) / 2.0
+    got = quant.round_e4m3(mids.astype(np.float32))
+    for lo, hi, g in zip(pos[:-1], pos[1:], got):
+        # even neighbour: its mantissa field (value / grid step) is even
+        step = hi - lo
+        lo_even = int(round(lo / step)) % 2 == 0
+        assert g == (lo if lo_even else hi), (lo, hi, g)
+    # nudged just off the midpoint, rounding goes to the nearer neighbour
+    up = quant.round_e4m3((mids * (1 + 1e-6)).astype(np.float32))
+    assert np.array_equal(up, pos[1:])
+
+
+def pin_quant_bounds(quant, seed=5):
+    """Thm 4.2, elementwise: |x - deq(q(x))| <= lambda^-1, here <= (1/2 + eps) s
+    under round-to-nearest; codes symmetric (q(-x) = -q(x)); the group's
+    largest magnitude maps to +-D; codes within +-D."""
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((37, 53)) * np.exp(rng.uniform(-4, 4, (37, 1)))).astype(np.float32)
+    for prec, D in ((quant.PREC_INT8, 127), (quant.PREC_INT4, 7)):
+        for axis in (1, 0, None):
+            c, lam, s = quant.quantize(X, prec, axis)
+            deq = quant.dequantize(c, s, axis)
+            sb = s[:, None] if axis == 1 else (s[None, :] if axis == 0 else s[0])
+            assert np.all(np.abs(X - deq) <= (0.5 + 1e-5) * sb + 1e-30)
+            cn, _, _ = quant.quantize(-X, prec, axis)
+            assert np.array_equal(cn, -c)
+            assert np.abs(c).max() == D
+            if axis == 1:
+                idx = np.argmax(np.abs(X), axis=1)
+                assert np.all(np.abs(c[np.arange(X.shape[0]), idx]) == D)
+    # e4m3: relative error at most 2^-4 (3 mantissa bits) for normal values
+    c, lam, s = quant.quantize(X, quant.PREC_E4M3, 1)
+    y = X * lam[:, None]
+    normal = np.abs(y) >= 2.0 ** -6
+    assert np.all(np.abs(c - y)[normal] <= 2.0 ** -4 * np.abs(y)[normal] + 1e-7)
+
+
+def pin_qm_bruteforce(quant, seed=6):
+    """The code product equals a brute-force loop in Python integers, including
+    the all-extreme worst case; QM equals the dequantised operands' product."""
+    rng = np.random.default_rng(seed)
+    for (M, K, N) in ((3, 5, 4), (6, 17, 5)):
+        a = rng.integers(-127, 128, (M, K))
+        b = rng.integers(-127, 128, (K, N))
+        want = [[sum(int(a[i, t]) * int(b[t, j]) for t in range(K)) for j in range(N)] for i in range(M)]
+        got = quant.code_product(a, b)
+        assert np.array_equal(got, np.array(want, dtype=np.float64))
+    a = np.full((2, 1024), 127.0)
+    b = np.full((1024, 2), -127.0)
+    b[::2] = 127.0
+    got = quant.code_product(a, b)
+    assert np.array_equal(got, np.zeros((2, 2)))
+    got = quant.code_product(a, np.full((1024, 1), -127.0))
+    assert got[0, 0] == -127 * 127 * 1024
+    # QM == deq(L) @ deq(R) (scales attached to the right indices)
+    L = (rng.standard_normal((9, 31)) * np.exp(rng.uniform(-3, 3, (9, 1)))).astype(np.float32)
+    R = (rng.standard_normal((31, 7)) * np.exp(rng.uniform(-3, 3, (1, 7)))).astype(np.float32)
+    for prec in (quant.PREC_INT8, quant.PREC_INT4, quant.PREC_E4M3):
+        for scale, (al, ar) in ((quant.SCALE_ROWCOL, (1, 0)), (quant.SCALE_TENSOR, (None, None))):
+            cl, _, sl = quant.quantize(L, prec, al)
+            cr, _, sr = quant.quantize(R, prec, ar)
+            ref = quant.dequantize(cl, sl, al).astype(np.float64) @ quant.dequantize(cr, sr, ar).astype(np.float64)
+            got = quant.qm(L, R, prec, scale).astype(np.float64)
+            assert np.allclose(got, ref, rtol=1e-5, atol=1e-6 * np.abs(ref).max()), (prec, scale)
+
+
+def pin_qm_error_bound(quant, seed=7):
+    """Eq. (er_quant) / Thm 4.3 for per-tensor scales, plus its elementwise
+    form: |C - C~|_ij <= sum_t |a_it| e_b + e_a |b_tj| + e_a e_b with
+    e = s/2 the largest rounding error of each operand."""
+    rng = np.random.default_rng(seed)
+    m, k, n = 40, 64, 30
+    A = rng.uniform(-1, 1, (m, k)).astype(np.float32)
+    Bm = rng.uniform(-1, 1, (k, n)).astype(np.float32)
+    C = A.astype(np.float64) @ Bm.astype(np.float64)
+    for prec in (quant.PREC_INT8, quant.PREC_INT4):
+        Ct = quant.qm(A, Bm, prec, quant.SCALE_TENSOR).astype(np.float64)
+        D = 127.0 if prec == quant.PREC_INT8 else 7.0
+        lam1 = D / np.abs(A).max()
+        lam2 = D / np.abs(Bm).max()
+        sig1 = np.linalg.norm(A, 2)
+        gam1 = np.linalg.norm(Bm, 2)
+        bound = k * (sig1 / lam2 * np.sqrt(n) + gam1 / lam1 * np.sqrt(m) + np.sqrt(m * n) / (lam1 * lam2))
+        assert np.linalg.norm(C - Ct) <= bound
+        ea, eb = 0.5 / lam1, 0.5 / lam2
+        elem = np.abs(A).astype(np.float64) @ np.full((k, n), eb) + np.full((m, k), ea) @ np.abs(Bm) + k * ea * eb
+        assert np.all(np.abs(C - Ct) <= elem * (1 + 1e-5) + 1e-6)
+
+
+# --------------------------------------------------------------------------
+# Randomized SVD
+# --------------------------------------------------------------------------
+def pin_orth(lr, seed=8):
+    """orth(Y) is the unique thin QR factor: Q^T Q = I, Q^T Y upper triangular
+    with positive diagonal, Y = Q (Q^T Y)."""
+    rng = np.random.default_rng(seed)
+    Y = rng.standard_normal((70, 12)) @ np.diag(np.logspace(0, -6, 12))
+    Q = lr.orth(Y)
+    R = Q.T @ Y
+    assert np.abs(Q.T @ Q - np.eye(12)).max() < 1e-13
+    assert np.abs(np.tril(R, -1)).max() < 1e-12 * np.abs(R).max()
+    assert np.all(np.diag(R) > 0)
+    assert np.abs(Q @ R - Y).max() < 1e-13 * np.abs(Y).max()
+
+
+def pin_rsvd_exact_rank(lr, wl, seed=9):
+    """A matrix of rank <= r is reproduced to 1e-12 (the sketch captures its
+    range with probability 1), for q = 0, 1, 2, and the factors are
+    orthonormal with descending positive singular values."""
+    for (m, k, rank, r, p) in ((60, 45, 6, 6, 4), (40, 70, 5, 8, 3), (33, 33, 10, 10, 2)):
+        A = wl.exact_rank(m, k, rank, seed)
+        for q in (0, 1, 2):
+            U, s, V = lr.rsvd(A, r, p, q, 77, 0)
+            assert U.shape == (m, r) and V.shape == (k, r) and s.shape == (r,)
+            assert lr.rel_fro((U * s) @ V.T, A) < 1e-12
+            assert np.abs(U.T @ U - np.eye(r)).max() < 1e-12
+            assert np.abs(V.T @ V - np.eye(r)).max() < 1e-12
+            assert np.all(np.diff(s) <= 0) and s[-1] >= 0
+            sv = np.linalg.svd(A, compute_uv=False)
+            assert np.allclose(s[:rank], sv[:rank], rtol=1e-12, atol=0)
+
+
+def pin_rsvd_full_sketch(lr, seed=10):
+    """With l = min(m, k) the range is captured exactly and RSVD reduces to the
+    exact truncated SVD (numpy's LAPACK SVD): singular values and the rank-r
+    product agree to 1e-12 (Thm 3.1: error = sqrt(sum_{j>r} sigma_j^2))."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((50, 30)) @ np.diag(0.8 ** np.arange(30)) @ rng.standard_normal((30, 30))
+    r = 7
+    U, s, V = lr.rsvd(A, r, 30 - r, 0, 3, 0)
+    Uf, sf, Vft = np.linalg.svd(A, full_matrices=False)
+    assert np.allclose(s, sf[:r], rtol=1e-12)
+    Ar = (Uf[:, :r] * sf[:r]) @ Vft[:r]
+    assert np.abs((U * s) @ V.T - Ar).max() < 1e-12 * np.abs(A).max()
+    err = np.linalg.norm(A - Ar)
+    assert abs(err - np.sqrt(np.sum(sf[r:] ** 2))) < 1e-12 * np.linalg.norm(A)
+    assert err <= sf[r] * np.sqrt(30 - r) + 1e-12          # Thm 3.1 bound
+
+
+def pin_rsvd_bounds(lr, wl, trials=120):
+    """Eckart-Young lower bound holds for every draw; the mean range error
+    obeys Halko-Martinsson-Tropp Thm 10.5 (Frobenius, q = 0) and the paper's
+    Eq. (rsvderror_z) (spectral, l = 2r, q = 0, 1); power iterations drive the
+    error to the optimum."""
+    m, k, r, p = 64, 48, 6, 6
+    sig = (1.0 + np.arange(min(m, k))) ** -1.0
+    A = wl.lowrank(m, k, sig, 2024)
+    tail_f = np.sqrt(np.sum(sig[r:] ** 2))
+    errs_f, errs_2 = {0: [], 1: []}, {0: [], 1: []}
+    for q in (0, 1):
+        for t in range(trials):
+            Q = lr.range_finder(A, r + p, q, 1000 + t, 0)
+            Res = A - Q @ (Q.T @ A)
+            errs_f[q].append(np.linalg.norm(Res))
+            errs_2[q].append(np.linalg.norm(Res, 2))
+            U, s, V = lr.rsvd(A, r, p, q, 1000 + t, 0)
+            assert np.linalg.norm(A - (U * s) @ V.T) >= tail_f * (1 - 1e-12)
+    hmt_f = np.sqrt(1.0 + r / (p - 1.0)) * tail_f
+    assert np.mean(errs_f[0]) <= hmt_f, (np.mean(errs_f[0]), hmt_f)
+    for q in (0, 1):
+        paper = (1.0 + 4.0 * np.sqrt(2.0 * min(m, k) / (r - 1.0))) ** (1.0 / (2 * q + 1)) * sig[r]
+        assert np.mean(errs_2[q]) <= paper, (q, np.mean(errs_2[q]), paper)
+    assert np.mean(errs_f[1]) < np.mean(errs_f[0])
+    U, s, V = lr.rsvd(A, r, p, 6, 5, 0)
+    assert np.linalg.norm(A - (U * s) @ V.T) <= tail_f * (1 + 1e-6)
+
+
+# --------------------------------------------------------------------------
+# LRAMM (Algorithm 3)
+# --------------------------------------------------------------------------
+def pin_lramm_exact(lr, wl, quant):
+    """Exact rank-r operands and unquantised factors: D = A B to 1e-12; the
+    alpha/beta form D = alpha A B + beta C."""
+    m, k, n, r = 48, 40, 36, 6
+    A = wl.exact_rank(m, k, r, 31)
+    B = wl.exact_rank(k, n, r, 32)
+    Cx = A @ B
+    F = (quant.PREC_F32,) * 3
+    # factors are stored in FP32, so compare the FP64 chain of the FP64 factors
+    U, s, V = lr.rsvd(A, r, 3, 1, 7, 0)
+    W, g, Z = lr.rsvd(B, r, 3, 1, 7, 1)
+    D = (U * s) @ (V.T @ W) @ (g[:, None] * Z.T)
+    assert lr.rel_fro(D, Cx) < 1e-12
+    Dq = lr.lramm(A, B, r, 3, 1, 7, F)
+    assert lr.rel_fro(Dq, Cx) < 1e-6
+    C0 = np.random.default_rng(3).standard_normal((m, n))
+    D2 = lr.lramm(A, B, r, 3, 1, 7, F, alpha=2.0, beta=-0.5, C=C0)
+    assert np.allclose(D2, 2.0 * Dq - 0.5 * C0, rtol=1e-12, atol=1e-12)
+
+
+def pin_lramm_factor_identity(lr, wl, quant):
+    """Algorithm 3's factors satisfy U~ V^T = A_r and W Z~ = B_r, so the
+    unquantised chain equals A_r B_r (FP32 storage of the factors only)."""
+    m, k, n, r, p = 50, 44, 38, 7, 4
+    A = wl.lowrank(m, k, 0.7 ** np.arange(min(m, k)), 41)
+    B = wl.lowrank(k, n, 0.6 ** np.arange(min(k, n)), 42)
+    U, s, V = lr.rsvd(A, r, p, 1, 9, 0)
+    W, g, Z = lr.rsvd(B, r, p, 1, 9, 1)
+    Ut, Vf, Wf, Zt = lr.factors(A, B, r, p, 1, 9)
+    assert np.allclose(Ut.astype(np.float64) @ Vf.T, (U * s) @ V.T, atol=1e-6)
+    assert np.allclose(Wf.astype(np.float64) @ Zt, (W * g) @ Z.T, atol=1e-6)
+    D = lr.chain(Ut, Vf, Wf, Zt, (quant.PREC_F32,) * 3)
+    ref = ((U * s) @ V.T) @ ((W * g) @ Z.T)
+    assert lr.rel_fro(D, ref) < 2e-6
+
+
+def pin_lramm_bit_ordering(lr, wl, quant):
+    """Sec. 4.2: with about a tenth of the dimension as rank, 884 and 844 are
+    more accurate than 444 on uniformly distributed matrices, and 888 is the
+    most accurate of the quantised triples."""
+    rng = np.random.default_rng(11)
+    m = 160
+    A = rng.uniform(0, 1, (m, m))
+    B = rng.uniform(0, 1, (m, m))
+    Cx = A @ B
+    r = m // 10
+    I8, I4 = quant.PREC_INT8, quant.PREC_INT4
+    Ut, V, W, Zt = lr.factors(A, B, r, 8, 1, 13)
+    err = {}
+    for name, pr in (("888", (I8, I8, I8)), ("884", (I8, I8, I4)), ("844", (I8, I4, I4)), ("444", (I4, I4, I4))):
+        err[name] = lr.rel_fro(lr.chain(Ut, V, W, Zt, pr), Cx)
+    assert err["884"] < err["444"] and err["844"] < err["444"], err
+    assert err["888"] <= min(err.values()) + 1e-12, err

@@ -1,0 +1,83 @@
+"""The CPU oracle against facts outside itself (CPU only, no GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from tests import pins
+
+
+def test_philox_matches_curand_host_generator():
+    try:
+        n = pins.pin_philox_curand(oracle.philox)
+    except RuntimeError as e:
+        pytest.skip(str(e))
+    assert n > 0
+
+
+def test_gaussian_statistics():
+    pins.pin_gaussian_stats(oracle.philox)
+
+
+def test_box_muller_closed_forms():
+    pins.pin_box_muller_special(oracle.philox)
+
+
+def test_gaussian_layout():
+    """Element e of Omega is output e mod 4 of block e // 4 (word pairs
+    (0,1) and (2,3) through Box-Muller), independent of the matrix shape."""
+    a = oracle.philox.gaussian_matrix(99, 3, 7, 13).ravel()
+    b = oracle.philox.gaussian_matrix(99, 3, 13, 7).ravel()
+    assert np.array_equal(a, b)
+    w = oracle.philox.philox_words(99, 3, 1, first_block=5)[0]
+    z0, z1 = oracle.philox.box_muller(w[0:1], w[1:2])
+    z2, z3 = oracle.philox.box_muller(w[2:3], w[3:4])
+    assert np.array_equal(a[20:24], np.array([z0[0], z1[0], z2[0], z3[0]], dtype=np.float32))
+
+
+def test_quantiser_worked_examples():
+    pins.pin_quant_golden(oracle.quant)
+
+
+def test_e4m3_rounding():
+    pins.pin_e4m3(oracle.quant)
+
+
+def test_quantiser_bounds_and_symmetry():
+    pins.pin_quant_bounds(oracle.quant)
+
+
+def test_qm_bruteforce_and_scales():
+    pins.pin_qm_bruteforce(oracle.quant)
+
+
+def test_qm_error_bound():
+    pins.pin_qm_error_bound(oracle.quant)
+
+
+def test_orth_is_unique_thin_qr():
+    pins.pin_orth(oracle.lramm)
+
+
+def test_rsvd_exact_rank():
+    pins.pin_rsvd_exact_rank(oracle.lramm, workloads)
+
+
+def test_rsvd_full_sketch_is_exact_svd():
+    pins.pin_rsvd_full_sketch(oracle.lramm)
+
+
+def test_rsvd_error_bounds():
+    pins.pin_rsvd_bounds(oracle.lramm, workloads)
+
+
+def test_lramm_exact_rank_and_alpha_beta():
+    pins.pin_lramm_exact(oracle.lramm, workloads, oracle.quant)
+
+
+def test_lramm_factor_identity():
+    pins.pin_lramm_factor_identity(oracle.lramm, workloads, oracle.quant)
+
+
+def test_lramm_bit_width_ordering():
+    pins.pin_lramm_bit_ordering(oracle.lramm, workloads, oracle.quant)
