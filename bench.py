@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""LRAMM benchmark: effective TFLOP/s (2mnk / t) of Algorithm 3 on one GB300.
+
+A step is one lramm_matmul call (RSVD of A and B, quantisation, E1/E2/E3
+chain) on the m=n=k=4096 workload (FP32 operands, sigma_i = (1+i)^-1,
+r=256, p=16, q=2) with inputs resident in HBM.  The L2 is flushed (256 MB
+write) before every timed step, outside the step's event pair.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--variant int8|fp32|e4m3]
+  python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
+
+Multi-GPU (torchrun): every rank runs an independent replica of the
+workload; value = all ranks' work / max rank time (weak scaling).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "effective TFLOP/s (2mnk/t) at stated rel. Frobenius error vs dense BF16 GEMM"
+VARIANTS = {"int8": (1, 1, 1), "fp32": (0, 0, 0), "e4m3": (3, 3, 3), "884": (1, 1, 2)}
+DTYPES = {"int8": "f32+int8", "fp32": "f32", "e4m3": "f32+e4m3", "884": "f32+int8+int4"}
+FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+def kernel_work(kind, cfg, l, variant):
+    """Algorithmic (bytes, flops) of ONE launch of a kernel kind on this workload.
+
+    sketch: one product of an operand X (rows x cols) with an l-column
+      matrix; bytes = X once + the l-column input + the l-column output.
+    e3: the m x n output written once (FP32) plus both code operands read;
+      flops 2 m n r.
+    """
+    m, n, k, r = cfg["m"], cfg["n"], cfg["k"], cfg["r"]
+    xb = 2 if cfg["dtype"] == "bf16" else 4
+    if kind == "sketch":
+        return (m * k * xb + (m + k) * l * 4, 2.0 * m * k * l)
+    if kind == "e3":
+        cb = 2 if VARIANTS[variant][2] == 1 else (4 if VARIANTS[variant][2] == 0 else 1)
+        return (4 * m * n + (m + n) * r * cb, 2.0 * m * n * r)
+    if kind == "gram":
+        return (4 * m * l, 2.0 * m * l * l)
+    if kind == "trsm":
+        return (8 * m * l, 1.0 * m * l * l)
+    return (None, None)
+
+
+def fp32_alu_peak_tflops(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------ CPU oracle
+def cpu_oracle_step(A, B, cfg, prec):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.lramm.lramm(A, B, cfg["r"], cfg["p"], cfg["q"], workloads.SEED_SKETCH, prec)
+    return time.perf_counter() - t0
+
+
+def cpu_sample(name):
+    """A bounded sample of the workload for the CPU oracle: the full workload
+    when it is small, else a stand-in with every size halved until one oracle
+    step is expected to take well under ~15 s."""
+    c = dict(workloads.CONFIGS[name])
+    sc = (c["m"], c["n"], c["k"])
+    while sc[0] * sc[1] * sc[2] > 4096 ** 3:
+        sc = tuple(max(256, s // 2) for s in sc)
+        c["r"] = max(16, c["r"] // 2)
+        c["p"] = max(4, c["p"] // 2)
+    A, B = workloads.operands(name, scale=sc)
+    c["m"], c["n"], c["k"] = sc
+    return A.astype(np.float32), B.astype(np.float32), c
+
+
+def cores_used():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    """--impl reference: the oracle as it stands, on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    prec = VARIANTS[args.variant]
+    A, B, c = cpu_sample(args.workload)
+    flops = 2.0 * c["m"] * c["n"] * c["k"]
+    for _ in range(args.warmup):
+        cpu_oracle_step(A, B, c, prec)
+    ts = [cpu_oracle_step(A, B, c, prec) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    v = flops / t / 1e12
+    sample = "oracle LRAMM at m=%d n=%d k=%d r=%d p=%d q=%d per step" % (c["m"], c["n"], c["k"], c["r"], c["p"], c["q"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "variant": args.variant, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_lramm(args):
+    import torch
+
+    import paper_2405_16917_gb300 as L
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    L.load()
+    cfg = workloads.CONFIGS[args.workload]
+    m, n, k, r, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["r"], cfg["p"], cfg["q"]
+    l = r + p
+    prec = VARIANTS[args.variant]
+    A, B = workloads.device_operands(args.workload, dev)
+    a_type = L.BF16 if A.dtype == torch.bfloat16 else L.F32
+    plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
+                  timing=True)
+    ws = plan.workspace(dev)
+    D = torch.empty((m, n), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 0)):
+        L.matmul(plan, A, B, out=D, ws=ws)
+    st = L.status_read(ws)
+    if st != 0:
+        raise RuntimeError("device status %d after warm-up" % st)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kinds = {}
+    gpu_id = local
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        L.matmul(plan, A, B, out=D, ws=ws)
+        ends[i].record(stream)
+        for kname, (ms, cnt) in plan.timing().items():
+            a = kinds.setdefault(kname, [0.0, 0])
+            a[0] += ms
+            a[1] += cnt
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    flops = 2.0 * m * n * k
+    value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
+    st = L.status_read(ws)
+
+    # accuracy of this variant and of the comparators (outside the timed region)
+    exact = A.double() @ B.double()
+    nrm = exact.norm().item()
+    err = ((D.double() - exact).norm() / nrm).item()
+
+    def timed(fn, reps=3):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    A16, B16 = A.to(torch.bfloat16), B.to(torch.bfloat16)
+    Cb = torch.empty((m, n), dtype=torch.bfloat16, device=dev)
+    t_bf16 = timed(lambda: torch.matmul(A16, B16, out=Cb))
+    err_bf16 = ((Cb.double() - exact).norm() / nrm).item()
+    plain = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=(0, 0, 0), a_type=a_type, b_type=a_type)
+    Dp = torch.empty_like(D)
+    t_plain = timed(lambda: L.matmul(plan=plain, A=A, B=B, out=Dp, ws=ws), reps=2)
+    err_plain = ((Dp.double() - exact).norm() / nrm).item()
+    del exact
+
+    # end to end through the public API with host buffers: H2D of A, B from
+    # pinned memory, lramm_matmul, D2H of D, every step
+    Ah, Bh = A.cpu().pin_memory(), B.cpu().pin_memory()
+    Dh = torch.empty((m, n), dtype=torch.float32).pin_memory()
+    Ad, Bd = torch.empty_like(A), torch.empty_like(B)
+
+    def e2e_step():
+        Ad.copy_(Ah, non_blocking=True)
+        Bd.copy_(Bh, non_blocking=True)
+        L.matmul(plan, Ad, Bd, out=D, ws=ws)
+        Dh.copy_(D, non_blocking=True)
+
+    e2e_steps = max(2, min(args.steps, 5))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    eb.record(stream)
+    eb.synchronize()
+    e2e_ms = ea.elapsed_time(eb) / e2e_steps
+    e2e_val = world * flops / (e2e_ms * 1e-3) / 1e12
+
+    # roofline of the dominant kernel kind (largest device time in the timed steps)
+    pk, peak_src = peaks()
+    dom = max(kinds.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dcnt) = dom
+    avg_s = dms / dcnt * 1e-3
+    nbytes, nflops = kernel_work(dname, cfg, l, args.variant)
+    sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    if dname in ("sketch", "e3", "gram", "trsm", "e1", "e2") and nflops is not None:
+        # these kernels are FP32 SIMT in this version: bound by FP32 FMA issue
+        roof = {"bound": "alu", "achieved": nflops / avg_s / 1e12,
+                "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
+                "kernel": dname, "launches_per_step": dcnt / args.steps,
+                "avg_launch_ms": avg_s * 1e3, "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        roof["algorithmic_bytes_per_launch"] = nbytes
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+                "note": "latency-bound small factorisation; no algorithmic roof"}
+
+    # CPU oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ac, Bc, cs = cpu_sample(args.workload)
+        t_cpu = cpu_oracle_step(Ac, Bc, cs, prec)
+        cpu = {"value": 2.0 * cs["m"] * cs["n"] * cs["k"] / t_cpu / 1e12, "unit": "TFLOP/s",
+               "cores": cores_used(), "kind": "oracle",
+               "sample": "one oracle LRAMM step at m=%d n=%d k=%d r=%d p=%d q=%d, %.1f s"
+                         % (cs["m"], cs["n"], cs["k"], cs["r"], cs["p"], cs["q"], t_cpu)}
+
+    launches = sum(c for _, c in kinds.values())
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPES[args.variant], "data": "synthetic",
+            "config": {"workload": args.workload, "m": m, "n": n, "k": k, "r": r, "p": p, "q": q,
+                       "variant": args.variant, "operands": cfg["dtype"], "spectrum": cfg["spectrum"],
+                       "sketch": "fp32", "scale": "rowcol", "l2": "flushed: 256 MB write before each step",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "rel_fro_err_vs_fp64_exact": err,
+                       "dense_bf16_gemm": {"tflops": flops / (t_bf16 * 1e-3) / 1e12, "ms": t_bf16,
+                                           "rel_fro_err_vs_fp64_exact": err_bf16},
+                       "plain_lramm_fp32": {"tflops": flops / (t_plain * 1e-3) / 1e12, "ms": t_plain,
+                                            "rel_fro_err_vs_fp64_exact": err_plain},
+                       "device_status": st},
+            "breakdown_ms_per_step": {kn: round(v[0] / args.steps, 4) for kn, v in
+                                      sorted(kinds.items(), key=lambda kv: -kv[1][0])},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": A.numel() * A.element_size() + B.numel() * B.element_size(),
+                    "d2h_bytes_per_step": D.numel() * D.element_size()},
+            "gpu_launches": launches,
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons"), "samples": clk.get("samples")},
+            "peaks": peak_src,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["lramm", "reference"], default="lramm")
+    ap.add_argument("--workload", default="lramm_4096", choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--variant", default="int8", choices=sorted(VARIANTS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_lramm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

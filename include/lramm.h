@@ -1,0 +1,233 @@
+/*
+ * lramm.h -- C ABI of the GB300 (sm_103a) LRAMM library.
+ *
+ * LRAMM (arXiv 2405.16917) approximates C = A B by a randomized SVD of each
+ * operand followed by a chain of three quantised factor GEMMs:
+ *
+ *   RSVD(A, r) = U_r Sigma_r V_r^T,  RSVD(B, r) = W_r Gamma_r Z_r^T
+ *   U~ = U_r Sigma_r,  Z~ = Gamma_r Z_r^T                      (Sec. 3.2)
+ *   E1 = QM(V_r^T W_r, d1), E2 = QM(E1 Z~, d2), E3 = QM(U~ E2, d3)
+ *   D  = alpha E3 + beta C                                     (Algorithm 3)
+ *
+ * QM is the quantised GEMM of Algorithm 2 with the symmetric linear
+ * quantiser of Eqs. (Quantization), (get_lambda), (Dequantization).  The
+ * RSVD is the two-stage randomized scheme of Sec. 2.2 (Gaussian sketch with
+ * oversampling p, q power iterations) followed by Algorithm 1.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major with a leading dimension (row stride) in
+ *     elements.  Device pointers unless stated otherwise.
+ *   - `stream` is a cudaStream_t passed as void*.  All device work is
+ *     enqueued on it; no entry point synchronises except lramm_status_read.
+ *   - The caller owns every device buffer (inputs, outputs, workspace) and
+ *     the stream.  A plan owns host metadata only; no entry point other than
+ *     lramm_plan_create/destroy allocates or frees host memory, and none
+ *     allocates device memory.
+ *   - Argument errors are returned synchronously and nothing is enqueued.
+ *     Errors found on the device (Cholesky breakdown, Jacobi not converged)
+ *     are latched in a status word at the start of the workspace and
+ *     returned by lramm_status_read.  Nothing throws across the ABI.
+ *   - On any error the contents of output buffers are unspecified.
+ */
+#ifndef LRAMM_H
+#define LRAMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LRAMM_API __attribute__((visibility("default")))
+#else
+#define LRAMM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRAMM_OK = 0,
+  LRAMM_ERR_INVALID_ARG = 1,   /* bad shape, stride, pointer or option        */
+  LRAMM_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. l > 320)    */
+  LRAMM_ERR_WORKSPACE = 3,     /* workspace smaller than lramm_workspace_size */
+  LRAMM_ERR_CUDA = 4,          /* a CUDA runtime call failed                  */
+  LRAMM_ERR_NUMERIC = 5,       /* Cholesky pivot <= 0 in an orthonormalisation */
+  LRAMM_ERR_TIMEOUT = 6,       /* a bounded device wait ran out               */
+  LRAMM_WARN_NOCONV = 7        /* Jacobi SVD hit its sweep cap                */
+} lramm_status;
+
+/* Storage type of the operands A and B. */
+typedef enum { LRAMM_F32 = 0, LRAMM_BF16 = 1 } lramm_dtype;
+
+/* Precision d_i of each QM in Algorithm 3.
+ *   F32  : no quantisation, FP32 product (the "plain LRAMM" of Sec. 4.2)
+ *   INT8 : N = 8 bits, codes in [-127, 127], exact integer product
+ *   INT4 : N = 4 bits, codes in [-7, 7], exact integer product
+ *   E4M3 : FP8 e4m3 codes with lambda = 448 / a_max, FP32 accumulation  */
+typedef enum { LRAMM_P_F32 = 0, LRAMM_P_INT8 = 1, LRAMM_P_INT4 = 2, LRAMM_P_E4M3 = 3 } lramm_prec;
+
+/* Scale groups of the quantiser (a_max of Eq. (get_lambda)):
+ *   ROWCOL: left operand one scale per row, right operand one per column
+ *   TENSOR: one scale per operand (the paper's per-matrix a_max)          */
+typedef enum { LRAMM_S_ROWCOL = 0, LRAMM_S_TENSOR = 1 } lramm_scale;
+
+/* Arithmetic of the products that touch A or B (sketch, power iterations,
+ * projection); the orthonormalisations and small SVD are FP32.
+ *   F32  : FP32-accurate products
+ *   TF32 : one TF32 pass (10-bit mantissa operands), FP32 accumulate
+ *   BF16 : BF16 operands, FP32 accumulate                               */
+typedef enum { LRAMM_SKETCH_F32 = 0, LRAMM_SKETCH_TF32 = 1, LRAMM_SKETCH_BF16 = 2 } lramm_sketch;
+
+typedef struct lramm_desc {
+  int64_t m, n, k;        /* A is m x k, B is k x n, C and D are m x n           */
+  int64_t lda, ldb, ldc;  /* row strides of A, B and of C / D (elements)         */
+  int32_t a_type, b_type; /* lramm_dtype of A and B                              */
+  int32_t r;              /* target rank, 1 <= r                                 */
+  int32_t p;              /* oversampling: l = r + p sketch columns, l <= 320,
+                             l <= min(m, k) and l <= min(k, n)                   */
+  int32_t q;              /* power iterations, 0 <= q <= 16                      */
+  uint64_t seed;          /* Philox4x32-10 key; Omega_A is stream 0, Omega_B 1   */
+  int32_t prec[3];        /* lramm_prec of E1, E2, E3 (d1, d2, d3)               */
+  int32_t scale;          /* lramm_scale                                         */
+  int32_t sketch;         /* lramm_sketch                                        */
+  float alpha, beta;      /* D = alpha E3 + beta C                               */
+  int32_t max_sweeps;     /* Jacobi sweep cap, 0 selects the default (40)        */
+  int32_t flags;          /* LRAMM_FLAG_* bits; other bits must be 0             */
+} lramm_desc;
+
+/* flags: record a CUDA event pair around every kernel launch of a call, on
+ * the call's stream, so lramm_timing_read can attribute device time per
+ * kernel kind (the per-operator time split of Sec. 4.1, Fig. 2). */
+#define LRAMM_FLAG_TIMING 1
+
+/* Kernel kinds reported by lramm_timing_read. */
+typedef enum {
+  LRAMM_K_OMEGA = 0,      /* Philox Gaussian test matrix                      */
+  LRAMM_K_SKETCH = 1,     /* products with A or B (sketch, power, projection) */
+  LRAMM_K_GRAM = 2,       /* Gram matrices of CholeskyQR                      */
+  LRAMM_K_CHOL = 3,       /* l x l Cholesky                                   */
+  LRAMM_K_TRSM = 4,       /* Q = Y L^-T                                       */
+  LRAMM_K_RFACTOR = 5,    /* R = R2 R1                                        */
+  LRAMM_K_SVD = 6,        /* one-sided Jacobi SVD of R^T                      */
+  LRAMM_K_SVDSORT = 7,    /* sort / truncate to rank r                        */
+  LRAMM_K_ASSEMBLE = 8,   /* U~, V^T, W^T, Z~^T from the small SVD            */
+  LRAMM_K_QUANT = 9,      /* absmax + quantise of a QM operand                */
+  LRAMM_K_E1 = 10,        /* QM E1                                            */
+  LRAMM_K_E2 = 11,        /* QM E2                                            */
+  LRAMM_K_E3 = 12,        /* QM E3 with the alpha/beta epilogue               */
+  LRAMM_K_OTHER = 13,
+  LRAMM_K_COUNT = 14
+} lramm_kernel_kind;
+
+typedef struct lramm_plan_s* lramm_plan_t;
+
+/* Validate a problem description and build a plan (host metadata only).
+ * Returns LRAMM_ERR_INVALID_ARG for inconsistent sizes or options,
+ * LRAMM_ERR_UNSUPPORTED for l = r + p > 320.  *out is set only on success. */
+LRAMM_API lramm_status lramm_plan_create(const lramm_desc* desc, lramm_plan_t* out);
+
+/* Release a plan.  NULL is accepted. */
+LRAMM_API lramm_status lramm_plan_destroy(lramm_plan_t plan);
+
+/* Bytes of device workspace lramm_matmul / lramm_rsvd / lramm_chain need.
+ * The workspace must be 256-byte aligned; its first 256 bytes hold the
+ * device status word. */
+LRAMM_API lramm_status lramm_workspace_size(lramm_plan_t plan, size_t* bytes);
+
+/* Randomized SVD of one operand (Sec. 2.2 range finder with q power
+ * iterations, then Algorithm 1), truncated to rank r.
+ *   which = 0: X is A (m x k, stride lda, type a_type), Omega stream 0
+ *   which = 1: X is B (k x n, stride ldb, type b_type), Omega stream 1
+ * Outputs (device, FP32, row-major, dense): U rows x r, S r (descending),
+ * V cols x r, with X ~ U diag(S) V^T.  The sign of each (U_i, V_i) pair is
+ * not canonicalised. */
+LRAMM_API lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X,
+                        float* U, float* S, float* V,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* LRAMM, Algorithm 3: D = alpha * E3 + beta * C (m x n, FP32, stride ldc).
+ * A and B as described by the plan.  C may be NULL when beta == 0 and may
+ * alias D. */
+LRAMM_API lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B,
+                          const float* C, float* D,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* The quantised factor chain of Algorithm 3 on given factors (all FP32,
+ * row-major, dense):
+ *   Ut  m x r : U~ = U_r Sigma_r           Vt r x k : V_r^T
+ *   Wt  r x k : W_r^T                      Zt n x r : Z~^T = Z_r Gamma_r
+ * computes E1 = QM(Vt Wt^T, d1), E2 = QM(E1 Zt^T, d2), E3 = QM(Ut E2, d3),
+ * D = alpha E3 + beta C (stride ldc). */
+LRAMM_API lramm_status lramm_chain(lramm_plan_t plan, const float* Ut, const float* Vt,
+                         const float* Wt, const float* Zt, const float* C, float* D,
+                         void* ws, size_t ws_bytes, void* stream);
+
+/* Wait for `stream`, read and clear the status word at the start of `ws`.
+ * Returns the first device error latched since the last read, or LRAMM_OK. */
+LRAMM_API lramm_status lramm_status_read(const void* ws, void* stream);
+
+/* Static description of a status code. */
+LRAMM_API const char* lramm_status_str(lramm_status s);
+
+/* Source location and CUDA error name/string of the last CUDA runtime call
+ * that failed in this thread (LRAMM_ERR_CUDA), or "" if none did. */
+LRAMM_API const char* lramm_last_cuda_error(void);
+
+/* Device time of the most recent lramm_matmul / lramm_rsvd / lramm_chain
+ * call of a plan created with LRAMM_FLAG_TIMING, per lramm_kernel_kind:
+ * ms[kind] = summed event time, launches[kind] = number of launches (arrays
+ * of LRAMM_K_COUNT entries, host memory).  Waits for the recorded events.
+ * Returns LRAMM_ERR_INVALID_ARG when the plan was created without the flag. */
+LRAMM_API lramm_status lramm_timing_read(lramm_plan_t plan, float* ms, int32_t* launches);
+
+/* Static name of a kernel kind ("sketch", "e3", ...). */
+LRAMM_API const char* lramm_kernel_kind_name(int32_t kind);
+
+/* ---- building blocks, exposed for parity tests -------------------------- */
+
+/* Philox4x32-10 words of blocks 0 .. n_blocks-1 (counter (n, 0, stream_id, 0),
+ * key (lo32 seed, hi32 seed)); out is n_blocks x 4 uint32 (device). */
+LRAMM_API lramm_status lramm_philox_words(uint64_t seed, uint32_t stream_id, int64_t n_blocks,
+                                uint32_t* out, void* stream);
+
+/* The Gaussian test matrix Omega (rows x cols, FP32, row-major, dense):
+ * element e = i * cols + j is Box-Muller output e mod 4 of Philox block
+ * e / 4 (Sec. 2.2, Gaussian sampling). */
+LRAMM_API lramm_status lramm_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols,
+                            float* out, void* stream);
+
+/* Symmetric quantiser, Eqs. (get_lambda) and (Quantization), per row
+ * (per_row = 1) or per tensor (per_row = 0) of X (rows x cols, stride ldx):
+ * lambda = D / a_max in FP32, code = rint(x * lambda) clamped to +-D
+ * (INT8: D = 127, INT4: D = 7) or rounded to e4m3 (E4M3: D = 448).
+ * codes: rows x ldcodes; INT8 codes are stored as bfloat16 values, INT4 and
+ * E4M3 codes as e4m3 bytes; columns cols .. ldcodes-1 are set to zero.
+ * scales: one FP32 dequantisation scale a_max / D per row (per_row = 1) or
+ * one value (per_row = 0).  Needs ws of lramm_quant_ws_bytes() bytes for
+ * per-tensor mode (may be NULL for per-row mode). */
+LRAMM_API lramm_status lramm_quantize(const float* X, int64_t rows, int64_t cols, int64_t ldx,
+                            int32_t prec, int32_t per_row, void* codes, int64_t ldcodes,
+                            float* scales, void* ws, void* stream);
+
+/* QM product of Algorithm 2 on quantised codes, both K-major:
+ *   L  M x K (stride ldl), Rt N x K (stride ldr); codes as lramm_quantize
+ *   writes them for `prec`.  acc(i,j) = sum_t L(i,t) Rt(j,t), exact for
+ *   INT8/INT4, FP32-accumulated for E4M3.
+ *   out_kind 0: D(i,j) = alpha * fp32(acc) * (sL[i or 0] * sR[j or 0])
+ *                        + beta * C(i,j)           (FP32, stride ldd)
+ *   out_kind 1: D receives acc itself, int32 for INT8/INT4, FP32 for E4M3.
+ * per_row = 1: sL, sR have M and N entries; 0: one entry each.
+ * K must be a multiple of 16; C may be NULL when beta == 0. */
+LRAMM_API lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K,
+                         int64_t ldl, int64_t ldr, int32_t prec, int32_t per_row,
+                         const float* sL, const float* sR, float alpha, float beta,
+                         const float* C, int64_t ldc, void* D, int64_t ldd,
+                         int32_t out_kind, void* stream);
+
+/* Bytes of workspace lramm_quantize needs in per-tensor mode. */
+LRAMM_API size_t lramm_quant_ws_bytes(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRAMM_H */

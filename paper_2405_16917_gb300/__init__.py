@@ -1,0 +1,268 @@
+"""Python binding of the LRAMM CUDA library (liblramm.so, C ABI in include/lramm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  PyTorch supplies device memory and streams.  The
+binding refuses to run when the library is missing; there is no fallback.
+"""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblramm.so")
+
+F32, BF16 = 0, 1
+P_F32, P_INT8, P_INT4, P_E4M3 = 0, 1, 2, 3
+S_ROWCOL, S_TENSOR = 0, 1
+SKETCH_F32, SKETCH_TF32, SKETCH_BF16 = 0, 1, 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace", 4: "cuda error",
+          5: "numeric (Cholesky breakdown)", 6: "timeout", 7: "Jacobi not converged"}
+
+_lib = None
+
+
+class LrammError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__("%s: LRAMM status %d (%s)" % (where, code, STATUS.get(code, "?")))
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("lda", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
+                ("a_type", ctypes.c_int32), ("b_type", ctypes.c_int32),
+                ("r", ctypes.c_int32), ("p", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32 * 3),
+                ("scale", ctypes.c_int32), ("sketch", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
+                ("max_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+_VP, _I64, _I32, _U64, _U32, _F = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
+                                   ctypes.c_uint32, ctypes.c_float)
+_SIGS = {
+    "lramm_plan_create": (_I32, [ctypes.POINTER(Desc), ctypes.POINTER(_VP)]),
+    "lramm_plan_destroy": (_I32, [_VP]),
+    "lramm_workspace_size": (_I32, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    "lramm_rsvd": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lramm_matmul": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lramm_chain": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lramm_status_read": (_I32, [_VP, _VP]),
+    "lramm_status_str": (ctypes.c_char_p, [_I32]),
+    "lramm_last_cuda_error": (ctypes.c_char_p, []),
+    "lramm_philox_words": (_I32, [_U64, _U32, _I64, _VP, _VP]),
+    "lramm_gaussian": (_I32, [_U64, _U32, _I64, _I64, _VP, _VP]),
+    "lramm_quantize": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _VP, _VP]),
+    "lramm_qgemm": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _VP, _VP, _F, _F,
+                           _VP, _I64, _VP, _I64, _I32, _VP]),
+    "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
+    "lramm_timing_read": (_I32, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]),
+    "lramm_kernel_kind_name": (ctypes.c_char_p, [_I32]),
+}
+
+FLAG_TIMING = 1
+K_COUNT = 14
+
+
+def load(path=LIB_PATH):
+    """Load liblramm.so (built in-tree by paper_2405_16917_gb300._build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("LRAMM CUDA library not found at %s; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % path)
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st, where):
+    if st != 0:
+        if st == 4 and _lib is not None:
+            where = "%s [%s]" % (where, _lib.lramm_last_cuda_error().decode())
+        raise LrammError(st, where)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    torch = _torch()
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.bfloat16:
+        return BF16
+    raise TypeError("operands must be float32 or bfloat16, got %s" % t.dtype)
+
+
+def _need_cuda(*ts):
+    for t in ts:
+        if t is not None and not t.is_cuda:
+            raise ValueError("LRAMM operands must be CUDA tensors")
+
+
+class Plan:
+    """An LRAMM problem: sizes, rank parameters, precisions, seed."""
+
+    def __init__(self, m, n, k, r, p, q, seed=7, prec=(P_INT8, P_INT8, P_INT8), scale=S_ROWCOL,
+                 sketch=SKETCH_F32, alpha=1.0, beta=0.0, a_type=F32, b_type=F32, lda=None, ldb=None,
+                 ldc=None, max_sweeps=0, timing=False):
+        lib = load()
+        d = Desc()
+        d.m, d.n, d.k = m, n, k
+        d.lda = lda if lda is not None else k
+        d.ldb = ldb if ldb is not None else n
+        d.ldc = ldc if ldc is not None else n
+        d.a_type, d.b_type = a_type, b_type
+        d.r, d.p, d.q = r, p, q
+        d.seed = seed
+        d.prec[0], d.prec[1], d.prec[2] = prec
+        d.scale, d.sketch = scale, sketch
+        d.alpha, d.beta = alpha, beta
+        d.max_sweeps, d.flags = max_sweeps, (FLAG_TIMING if timing else 0)
+        self.desc = d
+        h = ctypes.c_void_p()
+        _check(lib.lramm_plan_create(ctypes.byref(d), ctypes.byref(h)), "lramm_plan_create")
+        self.handle = h
+        sz = ctypes.c_size_t()
+        _check(lib.lramm_workspace_size(h, ctypes.byref(sz)), "lramm_workspace_size")
+        self.ws_bytes = sz.value
+
+    def timing(self):
+        """{kind name: (total ms, launches)} of the last call (plan made with timing=True)."""
+        lib = load()
+        ms = (ctypes.c_float * K_COUNT)()
+        n = (ctypes.c_int32 * K_COUNT)()
+        _check(lib.lramm_timing_read(self.handle, ms, n), "lramm_timing_read")
+        return {lib.lramm_kernel_kind_name(k).decode(): (ms[k], n[k]) for k in range(K_COUNT) if n[k]}
+
+    def workspace(self, device="cuda"):
+        torch = _torch()
+        return torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.lramm_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def matmul(plan, A, B, C=None, out=None, ws=None, stream=None):
+    """D = alpha * E3 + beta * C (Algorithm 3); returns D (m x n FP32)."""
+    torch = _torch()
+    _need_cuda(A, B, C)
+    d = plan.desc
+    if out is None:
+        out = torch.empty((d.m, d.ldc), dtype=torch.float32, device=A.device)[:, : d.n]
+    if ws is None:
+        ws = plan.workspace(A.device)
+    _check(load().lramm_matmul(plan.handle, _ptr(A), _ptr(B), _ptr(C), _ptr(out), _ptr(ws),
+                               ws.numel(), _stream(stream)), "lramm_matmul")
+    return out
+
+
+def rsvd(plan, which, X, ws=None, stream=None):
+    """Rank-r randomized SVD of A (which=0) or B (which=1): (U, S, V)."""
+    torch = _torch()
+    _need_cuda(X)
+    d = plan.desc
+    rows, cols = (d.m, d.k) if which == 0 else (d.k, d.n)
+    U = torch.empty((rows, d.r), dtype=torch.float32, device=X.device)
+    S = torch.empty((d.r,), dtype=torch.float32, device=X.device)
+    V = torch.empty((cols, d.r), dtype=torch.float32, device=X.device)
+    if ws is None:
+        ws = plan.workspace(X.device)
+    _check(load().lramm_rsvd(plan.handle, which, _ptr(X), _ptr(U), _ptr(S), _ptr(V), _ptr(ws),
+                             ws.numel(), _stream(stream)), "lramm_rsvd")
+    return U, S, V
+
+
+def chain(plan, Ut, Vt, Wt, Zt, C=None, out=None, ws=None, stream=None):
+    """Quantised factor chain of Algorithm 3 on given FP32 factors."""
+    torch = _torch()
+    _need_cuda(Ut, Vt, Wt, Zt, C)
+    d = plan.desc
+    for t in (Ut, Vt, Wt, Zt):
+        if t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError("factors must be contiguous float32")
+    if out is None:
+        out = torch.empty((d.m, d.ldc), dtype=torch.float32, device=Ut.device)[:, : d.n]
+    if ws is None:
+        ws = plan.workspace(Ut.device)
+    _check(load().lramm_chain(plan.handle, _ptr(Ut), _ptr(Vt), _ptr(Wt), _ptr(Zt), _ptr(C), _ptr(out),
+                              _ptr(ws), ws.numel(), _stream(stream)), "lramm_chain")
+    return out
+
+
+def status_read(ws, stream=None):
+    """Synchronise and return (and clear) the workspace's device status code."""
+    return load().lramm_status_read(_ptr(ws), _stream(stream))
+
+
+def philox_words(seed, stream_id, n_blocks, device="cuda"):
+    torch = _torch()
+    out = torch.empty((n_blocks, 4), dtype=torch.int32, device=device)
+    _check(load().lramm_philox_words(seed, stream_id, n_blocks, _ptr(out), _stream()), "lramm_philox_words")
+    return out
+
+
+def gaussian(seed, stream_id, rows, cols, device="cuda"):
+    torch = _torch()
+    out = torch.empty((rows, cols), dtype=torch.float32, device=device)
+    _check(load().lramm_gaussian(seed, stream_id, rows, cols, _ptr(out), _stream()), "lramm_gaussian")
+    return out
+
+
+def code_dtype(prec):
+    torch = _torch()
+    return torch.bfloat16 if prec == P_INT8 else torch.float8_e4m3fn
+
+
+def quantize(X, prec, per_row=True, ldcodes=None):
+    """Codes (rows x ldcodes, bf16 for INT8, e4m3 for INT4/E4M3) and FP32 scales."""
+    torch = _torch()
+    _need_cuda(X)
+    rows, cols = X.shape
+    ldc = ldcodes or cols
+    codes = torch.empty((rows, ldc), dtype=code_dtype(prec), device=X.device)
+    scales = torch.empty((rows if per_row else 1,), dtype=torch.float32, device=X.device)
+    lib = load()
+    ws = torch.empty(lib.lramm_quant_ws_bytes(), dtype=torch.uint8, device=X.device)
+    _check(lib.lramm_quantize(_ptr(X), rows, cols, X.stride(0), prec, int(per_row), _ptr(codes), ldc,
+                              _ptr(scales), _ptr(ws), _stream()), "lramm_quantize")
+    return codes, scales
+
+
+def qgemm(Lc, Rc, prec, sL=None, sR=None, per_row=True, alpha=1.0, beta=0.0, C=None, raw=False):
+    """QM product of K-major code matrices; raw=True returns the accumulator."""
+    torch = _torch()
+    _need_cuda(Lc, Rc, C)
+    M, K = Lc.shape
+    N = Rc.shape[0]
+    if raw:
+        out = torch.empty((M, N), dtype=torch.int32 if prec != P_E4M3 else torch.float32, device=Lc.device)
+    else:
+        out = torch.empty((M, N), dtype=torch.float32, device=Lc.device)
+    _check(load().lramm_qgemm(_ptr(Lc), _ptr(Rc), M, N, K, Lc.stride(0), Rc.stride(0), prec, int(per_row),
+                              _ptr(sL), _ptr(sR), alpha, beta, _ptr(C), C.stride(0) if C is not None else 0,
+                              _ptr(out), N, 1 if raw else 0, _stream()), "lramm_qgemm")
+    return out

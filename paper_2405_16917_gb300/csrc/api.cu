@@ -1,0 +1,464 @@
+// C ABI of the LRAMM library: plan, workspace layout and the pipeline
+//   RSVD(A), RSVD(B)  (Sec. 2.2 range finder + Algorithm 1)
+//   E1, E2, E3 chain  (Algorithm 3, QM of Algorithm 2)
+// Every kernel is enqueued on the caller's stream; nothing here allocates
+// device memory or synchronises (except lramm_status_read).
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace lramm;
+
+namespace lramm {
+static thread_local char g_cuda_err[256];
+void note_cuda_error(cudaError_t e, const char* where) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+}  // namespace lramm
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxL = 320;
+constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of the first CQR pass
+
+struct SideLayout {
+  int64_t rows, cols;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, R, Vj, sig, S1, S2;
+};
+
+}  // namespace
+
+struct TimerRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+struct lramm_plan_s {
+  lramm_desc d;
+  bool timing = false;
+  std::vector<TimerRec> recs;
+  size_t used = 0;
+  int l;
+  int64_t kp, rp;
+  SideLayout side[2];
+  size_t Ut, Vt, Wt, Zt, E1, E2t;
+  size_t cV, cW, cE1, cZ, cU, cE2;
+  size_t sV, sW, sE1, sZ, sU, sE2;
+  size_t amax;
+  size_t total;
+};
+
+namespace {
+
+struct Bump {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off += (bytes + kAlign - 1) / kAlign * kAlign;
+    return o;
+  }
+};
+
+bool valid_prec(int p) { return p >= LRAMM_P_F32 && p <= LRAMM_P_E4M3; }
+
+lramm_status validate(const lramm_desc* d) {
+  if (!d) return LRAMM_ERR_INVALID_ARG;
+  if (d->m < 1 || d->n < 1 || d->k < 1) return LRAMM_ERR_INVALID_ARG;
+  if (d->lda < d->k || d->ldb < d->n || d->ldc < d->n) return LRAMM_ERR_INVALID_ARG;
+  if ((d->a_type != LRAMM_F32 && d->a_type != LRAMM_BF16) ||
+      (d->b_type != LRAMM_F32 && d->b_type != LRAMM_BF16))
+    return LRAMM_ERR_INVALID_ARG;
+  if (d->r < 1 || d->p < 0 || d->q < 0 || d->q > 16) return LRAMM_ERR_INVALID_ARG;
+  const int64_t l = (int64_t)d->r + d->p;
+  if (l > d->m || l > d->k || l > d->n) return LRAMM_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i)
+    if (!valid_prec(d->prec[i])) return LRAMM_ERR_INVALID_ARG;
+  if (d->scale != LRAMM_S_ROWCOL && d->scale != LRAMM_S_TENSOR) return LRAMM_ERR_INVALID_ARG;
+  if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_BF16) return LRAMM_ERR_INVALID_ARG;
+  if (d->max_sweeps < 0 || (d->flags & ~LRAMM_FLAG_TIMING) != 0) return LRAMM_ERR_INVALID_ARG;
+  if (l > kMaxL) return LRAMM_ERR_UNSUPPORTED;
+  return LRAMM_OK;
+}
+
+void layout(lramm_plan_s* P) {
+  const lramm_desc& d = P->d;
+  const int64_t l = P->l, r = d.r;
+  Bump b;
+  b.take(kAlign);  // status word
+  for (int s = 0; s < 2; ++s) {
+    SideLayout& S = P->side[s];
+    S.rows = s == 0 ? d.m : d.k;
+    S.cols = s == 0 ? d.k : d.n;
+    S.omega = b.take(sizeof(float) * S.cols * l);
+    S.R0 = b.take(sizeof(float) * S.rows * l);
+    S.R1 = b.take(sizeof(float) * S.rows * l);
+    S.C0 = b.take(sizeof(float) * S.cols * l);
+    S.C1 = b.take(sizeof(float) * S.cols * l);
+    S.G = b.take(sizeof(float) * l * l);
+    S.L1 = b.take(sizeof(float) * l * l);
+    S.L2 = b.take(sizeof(float) * l * l);
+    S.R = b.take(sizeof(float) * l * l);
+    S.Vj = b.take(sizeof(float) * l * l);
+    S.sig = b.take(sizeof(float) * l);
+    S.S1 = b.take(sizeof(float) * l * r);
+    S.S2 = b.take(sizeof(float) * l * r);
+  }
+  P->kp = round_up(d.k, 16);
+  P->rp = round_up(r, 16);
+  P->Ut = b.take(sizeof(float) * d.m * r);
+  P->Vt = b.take(sizeof(float) * r * d.k);
+  P->Wt = b.take(sizeof(float) * r * d.k);
+  P->Zt = b.take(sizeof(float) * d.n * r);
+  P->E1 = b.take(sizeof(float) * r * r);
+  P->E2t = b.take(sizeof(float) * d.n * r);
+  const size_t cb = 2;  // widest code container (bfloat16)
+  P->cV = b.take(cb * r * P->kp);
+  P->cW = b.take(cb * r * P->kp);
+  P->cE1 = b.take(cb * r * P->rp);
+  P->cZ = b.take(cb * d.n * P->rp);
+  P->cU = b.take(cb * d.m * P->rp);
+  P->cE2 = b.take(cb * d.n * P->rp);
+  P->sV = b.take(sizeof(float) * r);
+  P->sW = b.take(sizeof(float) * r);
+  P->sE1 = b.take(sizeof(float) * r);
+  P->sZ = b.take(sizeof(float) * d.n);
+  P->sU = b.take(sizeof(float) * d.m);
+  P->sE2 = b.take(sizeof(float) * d.n);
+  P->amax = b.take(kAlign);
+  P->total = b.off;
+}
+
+template <typename T>
+T* at(void* ws, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(ws) + off);
+}
+
+// Event pair around one launch when the plan times its calls.
+int tbegin(lramm_plan_s* P, int kind, cudaStream_t s) {
+  if (!P->timing) return -1;
+  if (P->used == P->recs.size()) {
+    TimerRec r{kind, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+    P->recs.push_back(r);
+  }
+  TimerRec& r = P->recs[P->used];
+  r.kind = kind;
+  if (cudaEventRecord(r.a, s) != cudaSuccess) return -1;
+  return (int)P->used++;
+}
+
+void tend(lramm_plan_s* P, int h, cudaStream_t s) {
+  if (h >= 0) cudaEventRecord(P->recs[h].b, s);
+}
+
+#define TIMED(P, kind, s, expr)                  \
+  do {                                           \
+    const int _h = tbegin((P), (kind), (s));     \
+    const lramm_status _st = (expr);             \
+    tend((P), _h, (s));                          \
+    if (_st != LRAMM_OK) return _st;             \
+  } while (0)
+
+lramm_status check_ws(const lramm_plan_s* P, void* ws, size_t ws_bytes) {
+  if (!ws || ws_bytes < P->total) return LRAMM_ERR_WORKSPACE;
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return LRAMM_ERR_WORKSPACE;
+  return LRAMM_OK;
+}
+
+// Orthonormalise the rows x l matrix src (stride l) by CholeskyQR2:
+// G = src^T src = L1 L1^T, tmp = src L1^-T; G = tmp^T tmp = L2 L2^T,
+// dst = tmp L2^-T.  R = L2^T L1^T (src = dst R) when want_R.
+lramm_status orth(lramm_plan_s* P, const SideLayout& S, void* ws, float* src, float* tmp,
+                  float* dst, int64_t rows, bool want_R, int* st, cudaStream_t s) {
+  const int l = P->l;
+  float* G = at<float>(ws, S.G);
+  float* L1 = at<float>(ws, S.L1);
+  float* L2 = at<float>(ws, S.L2);
+  TIMED(P, LRAMM_K_GRAM, s, sgemm(1, 0, l, l, rows, 1.f, src, l, 0, src, l, 0.f, G, l, s));
+  TIMED(P, LRAMM_K_CHOL, s, launch_chol(G, l, kCholShift, L1, st, s));
+  TIMED(P, LRAMM_K_TRSM, s, launch_trsm_rows(src, rows, l, L1, tmp, s));
+  TIMED(P, LRAMM_K_GRAM, s, sgemm(1, 0, l, l, rows, 1.f, tmp, l, 0, tmp, l, 0.f, G, l, s));
+  TIMED(P, LRAMM_K_CHOL, s, launch_chol(G, l, 0.f, L2, st, s));
+  TIMED(P, LRAMM_K_TRSM, s, launch_trsm_rows(tmp, rows, l, L2, dst, s));
+  if (want_R)
+    TIMED(P, LRAMM_K_RFACTOR, s, sgemm(1, 1, l, l, l, 1.f, L2, l, 0, L1, l, 0.f, at<float>(ws, S.R), l, s));
+  return LRAMM_OK;
+}
+
+// Range finder, projection and small SVD of one operand X (rows x cols).
+// On exit (workspace): R0 = Q (rows x l), C0 = P (cols x l), sig[:r], and
+// S1 = U_s[:, :r] (x sigma if s1_sigma), S2 = V_s[:, :r] (x sigma if s2_sigma)
+// with X ~ Q U_s diag(sig) V_s^T P^T.
+lramm_status rsvd_core(lramm_plan_s* P, int which, const void* X, void* ws, int s1_sigma,
+                       int s2_sigma, cudaStream_t s) {
+  const lramm_desc& d = P->d;
+  const SideLayout& S = P->side[which];
+  const int l = P->l;
+  const int64_t ldx = which == 0 ? d.lda : d.ldb;
+  const int xbf = (which == 0 ? d.a_type : d.b_type) == LRAMM_BF16;
+  int* st = at<int>(ws, 0);
+  float* Om = at<float>(ws, S.omega);
+  float* R0 = at<float>(ws, S.R0);
+  float* R1 = at<float>(ws, S.R1);
+  float* C0 = at<float>(ws, S.C0);
+  float* C1 = at<float>(ws, S.C1);
+
+  TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, (uint32_t)which, S.cols, l, Om, l, s));
+  TIMED(P, LRAMM_K_SKETCH, s, sgemm(0, 0, S.rows, l, S.cols, 1.f, X, ldx, xbf, Om, l, 0.f, R0, l, s));  // X Omega
+  LRAMM_TRY(orth(P, S, ws, R0, R1, R0, S.rows, false, st, s));                                          // Q
+  for (int it = 0; it < d.q; ++it) {
+    TIMED(P, LRAMM_K_SKETCH, s, sgemm(1, 0, S.cols, l, S.rows, 1.f, X, ldx, xbf, R0, l, 0.f, C0, l, s));  // X^T Q
+    LRAMM_TRY(orth(P, S, ws, C0, C1, C0, S.cols, false, st, s));
+    TIMED(P, LRAMM_K_SKETCH, s, sgemm(0, 0, S.rows, l, S.cols, 1.f, X, ldx, xbf, C0, l, 0.f, R0, l, s));  // X Z^
+    LRAMM_TRY(orth(P, S, ws, R0, R1, R0, S.rows, false, st, s));
+  }
+  TIMED(P, LRAMM_K_SKETCH, s, sgemm(1, 0, S.cols, l, S.rows, 1.f, X, ldx, xbf, R0, l, 0.f, C0, l, s));  // B^T = X^T Q
+  LRAMM_TRY(orth(P, S, ws, C0, C1, C0, S.cols, true, st, s));                                            // B^T = P R
+  float* R = at<float>(ws, S.R);
+  float* Vj = at<float>(ws, S.Vj);
+  // R row-major is R^T column-major: one-sided Jacobi on R^T = U_s S V_s^T.
+  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(R, Vj, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s));
+  TIMED(P, LRAMM_K_SVDSORT, s,
+        launch_svd_finalize(R, Vj, l, d.r, at<float>(ws, S.sig), at<float>(ws, S.S1), s1_sigma,
+                            at<float>(ws, S.S2), s2_sigma, s));
+  return LRAMM_OK;
+}
+
+lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const float* Wt,
+                        const float* Zt, const float* C, float* D, void* ws, cudaStream_t s) {
+  const lramm_desc& d = P->d;
+  const int64_t r = d.r, kp = P->kp, rp = P->rp;
+  const int per_row = d.scale == LRAMM_S_ROWCOL;
+  unsigned int* am = at<unsigned int>(ws, P->amax);
+  float* E1 = at<float>(ws, P->E1);
+  float* E2t = at<float>(ws, P->E2t);
+  // E1 = QM(V^T W, d1): r x r, K = k
+  if (d.prec[0] == LRAMM_P_F32) {
+    TIMED(P, LRAMM_K_E1, s, sgemm(0, 1, r, r, d.k, 1.f, Vt, d.k, 0, Wt, d.k, 0.f, E1, r, s));
+  } else {
+    void* cV = at<void>(ws, P->cV);
+    void* cW = at<void>(ws, P->cW);
+    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Vt, r, d.k, d.k, d.prec[0], per_row, cV, kp, at<float>(ws, P->sV), am, s));
+    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Wt, r, d.k, d.k, d.prec[0], per_row, cW, kp, at<float>(ws, P->sW), am, s));
+    TIMED(P, LRAMM_K_E1, s, qgemm(cV, cW, r, r, kp, kp, kp, d.prec[0], per_row, at<float>(ws, P->sV),
+                                  at<float>(ws, P->sW), 1.f, 0.f, nullptr, 0, E1, r, 0, s));
+  }
+  // E2 = QM(E1 Z~, d2), computed transposed: E2^T = Z~^T E1^T (n x r, K = r)
+  if (d.prec[1] == LRAMM_P_F32) {
+    TIMED(P, LRAMM_K_E2, s, sgemm(0, 1, d.n, r, r, 1.f, Zt, r, 0, E1, r, 0.f, E2t, r, s));
+  } else {
+    void* cZ = at<void>(ws, P->cZ);
+    void* cE1 = at<void>(ws, P->cE1);
+    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Zt, d.n, r, r, d.prec[1], per_row, cZ, rp, at<float>(ws, P->sZ), am, s));
+    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(E1, r, r, r, d.prec[1], per_row, cE1, rp, at<float>(ws, P->sE1), am, s));
+    TIMED(P, LRAMM_K_E2, s, qgemm(cZ, cE1, d.n, r, rp, rp, rp, d.prec[1], per_row, at<float>(ws, P->sZ),
+                                  at<float>(ws, P->sE1), 1.f, 0.f, nullptr, 0, E2t, r, 0, s));
+  }
+  // E3 = QM(U~ E2, d3); D = alpha E3 + beta C  (m x n, K = r)
+  const float beta = d.beta;
+  if (beta != 0.f && !C) return LRAMM_ERR_INVALID_ARG;
+  if (d.prec[2] == LRAMM_P_F32) {
+    if (beta != 0.f && C != D)
+      LRAMM_CUDA_TRY(cudaMemcpy2DAsync(D, sizeof(float) * d.ldc, C, sizeof(float) * d.ldc,
+                                       sizeof(float) * d.n, d.m, cudaMemcpyDeviceToDevice, s));
+    TIMED(P, LRAMM_K_E3, s, sgemm(0, 1, d.m, d.n, r, d.alpha, Ut, r, 0, E2t, r, beta, D, d.ldc, s));
+  } else {
+    void* cU = at<void>(ws, P->cU);
+    void* cE2 = at<void>(ws, P->cE2);
+    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Ut, d.m, r, r, d.prec[2], per_row, cU, rp, at<float>(ws, P->sU), am, s));
+    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(E2t, d.n, r, r, d.prec[2], per_row, cE2, rp, at<float>(ws, P->sE2), am, s));
+    TIMED(P, LRAMM_K_E3, s, qgemm(cU, cE2, d.m, d.n, rp, rp, rp, d.prec[2], per_row, at<float>(ws, P->sU),
+                                  at<float>(ws, P->sE2), d.alpha, beta, C, d.ldc, D, d.ldc, 0, s));
+  }
+  return LRAMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lramm_last_cuda_error(void) { return g_cuda_err; }
+
+const char* lramm_status_str(lramm_status st) {
+  switch (st) {
+    case LRAMM_OK: return "ok";
+    case LRAMM_ERR_INVALID_ARG: return "invalid argument";
+    case LRAMM_ERR_UNSUPPORTED: return "unsupported configuration";
+    case LRAMM_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case LRAMM_ERR_CUDA: return "CUDA runtime error";
+    case LRAMM_ERR_NUMERIC: return "non-positive pivot in Cholesky (rank-deficient sketch)";
+    case LRAMM_ERR_TIMEOUT: return "bounded device wait ran out";
+    case LRAMM_WARN_NOCONV: return "Jacobi SVD reached its sweep cap";
+  }
+  return "unknown status";
+}
+
+lramm_status lramm_plan_create(const lramm_desc* desc, lramm_plan_t* out) {
+  if (!out) return LRAMM_ERR_INVALID_ARG;
+  const lramm_status v = validate(desc);
+  if (v != LRAMM_OK) return v;
+  lramm_plan_s* P = new (std::nothrow) lramm_plan_s();
+  if (!P) return LRAMM_ERR_INVALID_ARG;
+  P->d = *desc;
+  P->timing = (desc->flags & LRAMM_FLAG_TIMING) != 0;
+  P->l = desc->r + desc->p;
+  layout(P);
+  *out = P;
+  return LRAMM_OK;
+}
+
+lramm_status lramm_plan_destroy(lramm_plan_t plan) {
+  if (plan)
+    for (TimerRec& r : plan->recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+  delete plan;
+  return LRAMM_OK;
+}
+
+lramm_status lramm_timing_read(lramm_plan_t plan, float* ms, int32_t* launches) {
+  if (!plan || !ms || !launches || !plan->timing) return LRAMM_ERR_INVALID_ARG;
+  for (int k = 0; k < LRAMM_K_COUNT; ++k) {
+    ms[k] = 0.f;
+    launches[k] = 0;
+  }
+  for (size_t i = 0; i < plan->used; ++i) {
+    const TimerRec& r = plan->recs[i];
+    LRAMM_CUDA_TRY(cudaEventSynchronize(r.b));
+    float t = 0.f;
+    LRAMM_CUDA_TRY(cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.kind] += t;
+    launches[r.kind] += 1;
+  }
+  return LRAMM_OK;
+}
+
+const char* lramm_kernel_kind_name(int32_t kind) {
+  static const char* names[LRAMM_K_COUNT] = {"omega", "sketch", "gram", "chol", "trsm", "rfactor", "svd",
+                                             "svdsort", "assemble", "quant", "e1", "e2", "e3", "other"};
+  return (kind >= 0 && kind < LRAMM_K_COUNT) ? names[kind] : "unknown";
+}
+
+lramm_status lramm_workspace_size(lramm_plan_t plan, size_t* bytes) {
+  if (!plan || !bytes) return LRAMM_ERR_INVALID_ARG;
+  *bytes = plan->total;
+  return LRAMM_OK;
+}
+
+lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* U, float* S, float* V,
+                        void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || (which != 0 && which != 1) || !X || !U || !S || !V) return LRAMM_ERR_INVALID_ARG;
+  LRAMM_TRY(check_ws(plan, ws, ws_bytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const SideLayout& Sd = plan->side[which];
+  const int l = plan->l, r = plan->d.r;
+  plan->used = 0;
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
+  LRAMM_TRY(rsvd_core(plan, which, X, ws, 0, 0, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(0, 0, Sd.rows, r, l, 1.f, at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, 0.f, U, r, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(0, 0, Sd.cols, r, l, 1.f, at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, 0.f, V, r, s));
+  LRAMM_CUDA_TRY(cudaMemcpyAsync(S, at<float>(ws, Sd.sig), sizeof(float) * r, cudaMemcpyDeviceToDevice, s));
+  return LRAMM_OK;
+}
+
+lramm_status lramm_chain(lramm_plan_t plan, const float* Ut, const float* Vt, const float* Wt,
+                         const float* Zt, const float* C, float* D, void* ws, size_t ws_bytes,
+                         void* stream) {
+  if (!plan || !Ut || !Vt || !Wt || !Zt || !D) return LRAMM_ERR_INVALID_ARG;
+  LRAMM_TRY(check_ws(plan, ws, ws_bytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  plan->used = 0;
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
+  return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
+}
+
+lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const float* C, float* D,
+                          void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || !A || !B || !D) return LRAMM_ERR_INVALID_ARG;
+  if (plan->d.beta != 0.f && !C) return LRAMM_ERR_INVALID_ARG;
+  LRAMM_TRY(check_ws(plan, ws, ws_bytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const lramm_desc& d = plan->d;
+  const int l = plan->l, r = d.r;
+  plan->used = 0;
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
+  float* Ut = at<float>(ws, plan->Ut);
+  float* Vt = at<float>(ws, plan->Vt);
+  float* Wt = at<float>(ws, plan->Wt);
+  float* Zt = at<float>(ws, plan->Zt);
+  // A: U~ = Q_A (U_s Sigma) (m x r);  V^T = V_s^T P_A^T (r x k)
+  const SideLayout& SA = plan->side[0];
+  LRAMM_TRY(rsvd_core(plan, 0, A, ws, 1, 0, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(0, 0, d.m, r, l, 1.f, at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, 0.f, Ut, r, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SA.S2), r, 0, at<float>(ws, SA.C0), l, 0.f, Vt, d.k, s));
+  // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)
+  const SideLayout& SB = plan->side[1];
+  LRAMM_TRY(rsvd_core(plan, 1, B, ws, 0, 1, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SB.S1), r, 0, at<float>(ws, SB.R0), l, 0.f, Wt, d.k, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(0, 0, d.n, r, l, 1.f, at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, 0.f, Zt, r, s));
+  return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
+}
+
+lramm_status lramm_status_read(const void* ws, void* stream) {
+  if (!ws) return LRAMM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  LRAMM_CUDA_TRY(cudaMemcpyAsync(&h, ws, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LRAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(const_cast<void*>(ws), 0, sizeof(int), s));
+  return static_cast<lramm_status>(h);
+}
+
+lramm_status lramm_philox_words(uint64_t seed, uint32_t stream_id, int64_t n_blocks, uint32_t* out,
+                                void* stream) {
+  if (n_blocks < 0 || (n_blocks > 0 && !out)) return LRAMM_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(out) % 16) return LRAMM_ERR_INVALID_ARG;
+  return launch_philox_words(seed, stream_id, n_blocks, out, static_cast<cudaStream_t>(stream));
+}
+
+lramm_status lramm_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int64_t cols, float* out,
+                            void* stream) {
+  if (rows < 0 || cols < 0 || (rows * cols > 0 && !out)) return LRAMM_ERR_INVALID_ARG;
+  return launch_gaussian(seed, stream_id, rows, cols, out, cols, static_cast<cudaStream_t>(stream));
+}
+
+size_t lramm_quant_ws_bytes(void) { return kAlign; }
+
+lramm_status lramm_quantize(const float* X, int64_t rows, int64_t cols, int64_t ldx, int32_t prec,
+                            int32_t per_row, void* codes, int64_t ldcodes, float* scales, void* ws,
+                            void* stream) {
+  if (rows < 0 || cols < 0 || ldx < cols || ldcodes < cols) return LRAMM_ERR_INVALID_ARG;
+  if (prec == LRAMM_P_F32 || !valid_prec(prec)) return LRAMM_ERR_INVALID_ARG;
+  if (rows > 0 && (!X || !codes || !scales)) return LRAMM_ERR_INVALID_ARG;
+  if (!per_row && rows > 0 && !ws) return LRAMM_ERR_INVALID_ARG;
+  return quantize_rows(X, rows, cols, ldx, prec, per_row, codes, ldcodes, scales,
+                       static_cast<unsigned int*>(ws), static_cast<cudaStream_t>(stream));
+}
+
+lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                         int64_t ldr, int32_t prec, int32_t per_row, const float* sL, const float* sR,
+                         float alpha, float beta, const float* C, int64_t ldc, void* D, int64_t ldd,
+                         int32_t out_kind, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || K % 16 || ldl < K || ldr < K || ldd < N) return LRAMM_ERR_INVALID_ARG;
+  if (prec == LRAMM_P_F32 || !valid_prec(prec)) return LRAMM_ERR_INVALID_ARG;
+  if (out_kind != 0 && out_kind != 1) return LRAMM_ERR_INVALID_ARG;
+  if (M > 0 && N > 0 && (!L || !Rt || !D)) return LRAMM_ERR_INVALID_ARG;
+  if (out_kind == 0 && (!sL || !sR || (beta != 0.f && (!C || ldc < N)))) return LRAMM_ERR_INVALID_ARG;
+  return qgemm(L, Rt, M, N, K, ldl, ldr, prec, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, out_kind,
+               static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Shared device/host helpers of the LRAMM CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include "../../include/lramm.h"
+
+namespace lramm {
+
+// First device error wins; later ones are dropped.
+__device__ __forceinline__ void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+__host__ __device__ __forceinline__ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+// Code containers of the quantised factors: INT8 codes as bfloat16 values
+// (exact: |code| <= 127 < 2^8), INT4 and E4M3 codes as e4m3 bytes (|int4| <= 7
+// is exact in e4m3).
+enum CodeType : int { CODE_BF16 = 0, CODE_E4M3 = 1 };
+
+__host__ __device__ __forceinline__ int code_type_of(int prec) {
+  return prec == LRAMM_P_INT8 ? CODE_BF16 : CODE_E4M3;
+}
+__host__ __device__ __forceinline__ int code_bytes_of(int prec) { return prec == LRAMM_P_INT8 ? 2 : 1; }
+__host__ __device__ __forceinline__ float qmax_of(int prec) {
+  return prec == LRAMM_P_INT8 ? 127.0f : (prec == LRAMM_P_INT4 ? 7.0f : 448.0f);
+}
+
+__device__ __forceinline__ float e4m3_to_float(uint8_t b) {
+  __nv_fp8_e4m3 v;
+  v.__x = b;
+  return static_cast<float>(v);
+}
+
+__device__ __forceinline__ float load_as_float(const float* p) { return *p; }
+__device__ __forceinline__ float load_as_float(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
+// Host-side launch helpers -----------------------------------------------
+// The last failing CUDA call of this thread, for lramm_last_cuda_error().
+void note_cuda_error(cudaError_t e, const char* where);
+
+#define LRAMM_STR2(x) #x
+#define LRAMM_STR(x) LRAMM_STR2(x)
+#define LRAMM_CUDA_TRY(expr)                                          \
+  do {                                                                \
+    cudaError_t _e = (expr);                                          \
+    if (_e != cudaSuccess) {                                          \
+      ::lramm::note_cuda_error(_e, __FILE__ ":" LRAMM_STR(__LINE__)); \
+      return LRAMM_ERR_CUDA;                                          \
+    }                                                                 \
+  } while (0)
+
+#define LRAMM_TRY(expr)                                       \
+  do {                                                        \
+    lramm_status _s = (expr);                                 \
+    if (_s != LRAMM_OK) return _s;                            \
+  } while (0)
+
+inline lramm_status last_launch_at(const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) return LRAMM_OK;
+  note_cuda_error(e, where);
+  return LRAMM_ERR_CUDA;
+}
+#define last_launch() ::lramm::last_launch_at(__FILE__ ":" LRAMM_STR(__LINE__))
+
+// ---- kernels implemented in the .cu files (host launchers) ---------------
+
+// philox.cu
+lramm_status launch_philox_words(uint64_t seed, uint32_t sid, int64_t n_blocks, uint32_t* out,
+                                 cudaStream_t s);
+lramm_status launch_gaussian(uint64_t seed, uint32_t sid, int64_t rows, int64_t cols, float* out,
+                             int64_t ldo, cudaStream_t s);
+
+// gemm_simt.cu: C = alpha * op(A) op(B) + beta * C, FP32 accumulation.
+// op(A) is M x K: ta = 0 -> A[m*lda + k], ta = 1 -> A[k*lda + m].
+// op(B) is K x N: tb = 0 -> B[k*ldb + n], tb = 1 -> B[n*ldb + k].
+// a_bf16 = 1 reads A as bfloat16 (same layout rules).
+lramm_status sgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const void* A,
+                   int64_t lda, int a_bf16, const float* B, int64_t ldb, float beta, float* C,
+                   int64_t ldc, cudaStream_t s);
+
+// smallla.cu
+// Cholesky of the l x l SPD matrix G (row-major, stride l) with a diagonal
+// shift of shift_rel * max(diag G); writes L (lower, zeros above).
+lramm_status launch_chol(const float* G, int l, float shift_rel, float* L, int* status,
+                         cudaStream_t s);
+// Q = Y L^-T for the rows x l matrix Y (row-major, stride l).
+lramm_status launch_trsm_rows(const float* Y, int64_t rows, int l, const float* L, float* Q,
+                              cudaStream_t s);
+// One-sided Jacobi SVD of M (l x l, stored column-major: column j at M + j*l).
+// On exit M's columns are U_s Sigma (unsorted), V (column-major) the rotations.
+lramm_status launch_jacobi(float* M, float* V, int l, int max_sweeps, int* status, cudaStream_t s);
+// Sort the Jacobi result by descending sigma and write the rank-r pieces:
+//   sig[r]; S1 (l x r, row-major) = U_s[:, :r] (times sigma if s1_sigma);
+//   S2 (l x r, row-major) = V_s[:, :r] (times sigma if s2_sigma).
+lramm_status launch_svd_finalize(const float* M, const float* V, int l, int r, float* sig, float* S1,
+                                 int s1_sigma, float* S2, int s2_sigma, cudaStream_t s);
+
+// quant.cu
+lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
+                           int per_row, void* codes, int64_t ldcodes, float* scales,
+                           unsigned int* amax_ws, cudaStream_t s);
+lramm_status qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                   int64_t ldr, int prec, int per_row, const float* sL, const float* sR, float alpha,
+                   float beta, const float* C, int64_t ldc, void* D, int64_t ldd, int out_kind,
+                   cudaStream_t s);
+
+}  // namespace lramm

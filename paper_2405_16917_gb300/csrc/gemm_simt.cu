@@ -1,0 +1,136 @@
+// FP32 SIMT GEMM, C = alpha * op(A) op(B) + beta * C, for the small and
+// medium contractions of the pipeline (Gram matrices, triangular applies,
+// factor assembly, unquantised factor chain) and as the FP32-accurate
+// sketch product.  64 x 64 output tile per 256-thread block, 4 x 4 per
+// thread, K staged through shared memory 16 at a time.
+//
+// Accumulation: each 16-deep K tile is summed in a fresh FP32 register and
+// added to the running sum with Kahan compensation, so the rounding error
+// of an entry is ~ (4 + O(1)) u sum|a_k b_k| whatever K is (a plain FMA
+// chain grows like sqrt(K) u; K reaches 32768 here).
+#include "common.cuh"
+
+namespace lramm {
+
+template <int TA, int TB, typename TAe>
+__global__ void __launch_bounds__(256)
+sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict__ A, int64_t lda,
+             const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C,
+             int64_t ldc) {
+  __shared__ float As[16][64 + 4];
+  __shared__ float Bs[16][64 + 4];
+  const int tid = threadIdx.x;
+  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[4][4], cmp[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = 0.f;
+
+  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256;
+      int mm, kk;
+      if (TA == 0) {  // A row-major M x K: contiguous along k
+        kk = e & 15;
+        mm = e >> 4;
+      } else {        // A stored K x M: contiguous along m
+        mm = e & 63;
+        kk = e >> 6;
+      }
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      float v = 0.f;
+      if (gm < M && gk < K) v = load_as_float(TA == 0 ? A + gm * lda + gk : A + gk * lda + gm);
+      As[kk][mm] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256;
+      int nn, kk;
+      if (TB == 0) {  // B row-major K x N: contiguous along n
+        nn = e & 63;
+        kk = e >> 6;
+      } else {        // B stored N x K: contiguous along k
+        kk = e & 15;
+        nn = e >> 4;
+      }
+      const int64_t gn = n0 + nn, gk = k0 + kk;
+      float v = 0.f;
+      if (gn < N && gk < K) v = TB == 0 ? B[gk * ldb + gn] : B[gn * ldb + gk];
+      Bs[kk][nn] = v;
+    }
+    __syncthreads();
+    float blk[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) blk[i][j] = 0.f;
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) blk[i][j] = fmaf(a[i], b[j], blk[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {  // Kahan: acc += blk
+        const float y = blk[i][j] - cmp[i][j];
+        const float t = acc[i][j] + y;
+        cmp[i][j] = (t - acc[i][j]) - y;
+        acc[i][j] = t;
+      }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      float v = alpha * acc[i][j];
+      if (beta != 0.f) v = fmaf(beta, C[gm * ldc + gn], v);
+      C[gm * ldc + gn] = v;
+    }
+  }
+}
+
+template <typename TAe>
+static lramm_status sgemm_t(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha,
+                            const TAe* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                            float* C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return LRAMM_OK;
+  if (ceil_div(M, 64) > 65535) return LRAMM_ERR_UNSUPPORTED;
+  dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
+  if (ta == 0 && tb == 0)
+    sgemm_kernel<0, 0, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta == 0 && tb == 1)
+    sgemm_kernel<0, 1, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else if (ta == 1 && tb == 0)
+    sgemm_kernel<1, 0, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  else
+    sgemm_kernel<1, 1, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+  return last_launch();
+}
+
+lramm_status sgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const void* A,
+                   int64_t lda, int a_bf16, const float* B, int64_t ldb, float beta, float* C,
+                   int64_t ldc, cudaStream_t s) {
+  if (a_bf16)
+    return sgemm_t<__nv_bfloat16>(ta, tb, M, N, K, alpha, static_cast<const __nv_bfloat16*>(A), lda,
+                                  B, ldb, beta, C, ldc, s);
+  return sgemm_t<float>(ta, tb, M, N, K, alpha, static_cast<const float*>(A), lda, B, ldb, beta, C,
+                        ldc, s);
+}
+
+}  // namespace lramm

@@ -1,0 +1,228 @@
+// Symmetric linear quantiser (Eqs. (Quantization), (get_lambda), Sec. 3.1)
+// and the quantised GEMM QM of Algorithm 2 with a fused FP32 dequantisation
+// (Eq. (Dequantization)) and the alpha/beta epilogue of Algorithm 3.
+//
+// The decisions are taken in FP32: a_max exact, lambda = D / a_max (IEEE
+// division), code = rint(x * lambda) (one FP32 multiply, round half to even)
+// clamped to +-D; e4m3 codes are the round-to-nearest-even, saturating FP8
+// conversion of x * lambda.  Dequantisation of a product entry:
+//   fp32(acc) * fp32(s_left[i] * s_right[j]),  s = a_max / D.
+#include "common.cuh"
+
+namespace lramm {
+
+__device__ __forceinline__ float warp_max_q(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Whole-tensor a_max into *amax (as the bits of a non-negative float, so an
+// unsigned atomicMax orders them correctly).  *amax must start at 0.
+__global__ void tensor_amax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                   unsigned int* amax) {
+  float m = 0.f;
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    m = fmaxf(m, fabsf(X[i * ldx + j]));
+  }
+  m = warp_max_q(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(amax, __float_as_uint(m));
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_code(void* codes, int64_t idx, float y, float D) {
+  if (PREC == LRAMM_P_E4M3) {
+    static_cast<uint8_t*>(codes)[idx] = __nv_cvt_float_to_fp8(y, __NV_SATFINITE, __NV_E4M3);
+  } else {
+    const float v = fminf(fmaxf(rintf(y), -D), D);
+    if (PREC == LRAMM_P_INT8)
+      static_cast<__nv_bfloat16*>(codes)[idx] = __float2bfloat16_rn(v);
+    else
+      static_cast<uint8_t*>(codes)[idx] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// One warp per row.  Per-row mode finds the row's a_max; per-tensor mode
+// reads the whole-tensor a_max from *tensor_amax.
+template <int PREC>
+__global__ void quant_rows_kernel(const float* __restrict__ X, int64_t rows, int64_t cols, int64_t ldx,
+                                  void* __restrict__ codes, int64_t ldcodes, float* __restrict__ scales,
+                                  const unsigned int* __restrict__ tensor_amax) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const float D = PREC == LRAMM_P_INT8 ? 127.0f : (PREC == LRAMM_P_INT4 ? 7.0f : 448.0f);
+  for (int64_t row = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); row < rows;
+       row += warps) {
+    const float* x = X + row * ldx;
+    float amax;
+    if (tensor_amax) {
+      amax = __uint_as_float(*tensor_amax);
+    } else {
+      amax = 0.f;
+      for (int64_t j = lane; j < cols; j += 32) amax = fmaxf(amax, fabsf(x[j]));
+      amax = warp_max_q(amax);
+    }
+    const float lam = amax > 0.f ? __fdiv_rn(D, amax) : 0.f;
+    if (lane == 0 && (tensor_amax == nullptr || row == 0))
+      scales[tensor_amax ? 0 : row] = __fdiv_rn(amax, D);
+    for (int64_t j = lane; j < ldcodes; j += 32) {
+      const float y = j < cols ? __fmul_rn(x[j], lam) : 0.f;
+      store_code<PREC>(codes, row * ldcodes + j, y, D);
+    }
+  }
+}
+
+lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
+                           int per_row, void* codes, int64_t ldcodes, float* scales,
+                           unsigned int* amax_ws, cudaStream_t s) {
+  if (rows <= 0) return LRAMM_OK;
+  const unsigned int* tam = nullptr;
+  if (!per_row) {
+    if (!amax_ws) return LRAMM_ERR_INVALID_ARG;
+    LRAMM_CUDA_TRY(cudaMemsetAsync(amax_ws, 0, sizeof(unsigned int), s));
+    int64_t g = ceil_div(rows * cols, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) g = 1;
+    tensor_amax_kernel<<<(unsigned)g, 256, 0, s>>>(X, rows, cols, ldx, amax_ws);
+    LRAMM_TRY(last_launch());
+    tam = amax_ws;
+  }
+  const int threads = 256, wpb = threads / 32;
+  int64_t g = ceil_div(rows, wpb);
+  if (g > 152 * 16) g = 152 * 16;
+  switch (prec) {
+    case LRAMM_P_INT8:
+      quant_rows_kernel<LRAMM_P_INT8><<<(unsigned)g, threads, 0, s>>>(X, rows, cols, ldx, codes, ldcodes, scales, tam);
+      break;
+    case LRAMM_P_INT4:
+      quant_rows_kernel<LRAMM_P_INT4><<<(unsigned)g, threads, 0, s>>>(X, rows, cols, ldx, codes, ldcodes, scales, tam);
+      break;
+    case LRAMM_P_E4M3:
+      quant_rows_kernel<LRAMM_P_E4M3><<<(unsigned)g, threads, 0, s>>>(X, rows, cols, ldx, codes, ldcodes, scales, tam);
+      break;
+    default:
+      return LRAMM_ERR_INVALID_ARG;
+  }
+  return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// QM product, SIMT: acc(i,j) = sum_t L(i,t) Rt(j,t) with both operands
+// K-major code matrices.  Integer codes accumulate exactly: FP32 partial
+// sums of at most 1024 products (|sum| <= 1024 * 127^2 < 2^24) are moved
+// into an int32 accumulator.
+// ---------------------------------------------------------------------------
+template <int CT>
+__device__ __forceinline__ float load_code(const void* p, int64_t idx) {
+  if (CT == CODE_BF16) return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[idx]);
+  return e4m3_to_float(static_cast<const uint8_t*>(p)[idx]);
+}
+
+template <int CT, bool EXACT>
+__global__ void __launch_bounds__(256)
+qgemm_simt_kernel(const void* __restrict__ Lc, const void* __restrict__ Rc, int64_t M, int64_t N, int64_t K,
+                  int64_t ldl, int64_t ldr, int per_row, const float* __restrict__ sL,
+                  const float* __restrict__ sR, float alpha, float beta, const float* __restrict__ C,
+                  int64_t ldc, void* __restrict__ D, int64_t ldd, int out_kind) {
+  __shared__ float As[32][64 + 4];
+  __shared__ float Bs[32][64 + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
+  float acc[4][4];
+  int iacc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      acc[i][j] = 0.f;
+      iacc[i][j] = 0;
+    }
+  int chunk = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += 32) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + u * 256;
+      const int kk = e & 31, rr = e >> 5;
+      const int64_t gk = k0 + kk;
+      const int64_t gm = m0 + rr, gn = n0 + rr;
+      As[kk][rr] = (gm < M && gk < K) ? load_code<CT>(Lc, gm * ldl + gk) : 0.f;
+      Bs[kk][rr] = (gn < N && gk < K) ? load_code<CT>(Rc, gn * ldr + gk) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+    if (EXACT && ++chunk == 32) {  // 32 * 32 = 1024 products per FP32 partial
+      chunk = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          iacc[i][j] += __float2int_rn(acc[i][j]);
+          acc[i][j] = 0.f;
+        }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t gm = m0 + ty * 4 + i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gn = n0 + tx * 4 + j;
+      if (gn >= N) continue;
+      if (EXACT) {
+        const int tot = iacc[i][j] + __float2int_rn(acc[i][j]);
+        if (out_kind == 1) {
+          static_cast<int*>(D)[gm * ldd + gn] = tot;
+          continue;
+        }
+        acc[i][j] = (float)tot;  // cvt.rn.f32.s32
+      } else if (out_kind == 1) {
+        static_cast<float*>(D)[gm * ldd + gn] = acc[i][j];
+        continue;
+      }
+      const float sp = __fmul_rn(per_row ? sL[gm] : sL[0], per_row ? sR[gn] : sR[0]);
+      const float deq = __fmul_rn(acc[i][j], sp);
+      float v = __fmul_rn(alpha, deq);
+      if (beta != 0.f) v = fmaf(beta, C[gm * ldc + gn], v);
+      static_cast<float*>(D)[gm * ldd + gn] = v;
+    }
+  }
+}
+
+lramm_status qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                   int64_t ldr, int prec, int per_row, const float* sL, const float* sR, float alpha,
+                   float beta, const float* C, int64_t ldc, void* D, int64_t ldd, int out_kind,
+                   cudaStream_t s) {
+  if (M <= 0 || N <= 0) return LRAMM_OK;
+  if (ceil_div(M, 64) > 65535) return LRAMM_ERR_UNSUPPORTED;
+  dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
+  if (prec == LRAMM_P_INT8)
+    qgemm_simt_kernel<CODE_BF16, true><<<grid, 256, 0, s>>>(L, Rt, M, N, K, ldl, ldr, per_row, sL, sR, alpha,
+                                                           beta, C, ldc, D, ldd, out_kind);
+  else if (prec == LRAMM_P_INT4)
+    qgemm_simt_kernel<CODE_E4M3, true><<<grid, 256, 0, s>>>(L, Rt, M, N, K, ldl, ldr, per_row, sL, sR, alpha,
+                                                           beta, C, ldc, D, ldd, out_kind);
+  else if (prec == LRAMM_P_E4M3)
+    qgemm_simt_kernel<CODE_E4M3, false><<<grid, 256, 0, s>>>(L, Rt, M, N, K, ldl, ldr, per_row, sL, sR, alpha,
+                                                            beta, C, ldc, D, ldd, out_kind);
+  else
+    return LRAMM_ERR_INVALID_ARG;
+  return last_launch();
+}
+
+}  // namespace lramm

@@ -1,0 +1,90 @@
+"""The C-ABI library loads and exports every declared symbol; plan creation
+validates its arguments (host logic only, no GPU work)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lramm.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lramm_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    import paper_2405_16917_gb300 as L
+    if not os.path.exists(L.LIB_PATH):
+        from paper_2405_16917_gb300 import _build
+        _build.build()
+    L.load()
+    return L
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for s in ("lramm_plan_create", "lramm_rsvd", "lramm_matmul", "lramm_chain", "lramm_workspace_size",
+              "lramm_plan_destroy", "lramm_status_read", "lramm_quantize", "lramm_qgemm",
+              "lramm_gaussian", "lramm_philox_words"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(L):
+    lib = ctypes.CDLL(L.LIB_PATH)
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol(L):
+    assert set(declared_symbols()) <= set(L._SIGS)
+
+
+def _plan(L, **kw):
+    args = dict(m=512, n=512, k=512, r=64, p=10, q=1)
+    args.update(kw)
+    return L.Plan(**args)
+
+
+def test_plan_create_and_workspace(L):
+    p = _plan(L)
+    assert p.ws_bytes > 0 and p.ws_bytes % 256 == 0
+    big = _plan(L, m=4096, n=4096, k=4096, r=256, p=16, q=2)
+    assert big.ws_bytes > p.ws_bytes
+    p.close()
+    big.close()
+
+
+@pytest.mark.parametrize("kw", [dict(m=0), dict(r=0), dict(p=-1), dict(q=17), dict(r=500, p=20),
+                                dict(lda=100), dict(prec=(9, 1, 1)), dict(scale=5), dict(sketch=7),
+                                dict(a_type=3)])
+def test_plan_rejects_invalid(L, kw):
+    with pytest.raises(L.LrammError) as e:
+        _plan(L, **kw)
+    assert e.value.code == 1
+
+
+def test_plan_unsupported_sketch_width(L):
+    with pytest.raises(L.LrammError) as e:
+        _plan(L, m=4096, n=4096, k=4096, r=500, p=30)
+    assert e.value.code == 2
+
+
+def test_calls_reject_bad_arguments_without_gpu_work(L):
+    lib = L.load()
+    p = _plan(L)
+    nul = ctypes.c_void_p(0)
+    assert lib.lramm_matmul(p.handle, nul, nul, nul, nul, nul, 0, nul) == 1
+    assert lib.lramm_rsvd(p.handle, 2, nul, nul, nul, nul, nul, 0, nul) == 1
+    fake = ctypes.c_void_p(256)
+    assert lib.lramm_matmul(p.handle, fake, fake, nul, fake, fake, 16, nul) == 3     # workspace too small
+    assert lib.lramm_matmul(p.handle, fake, fake, nul, fake, ctypes.c_void_p(300), p.ws_bytes, nul) == 3
+    assert lib.lramm_qgemm(fake, fake, 4, 4, 17, 17, 17, 1, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, 0,
+                           nul) == 1                                                   # K % 16
+    assert lib.lramm_quantize(fake, 4, 8, 8, 0, 1, fake, 8, fake, nul, nul) == 1      # F32 is not a code
+    assert lib.lramm_philox_words(1, 0, 4, ctypes.c_void_p(4), nul) == 1               # misaligned
+    assert lib.lramm_status_str(5).decode().startswith("non-positive")
