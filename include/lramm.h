@@ -227,6 +227,32 @@ LRAMM_API lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int
 /* Bytes of workspace lramm_quantize needs in per-tensor mode. */
 LRAMM_API size_t lramm_quant_ws_bytes(void);
 
+/* lramm_quantize without the caller-supplied workspace.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory
+ * themselves -- for example code running under a framework that owns all
+ * GPU memory through its own pool and forbids raw device allocations, or a
+ * plug-in whose host gives it no allocator.  Arguments, codes and scales
+ * are exactly those of lramm_quantize (the caller still passes X, codes
+ * and scales).
+ * Scratch: per-tensor mode (per_row = 0) keeps its single 32-bit a_max
+ * accumulator in a 256-byte array compiled into the library
+ * (lramm_noalloc_scratch_bytes()); every GPU that loads the library holds
+ * that array until the process exits.  A call that would need more scratch
+ * than the array holds is rejected with LRAMM_ERR_UNSUPPORTED; per-row mode
+ * uses no scratch.  Nothing is allocated: no cudaMalloc, no cudaFree.
+ * The first per-tensor call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture on the device.
+ * All calls share the one array: each call clears the accumulator before
+ * using it, but calls whose kernels overlap on the GPU (different streams,
+ * no ordering between them) race on it and may produce wrong scales. */
+LRAMM_API lramm_status lramm_quantize_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx,
+                                              int32_t prec, int32_t per_row, void* codes,
+                                              int64_t ldcodes, float* scales, void* stream);
+
+/* Size in bytes of the scratch array used by lramm_quantize_noalloc. */
+LRAMM_API size_t lramm_noalloc_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

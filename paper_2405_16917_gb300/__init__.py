@@ -56,6 +56,8 @@ _SIGS = {
     "lramm_qgemm": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _VP, _VP, _F, _F,
                            _VP, _I64, _VP, _I64, _I32, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
+    "lramm_quantize_noalloc": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _VP]),
+    "lramm_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "lramm_timing_read": (_I32, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]),
     "lramm_kernel_kind_name": (ctypes.c_char_p, [_I32]),
 }
@@ -249,6 +251,26 @@ def quantize(X, prec, per_row=True, ldcodes=None):
     ws = torch.empty(lib.lramm_quant_ws_bytes(), dtype=torch.uint8, device=X.device)
     _check(lib.lramm_quantize(_ptr(X), rows, cols, X.stride(0), prec, int(per_row), _ptr(codes), ldc,
                               _ptr(scales), _ptr(ws), _stream()), "lramm_quantize")
+    return codes, scales
+
+
+def quantize_noalloc(X, prec, per_row=False, ldcodes=None, codes=None, scales=None):
+    """lramm_quantize_noalloc: the quantiser without a caller workspace.
+
+    For callers that cannot allocate device memory: the per-tensor a_max
+    accumulator lives in the library's own device array.  Output buffers
+    may be passed in (codes, scales) so the call itself allocates nothing.
+    """
+    torch = _torch()
+    _need_cuda(X)
+    rows, cols = X.shape
+    ldc = ldcodes or cols
+    if codes is None:
+        codes = torch.empty((rows, ldc), dtype=code_dtype(prec), device=X.device)
+    if scales is None:
+        scales = torch.empty((rows if per_row else 1,), dtype=torch.float32, device=X.device)
+    _check(load().lramm_quantize_noalloc(_ptr(X), rows, cols, X.stride(0), prec, int(per_row), _ptr(codes),
+                                         ldc, _ptr(scales), _stream()), "lramm_quantize_noalloc")
     return codes, scales
 
 

@@ -448,6 +448,18 @@ lramm_status lramm_quantize(const float* X, int64_t rows, int64_t cols, int64_t 
                        static_cast<unsigned int*>(ws), static_cast<cudaStream_t>(stream));
 }
 
+lramm_status lramm_quantize_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx, int32_t prec,
+                                    int32_t per_row, void* codes, int64_t ldcodes, float* scales,
+                                    void* stream) {
+  if (rows < 0 || cols < 0 || ldx < cols || ldcodes < cols) return LRAMM_ERR_INVALID_ARG;
+  if (prec == LRAMM_P_F32 || !valid_prec(prec)) return LRAMM_ERR_INVALID_ARG;
+  if (rows > 0 && (!X || !codes || !scales)) return LRAMM_ERR_INVALID_ARG;
+  return quantize_rows_noalloc(X, rows, cols, ldx, prec, per_row, codes, ldcodes, scales,
+                               static_cast<cudaStream_t>(stream));
+}
+
+size_t lramm_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
+
 lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
                          int64_t ldr, int32_t prec, int32_t per_row, const float* sL, const float* sR,
                          float alpha, float beta, const float* C, int64_t ldc, void* D, int64_t ldd,

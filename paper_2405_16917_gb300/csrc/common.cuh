@@ -106,6 +106,10 @@ lramm_status launch_svd_finalize(const float* M, const float* V, int l, int r, f
 lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
                            int per_row, void* codes, int64_t ldcodes, float* scales,
                            unsigned int* amax_ws, cudaStream_t s);
+lramm_status quantize_rows_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
+                                   int per_row, void* codes, int64_t ldcodes, float* scales,
+                                   cudaStream_t s);
+size_t noalloc_scratch_bytes();
 lramm_status qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
                    int64_t ldr, int prec, int per_row, const float* sL, const float* sR, float alpha,
                    float beta, const float* C, int64_t ldc, void* D, int64_t ldd, int out_kind,

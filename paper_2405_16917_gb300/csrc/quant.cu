@@ -7,6 +7,8 @@
 // clamped to +-D; e4m3 codes are the round-to-nearest-even, saturating FP8
 // conversion of x * lambda.  Dequantisation of a product entry:
 //   fp32(acc) * fp32(s_left[i] * s_right[j]),  s = a_max / D.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace lramm {
@@ -223,6 +225,49 @@ lramm_status qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t 
   else
     return LRAMM_ERR_INVALID_ARG;
   return last_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free form of the quantiser, for callers that cannot allocate
+// device memory themselves.  Per-tensor mode needs one 32-bit a_max
+// accumulator; here it lives in this file's own device array instead of a
+// caller-supplied workspace.  The array is part of the library image, so
+// every GPU the library is loaded on holds its 256 bytes until the process
+// exits.  Its device address is looked up once per device (first call on
+// that device, with the device current) and handed to the kernels.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned int g_noalloc_scratch[64];
+static void* g_noalloc_ptr[256];
+static std::mutex g_noalloc_mu;
+
+static lramm_status noalloc_scratch(unsigned int** out) {
+  int dev = 0;
+  LRAMM_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return LRAMM_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    LRAMM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned int*>(g_noalloc_ptr[dev]);
+  return LRAMM_OK;
+}
+
+// Scratch bytes the allocation-free quantiser may use (the size of the array).
+size_t noalloc_scratch_bytes() { return sizeof(g_noalloc_scratch); }
+
+lramm_status quantize_rows_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
+                                   int per_row, void* codes, int64_t ldcodes, float* scales,
+                                   cudaStream_t s) {
+  unsigned int* am = nullptr;
+  if (!per_row && rows > 0) {
+    // one accumulator per call; cleared by quantize_rows before its kernels run
+    const size_t need = sizeof(unsigned int);
+    if (need > sizeof(g_noalloc_scratch)) return LRAMM_ERR_UNSUPPORTED;
+    LRAMM_TRY(noalloc_scratch(&am));
+  }
+  return quantize_rows(X, rows, cols, ldx, prec, per_row, codes, ldcodes, scales, am, s);
 }
 
 }  // namespace lramm
