@@ -224,6 +224,25 @@ LRAMM_API lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int
                          const float* C, int64_t ldc, void* D, int64_t ldd,
                          int32_t out_kind, void* stream);
 
+/* The products of an operand with an l-column matrix that the range finder
+ * runs (Sec. 2.2 sketch Y = X Omega, the power-iteration products, and the
+ * projection B^T = X^T Q of Algorithm 1):
+ *   transpose = 0: out = X B    (X rows x cols, B cols x l, out rows x l)
+ *   transpose = 1: out = X^T B  (B rows x l, out cols x l)
+ * X has row stride ldx and type x_type; B and out are dense row-major FP32.
+ * sketch = LRAMM_SKETCH_F32: FP32 SIMT product (compensated accumulation);
+ * LRAMM_SKETCH_TF32: tcgen05 tensor cores, TF32 inputs, FP32 accumulation
+ * (needs FP32 X, l and ldx divisible by 4, 16-byte aligned X and B, l <= 512,
+ * else LRAMM_ERR_UNSUPPORTED) with ws of lramm_sketch_ws_bytes(l) bytes for
+ * split-K partials (256-byte aligned; its first word is the status word). */
+LRAMM_API lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t cols, int64_t ldx,
+                                            int32_t x_type, int32_t transpose, const float* B, int64_t l,
+                                            float* out, int32_t sketch, void* ws, size_t ws_bytes,
+                                            void* stream);
+
+/* Bytes of workspace lramm_sketch_product needs for an l-column product. */
+LRAMM_API size_t lramm_sketch_ws_bytes(int64_t l);
+
 /* Bytes of workspace lramm_quantize needs in per-tensor mode. */
 LRAMM_API size_t lramm_quant_ws_bytes(void);
 

@@ -56,6 +56,9 @@ _SIGS = {
     "lramm_qgemm": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _VP, _VP, _F, _F,
                            _VP, _I64, _VP, _I64, _I32, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
+    "lramm_sketch_product": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _I32, _VP, ctypes.c_size_t,
+                                    _VP]),
+    "lramm_sketch_ws_bytes": (ctypes.c_size_t, [_I64]),
     "lramm_quantize_noalloc": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _VP]),
     "lramm_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "lramm_timing_read": (_I32, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]),
@@ -231,6 +234,23 @@ def gaussian(seed, stream_id, rows, cols, device="cuda"):
     torch = _torch()
     out = torch.empty((rows, cols), dtype=torch.float32, device=device)
     _check(load().lramm_gaussian(seed, stream_id, rows, cols, _ptr(out), _stream()), "lramm_gaussian")
+    return out
+
+
+def sketch_product(X, B, transpose=False, sketch=SKETCH_TF32):
+    """X B or X^T B (the range finder's products) through lramm_sketch_product."""
+    torch = _torch()
+    _need_cuda(X, B)
+    rows, cols = X.shape
+    l = B.shape[1]
+    out = torch.empty((cols if transpose else rows, l), dtype=torch.float32, device=X.device)
+    lib = load()
+    ws = torch.zeros(lib.lramm_sketch_ws_bytes(l), dtype=torch.uint8, device=X.device)
+    _check(lib.lramm_sketch_product(_ptr(X), rows, cols, X.stride(0), _dtype_code(X), int(transpose), _ptr(B), l,
+                                    _ptr(out), sketch, _ptr(ws), ws.numel(), _stream()), "lramm_sketch_product")
+    st = int(ws[:4].view(torch.int32).item())
+    if st != 0:
+        raise LrammError(st, "lramm_sketch_product (device)")
     return out
 
 

@@ -24,8 +24,8 @@ void note_cuda_error(cudaError_t e, const char* where) {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxL = 320;
-constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of the first CQR pass
+constexpr int kMaxL = 300;
+constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of every CholeskyQR pass
 
 struct SideLayout {
   int64_t rows, cols;
@@ -51,6 +51,7 @@ struct lramm_plan_s {
   size_t cV, cW, cE1, cZ, cU, cE2;
   size_t sV, sW, sE1, sZ, sU, sE2;
   size_t amax;
+  size_t part;
   size_t total;
 };
 
@@ -131,6 +132,7 @@ void layout(lramm_plan_s* P) {
   P->sU = b.take(sizeof(float) * d.m);
   P->sE2 = b.take(sizeof(float) * d.n);
   P->amax = b.take(kAlign);
+  P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
   P->total = b.off;
 }
 
@@ -171,63 +173,124 @@ lramm_status check_ws(const lramm_plan_s* P, void* ws, size_t ws_bytes) {
   return LRAMM_OK;
 }
 
-// Orthonormalise the rows x l matrix src (stride l) by CholeskyQR2:
-// G = src^T src = L1 L1^T, tmp = src L1^-T; G = tmp^T tmp = L2 L2^T,
-// dst = tmp L2^-T.  R = L2^T L1^T (src = dst R) when want_R.
-lramm_status orth(lramm_plan_s* P, const SideLayout& S, void* ws, float* src, float* tmp,
-                  float* dst, int64_t rows, bool want_R, int* st, cudaStream_t s) {
+// X B (a_mn = 0) or X^T B (a_mn = 1) for the range finder: on the tensor
+// cores in TF32 when the plan asks for a TF32 sketch and the shapes allow
+// (TMA needs l and the row stride of X divisible by 4, 16-byte aligned
+// bases), else the FP32 SIMT product.
+lramm_status x_product(lramm_plan_s* P, void* ws, int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx,
+                       int xbf, const float* B, float* out, cudaStream_t s) {
   const int l = P->l;
-  float* G = at<float>(ws, S.G);
-  float* L1 = at<float>(ws, S.L1);
-  float* L2 = at<float>(ws, S.L2);
-  TIMED(P, LRAMM_K_GRAM, s, sgemm(1, 0, l, l, rows, 1.f, src, l, 0, src, l, 0.f, G, l, s));
-  TIMED(P, LRAMM_K_CHOL, s, launch_chol(G, l, kCholShift, L1, st, s));
-  TIMED(P, LRAMM_K_TRSM, s, launch_trsm_rows(src, rows, l, L1, tmp, s));
-  TIMED(P, LRAMM_K_GRAM, s, sgemm(1, 0, l, l, rows, 1.f, tmp, l, 0, tmp, l, 0.f, G, l, s));
-  TIMED(P, LRAMM_K_CHOL, s, launch_chol(G, l, 0.f, L2, st, s));
-  TIMED(P, LRAMM_K_TRSM, s, launch_trsm_rows(tmp, rows, l, L2, dst, s));
+  if (P->d.sketch == LRAMM_SKETCH_TF32 && sketch_tc_supported(xbf, ldx, l, X, B))
+    return sketch_tc(a_mn, X, rows, cols, ldx, xbf, B, l, out, at<float>(ws, P->part),
+                     sketch_tc_part_floats(l), at<int>(ws, 0), s);
+  if (a_mn) return sgemm(1, 0, cols, l, rows, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
+  return sgemm(0, 0, rows, l, cols, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
+}
+
+// One operand's share of a randomized SVD run.
+struct SideRun {
+  const void* X;
+  int64_t ldx;
+  int xbf;
+  const SideLayout* S;
+};
+
+// Orthonormalise, for every side s, the rows_s x l matrix src[s] (stride l)
+// by `passes` CholeskyQR passes (Gram, Cholesky, Q = Y L^-T); every pass
+// shifts the Gram diagonal by 4u max(diag) so a rank-deficient sketch still
+// factors (the shift costs ~4u in orthonormality).  One pass suffices where only the span matters (the intermediate
+// bases of the power iterations); two give orthonormality to working
+// precision.  dst may equal src.  With want_R (two passes): R = L2^T L1^T,
+// so that src = dst R.
+lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, float* const* src,
+                        float* const* tmp, float* const* dst, const int64_t* rows, int passes, bool want_R,
+                        int* st, cudaStream_t s) {
+  const int l = P->l;
+  const float* in[2] = {src[0], ns > 1 ? src[1] : nullptr};
+  for (int pass = 0; pass < passes; ++pass) {
+    float* out[2];
+    SmallBatch cb{}, tb{};
+    cb.n = tb.n = ns;
+    for (int i = 0; i < ns; ++i) {
+      float* G = at<float>(ws, sd[i].S->G);
+      float* Lf = at<float>(ws, pass == 0 ? sd[i].S->L1 : sd[i].S->L2);
+      out[i] = pass == passes - 1 ? dst[i] : tmp[i];
+      TIMED(P, LRAMM_K_GRAM, s, sgemm(1, 0, l, l, rows[i], 1.f, in[i], l, 0, in[i], l, 0.f, G, l, s));
+      cb.p[i] = SmallProb{G, Lf, nullptr, 0};
+      tb.p[i] = SmallProb{in[i], out[i], Lf, rows[i]};
+    }
+    TIMED(P, LRAMM_K_CHOL, s, launch_chol(cb, l, kCholShift, st, s));
+    TIMED(P, LRAMM_K_TRSM, s, launch_trsm_rows(tb, l, s));
+    for (int i = 0; i < ns; ++i) in[i] = out[i];
+  }
   if (want_R)
-    TIMED(P, LRAMM_K_RFACTOR, s, sgemm(1, 1, l, l, l, 1.f, L2, l, 0, L1, l, 0.f, at<float>(ws, S.R), l, s));
+    for (int i = 0; i < ns; ++i) {
+      const SideLayout& S = *sd[i].S;
+      if (passes == 2)
+        TIMED(P, LRAMM_K_RFACTOR, s,
+              sgemm(1, 1, l, l, l, 1.f, at<float>(ws, S.L2), l, 0, at<float>(ws, S.L1), l, 0.f,
+                    at<float>(ws, S.R), l, s));
+      else
+        return LRAMM_ERR_INVALID_ARG;
+    }
   return LRAMM_OK;
 }
 
-// Range finder, projection and small SVD of one operand X (rows x cols).
-// On exit (workspace): R0 = Q (rows x l), C0 = P (cols x l), sig[:r], and
-// S1 = U_s[:, :r] (x sigma if s1_sigma), S2 = V_s[:, :r] (x sigma if s2_sigma)
-// with X ~ Q U_s diag(sig) V_s^T P^T.
-lramm_status rsvd_core(lramm_plan_s* P, int which, const void* X, void* ws, int s1_sigma,
-                       int s2_sigma, cudaStream_t s) {
+// Range finder, projection and small SVD of one or two operands in lockstep
+// (X rows x cols each).  On exit (workspace, per side): R0 = Q (rows x l),
+// C0 = P (cols x l), sig[:r], S1 = U_s[:, :r] (x sigma if s1_sigma[i]),
+// S2 = V_s[:, :r] (x sigma if s2_sigma[i]), with X ~ Q U_s diag(sig) V_s^T P^T.
+lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, int ns, void* ws,
+                        const int* s1_sigma, const int* s2_sigma, cudaStream_t s) {
   const lramm_desc& d = P->d;
-  const SideLayout& S = P->side[which];
   const int l = P->l;
-  const int64_t ldx = which == 0 ? d.lda : d.ldb;
-  const int xbf = (which == 0 ? d.a_type : d.b_type) == LRAMM_BF16;
   int* st = at<int>(ws, 0);
-  float* Om = at<float>(ws, S.omega);
-  float* R0 = at<float>(ws, S.R0);
-  float* R1 = at<float>(ws, S.R1);
-  float* C0 = at<float>(ws, S.C0);
-  float* C1 = at<float>(ws, S.C1);
-
-  TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, (uint32_t)which, S.cols, l, Om, l, s));
-  TIMED(P, LRAMM_K_SKETCH, s, sgemm(0, 0, S.rows, l, S.cols, 1.f, X, ldx, xbf, Om, l, 0.f, R0, l, s));  // X Omega
-  LRAMM_TRY(orth(P, S, ws, R0, R1, R0, S.rows, false, st, s));                                          // Q
-  for (int it = 0; it < d.q; ++it) {
-    TIMED(P, LRAMM_K_SKETCH, s, sgemm(1, 0, S.cols, l, S.rows, 1.f, X, ldx, xbf, R0, l, 0.f, C0, l, s));  // X^T Q
-    LRAMM_TRY(orth(P, S, ws, C0, C1, C0, S.cols, false, st, s));
-    TIMED(P, LRAMM_K_SKETCH, s, sgemm(0, 0, S.rows, l, S.cols, 1.f, X, ldx, xbf, C0, l, 0.f, R0, l, s));  // X Z^
-    LRAMM_TRY(orth(P, S, ws, R0, R1, R0, S.rows, false, st, s));
+  float *R0[2], *R1[2], *C0[2], *C1[2];
+  int64_t rows[2], cols[2];
+  for (int i = 0; i < ns; ++i) {
+    const SideLayout& S = *sd[i].S;
+    R0[i] = at<float>(ws, S.R0);
+    R1[i] = at<float>(ws, S.R1);
+    C0[i] = at<float>(ws, S.C0);
+    C1[i] = at<float>(ws, S.C1);
+    rows[i] = S.rows;
+    cols[i] = S.cols;
+    float* Om = at<float>(ws, S.omega);
+    TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, (uint32_t)which[i], S.cols, l, Om, l, s));
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s));
   }
-  TIMED(P, LRAMM_K_SKETCH, s, sgemm(1, 0, S.cols, l, S.rows, 1.f, X, ldx, xbf, R0, l, 0.f, C0, l, s));  // B^T = X^T Q
-  LRAMM_TRY(orth(P, S, ws, C0, C1, C0, S.cols, true, st, s));                                            // B^T = P R
-  float* R = at<float>(ws, S.R);
-  float* Vj = at<float>(ws, S.Vj);
+  LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, d.q > 0 ? 1 : 2, false, st, s));  // Q
+  for (int it = 0; it < d.q; ++it) {
+    for (int i = 0; i < ns; ++i)
+      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));
+    LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 1, false, st, s));  // Z^ (span only)
+    for (int i = 0; i < ns; ++i)
+      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, C0[i], R0[i], s));
+    LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, it == d.q - 1 ? 2 : 1, false, st, s));
+  }
+  for (int i = 0; i < ns; ++i)
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));  // B^T
+  LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 2, true, st, s));  // B^T = P R
   // R row-major is R^T column-major: one-sided Jacobi on R^T = U_s S V_s^T.
-  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(R, Vj, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s));
-  TIMED(P, LRAMM_K_SVDSORT, s,
-        launch_svd_finalize(R, Vj, l, d.r, at<float>(ws, S.sig), at<float>(ws, S.S1), s1_sigma,
-                            at<float>(ws, S.S2), s2_sigma, s));
+  JacobiBatch jb{};
+  FinalBatch fb{};
+  jb.n = fb.n = ns;
+  for (int i = 0; i < ns; ++i) {
+    const SideLayout& S = *sd[i].S;
+    jb.M[i] = at<float>(ws, S.R);
+    jb.V[i] = at<float>(ws, S.Vj);
+    fb.p[i] = FinalProb{at<float>(ws, S.R), at<float>(ws, S.Vj), at<float>(ws, S.sig), at<float>(ws, S.S1),
+                        at<float>(ws, S.S2), s1_sigma[i], s2_sigma[i]};
+  }
+  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s));
+  TIMED(P, LRAMM_K_SVDSORT, s, launch_svd_finalize(fb, l, d.r, s));
   return LRAMM_OK;
+}
+
+SideRun side_run(const lramm_plan_s* P, int which, const void* X) {
+  const lramm_desc& d = P->d;
+  return SideRun{X, which == 0 ? d.lda : d.ldb, (which == 0 ? d.a_type : d.b_type) == LRAMM_BF16,
+                 &P->side[which]};
 }
 
 lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const float* Wt,
@@ -361,7 +424,9 @@ lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* 
   const int l = plan->l, r = plan->d.r;
   plan->used = 0;
   LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
-  LRAMM_TRY(rsvd_core(plan, which, X, ws, 0, 0, s));
+  const SideRun sd = side_run(plan, which, X);
+  const int zero[1] = {0};
+  LRAMM_TRY(rsvd_sides(plan, &sd, &which, 1, ws, zero, zero, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
         sgemm(0, 0, Sd.rows, r, l, 1.f, at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, 0.f, U, r, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
@@ -397,14 +462,15 @@ lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const
   float* Zt = at<float>(ws, plan->Zt);
   // A: U~ = Q_A (U_s Sigma) (m x r);  V^T = V_s^T P_A^T (r x k)
   const SideLayout& SA = plan->side[0];
-  LRAMM_TRY(rsvd_core(plan, 0, A, ws, 1, 0, s));
+  const SideLayout& SB = plan->side[1];
+  const SideRun sd[2] = {side_run(plan, 0, A), side_run(plan, 1, B)};
+  const int which[2] = {0, 1}, s1s[2] = {1, 0}, s2s[2] = {0, 1};
+  LRAMM_TRY(rsvd_sides(plan, sd, which, 2, ws, s1s, s2s, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
         sgemm(0, 0, d.m, r, l, 1.f, at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, 0.f, Ut, r, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
         sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SA.S2), r, 0, at<float>(ws, SA.C0), l, 0.f, Vt, d.k, s));
   // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)
-  const SideLayout& SB = plan->side[1];
-  LRAMM_TRY(rsvd_core(plan, 1, B, ws, 0, 1, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
         sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SB.S1), r, 0, at<float>(ws, SB.R0), l, 0.f, Wt, d.k, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
@@ -436,6 +502,29 @@ lramm_status lramm_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int
 }
 
 size_t lramm_quant_ws_bytes(void) { return kAlign; }
+
+size_t lramm_sketch_ws_bytes(int64_t l) {
+  return l < 1 ? 0 : kAlign + sizeof(float) * sketch_tc_part_floats((int)l);
+}
+
+lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t cols, int64_t ldx, int32_t x_type,
+                                  int32_t transpose, const float* B, int64_t l, float* out, int32_t sketch,
+                                  void* ws, size_t ws_bytes, void* stream) {
+  if (rows < 1 || cols < 1 || ldx < cols || l < 1 || l > 4096 || !X || !B || !out) return LRAMM_ERR_INVALID_ARG;
+  if ((x_type != LRAMM_F32 && x_type != LRAMM_BF16) || (transpose != 0 && transpose != 1)) return LRAMM_ERR_INVALID_ARG;
+  if (sketch != LRAMM_SKETCH_F32 && sketch != LRAMM_SKETCH_TF32) return LRAMM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int xbf = x_type == LRAMM_BF16;
+  if (sketch == LRAMM_SKETCH_TF32) {
+    if (!sketch_tc_supported(xbf, ldx, (int)l, X, B)) return LRAMM_ERR_UNSUPPORTED;
+    if (!ws || ws_bytes < lramm_sketch_ws_bytes(l) || reinterpret_cast<uintptr_t>(ws) % kAlign)
+      return LRAMM_ERR_WORKSPACE;
+    return sketch_tc(transpose, X, rows, cols, ldx, xbf, B, (int)l, out, at<float>(ws, kAlign),
+                     sketch_tc_part_floats((int)l), at<int>(ws, 0), s);
+  }
+  if (transpose) return sgemm(1, 0, cols, l, rows, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
+  return sgemm(0, 0, rows, l, cols, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
+}
 
 lramm_status lramm_quantize(const float* X, int64_t rows, int64_t cols, int64_t ldx, int32_t prec,
                             int32_t per_row, void* codes, int64_t ldcodes, float* scales, void* ws,

@@ -85,22 +85,51 @@ lramm_status sgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha,
                    int64_t lda, int a_bf16, const float* B, int64_t ldb, float beta, float* C,
                    int64_t ldc, cudaStream_t s);
 
-// smallla.cu
-// Cholesky of the l x l SPD matrix G (row-major, stride l) with a diagonal
-// shift of shift_rel * max(diag G); writes L (lower, zeros above).
-lramm_status launch_chol(const float* G, int l, float shift_rel, float* L, int* status,
-                         cudaStream_t s);
-// Q = Y L^-T for the rows x l matrix Y (row-major, stride l).
-lramm_status launch_trsm_rows(const float* Y, int64_t rows, int l, const float* L, float* Q,
-                              cudaStream_t s);
-// One-sided Jacobi SVD of M (l x l, stored column-major: column j at M + j*l).
-// On exit M's columns are U_s Sigma (unsorted), V (column-major) the rotations.
-lramm_status launch_jacobi(float* M, float* V, int l, int max_sweeps, int* status, cudaStream_t s);
-// Sort the Jacobi result by descending sigma and write the rank-r pieces:
-//   sig[r]; S1 (l x r, row-major) = U_s[:, :r] (times sigma if s1_sigma);
-//   S2 (l x r, row-major) = V_s[:, :r] (times sigma if s2_sigma).
-lramm_status launch_svd_finalize(const float* M, const float* V, int l, int r, float* sig, float* S1,
-                                 int s1_sigma, float* S2, int s2_sigma, cudaStream_t s);
+// smallla.cu -- small dense linear algebra, batched over up to two problems
+// (the A-side and B-side randomized SVDs run in the same launches).
+struct SmallProb {
+  const float* in;    // chol: G (l x l); trsm: Y (rows x l)
+  float* out;         // chol: L (l x l, lower, zeros above); trsm: Q = Y L^-T
+  const float* aux;   // trsm: L
+  int64_t rows;       // trsm: rows of Y
+};
+struct SmallBatch {
+  SmallProb p[2];
+  int n;
+};
+struct JacobiBatch {
+  float* M[2];  // l x l column-major: in R^T, out U_s Sigma (unsorted columns)
+  float* V[2];  // l x l column-major: out the accumulated rotations V_s
+  int n;
+};
+struct FinalProb {
+  const float* M;
+  const float* V;
+  float* sig;   // r, descending
+  float* S1;    // l x r row-major: U_s[:, :r] (x sigma if s1_sigma)
+  float* S2;    // l x r row-major: V_s[:, :r] (x sigma if s2_sigma)
+  int s1_sigma, s2_sigma;
+};
+struct FinalBatch {
+  FinalProb p[2];
+  int n;
+};
+// Cholesky G + shift_rel * max(diag G) I = L L^T.
+lramm_status launch_chol(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s);
+// Q = Y L^-T.
+lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s);
+// One-sided Jacobi SVD of each M (thread-block cluster per problem).
+lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s);
+// Sort by descending sigma and write the rank-r pieces.
+lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s);
+// Largest l the small-SVD kernels accept.
+int jacobi_max_l();
+
+// sketch_tc.cu -- X B / X^T B on the tensor cores (TF32, FP32 accumulate)
+bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void* B);
+size_t sketch_tc_part_floats(int l);
+lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, int xbf, const float* B,
+                       int l, float* out, float* part, size_t part_floats, int* status, cudaStream_t s);
 
 // quant.cu
 lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,

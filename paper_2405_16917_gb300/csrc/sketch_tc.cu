@@ -1,0 +1,389 @@
+// Products of an operand X with an l-column matrix on the 5th-generation
+// tensor cores (tcgen05, sm_103a), TF32 inputs, FP32 accumulation:
+//   a_mn = 0:  out = X   * B   (X rows x cols read K-major,  M = rows, K = cols)
+//   a_mn = 1:  out = X^T * B   (X read in place MN-major,    M = cols, K = rows)
+// B is K x l row-major (an MN-major operand), out M x l FP32 row-major.
+// These are the sketch, power-iteration and projection products of the
+// randomized range finder (Sec. 2.2, Algorithm 1's B = Q^* A): one pass over
+// X each, so they are bound by HBM bandwidth.
+//
+// One CTA computes a 128-row block of out over a K range: a TMA producer
+// warp streams 128 x 32 tiles of X and 32 x l tiles of B (128-byte swizzled)
+// into a ring of shared-memory stages guarded by mbarriers, one thread of
+// the MMA warp issues tcgen05.mma (M = 128, N <= 256 per instruction, two
+// instructions when l > 256) into a TMEM accumulator, and four epilogue
+// warps read TMEM back (tcgen05.ld) and store FP32 rows.  When the K range
+// is split across CTAs, each writes a partial block and a reduction kernel
+// adds the partials in a fixed order (deterministic results).
+// Every mbarrier wait is bounded; on expiry the kernel latches
+// LRAMM_ERR_TIMEOUT, stops issuing, waits (bounded) for its own copies and
+// MMAs in flight, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace lramm {
+namespace {
+
+constexpr int kBM = 128;               // output rows per CTA = TMEM lanes
+constexpr int kBK = 32;                // K per stage: 32 TF32 = one 128-byte swizzle row
+constexpr int kAtom = 32;              // TF32 elements per 128-byte swizzle atom
+constexpr uint32_t kWaitLimit = 1u << 26;
+constexpr int kThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kMaxStages = 8;
+
+struct TcParams {
+  int64_t M, K;
+  int l, npad, n1, n2;
+  int a_mn;
+  int64_t kblocks;
+  int kb_per_split;
+  int stages;
+  uint32_t a_bytes, b_bytes, tmem_cols;
+  float* out;   // splits x M x l (or M x l when not split)
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false on expiry or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor (sm_100 format: start address, leading /
+// stride byte offsets in 16-byte units, version 1 at bit 46, layout type at
+// bits 61..63).  Two layouts are used:
+//  * K-major operands: 128-byte swizzle (type 2), rows of 32 TF32 along K,
+//    8-row swizzle atoms 1024 bytes apart (SBO); a K step of 8 advances the
+//    start address by 32 bytes inside the swizzled row.
+//  * MN-major TF32 operands: 128-byte swizzle with 32-byte atomicity
+//    (type 1, written by TMA's SWIZZLE_128B_ATOM_32B): K rows of 32 MN
+//    elements, core matrices 4 K rows tall (SBO = 512 bytes), 32-element
+//    MN atoms LBO apart.  (The plain 128-byte swizzle reads as zeros for
+//    32-bit MN-major operands; measured on GB300.)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes, uint32_t layout) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo_bytes >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo_bytes >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(layout) << 61;
+  return d;
+}
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr) { return smem_desc(saddr, 16, 1024, 2); }
+__device__ __forceinline__ uint64_t mnmajor_desc(uint32_t saddr) { return smem_desc(saddr, kAtom * kBK * 4, 512, 1); }
+
+// Instruction descriptor of kind::tf32: D F32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9, 10-12 = 2), A / B major (bits 15, 16: 0 K-major, 1 MN-major),
+// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__device__ __forceinline__ uint32_t idesc_tf32(int M, int N, int a_mn, int b_mn) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(a_mn) << 15) |
+         (static_cast<uint32_t>(b_mn) << 16) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmB, TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + static_cast<size_t>(p.stages) * p.a_bytes;
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kBM;
+  const int split = blockIdx.y;
+  const int64_t kb0 = static_cast<int64_t>(split) * p.kb_per_split;
+  const int64_t kb1 = min(p.kblocks, kb0 + p.kb_per_split);
+  const int nkb = static_cast<int>(kb1 - kb0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tmem_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t tx_bytes = p.a_bytes + p.b_bytes;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (i >= p.stages && !mbar_wait(&empty_bar[s], ((i / p.stages) & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], tx_bytes);
+      const int k0 = static_cast<int>((kb0 + i) * kBK);
+      uint8_t* a_dst = sA + static_cast<size_t>(s) * p.a_bytes;
+      if (p.a_mn) {
+        for (int j = 0; j < kBM / kAtom; ++j)
+          tma_load_2d(a_dst + j * (kAtom * kBK * 4), &tmX, &full_bar[s], static_cast<int>(m0) + j * kAtom, k0);
+      } else {
+        tma_load_2d(a_dst, &tmX, &full_bar[s], k0, static_cast<int>(m0));
+      }
+      uint8_t* b_dst = sB + static_cast<size_t>(s) * p.b_bytes;
+      for (int j = 0; j < p.npad / kAtom; ++j)
+        tma_load_2d(b_dst + j * (kAtom * kBK * 4), &tmB, &full_bar[s], j * kAtom, k0);
+      ++issued;
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      // wait (bounded) for this CTA's copies still in flight
+      const int first = issued > p.stages ? issued - p.stages : 0;
+      for (int i = first; i < issued; ++i) {
+        volatile int zero = 0;
+        mbar_wait(&full_bar[i % p.stages], (i / p.stages) & 1, &zero);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const int n1 = p.n1, n2 = p.n2;
+    const uint32_t id1 = idesc_tf32(kBM, n1, p.a_mn, 1);
+    const uint32_t id2 = n2 ? idesc_tf32(kBM, n2, p.a_mn, 1) : 0u;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(sA + static_cast<size_t>(s) * p.a_bytes);
+      const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * p.b_bytes);
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {  // 8 TF32 (32 bytes) of K per instruction
+        const uint64_t ad = p.a_mn ? mnmajor_desc(a_base + kk * 1024) : kmajor_desc(a_base + kk * 32);
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, ad, mnmajor_desc(b_base + kk * 1024), id1, acc);
+        if (n2) mma_tf32(tmem + n1, ad, mnmajor_desc(b_base + (n1 / kAtom) * (kAtom * kBK * 4) + kk * 1024), id2, acc);
+      }
+      mma_commit(&empty_bar[s]);  // stage free once these MMAs have read it
+    }
+    mma_commit(&tmem_bar);        // accumulator complete (or every issued MMA done, on abort)
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lanes 32q .. 32q+31 are rows m0 + 32q + lane
+    const int q = warp & 3;
+    volatile int zero = 0;  // wait for the MMAs even after an abort: they read shared memory
+    const bool ok = mbar_wait(&tmem_bar, 0, &zero);
+    tc_fence_after();
+    const int64_t row = m0 + q * 32 + lane;
+    float* dst = p.out + (static_cast<int64_t>(split) * p.M + row) * p.l;
+    for (int c0 = 0; c0 < p.l; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+      if (!ok) continue;
+      if (row < p.M) {
+        const int nv = min(32, p.l - c0);  // multiple of 4
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          if (j < nv) *reinterpret_cast<float4*>(dst + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+    }
+    if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// out = sum over splits of part[s] (fixed order), n4 float4 per split.
+__global__ void split_reduce_kernel(const float4* __restrict__ part, int splits, int64_t n4, float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    float4 a = part[i];
+    for (int s = 1; s < splits; ++s) {
+      const float4 b = part[static_cast<int64_t>(s) * n4 + i];
+      a.x += b.x;
+      a.y += b.y;
+      a.z += b.z;
+      a.w += b.w;
+    }
+    out[i] = a;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map_f32(CUtensorMap* map, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes, uint32_t box_in,
+                  uint32_t box_out, CUtensorMapSwizzle swizzle) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {inner, outer};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box_in, box_out};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+constexpr int kSmemBudget = 232448 - 2048;  // opt-in maximum minus alignment slack and static barriers
+
+}  // namespace
+
+bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void* B) {
+  return !xbf && l % 4 == 0 && l >= 4 && l <= 512 && ldx % 4 == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0 &&
+         (reinterpret_cast<uintptr_t>(B) % 16) == 0;
+}
+
+size_t sketch_tc_part_floats(int l) { return static_cast<size_t>(152) * kBM * l; }
+
+lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, int xbf, const float* B,
+                       int l, float* out, float* part, size_t part_floats, int* status, cudaStream_t s) {
+  if (!sketch_tc_supported(xbf, ldx, l, X, B)) return LRAMM_ERR_UNSUPPORTED;
+  const int64_t M = a_mn ? cols : rows, K = a_mn ? rows : cols;
+  if (M <= 0 || K <= 0) return LRAMM_OK;
+  if (M > INT32_MAX || K > INT32_MAX) return LRAMM_ERR_UNSUPPORTED;
+  TcParams p{};
+  p.M = M;
+  p.K = K;
+  p.l = l;
+  p.npad = static_cast<int>(round_up(l, kAtom));
+  p.n1 = l <= 256 ? static_cast<int>(round_up(l, 16)) : 256;
+  p.n2 = l <= 256 ? 0 : static_cast<int>(round_up(l - 256, 16));
+  p.a_mn = a_mn;
+  p.kblocks = ceil_div(K, kBK);
+  p.a_bytes = kBM * kBK * 4;
+  p.b_bytes = static_cast<uint32_t>(p.npad) * kBK * 4;
+  p.stages = static_cast<int>((kSmemBudget - 1024) / (p.a_bytes + p.b_bytes));
+  if (p.stages > kMaxStages) p.stages = kMaxStages;
+  if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
+  uint32_t tc = 32;
+  while (tc < static_cast<uint32_t>(p.n1 + p.n2)) tc <<= 1;
+  p.tmem_cols = tc;
+  p.status = status;
+  const int64_t mtiles = ceil_div(M, kBM);
+  int64_t splits = 152 / mtiles;
+  if (splits > p.kblocks / 4) splits = p.kblocks / 4;
+  if (splits < 1) splits = 1;
+  while (splits > 1 && static_cast<size_t>(splits) * M * l > part_floats) --splits;
+  p.kb_per_split = static_cast<int>(ceil_div(p.kblocks, splits));
+  splits = ceil_div(p.kblocks, p.kb_per_split);
+  p.out = splits > 1 ? part : out;
+
+  CUtensorMap mX, mB;
+  if (!make_map_f32(&mX, X, cols, rows, ldx * 4, kAtom, a_mn ? kBK : kBM,
+                    a_mn ? CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B : CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  if (!make_map_f32(&mB, B, l, K, static_cast<uint64_t>(l) * 4, kAtom, kBK, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
+    return LRAMM_ERR_CUDA;
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(mX, mB, p);
+  LRAMM_TRY(last_launch());
+  if (splits > 1) {
+    const int64_t n4 = M * l / 4;
+    int64_t g = ceil_div(n4, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    split_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
+                                                                  static_cast<int>(splits), n4,
+                                                                  reinterpret_cast<float4*>(out));
+    LRAMM_TRY(last_launch());
+  }
+  return LRAMM_OK;
+}
+
+}  // namespace lramm

@@ -8,6 +8,8 @@
 // All FP32.  Every loop has a fixed trip count; nothing waits on a flag.
 #include <float.h>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace lramm {
@@ -31,9 +33,9 @@ __device__ __forceinline__ float warp_max(float v) {
 // LRAMM_ERR_NUMERIC and is replaced by a tiny positive value so the
 // factorisation (and everything after it) still terminates.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) chol_kernel(const float* __restrict__ G, int l,
-                                                    float shift_rel, float* __restrict__ L,
-                                                    int* status) {
+__global__ void __launch_bounds__(1024) chol_kernel(SmallBatch bt, int l, float shift_rel, int* status) {
+  const float* __restrict__ G = bt.p[blockIdx.x].in;
+  float* __restrict__ L = bt.p[blockIdx.x].out;
   extern __shared__ float P[];
   __shared__ float s_red[32];
   __shared__ float s_piv;
@@ -87,9 +89,11 @@ __global__ void __launch_bounds__(1024) chol_kernel(const float* __restrict__ G,
 // Q = Y L^-T row by row: q_i = (y_i - sum_{j<i} q_j L_ij) / L_ii.
 // One warp per row; L (packed) and a per-warp row buffer in shared memory.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) trsm_rows_kernel(const float* __restrict__ Y, int64_t rows,
-                                                         int l, const float* __restrict__ L,
-                                                         float* __restrict__ Q) {
+__global__ void __launch_bounds__(1024) trsm_rows_kernel(SmallBatch bt, int l) {
+  const float* __restrict__ Y = bt.p[blockIdx.y].in;
+  float* __restrict__ Q = bt.p[blockIdx.y].out;
+  const float* __restrict__ L = bt.p[blockIdx.y].aux;
+  const int64_t rows = bt.p[blockIdx.y].rows;
   extern __shared__ float sm[];
   const int np = l * (l + 1) / 2;
   float* Lp = sm;
@@ -117,90 +121,15 @@ __global__ void __launch_bounds__(1024) trsm_rows_kernel(const float* __restrict
   }
 }
 
-// ---------------------------------------------------------------------------
-// One-sided Jacobi (Hestenes) SVD of an l x l matrix M, column-major.
-// Round-robin (circle) ordering: l-1 rounds of l/2 disjoint column pairs per
-// sweep; a pair (a, b) is rotated when |a.b| > tol sqrt(|a|^2 |b|^2), with
-// the rotation that zeroes the new inner product.  V accumulates the
-// rotations.  Stops after a sweep without rotations or after max_sweeps
-// (then LRAMM_WARN_NOCONV is latched).
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) jacobi_kernel(float* __restrict__ M, float* __restrict__ V,
-                                                      int l, int max_sweeps, float tol, int* status) {
-  __shared__ int s_rot;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int64_t e = tid; e < (int64_t)l * l; e += blockDim.x) V[e] = (e / l == e % l) ? 1.f : 0.f;
-  const int n = (l + 1) & ~1;  // players; player l is a dummy when l is odd
-  const int np = n / 2;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int t = 0; t < n - 1; ++t) {
-      for (int kp = warp; kp < np; kp += nw) {
-        int a, b;
-        if (kp == 0) {
-          a = 0;
-          b = 1 + t % (n - 1);
-        } else {
-          a = 1 + (t + kp) % (n - 1);
-          b = 1 + (t - kp + (n - 1)) % (n - 1);
-        }
-        if (a >= l || b >= l) continue;
-        float* ca = M + (int64_t)a * l;
-        float* cb = M + (int64_t)b * l;
-        float al = 0.f, be = 0.f, ga = 0.f;
-        for (int i = lane; i < l; i += 32) {
-          const float x = ca[i], y = cb[i];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (!(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) continue;
-        const float zeta = (be - al) / (2.0f * ga);
-        float tt;
-        if (fabsf(zeta) > 1e18f)
-          tt = 0.5f / zeta;
-        else
-          tt = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
-        const float c = 1.0f / sqrtf(fmaf(tt, tt, 1.0f));
-        const float s = c * tt;
-        // x' = c x - s y, y' = s x + c y applied as x - s (y + tau x) and
-        // y + s (x - tau y), tau = s / (1 + c): for small angles fl(c) = 1
-        // and the plain form would dilate both columns by 1 + t^2.
-        const float tau = s / (1.0f + c);
-        for (int i = lane; i < l; i += 32) {
-          const float x = ca[i], y = cb[i];
-          ca[i] = x - s * fmaf(tau, x, y);
-          cb[i] = y + s * fmaf(-tau, y, x);
-        }
-        float* va = V + (int64_t)a * l;
-        float* vb = V + (int64_t)b * l;
-        for (int i = lane; i < l; i += 32) {
-          const float x = va[i], y = vb[i];
-          va[i] = x - s * fmaf(tau, x, y);
-          vb[i] = y + s * fmaf(-tau, y, x);
-        }
-        if (lane == 0) s_rot = 1;
-      }
-      __syncthreads();
-    }
-    const int rot = s_rot;
-    __syncthreads();
-    if (!rot) break;
-  }
-  if (sweep >= max_sweeps && tid == 0) set_status(status, LRAMM_WARN_NOCONV);
-}
-
 // Sort columns by descending norm (sigma) and write the rank-r outputs.
-__global__ void __launch_bounds__(1024) svd_finalize_kernel(const float* __restrict__ M,
-                                                            const float* __restrict__ V, int l, int r,
-                                                            float* __restrict__ sig,
-                                                            float* __restrict__ S1, int s1_sigma,
-                                                            float* __restrict__ S2, int s2_sigma) {
+__global__ void __launch_bounds__(1024) svd_finalize_kernel(FinalBatch fb, int l, int r) {
+  const FinalProb& fp = fb.p[blockIdx.x];
+  const float* __restrict__ M = fp.M;
+  const float* __restrict__ V = fp.V;
+  float* __restrict__ sig = fp.sig;
+  float* __restrict__ S1 = fp.S1;
+  float* __restrict__ S2 = fp.S2;
+  const int s1_sigma = fp.s1_sigma, s2_sigma = fp.s2_sigma;
   extern __shared__ float sm[];
   float* nrm = sm;                               // l
   int* pos = reinterpret_cast<int*>(sm + l);     // l
@@ -237,41 +166,286 @@ __global__ void __launch_bounds__(1024) svd_finalize_kernel(const float* __restr
 }
 
 // ---------------------------------------------------------------------------
+// One-sided Jacobi on a thread-block cluster, columns resident in shared
+// memory.  The l columns (padded with zero columns to 2*C*b) form 2C blocks
+// of b columns; CTA c of the cluster holds two of them (a "top" and a
+// "bottom" slot) in three b-column buffers (two in use, one free).  A sweep
+// is 2C-1 block rounds; in each, a CTA rotates every (top, bottom) column
+// pair -- b rounds of b disjoint pairs, one warp per pair, CTA barriers only
+// -- and in the first block round also every pair inside its two blocks.
+// Between block rounds the blocks circulate through distributed shared
+// memory in round-robin (circle) order: the top of CTA 0 stays, every other
+// block moves one place along the ring B0 -> T1 -> T2 ... -> T(C-1) ->
+// B(C-1) -> ... -> B0, so in 2C-1 block rounds every pair of blocks meets
+// once.  A pair (a, b) is rotated when |a.b| > tol |a| |b|; the sweep loop
+// stops after a sweep without rotations anywhere in the cluster, or after
+// max_sweeps (then LRAMM_WARN_NOCONV is latched).  All loops have fixed
+// bounds and every CTA of a cluster takes the same branches.
+// ---------------------------------------------------------------------------
+namespace cg = cooperative_groups;
+
+// Physical buffers (top, bottom, free) of cluster rank `rank` after e moves.
+__device__ __forceinline__ void jc_bufs(int rank, int e, int& t, int& bo, int& f) {
+  if (rank == 0) {
+    t = 0; bo = 1; f = 2;
+    return;
+  }
+  const int m = e % 3;
+  if (m == 0) { t = 0; bo = 1; f = 2; }
+  else if (m == 1) { t = 2; bo = 0; f = 1; }
+  else { t = 1; bo = 2; f = 0; }
+}
+
+// Rotate columns (a, b) (M part at the pointer, V part ls floats further)
+// so that their inner product vanishes; one warp.  Returns whether it did.
+__device__ __forceinline__ bool jc_rotate(float* __restrict__ a, float* __restrict__ b, int l, int ls,
+                                          float tol, int lane) {
+  float al = 0.f, be = 0.f, ga = 0.f;
+  for (int i = lane; i < l; i += 32) {
+    const float x = a[i], y = b[i];
+    al = fmaf(x, x, al);
+    be = fmaf(y, y, be);
+    ga = fmaf(x, y, ga);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (!(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float zeta = (be - al) / (2.0f * ga);
+  const float tt = fabsf(zeta) > 1e18f ? 0.5f / zeta
+                                       : copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+  const float c = 1.0f / sqrtf(fmaf(tt, tt, 1.0f));
+  const float s = c * tt;
+  // x' = c x - s y, y' = s x + c y applied as x - s (y + tau x) and
+  // y + s (x - tau y), tau = s / (1 + c): for small angles fl(c) = 1 and the
+  // plain form would dilate both columns by 1 + t^2.
+  const float tau = s / (1.0f + c);
+  for (int i = lane; i < l; i += 32) {
+    const float x = a[i], y = b[i];
+    a[i] = x - s * fmaf(tau, x, y);
+    b[i] = y + s * fmaf(-tau, y, x);
+  }
+  float* va = a + ls;
+  float* vb = b + ls;
+  for (int i = lane; i < l; i += 32) {
+    const float x = va[i], y = vb[i];
+    va[i] = x - s * fmaf(tau, x, y);
+    vb[i] = y + s * fmaf(-tau, y, x);
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(1024)
+jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float tol, int* status) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int prob = blockIdx.x / C;
+  float* __restrict__ Mg = jb.M[prob];
+  float* __restrict__ Vg = jb.V[prob];
+  extern __shared__ float4 jc_smem4[];
+  float* sm = reinterpret_cast<float*>(jc_smem4);
+  const int64_t bufsz = (int64_t)b * 2 * ls;  // floats per buffer
+  __shared__ int s_flags[16];
+  __shared__ int s_ids[32];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const int nslots = 2 * C;
+
+  if (tid < nslots) s_ids[tid] = tid;
+  // initial blocks: top = block 2 rank (buffer 0), bottom = block 2 rank + 1 (buffer 1)
+  for (int half = 0; half < 2; ++half) {
+    float* buf = sm + half * bufsz;
+    const int blk = 2 * rank + half;
+    for (int j = warp; j < b; j += nw) {
+      const int g = blk * b + j;
+      float* col = buf + (int64_t)j * 2 * ls;
+      for (int i = lane; i < ls; i += 32) {
+        col[i] = (g < l && i < l) ? Mg[(int64_t)g * l + i] : 0.f;
+        col[ls + i] = (g < l && i == g) ? 1.f : 0.f;
+      }
+    }
+  }
+  cluster.sync();
+
+  int e = 0;  // block moves so far
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int br = 0; br < 2 * C - 1; ++br) {
+      int bt_, bb_, bf_;
+      jc_bufs(rank, e, bt_, bb_, bf_);
+      float* topb = sm + bt_ * bufsz;
+      float* botb = sm + bb_ * bufsz;
+      if (br == 0) {  // pairs inside each of the two blocks (circle method on b columns)
+        const int be = b + (b & 1), half = be / 2;
+        for (int t = 0; t < be - 1; ++t) {
+          for (int kp = warp; kp < 2 * half; kp += nw) {
+            float* base = kp < half ? topb : botb;
+            const int k = kp % half;
+            int x, y;
+            if (k == 0) {
+              x = 0;
+              y = 1 + t % (be - 1);
+            } else {
+              x = 1 + (t + k) % (be - 1);
+              y = 1 + (t - k + (be - 1)) % (be - 1);
+            }
+            if (x >= b || y >= b) continue;
+            if (jc_rotate(base + (int64_t)x * 2 * ls, base + (int64_t)y * 2 * ls, l, ls, tol, lane) && lane == 0)
+              s_rot = 1;
+          }
+          __syncthreads();
+        }
+      }
+      for (int j = 0; j < b; ++j) {  // top column i against bottom column (i + j) mod b
+        for (int i = warp; i < b; i += nw) {
+          const int k = (i + j) % b;
+          if (jc_rotate(topb + (int64_t)i * 2 * ls, botb + (int64_t)k * 2 * ls, l, ls, tol, lane) && lane == 0)
+            s_rot = 1;
+        }
+        __syncthreads();
+      }
+      if (C > 1) {
+        cluster.sync();  // every CTA has finished rotating the blocks it is about to hand on
+        // move 1: every CTA but 0 pulls its new top into its free buffer
+        if (rank >= 1) {
+          int st, sb, sf;
+          jc_bufs(rank - 1, e, st, sb, sf);
+          const float4* src =
+              cluster.map_shared_rank(reinterpret_cast<float4*>(sm + (rank == 1 ? sb : st) * bufsz), rank - 1);
+          float4* dst = reinterpret_cast<float4*>(sm + bf_ * bufsz);
+          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        cluster.sync();
+        // move 2: every CTA but the last pulls its new bottom from the next CTA
+        // (the last one's new bottom is its old top, already in place)
+        if (rank <= C - 2) {
+          int st, sb, sf;
+          jc_bufs(rank + 1, e, st, sb, sf);
+          const float4* src = cluster.map_shared_rank(reinterpret_cast<float4*>(sm + sb * bufsz), rank + 1);
+          float4* dst = reinterpret_cast<float4*>(sm + (rank == 0 ? bb_ : bt_) * bufsz);
+          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        if (tid == 0) {  // slot -> block bookkeeping, identical on every CTA
+          int nid[32];
+          nid[0] = s_ids[0];
+          nid[2] = s_ids[1];
+          for (int c = 2; c < C; ++c) nid[2 * c] = s_ids[2 * c - 2];
+          nid[2 * C - 1] = s_ids[2 * C - 2];
+          for (int c = 0; c <= C - 2; ++c) nid[2 * c + 1] = s_ids[2 * c + 3];
+          for (int q = 0; q < nslots; ++q) s_ids[q] = nid[q];
+        }
+        cluster.sync();
+        ++e;
+      }
+    }
+    // did any CTA of the cluster rotate in this sweep?
+    __syncthreads();
+    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rot;
+    cluster.sync();
+    int any = 0;
+    for (int c = 0; c < C; ++c) any |= s_flags[c];
+    cluster.sync();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
+  int bt_, bb_, bf_;
+  jc_bufs(rank, e, bt_, bb_, bf_);
+  for (int half = 0; half < 2; ++half) {
+    const float* buf = sm + (half == 0 ? bt_ : bb_) * bufsz;
+    const int blk = s_ids[2 * rank + half];
+    for (int j = warp; j < b; j += nw) {
+      const int g = blk * b + j;
+      if (g >= l) continue;
+      const float* col = buf + (int64_t)j * 2 * ls;
+      for (int i = lane; i < l; i += 32) {
+        Mg[(int64_t)g * l + i] = col[i];
+        Vg[(int64_t)g * l + i] = col[ls + i];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Opt-in shared memory per block on sm_100-class GPUs (227 KB), minus the
 // static shared memory the kernels declare themselves.
 static const int kSmemMax = 232448 - 1024;
 
-lramm_status launch_chol(const float* G, int l, float shift_rel, float* L, int* status,
-                         cudaStream_t s) {
+lramm_status launch_chol(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s) {
   const size_t smem = sizeof(float) * (size_t)l * (l + 1) / 2;
   if (smem > (size_t)kSmemMax) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  chol_kernel<<<1, 1024, smem, s>>>(G, l, shift_rel, L, status);
+  chol_kernel<<<bt.n, 1024, smem, s>>>(bt, l, shift_rel, status);
   return last_launch();
 }
 
-lramm_status launch_trsm_rows(const float* Y, int64_t rows, int l, const float* L, float* Q,
-                              cudaStream_t s) {
+lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s) {
   const int threads = 1024, nw = threads / 32;
   const size_t smem = sizeof(float) * ((size_t)l * (l + 1) / 2 + l + (size_t)nw * l);
   if (smem > (size_t)kSmemMax) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int64_t rows = 0;
+  for (int i = 0; i < bt.n; ++i) rows = bt.p[i].rows > rows ? bt.p[i].rows : rows;
   int64_t grid = ceil_div(rows, nw);
-  if (grid > 152) grid = 152;
-  trsm_rows_kernel<<<(unsigned)grid, threads, smem, s>>>(Y, rows, l, L, Q);
+  const int64_t cap = (152 + bt.n - 1) / bt.n;
+  if (grid > cap) grid = cap;
+  trsm_rows_kernel<<<dim3((unsigned)grid, bt.n), threads, smem, s>>>(bt, l);
   return last_launch();
 }
 
-lramm_status launch_jacobi(float* M, float* V, int l, int max_sweeps, int* status, cudaStream_t s) {
+// Cluster size C and block width b for l columns: about 32 column pairs per
+// CTA round (b <= 32 keeps one pair per warp), three b-column buffers of
+// M and V per CTA within the shared-memory limit, at most 16 CTAs.
+static bool jacobi_shape(int l, int& C, int& b, int& ls, size_t& smem) {
+  ls = (int)round_up(l, 4);
+  for (C = (int)ceil_div(l, 64); C <= 16; ++C) {
+    if (C < 1) C = 1;
+    b = (int)ceil_div(l, 2 * C);
+    smem = sizeof(float) * 3 * (size_t)b * 2 * ls;
+    if (smem <= (size_t)kSmemMax) return true;
+  }
+  return false;
+}
+
+int jacobi_max_l() {
+  int best = 0;
+  for (int l = 2; l <= 1024; ++l) {
+    int C, b, ls;
+    size_t smem;
+    if (jacobi_shape(l, C, b, ls, smem)) best = l;
+  }
+  return best;
+}
+
+lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s) {
+  int C, b, ls;
+  size_t smem;
+  if (!jacobi_shape(l, C, b, ls, smem)) return LRAMM_ERR_UNSUPPORTED;
   const float tol = 4.0f * sqrtf((float)l) * 0x1p-24f;
-  jacobi_kernel<<<1, 1024, 0, s>>>(M, V, l, max_sweeps, tol, status);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (C > 8)
+    LRAMM_CUDA_TRY(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
+  cfg.blockDim = dim3(1024, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  LRAMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel, jb, l, ls, b, max_sweeps, tol, status));
   return last_launch();
 }
 
-lramm_status launch_svd_finalize(const float* M, const float* V, int l, int r, float* sig, float* S1,
-                                 int s1_sigma, float* S2, int s2_sigma, cudaStream_t s) {
+lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s) {
   const size_t smem = sizeof(float) * 2 * (size_t)l;
-  svd_finalize_kernel<<<1, 1024, smem, s>>>(M, V, l, r, sig, S1, s1_sigma, S2, s2_sigma);
+  svd_finalize_kernel<<<fb.n, 1024, smem, s>>>(fb, l, r);
   return last_launch();
 }
 

@@ -230,6 +230,37 @@ def test_rsvd_matches_oracle(L, m, k, r, p, q, which):
     assert np.abs(V.T @ V - np.eye(r)).max() < tol
 
 
+@pytest.mark.parametrize("m,k,r,p,q", [(900, 800, 200, 16, 1), (1100, 1024, 256, 16, 2)])
+def test_rsvd_wide_sketch_matches_oracle(L, m, k, r, p, q):
+    """l = 216 and 272: the small SVD runs on 4- and 5-CTA clusters."""
+    X = workloads.lowrank(m, k, workloads.spectrum("poly1", min(m, k)), 600 + m).astype(np.float32)
+    plan = L.Plan(m, m, k, r, p, q, seed=7)
+    ws = plan.workspace()
+    U, S, V = (np_(t) for t in L.rsvd(plan, 0, dev(X), ws=ws))
+    assert L.status_read(ws) == 0
+    Uo, so, Vo = oracle.lramm.rsvd(X, r, p, q, 7, 0)
+    assert np.allclose(S, so, rtol=2e-5, atol=2e-6 * so[0])
+    assert oracle.lramm.rel_fro((U * S) @ V.T, (Uo * so) @ Vo.T) < 2e-5
+    tol = 4.0 * np.sqrt(max(m, k) * (r + p)) * 2.0 ** -24
+    assert np.abs(U.T @ U - np.eye(r)).max() < tol
+    assert np.abs(V.T @ V - np.eye(r)).max() < tol
+
+
+def test_rsvd_rank_deficient_sketch(L):
+    """rank(X) = 10 < l = 18: the sketch is rank-deficient, the shifted first
+    CholeskyQR pass still factors it, X is reproduced and the trailing singular
+    values vanish."""
+    m, k, rank, r, p = 300, 200, 10, 12, 6
+    X = workloads.exact_rank(m, k, rank, 77).astype(np.float32)
+    plan = L.Plan(m, m, k, r, p, 1, seed=7)
+    ws = plan.workspace()
+    U, S, V = (np_(t) for t in L.rsvd(plan, 0, dev(X), ws=ws))
+    st = L.status_read(ws)
+    assert st in (0, 7)
+    assert oracle.lramm.rel_fro((U[:, :rank] * S[:rank]) @ V[:, :rank].T, X) < 1e-5
+    assert np.all(S[rank:] < 1e-5 * S[0])
+
+
 # ---------------------------------------------------------------- end to end
 def _e2e(L, name, prec, scale=None, **kw):
     c = workloads.CONFIGS[name]

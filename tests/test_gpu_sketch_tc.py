@@ -1,0 +1,77 @@
+"""Range-finder products on the tcgen05 tensor cores (TF32) through the C ABI.
+
+The operand X and the l-column matrix B enter the MMA as TF32 (10 explicit
+mantissa bits); each product term then carries a relative error of at most
+about 2^-10 (both inputs rounded or truncated), so every entry obeys
+|out - X B| <= 2^-9 (|X| |B|) entrywise, FP32 accumulation error included.
+The FP32 path through the same entry point is checked to 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2405_16917_gb300 as L
+    L.load()
+    return L
+
+
+SHAPES = [(4096, 4096, 272), (700, 520, 64), (130, 1000, 8), (1000, 132, 144), (513, 2052, 400), (256, 256, 256)]
+
+
+@pytest.mark.parametrize("rows,cols,l", SHAPES)
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_sketch_product_tf32(L, rows, cols, l, transpose):
+    rng = np.random.default_rng(rows + 3 * cols + 7 * l + transpose)
+    X = rng.standard_normal((rows, cols)).astype(np.float32)
+    B = rng.standard_normal((rows if transpose else cols, l)).astype(np.float32)
+    out = L.sketch_product(torch.from_numpy(X).cuda(), torch.from_numpy(B).cuda(), transpose=bool(transpose),
+                           sketch=L.SKETCH_TF32).cpu().numpy().astype(np.float64)
+    Xd = X.astype(np.float64).T if transpose else X.astype(np.float64)
+    ref = Xd @ B.astype(np.float64)
+    mag = np.abs(Xd) @ np.abs(B.astype(np.float64))
+    assert np.all(np.abs(out - ref) <= 2.0 ** -9 * mag), np.max(np.abs(out - ref) / mag)
+    assert oracle.lramm.rel_fro(out, ref) < 2e-3
+
+
+@pytest.mark.parametrize("transpose", [0, 1])
+def test_sketch_product_fp32(L, transpose):
+    rng = np.random.default_rng(5 + transpose)
+    X = rng.standard_normal((333, 517)).astype(np.float32)
+    B = rng.standard_normal((333 if transpose else 517, 37)).astype(np.float32)
+    out = L.sketch_product(torch.from_numpy(X).cuda(), torch.from_numpy(B).cuda(), transpose=bool(transpose),
+                           sketch=L.SKETCH_F32).cpu().numpy().astype(np.float64)
+    ref = (X.astype(np.float64).T if transpose else X.astype(np.float64)) @ B.astype(np.float64)
+    assert oracle.lramm.rel_fro(out, ref) < 1e-6
+
+
+def test_sketch_product_tf32_rejects_unaligned_width(L):
+    X = torch.zeros((64, 64), device="cuda")
+    B = torch.zeros((64, 74), device="cuda")
+    with pytest.raises(L.LrammError) as e:
+        L.sketch_product(X, B, sketch=L.SKETCH_TF32)
+    assert e.value.code == 2
+
+
+def test_rsvd_with_tf32_sketch(L):
+    """The whole range finder on tensor-core products: the rank-r
+    approximation stays within a few TF32 roundings of the FP64 oracle."""
+    m, k, r, p, q = 900, 700, 60, 8, 1
+    X = workloads.lowrank(m, k, workloads.spectrum("exp32", min(m, k)), 77).astype(np.float32)
+    plan = L.Plan(m, m, k, r, p, q, seed=7, sketch=L.SKETCH_TF32)
+    ws = plan.workspace()
+    U, S, V = (t.cpu().numpy() for t in L.rsvd(plan, 0, torch.from_numpy(X).cuda(), ws=ws))
+    assert L.status_read(ws) == 0
+    Uo, so, Vo = oracle.lramm.rsvd(X, r, p, q, 7, 0)
+    err = oracle.lramm.rel_fro((U * S) @ V.T, (Uo * so) @ Vo.T)
+    assert err < 4 * 2.0 ** -10, err
