@@ -206,8 +206,10 @@ def run_lramm(args):
     prec = VARIANTS[args.variant]
     A, B = workloads.device_operands(args.workload, dev)
     a_type = L.BF16 if A.dtype == torch.bfloat16 else L.F32
+    sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
+    sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
     plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
-                  timing=True)
+                  sketch=sketch, timing=True)
     ws = plan.workspace(dev)
     D = torch.empty((m, n), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -215,6 +217,7 @@ def run_lramm(args):
 
     for _ in range(max(args.warmup, 0)):
         L.matmul(plan, A, B, out=D, ws=ws)
+    info = L.info_read(ws, 3)
     st = L.status_read(ws)
     if st != 0:
         raise RuntimeError("device status %d after warm-up" % st)
@@ -319,7 +322,13 @@ def run_lramm(args):
     avg_s = dms / dcnt * 1e-3
     nbytes, nflops = kernel_work(dname, cfg, l, args.variant)
     sm_mhz = clk.get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    if dname in ("sketch", "e3", "gram", "trsm", "e1", "e2") and nflops is not None:
+    if dname == "sketch" and sketch_name == "tf32":
+        # tcgen05 products streaming X once: bound by HBM bandwidth
+        roof = {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": peak_src + " hbm_gbs", "traffic": None, "algorithmic_bytes_per_launch": nbytes}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    elif dname in ("sketch", "e3", "gram", "trsm", "e1", "e2") and nflops is not None:
         # these kernels are FP32 SIMT in this version: bound by FP32 FMA issue
         roof = {"bound": "alu", "achieved": nflops / avg_s / 1e12,
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
@@ -351,7 +360,8 @@ def run_lramm(args):
             "vs_baseline": None, "dtype": DTYPES[args.variant], "data": "synthetic",
             "config": {"workload": args.workload, "m": m, "n": n, "k": k, "r": r, "p": p, "q": q,
                        "variant": args.variant, "operands": cfg["dtype"], "spectrum": cfg["spectrum"],
-                       "sketch": "fp32", "scale": "rowcol", "l2": "flushed: 256 MB write before each step",
+                       "sketch": sketch_name, "scale": "rowcol",
+                       "jacobi_sweeps": info[1:3], "l2": "flushed: 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "rel_fro_err_vs_fp64_exact": err,
                        "dense_bf16_gemm": {"tflops": flops / (t_bf16 * 1e-3) / 1e12, "ms": t_bf16,
@@ -386,6 +396,8 @@ def main():
     ap.add_argument("--impl", choices=["lramm", "reference"], default="lramm")
     ap.add_argument("--workload", default="lramm_4096", choices=sorted(workloads.CONFIGS))
     ap.add_argument("--variant", default="int8", choices=sorted(VARIANTS))
+    ap.add_argument("--sketch", choices=["tf32", "fp32"], default=None,
+                    help="products with A and B: tf32 tensor cores (default for quantised variants) or fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

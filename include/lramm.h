@@ -166,6 +166,12 @@ LRAMM_API lramm_status lramm_chain(lramm_plan_t plan, const float* Ut, const flo
  * Returns the first device error latched since the last read, or LRAMM_OK. */
 LRAMM_API lramm_status lramm_status_read(const void* ws, void* stream);
 
+/* Wait for `stream` and copy the first n (1..64) 32-bit words of the
+ * workspace's status area into info (host): info[0] = the status word,
+ * info[1], info[2] = Jacobi sweeps of the A- and B-side SVDs of the last
+ * call.  Nothing is cleared. */
+LRAMM_API lramm_status lramm_info_read(const void* ws, int32_t* info, int32_t n, void* stream);
+
 /* Static description of a status code. */
 LRAMM_API const char* lramm_status_str(lramm_status s);
 

@@ -48,6 +48,7 @@ _SIGS = {
     "lramm_matmul": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "lramm_chain": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "lramm_status_read": (_I32, [_VP, _VP]),
+    "lramm_info_read": (_I32, [_VP, ctypes.POINTER(ctypes.c_int32), _I32, _VP]),
     "lramm_status_str": (ctypes.c_char_p, [_I32]),
     "lramm_last_cuda_error": (ctypes.c_char_p, []),
     "lramm_philox_words": (_I32, [_U64, _U32, _I64, _VP, _VP]),
@@ -216,6 +217,13 @@ def chain(plan, Ut, Vt, Wt, Zt, C=None, out=None, ws=None, stream=None):
     _check(load().lramm_chain(plan.handle, _ptr(Ut), _ptr(Vt), _ptr(Wt), _ptr(Zt), _ptr(C), _ptr(out),
                               _ptr(ws), ws.numel(), _stream(stream)), "lramm_chain")
     return out
+
+
+def info_read(ws, n=3, stream=None):
+    """[status word, Jacobi sweeps A side, Jacobi sweeps B side, ...] of the last call."""
+    buf = (ctypes.c_int32 * n)()
+    _check(load().lramm_info_read(_ptr(ws), buf, n, _stream(stream)), "lramm_info_read")
+    return list(buf)
 
 
 def status_read(ws, stream=None):

@@ -24,7 +24,7 @@ void note_cuda_error(cudaError_t e, const char* where) {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxL = 300;
+constexpr int kMaxL = 320;
 constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of every CholeskyQR pass
 
 struct SideLayout {
@@ -51,7 +51,7 @@ struct lramm_plan_s {
   size_t cV, cW, cE1, cZ, cU, cE2;
   size_t sV, sW, sE1, sZ, sU, sE2;
   size_t amax;
-  size_t part;
+  size_t part, gpart;
   size_t total;
 };
 
@@ -133,6 +133,7 @@ void layout(lramm_plan_s* P) {
   P->sE2 = b.take(sizeof(float) * d.n);
   P->amax = b.take(kAlign);
   P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
+  P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
   P->total = b.off;
 }
 
@@ -210,17 +211,19 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
   for (int pass = 0; pass < passes; ++pass) {
     float* out[2];
     SmallBatch cb{}, tb{};
-    cb.n = tb.n = ns;
+    GramBatch gb{};
+    cb.n = tb.n = gb.n = ns;
     for (int i = 0; i < ns; ++i) {
       float* G = at<float>(ws, sd[i].S->G);
       float* Lf = at<float>(ws, pass == 0 ? sd[i].S->L1 : sd[i].S->L2);
       out[i] = pass == passes - 1 ? dst[i] : tmp[i];
-      TIMED(P, LRAMM_K_GRAM, s, sgemm(1, 0, l, l, rows[i], 1.f, in[i], l, 0, in[i], l, 0.f, G, l, s));
+      gb.p[i] = GramProb{in[i], rows[i], G};
       cb.p[i] = SmallProb{G, Lf, nullptr, 0};
       tb.p[i] = SmallProb{in[i], out[i], Lf, rows[i]};
     }
-    TIMED(P, LRAMM_K_CHOL, s, launch_chol(cb, l, kCholShift, st, s));
-    TIMED(P, LRAMM_K_TRSM, s, launch_trsm_rows(tb, l, s));
+    TIMED(P, LRAMM_K_GRAM, s, launch_gram(gb, l, at<float>(ws, P->gpart), s));
+    TIMED(P, LRAMM_K_CHOL, s, launch_chol2(cb, l, kCholShift, st, s));
+    TIMED(P, LRAMM_K_TRSM, s, launch_trsm_panel(tb, l, s));
     for (int i = 0; i < ns; ++i) in[i] = out[i];
   }
   if (want_R)
@@ -423,7 +426,7 @@ lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* 
   const SideLayout& Sd = plan->side[which];
   const int l = plan->l, r = plan->d.r;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
   const SideRun sd = side_run(plan, which, X);
   const int zero[1] = {0};
   LRAMM_TRY(rsvd_sides(plan, &sd, &which, 1, ws, zero, zero, s));
@@ -442,7 +445,7 @@ lramm_status lramm_chain(lramm_plan_t plan, const float* Ut, const float* Vt, co
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
   return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
 }
 
@@ -455,7 +458,7 @@ lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const
   const lramm_desc& d = plan->d;
   const int l = plan->l, r = d.r;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
   float* Ut = at<float>(ws, plan->Ut);
   float* Vt = at<float>(ws, plan->Vt);
   float* Wt = at<float>(ws, plan->Wt);
@@ -476,6 +479,14 @@ lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
         sgemm(0, 0, d.n, r, l, 1.f, at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, 0.f, Zt, r, s));
   return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
+}
+
+lramm_status lramm_info_read(const void* ws, int32_t* info, int32_t n, void* stream) {
+  if (!ws || !info || n < 1 || n > 64) return LRAMM_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LRAMM_CUDA_TRY(cudaMemcpyAsync(info, ws, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  LRAMM_CUDA_TRY(cudaStreamSynchronize(s));
+  return LRAMM_OK;
 }
 
 lramm_status lramm_status_read(const void* ws, void* stream) {

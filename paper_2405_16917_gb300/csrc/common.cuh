@@ -122,6 +122,20 @@ lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s);
 lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s);
 // Sort by descending sigma and write the rank-r pieces.
 lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s);
+// orth.cu -- CholeskyQR building blocks, batched over up to two problems.
+struct GramProb {
+  const float* Y;   // rows x l, stride l
+  int64_t rows;
+  float* G;         // l x l
+};
+struct GramBatch {
+  GramProb p[2];
+  int n;
+};
+size_t gram_part_floats(int l);
+lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s);
+lramm_status launch_chol2(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s);
+lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s);
 // Largest l the small-SVD kernels accept.
 int jacobi_max_l();
 
