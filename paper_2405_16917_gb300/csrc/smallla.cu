@@ -370,6 +370,253 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
 }
 
 // ---------------------------------------------------------------------------
+// The same one-sided Jacobi schedule on a cluster of up to 16 CTAs with two
+// warps per column pair: C = min(16, ceil(l/16)) CTAs, blocks of b <= 10
+// columns, 64 b threads per CTA.  Thread p of pair group g owns rows
+// p, p + 64, ... (RP of them) of both columns of its pair; the three inner
+// products are reduced by warp shuffles and summed over the group's two
+// warps through shared memory behind a 64-thread named barrier (the same
+// order in every thread, so the whole group takes identical decisions).
+// During a block round group g keeps top column g in registers and meets
+// bottom column (g + j) mod b in round j.  Rotation formulas, threshold,
+// round-robin order and stopping rule are those of jacobi_cluster_kernel.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
+}
+
+template <int RP>
+__device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], float (&ym)[RP], float (&yv)[RP],
+                                           float tol, int grp, int wig, int lane, float (*s_part)[2][4]) {
+  float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+  for (int u = 0; u < RP; ++u) {
+    al = fmaf(xm[u], xm[u], al);
+    be = fmaf(ym[u], ym[u], be);
+    ga = fmaf(xm[u], ym[u], ga);
+  }
+  al = warp_sum(al);
+  be = warp_sum(be);
+  ga = warp_sum(ga);
+  if (lane == 0) {
+    s_part[grp][wig][0] = al;
+    s_part[grp][wig][1] = be;
+    s_part[grp][wig][2] = ga;
+  }
+  group_bar(1 + grp);
+  al = s_part[grp][0][0] + s_part[grp][1][0];
+  be = s_part[grp][0][1] + s_part[grp][1][1];
+  ga = s_part[grp][0][2] + s_part[grp][1][2];
+  if (!(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float zeta = (be - al) / (2.0f * ga);
+  const float tt = fabsf(zeta) > 1e18f ? 0.5f / zeta
+                                       : copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+  const float c = 1.0f / sqrtf(fmaf(tt, tt, 1.0f));
+  const float s = c * tt;
+  const float tau = s / (1.0f + c);
+#pragma unroll
+  for (int u = 0; u < RP; ++u) {
+    const float x = xm[u], y = ym[u];
+    xm[u] = x - s * fmaf(tau, x, y);
+    ym[u] = y + s * fmaf(-tau, y, x);
+    const float vx = xv[u], vy = yv[u];
+    xv[u] = vx - s * fmaf(tau, vx, vy);
+    yv[u] = vy + s * fmaf(-tau, vy, vx);
+  }
+  return true;
+}
+
+template <int RP>
+__device__ __forceinline__ void jc2_load(const float* __restrict__ col, int ls, int l, int p, float (&m)[RP],
+                                         float (&v)[RP]) {
+#pragma unroll
+  for (int u = 0; u < RP; ++u) {
+    const int i = p + 64 * u;
+    m[u] = i < l ? col[i] : 0.f;
+    v[u] = i < l ? col[ls + i] : 0.f;
+  }
+}
+
+template <int RP>
+__device__ __forceinline__ void jc2_store(float* __restrict__ col, int ls, int l, int p, const float (&m)[RP],
+                                          const float (&v)[RP]) {
+#pragma unroll
+  for (int u = 0; u < RP; ++u) {
+    const int i = p + 64 * u;
+    if (i < l) {
+      col[i] = m[u];
+      col[ls + i] = v[u];
+    }
+  }
+}
+
+template <int RP>
+__global__ void __launch_bounds__(640)
+jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float tol, int* status) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int prob = blockIdx.x / C;
+  float* __restrict__ Mg = jb.M[prob];
+  float* __restrict__ Vg = jb.V[prob];
+  extern __shared__ float4 jc2_smem4[];
+  float* sm = reinterpret_cast<float*>(jc2_smem4);
+  const int cs = 2 * ls;                      // floats per column: M part, then V part
+  const int64_t bufsz = (int64_t)b * cs;      // floats per b-column buffer
+  __shared__ float s_part[16][2][4];
+  __shared__ int s_flags[16];
+  __shared__ int s_ids[32];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = warp >> 1, wig = warp & 1, p = tid & 63;
+  const int nslots = 2 * C;
+
+  if (tid < nslots) s_ids[tid] = tid;
+  for (int half = 0; half < 2; ++half) {
+    float* buf = sm + half * bufsz;
+    const int blk = 2 * rank + half;
+    for (int64_t e = tid; e < bufsz; e += blockDim.x) {
+      const int j = (int)(e / cs), i = (int)(e - (int64_t)j * cs);
+      const int g = blk * b + j;
+      float v = 0.f;
+      if (g < l) {
+        if (i < l) v = Mg[(int64_t)g * l + i];
+        else if (i >= ls && i - ls < l) v = (i - ls == g) ? 1.f : 0.f;
+      }
+      buf[e] = v;
+    }
+  }
+  cluster.sync();
+
+  const int be = b + (b & 1), half = be / 2, nreal = b / 2;
+  int e = 0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    for (int br = 0; br < 2 * C - 1; ++br) {
+      int bt_, bb_, bf_;
+      jc_bufs(rank, e, bt_, bb_, bf_);
+      float* topb = sm + bt_ * bufsz;
+      float* botb = sm + bb_ * bufsz;
+      if (br == 0) {  // pairs inside each block, circle method on b (+1 dummy) columns
+        for (int t = 0; t < be - 1; ++t) {
+          if (grp < 2 * nreal) {
+            float* base = grp < nreal ? topb : botb;
+            int q = grp < nreal ? grp : grp - nreal;
+            int x = 0, y = 0;
+            for (int k = 0; k < half; ++k) {
+              int xx, yy;
+              if (k == 0) {
+                xx = 0;
+                yy = 1 + t % (be - 1);
+              } else {
+                xx = 1 + (t + k) % (be - 1);
+                yy = 1 + (t - k + (be - 1)) % (be - 1);
+              }
+              if (xx >= b || yy >= b) continue;
+              if (q == 0) {
+                x = xx;
+                y = yy;
+              }
+              --q;
+            }
+            float xm[RP], xv[RP], ym[RP], yv[RP];
+            float* cx = base + (int64_t)x * cs;
+            float* cy = base + (int64_t)y * cs;
+            jc2_load<RP>(cx, ls, l, p, xm, xv);
+            jc2_load<RP>(cy, ls, l, p, ym, yv);
+            if (jc2_rotate<RP>(xm, xv, ym, yv, tol, grp, wig, lane, s_part)) {
+              jc2_store<RP>(cx, ls, l, p, xm, xv);
+              jc2_store<RP>(cy, ls, l, p, ym, yv);
+              if (p == 0) s_rot = 1;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      {  // top column grp against bottom column (grp + j) mod b, top held in registers
+        float tm[RP], tv[RP];
+        float* tcol = topb + (int64_t)grp * cs;
+        jc2_load<RP>(tcol, ls, l, p, tm, tv);
+        bool trot = false;
+        for (int j = 0; j < b; ++j) {
+          int k = grp + j;
+          if (k >= b) k -= b;
+          float* bcol = botb + (int64_t)k * cs;
+          float bm[RP], bv[RP];
+          jc2_load<RP>(bcol, ls, l, p, bm, bv);
+          if (jc2_rotate<RP>(tm, tv, bm, bv, tol, grp, wig, lane, s_part)) {
+            jc2_store<RP>(bcol, ls, l, p, bm, bv);
+            trot = true;
+          }
+          __syncthreads();
+        }
+        if (trot) {
+          jc2_store<RP>(tcol, ls, l, p, tm, tv);
+          if (p == 0) s_rot = 1;
+        }
+      }
+      if (C > 1) {
+        cluster.sync();
+        if (rank >= 1) {
+          int st, sb, sf;
+          jc_bufs(rank - 1, e, st, sb, sf);
+          const float4* src =
+              cluster.map_shared_rank(reinterpret_cast<float4*>(sm + (rank == 1 ? sb : st) * bufsz), rank - 1);
+          float4* dst = reinterpret_cast<float4*>(sm + bf_ * bufsz);
+          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        cluster.sync();
+        if (rank <= C - 2) {
+          int st, sb, sf;
+          jc_bufs(rank + 1, e, st, sb, sf);
+          const float4* src = cluster.map_shared_rank(reinterpret_cast<float4*>(sm + sb * bufsz), rank + 1);
+          float4* dst = reinterpret_cast<float4*>(sm + (rank == 0 ? bb_ : bt_) * bufsz);
+          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        if (tid == 0) {
+          int nid[32];
+          nid[0] = s_ids[0];
+          nid[2] = s_ids[1];
+          for (int c = 2; c < C; ++c) nid[2 * c] = s_ids[2 * c - 2];
+          nid[2 * C - 1] = s_ids[2 * C - 2];
+          for (int c = 0; c <= C - 2; ++c) nid[2 * c + 1] = s_ids[2 * c + 3];
+          for (int q = 0; q < nslots; ++q) s_ids[q] = nid[q];
+        }
+        cluster.sync();
+        ++e;
+      } else {
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rot;
+    cluster.sync();
+    int any = 0;
+    for (int c = 0; c < C; ++c) any |= s_flags[c];
+    cluster.sync();
+    if (!any) break;
+  }
+  if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
+  if (tid == 0 && rank == 0 && status) status[1 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
+  int bt_, bb_, bf_;
+  jc_bufs(rank, e, bt_, bb_, bf_);
+  for (int hf = 0; hf < 2; ++hf) {
+    const float* buf = sm + (hf == 0 ? bt_ : bb_) * bufsz;
+    const int blk = s_ids[2 * rank + hf];
+    for (int64_t q = tid; q < (int64_t)b * l; q += blockDim.x) {
+      const int j = (int)(q / l), i = (int)(q - (int64_t)j * l);
+      const int g = blk * b + j;
+      if (g >= l) continue;
+      const float* col = buf + (int64_t)j * cs;
+      Mg[(int64_t)g * l + i] = col[i];
+      Vg[(int64_t)g * l + i] = col[ls + i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Opt-in shared memory per block on sm_100-class GPUs (227 KB), minus the
 // static shared memory the kernels declare themselves.
 static const int kSmemMax = 232448 - 1024;
@@ -420,7 +667,62 @@ int jacobi_max_l() {
   return best;
 }
 
+static bool jacobi2_shape(int l, int& C, int& b, int& ls, int& rp, size_t& smem) {
+  ls = (int)round_up(l, 4);
+  C = (int)ceil_div(l, 16);
+  if (C < 1) C = 1;
+  if (C > 16) C = 16;
+  b = (int)ceil_div(l, 2 * C);
+  rp = (int)ceil_div(l, 64);
+  smem = sizeof(float) * 3 * (size_t)b * 2 * ls;
+  return b <= 10 && rp <= 5 && smem <= (size_t)kSmemMax;  // 64 b <= 640 threads
+}
+
+template <int RP>
+static lramm_status launch_jacobi2_rp(JacobiBatch jb, int l, int ls, int C, int b, size_t smem, int max_sweeps,
+                                      float tol, int* status, cudaStream_t s, bool& launched) {
+  launched = false;
+  auto kern = jacobi_pair2_kernel<RP>;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (C > 8) LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
+  cfg.blockDim = dim3((unsigned)(64 * b), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  LRAMM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg));
+  if (nclusters < 1) return LRAMM_OK;  // this cluster shape does not fit: caller falls back
+  LRAMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jb, l, ls, b, max_sweeps, tol, status));
+  launched = true;
+  return last_launch();
+}
+
 lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s) {
+  {
+    int C2, b2, ls2, rp;
+    size_t smem2;
+    if (jacobi2_shape(l, C2, b2, ls2, rp, smem2)) {
+      const float tol2 = 4.0f * sqrtf((float)l) * 0x1p-24f;
+      bool done = false;
+      lramm_status st2 = LRAMM_OK;
+      switch (rp) {
+        case 1: st2 = launch_jacobi2_rp<1>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
+        case 2: st2 = launch_jacobi2_rp<2>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
+        case 3: st2 = launch_jacobi2_rp<3>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
+        case 4: st2 = launch_jacobi2_rp<4>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
+        default: st2 = launch_jacobi2_rp<5>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
+      }
+      if (st2 != LRAMM_OK || done) return st2;
+    }
+  }
   int C, b, ls;
   size_t smem;
   if (!jacobi_shape(l, C, b, ls, smem)) return LRAMM_ERR_UNSUPPORTED;
