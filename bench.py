@@ -124,6 +124,14 @@ def kernel_work(kind, cfg, l, variant):
     return (None, None)
 
 
+def jacobi_work(l, sweeps):
+    """Algorithmic FP32 flops of one launch of the one-sided Jacobi SVD (both
+    operands): per sweep every one of the l(l-1)/2 column pairs forms three
+    inner products of length l (6 l flops) and rotates its two columns of M
+    and of V (4 vectors x 3 l flops) -- 18 l flops per pair."""
+    return sum(s * l * (l - 1) / 2 * 18.0 * l for s in sweeps)
+
+
 def fp32_alu_peak_tflops(sm_mhz):
     """152 SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -337,10 +345,33 @@ def run_lramm(args):
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = None
         roof["algorithmic_bytes_per_launch"] = nbytes
+    elif dname == "svd":
+        # latency-bound: l sequential rounds per sweep; reported against the FP32 ALU roof
+        jf = jacobi_work(l, [int(x) for x in info[1:3] if int(x) > 0])
+        roof = {"bound": "alu", "achieved": jf / avg_s / 1e12,
+                "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
+                "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz", "traffic": None,
+                "algorithmic_flops_per_launch": jf,
+                "note": "one-sided Jacobi, sequential rounds of column-pair rotations on 2 x 16-CTA clusters"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                 "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
                 "note": "latency-bound small factorisation; no algorithmic roof"}
+    # the bandwidth-bound kernels, each against its own roof (same definitions)
+    kroofs = {}
+    for kn in ("sketch", "e3"):
+        if kn not in kinds:
+            continue
+        kms, kc = kinds[kn]
+        ks = kms / kc * 1e-3
+        kb, kf = kernel_work(kn, cfg, l, args.variant)
+        if kn == "sketch" and sketch_name != "tf32":
+            continue
+        kroofs[kn] = {"bound": "hbm", "achieved": kb / ks / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": kb / ks / 1e9 / pk["hbm_gbs"], "avg_launch_ms": ks * 1e3,
+                      "launches_per_step": kc / args.steps, "algorithmic_bytes_per_launch": kb}
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -372,6 +403,7 @@ def run_lramm(args):
             "breakdown_ms_per_step": {kn: round(v[0] / args.steps, 4) for kn, v in
                                       sorted(kinds.items(), key=lambda kv: -kv[1][0])},
             "roofline": roof,
+            "kernel_rooflines": kroofs,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": A.numel() * A.element_size() + B.numel() * B.element_size(),

@@ -230,6 +230,28 @@ LRAMM_API lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int
                          const float* C, int64_t ldc, void* D, int64_t ldd,
                          int32_t out_kind, void* stream);
 
+/* The INT8 QM product of Algorithm 2 on the tensor cores (tcgen05.mma
+ * kind::f16; the INT8 codes lramm_quantize writes as bfloat16 values are
+ * exact BF16 operands):
+ *   acc(i,j) = sum_t L(i,t) Rt(j,t), L M x K (stride ldl), Rt N x K (stride ldr),
+ *   summed exactly (each CTA adds at most 1024 products in FP32, where every
+ *   partial sum is an exact integer; longer K is split across CTAs and the
+ *   partials are added as 32-bit integers), then
+ *   D(i,j) = alpha * fp32( fp32(acc) * fp32(sL[i or 0] * sR[j or 0]) ) + beta * C(i,j)
+ * (FP32, stride ldd), as lramm_qgemm with out_kind 0.  per_row as in
+ * lramm_qgemm.  K a multiple of 16; L and Rt 16-byte aligned with ldl, ldr
+ * multiples of 8 (else LRAMM_ERR_UNSUPPORTED).  ws: device buffer of
+ * lramm_qgemm_tc_ws_bytes(M, N, K) bytes, 256-byte aligned (first word: the
+ * status word, LRAMM_ERR_TIMEOUT if a bounded wait expired; then the
+ * split-K partials).  Asynchronous on `stream`. */
+LRAMM_API lramm_status lramm_qgemm_tc(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K,
+                                      int64_t ldl, int64_t ldr, int32_t per_row, const float* sL,
+                                      const float* sR, float alpha, float beta, const float* C, int64_t ldc,
+                                      float* D, int64_t ldd, void* ws, size_t ws_bytes, void* stream);
+
+/* Bytes of workspace lramm_qgemm_tc needs for an M x N x K product. */
+LRAMM_API size_t lramm_qgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K);
+
 /* The products of an operand with an l-column matrix that the range finder
  * runs (Sec. 2.2 sketch Y = X Omega, the power-iteration products, and the
  * projection B^T = X^T Q of Algorithm 1):

@@ -56,6 +56,9 @@ _SIGS = {
     "lramm_quantize": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _VP, _VP]),
     "lramm_qgemm": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _VP, _VP, _F, _F,
                            _VP, _I64, _VP, _I64, _I32, _VP]),
+    "lramm_qgemm_tc": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _VP, _VP, _F, _F, _VP, _I64, _VP, _I64,
+                              _VP, ctypes.c_size_t, _VP]),
+    "lramm_qgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
     "lramm_sketch_product": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _I32, _VP, ctypes.c_size_t,
                                     _VP]),
@@ -300,6 +303,22 @@ def quantize_noalloc(X, prec, per_row=False, ldcodes=None, codes=None, scales=No
     _check(load().lramm_quantize_noalloc(_ptr(X), rows, cols, X.stride(0), prec, int(per_row), _ptr(codes),
                                          ldc, _ptr(scales), _stream()), "lramm_quantize_noalloc")
     return codes, scales
+
+
+def qgemm_tc(Lc, Rc, sL, sR, per_row=True, alpha=1.0, beta=0.0, C=None, ws=None):
+    """INT8 QM product on the tensor cores (codes as lramm_quantize writes them, K-major)."""
+    torch = _torch()
+    _need_cuda(Lc, Rc, C)
+    M, K = Lc.shape
+    N = Rc.shape[0]
+    out = torch.empty((M, N), dtype=torch.float32, device=Lc.device)
+    need = load().lramm_qgemm_tc_ws_bytes(M, N, K)
+    if ws is None or ws.numel() < need:
+        ws = torch.zeros(need, dtype=torch.uint8, device=Lc.device)
+    _check(load().lramm_qgemm_tc(_ptr(Lc), _ptr(Rc), M, N, K, Lc.stride(0), Rc.stride(0), int(per_row),
+                                 _ptr(sL), _ptr(sR), alpha, beta, _ptr(C), C.stride(0) if C is not None else 0,
+                                 _ptr(out), N, _ptr(ws), ws.numel(), _stream()), "lramm_qgemm_tc")
+    return out
 
 
 def qgemm(Lc, Rc, prec, sL=None, sR=None, per_row=True, alpha=1.0, beta=0.0, C=None, raw=False):

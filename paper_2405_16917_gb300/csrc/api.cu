@@ -10,6 +10,8 @@
 #include <new>
 #include <vector>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 using namespace lramm;
@@ -29,7 +31,7 @@ constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of eve
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, R, Vj, sig, S1, S2;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2;
 };
 
 }  // namespace
@@ -51,7 +53,8 @@ struct lramm_plan_s {
   size_t cV, cW, cE1, cZ, cU, cE2;
   size_t sV, sW, sE1, sZ, sU, sE2;
   size_t amax;
-  size_t part, gpart;
+  size_t part, gpart, qpart;
+  size_t qpart_floats;
   size_t total;
 };
 
@@ -104,6 +107,7 @@ void layout(lramm_plan_s* P) {
     S.G = b.take(sizeof(float) * l * l);
     S.L1 = b.take(sizeof(float) * l * l);
     S.L2 = b.take(sizeof(float) * l * l);
+    S.Xd = b.take(sizeof(float) * ceil_div(l, 32) * 32 * 32);
     S.R = b.take(sizeof(float) * l * l);
     S.Vj = b.take(sizeof(float) * l * l);
     S.sig = b.take(sizeof(float) * l);
@@ -134,6 +138,13 @@ void layout(lramm_plan_s* P) {
   P->amax = b.take(kAlign);
   P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
   P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
+  {  // split-K partials of the tensor-core code products (E1 with long K)
+    size_t q = qgemm_tc_part_floats(r, r, P->kp);
+    q = std::max(q, qgemm_tc_part_floats(d.n, r, P->rp));
+    q = std::max(q, qgemm_tc_part_floats(d.m, d.n, P->rp));
+    P->qpart_floats = q;
+    P->qpart = b.take(sizeof(float) * (q > 0 ? q : 4));
+  }
   P->total = b.off;
 }
 
@@ -211,19 +222,29 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
   for (int pass = 0; pass < passes; ++pass) {
     float* out[2];
     SmallBatch cb{}, tb{};
+    CholBatch cb3{};
+    TrsmBatch tb3{};
     GramBatch gb{};
-    cb.n = tb.n = gb.n = ns;
+    cb.n = tb.n = gb.n = cb3.n = tb3.n = ns;
     for (int i = 0; i < ns; ++i) {
       float* G = at<float>(ws, sd[i].S->G);
       float* Lf = at<float>(ws, pass == 0 ? sd[i].S->L1 : sd[i].S->L2);
+      float* Xd = at<float>(ws, sd[i].S->Xd);
       out[i] = pass == passes - 1 ? dst[i] : tmp[i];
       gb.p[i] = GramProb{in[i], rows[i], G};
       cb.p[i] = SmallProb{G, Lf, nullptr, 0};
       tb.p[i] = SmallProb{in[i], out[i], Lf, rows[i]};
+      cb3.p[i] = CholProb{G, Lf, Xd};
+      tb3.p[i] = TrsmProb{in[i], out[i], Lf, Xd, rows[i]};
     }
     TIMED(P, LRAMM_K_GRAM, s, launch_gram(gb, l, at<float>(ws, P->gpart), s));
-    TIMED(P, LRAMM_K_CHOL, s, launch_chol2(cb, l, kCholShift, st, s));
-    TIMED(P, LRAMM_K_TRSM, s, launch_trsm_panel(tb, l, s));
+    if (chol3_supported(l) && l % 4 == 0) {  // blocked Cholesky + panel solve with inverted diagonal blocks
+      TIMED(P, LRAMM_K_CHOL, s, launch_chol3(cb3, l, kCholShift, st, s));
+      TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
+    } else {
+      TIMED(P, LRAMM_K_CHOL, s, launch_chol2(cb, l, kCholShift, st, s));
+      TIMED(P, LRAMM_K_TRSM, s, launch_trsm_panel(tb, l, s));
+    }
     for (int i = 0; i < ns; ++i) in[i] = out[i];
   }
   if (want_R)
@@ -296,6 +317,17 @@ SideRun side_run(const lramm_plan_s* P, int which, const void* X) {
                  &P->side[which]};
 }
 
+// One QM product on codes: the tensor-core kernel for INT8 codes (exact
+// integer sums, fused dequantisation), the SIMT kernel otherwise.
+lramm_status qm_product(lramm_plan_s* P, void* ws, const void* L, const void* R, int64_t M, int64_t N, int64_t K,
+                        int64_t ldl, int64_t ldr, int prec, int per_row, const float* sL, const float* sR, float alpha,
+                        float beta, const float* C, int64_t ldc, float* D, int64_t ldd, cudaStream_t s) {
+  if (qgemm_tc_supported(prec, L, R, ldl, ldr, M, N, K))
+    return qgemm_tc(L, R, M, N, K, ldl, ldr, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, at<float>(ws, P->qpart),
+                    P->qpart_floats, at<int>(ws, 0), s);
+  return qgemm(L, R, M, N, K, ldl, ldr, prec, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, 0, s);
+}
+
 lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const float* Wt,
                         const float* Zt, const float* C, float* D, void* ws, cudaStream_t s) {
   const lramm_desc& d = P->d;
@@ -312,8 +344,8 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
     void* cW = at<void>(ws, P->cW);
     TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Vt, r, d.k, d.k, d.prec[0], per_row, cV, kp, at<float>(ws, P->sV), am, s));
     TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Wt, r, d.k, d.k, d.prec[0], per_row, cW, kp, at<float>(ws, P->sW), am, s));
-    TIMED(P, LRAMM_K_E1, s, qgemm(cV, cW, r, r, kp, kp, kp, d.prec[0], per_row, at<float>(ws, P->sV),
-                                  at<float>(ws, P->sW), 1.f, 0.f, nullptr, 0, E1, r, 0, s));
+    TIMED(P, LRAMM_K_E1, s, qm_product(P, ws, cV, cW, r, r, kp, kp, kp, d.prec[0], per_row, at<float>(ws, P->sV),
+                                       at<float>(ws, P->sW), 1.f, 0.f, nullptr, 0, E1, r, s));
   }
   // E2 = QM(E1 Z~, d2), computed transposed: E2^T = Z~^T E1^T (n x r, K = r)
   if (d.prec[1] == LRAMM_P_F32) {
@@ -323,8 +355,8 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
     void* cE1 = at<void>(ws, P->cE1);
     TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Zt, d.n, r, r, d.prec[1], per_row, cZ, rp, at<float>(ws, P->sZ), am, s));
     TIMED(P, LRAMM_K_QUANT, s, quantize_rows(E1, r, r, r, d.prec[1], per_row, cE1, rp, at<float>(ws, P->sE1), am, s));
-    TIMED(P, LRAMM_K_E2, s, qgemm(cZ, cE1, d.n, r, rp, rp, rp, d.prec[1], per_row, at<float>(ws, P->sZ),
-                                  at<float>(ws, P->sE1), 1.f, 0.f, nullptr, 0, E2t, r, 0, s));
+    TIMED(P, LRAMM_K_E2, s, qm_product(P, ws, cZ, cE1, d.n, r, rp, rp, rp, d.prec[1], per_row, at<float>(ws, P->sZ),
+                                       at<float>(ws, P->sE1), 1.f, 0.f, nullptr, 0, E2t, r, s));
   }
   // E3 = QM(U~ E2, d3); D = alpha E3 + beta C  (m x n, K = r)
   const float beta = d.beta;
@@ -339,8 +371,8 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
     void* cE2 = at<void>(ws, P->cE2);
     TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Ut, d.m, r, r, d.prec[2], per_row, cU, rp, at<float>(ws, P->sU), am, s));
     TIMED(P, LRAMM_K_QUANT, s, quantize_rows(E2t, d.n, r, r, d.prec[2], per_row, cE2, rp, at<float>(ws, P->sE2), am, s));
-    TIMED(P, LRAMM_K_E3, s, qgemm(cU, cE2, d.m, d.n, rp, rp, rp, d.prec[2], per_row, at<float>(ws, P->sU),
-                                  at<float>(ws, P->sE2), d.alpha, beta, C, d.ldc, D, d.ldc, 0, s));
+    TIMED(P, LRAMM_K_E3, s, qm_product(P, ws, cU, cE2, d.m, d.n, rp, rp, rp, d.prec[2], per_row, at<float>(ws, P->sU),
+                                       at<float>(ws, P->sE2), d.alpha, beta, C, d.ldc, D, d.ldc, s));
   }
   return LRAMM_OK;
 }
@@ -571,6 +603,29 @@ lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, in
   if (out_kind == 0 && (!sL || !sR || (beta != 0.f && (!C || ldc < N)))) return LRAMM_ERR_INVALID_ARG;
   return qgemm(L, Rt, M, N, K, ldl, ldr, prec, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, out_kind,
                static_cast<cudaStream_t>(stream));
+}
+
+size_t lramm_qgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0) return kAlign;
+  return kAlign + sizeof(float) * qgemm_tc_part_floats(M, N, K);
+}
+
+lramm_status lramm_qgemm_tc(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                            int64_t ldr, int32_t per_row, const float* sL, const float* sR, float alpha, float beta,
+                            const float* C, int64_t ldc, float* D, int64_t ldd, void* ws, size_t ws_bytes,
+                            void* stream) {
+  if (M < 0 || N < 0 || K < 0 || K % 16 || ldl < K || ldr < K || ldd < N) return LRAMM_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return LRAMM_OK;
+  if (!L || !Rt || !D || !sL || !sR || (beta != 0.f && (!C || ldc < N))) return LRAMM_ERR_INVALID_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) || ws_bytes < lramm_qgemm_tc_ws_bytes(M, N, K))
+    return LRAMM_ERR_WORKSPACE;
+  if (!qgemm_tc_supported(LRAMM_P_INT8, L, Rt, ldl, ldr, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* st = static_cast<int*>(ws);
+  LRAMM_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int) * 4, s));
+  float* part = reinterpret_cast<float*>(static_cast<char*>(ws) + kAlign);
+  return qgemm_tc(L, Rt, M, N, K, ldl, ldr, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, part,
+                  (ws_bytes - kAlign) / sizeof(float), st, s);
 }
 
 }  // extern "C"

@@ -132,6 +132,29 @@ struct GramBatch {
   GramProb p[2];
   int n;
 };
+struct CholProb {
+  const float* G;   // l x l
+  float* L;         // l x l, lower, zeros above
+  float* Xd;        // ceil(l/32) blocks of 32 x 32: inverses of L's diagonal blocks
+};
+struct CholBatch {
+  CholProb p[2];
+  int n;
+};
+struct TrsmProb {
+  const float* Y;   // rows x l, stride l
+  float* Q;         // rows x l: Y L^-T
+  const float* L;
+  const float* Xd;
+  int64_t rows;
+};
+struct TrsmBatch {
+  TrsmProb p[2];
+  int n;
+};
+bool chol3_supported(int l);
+lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s);
+lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s);
 size_t gram_part_floats(int l);
 lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s);
 lramm_status launch_chol2(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s);
@@ -139,6 +162,15 @@ lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s);
 // Largest l the small-SVD kernels accept.
 int jacobi_max_l();
 
+// qgemm_tc.cu -- INT8 code products on the tensor cores (codes as BF16,
+// exact integer sums), fused dequantisation epilogue.
+bool qgemm_tc_supported(int prec, const void* L, const void* R, int64_t ldl, int64_t ldr, int64_t M, int64_t N,
+                        int64_t K);
+size_t qgemm_tc_part_floats(int64_t M, int64_t N, int64_t K);
+lramm_status qgemm_tc(const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl, int64_t ldr,
+                      int per_row, const float* sL, const float* sR, float alpha, float beta, const float* C,
+                      int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats, int* status,
+                      cudaStream_t s);
 // sketch_tc.cu -- X B / X^T B on the tensor cores (TF32, FP32 accumulate)
 bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void* B);
 size_t sketch_tc_part_floats(int l);

@@ -2,7 +2,8 @@
 // medium contractions of the pipeline (Gram matrices, triangular applies,
 // factor assembly, unquantised factor chain) and as the FP32-accurate
 // sketch product.  64 x 64 output tile per 256-thread block, 4 x 4 per
-// thread, K staged through shared memory 16 at a time.
+// thread, K staged through a double-buffered shared-memory tile 16 at a
+// time, operands read back as float4 broadcasts.
 //
 // Accumulation: each 16-deep K tile is summed in a fresh FP32 register and
 // added to the running sum with Kahan compensation, so the rounding error
@@ -17,8 +18,11 @@ __global__ void __launch_bounds__(256)
 sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict__ A, int64_t lda,
              const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C,
              int64_t ldc) {
-  __shared__ float As[16][64 + 4];
-  __shared__ float Bs[16][64 + 4];
+  // double-buffered K tiles: the next tile's elements are fetched into
+  // registers while the current one is multiplied (one barrier per tile);
+  // rows padded to 68 floats (aligned float4 reads, few store conflicts)
+  __shared__ __align__(16) float As[2][16][68];
+  __shared__ __align__(16) float Bs[2][16][68];
   const int tid = threadIdx.x;
   const int64_t m0 = (int64_t)blockIdx.y * 64, n0 = (int64_t)blockIdx.x * 64;
   const int tx = tid & 15, ty = tid >> 4;
@@ -27,8 +31,8 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = 0.f;
-
-  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+  float ra[4], rb[4];
+  auto fetch = [&](int64_t k0) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int e = tid + u * 256;
@@ -41,9 +45,7 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict
         kk = e >> 6;
       }
       const int64_t gm = m0 + mm, gk = k0 + kk;
-      float v = 0.f;
-      if (gm < M && gk < K) v = load_as_float(TA == 0 ? A + gm * lda + gk : A + gk * lda + gm);
-      As[kk][mm] = v;
+      ra[u] = (gm < M && gk < K) ? load_as_float(TA == 0 ? A + gm * lda + gk : A + gk * lda + gm) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -57,11 +59,28 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict
         nn = e >> 4;
       }
       const int64_t gn = n0 + nn, gk = k0 + kk;
-      float v = 0.f;
-      if (gn < N && gk < K) v = TB == 0 ? B[gk * ldb + gn] : B[gn * ldb + gk];
-      Bs[kk][nn] = v;
+      rb[u] = (gn < N && gk < K) ? (TB == 0 ? B[gk * ldb + gn] : B[gn * ldb + gk]) : 0.f;
     }
-    __syncthreads();
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + u * 256;
+      if (TA == 0) As[buf][e & 15][e >> 4] = ra[u];
+      else As[buf][e >> 6][e & 63] = ra[u];
+      if (TB == 0) Bs[buf][e >> 6][e & 63] = rb[u];
+      else Bs[buf][e & 15][e >> 4] = rb[u];
+    }
+  };
+  if (K > 0) {
+    fetch(0);
+    stash(0);
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int64_t k0 = 0; k0 < K; k0 += 16) {
+    const bool more = k0 + 16 < K;
+    if (more) fetch(k0 + 16);
     float blk[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -69,11 +88,10 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict
       for (int j = 0; j < 4; ++j) blk[i][j] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -88,7 +106,9 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict
         cmp[i][j] = (t - acc[i][j]) - y;
         acc[i][j] = t;
       }
+    if (more) stash(cur ^ 1);
     __syncthreads();
+    cur ^= 1;
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {

@@ -32,7 +32,11 @@ __device__ __forceinline__ void tile_of(int t, int& ti, int& tj) {
 }
 
 // Partial Gram of one lower 64 x 64 tile over a slice of rows: FP32 with
-// 16-deep blocks added under Kahan compensation.
+// 16-deep blocks added under Kahan compensation.  Rows arrive through a
+// register-prefetched double buffer (one barrier per 16 rows); every thread
+// owns a 4 x 4 block and reads its operands as float4 broadcasts.  VEC: rows
+// of Y are 16-byte aligned (l % 4 == 0), one float4 per thread and operand.
+template <bool VEC>
 __global__ void __launch_bounds__(256)
 gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_per_split, float* __restrict__ part) {
   const GramProb& gp = gb.p[blockIdx.z];
@@ -43,24 +47,44 @@ gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_pe
   const int64_t k0 = static_cast<int64_t>(blockIdx.y) * rows_per_split;
   const int64_t k1 = min(rows, k0 + rows_per_split);
   const int m0 = ti * kGT, n0 = tj * kGT;
-  __shared__ float As[16][kGT + 4];
-  __shared__ float Bs[16][kGT + 4];
+  __shared__ __align__(16) float As[2][16][kGT];
+  __shared__ __align__(16) float Bs[2][16][kGT];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lk = tid >> 4, lc = (tid & 15) * 4;   // loader: row lk, columns lc .. lc+3
   float acc[4][4], cmp[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = cmp[i][j] = 0.f;
-  for (int64_t kb = k0; kb < k1; kb += 16) {
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int e = tid + u * 256;
-      const int mm = e & 63, kk = e >> 6;
-      const int64_t gk = kb + kk;
-      As[kk][mm] = (gk < k1 && m0 + mm < l) ? Y[gk * l + m0 + mm] : 0.f;
-      Bs[kk][mm] = (gk < k1 && n0 + mm < l) ? Y[gk * l + n0 + mm] : 0.f;
+  float4 ra, rb;
+  auto fetch = [&](int64_t kb) {
+    const int64_t gk = kb + lk;
+    const float* yr = Y + gk * l;
+    const bool rok = gk < k1;
+    if (VEC) {
+      ra = (rok && m0 + lc < l) ? *reinterpret_cast<const float4*>(yr + m0 + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
+      rb = (rok && n0 + lc < l) ? *reinterpret_cast<const float4*>(yr + n0 + lc) : make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      ra.x = (rok && m0 + lc + 0 < l) ? yr[m0 + lc + 0] : 0.f;
+      ra.y = (rok && m0 + lc + 1 < l) ? yr[m0 + lc + 1] : 0.f;
+      ra.z = (rok && m0 + lc + 2 < l) ? yr[m0 + lc + 2] : 0.f;
+      ra.w = (rok && m0 + lc + 3 < l) ? yr[m0 + lc + 3] : 0.f;
+      rb.x = (rok && n0 + lc + 0 < l) ? yr[n0 + lc + 0] : 0.f;
+      rb.y = (rok && n0 + lc + 1 < l) ? yr[n0 + lc + 1] : 0.f;
+      rb.z = (rok && n0 + lc + 2 < l) ? yr[n0 + lc + 2] : 0.f;
+      rb.w = (rok && n0 + lc + 3 < l) ? yr[n0 + lc + 3] : 0.f;
     }
-    __syncthreads();
+  };
+  if (k0 < k1) {
+    fetch(k0);
+    *reinterpret_cast<float4*>(&As[0][lk][lc]) = ra;
+    *reinterpret_cast<float4*>(&Bs[0][lk][lc]) = rb;
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int64_t kb = k0; kb < k1; kb += 16) {
+    const bool more = kb + 16 < k1;
+    if (more) fetch(kb + 16);
     float blk[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -68,11 +92,10 @@ gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_pe
       for (int j = 0; j < 4; ++j) blk[i][j] = 0.f;
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+      const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float b[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -87,31 +110,39 @@ gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_pe
         cmp[i][j] = (t - acc[i][j]) - y;
         acc[i][j] = t;
       }
+    if (more) {
+      *reinterpret_cast<float4*>(&As[cur ^ 1][lk][lc]) = ra;
+      *reinterpret_cast<float4*>(&Bs[cur ^ 1][lk][lc]) = rb;
+    }
     __syncthreads();
+    cur ^= 1;
   }
   float* dst = part + ((static_cast<int64_t>(blockIdx.z) * splits + blockIdx.y) * ntiles + blockIdx.x) * kGT * kGT;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) dst[(ty * 4 + i) * kGT + tx * 4 + j] = acc[i][j];
+    *reinterpret_cast<float4*>(dst + (ty * 4 + i) * kGT + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 }
 
-// G[i][j] = sum over slices (FP64, fixed order) of the lower-tile partial
-// holding (max(i,j), min(i,j)): symmetric by construction.
+// G = sum over slices (FP64, fixed order) of the lower-tile partials; the
+// transposed entry of an off-diagonal tile is written from the same sum, and
+// a diagonal tile holds both triangles computed from identical products, so
+// G is exactly symmetric.  Consecutive threads read consecutive partials.
 __global__ void gram_reduce_kernel(GramBatch gb, int l, int ntiles, int splits, const float* __restrict__ part) {
-  const int64_t per = static_cast<int64_t>(l) * l;
+  const int64_t per = static_cast<int64_t>(ntiles) * kGT * kGT;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < per * gb.n;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int side = static_cast<int>(e / per);
     const int64_t rem = e - side * per;
-    int i = static_cast<int>(rem / l), j = static_cast<int>(rem - static_cast<int64_t>(i) * l);
-    const int a = i >= j ? i : j, b = i >= j ? j : i;
-    const int ti = a / kGT, tj = b / kGT;
-    const int tile = ti * (ti + 1) / 2 + tj;
+    const int tile = static_cast<int>(rem >> 12), idx = static_cast<int>(rem & 4095);
+    int ti, tj;
+    tile_of(tile, ti, tj);
+    const int i = ti * kGT + (idx >> 6), j = tj * kGT + (idx & 63);
+    if (i >= l || j >= l) continue;
     double s = 0.0;
-    for (int sp = 0; sp < splits; ++sp)
-      s += part[((static_cast<int64_t>(side) * splits + sp) * ntiles + tile) * kGT * kGT + (a % kGT) * kGT + (b % kGT)];
-    gb.p[side].G[rem] = static_cast<float>(s);
+    for (int sp = 0; sp < splits; ++sp) s += part[((static_cast<int64_t>(side) * splits + sp) * ntiles + tile) * kGT * kGT + idx];
+    float* G = gb.p[side].G;
+    G[static_cast<int64_t>(i) * l + j] = static_cast<float>(s);
+    if (ti != tj) G[static_cast<int64_t>(j) * l + i] = static_cast<float>(s);
   }
 }
 
@@ -293,6 +324,350 @@ __global__ void __launch_bounds__(256) trsm_panel_kernel(SmallBatch bt, int l, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Blocked Cholesky with 32-column panels (one CTA per problem, 512 threads,
+// packed lower triangle in shared memory).  Per panel J:
+//   (a) warp 0 factors the 32 x 32 diagonal block in registers: lane i holds
+//       row i, pivots and columns travel by shuffles (no CTA barrier inside);
+//   (b) one thread per row below solves L_IJ L_JJ^T = A_IJ in registers by
+//       forward substitution, reading columns of L_JJ as float4 broadcasts;
+//   (c) the trailing update A_22 -= L_2J L_2J^T in 4 x 4 register tiles from
+//       a transposed copy of the panel.
+// At the end every warp inverts some diagonal blocks L_JJ (lane c forms
+// column c of the inverse) for the triangular solve of the tall sketch.
+// A non-positive pivot latches LRAMM_ERR_NUMERIC and is replaced by a tiny
+// positive value, as in chol2_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kCB = 32;
+constexpr int kLC = kCB + 4;   // row stride of the column-major copy of L_JJ
+
+__global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, float shift_rel, int* status) {
+  const CholProb& cp = cb.p[blockIdx.x];
+  const float* __restrict__ G = cp.G;
+  float* __restrict__ Lo = cp.L;
+  float* __restrict__ Xd = cp.Xd;
+  extern __shared__ float4 c3_smem4[];
+  float* P = reinterpret_cast<float*>(c3_smem4);
+  const int np = l * (l + 1) / 2;
+  const int lp = static_cast<int>(round_up(l, 4)) + 4;   // row stride of the transposed panel
+  float* PnT = P + round_up(np, 4);                       // kCB x lp
+  float* LC = PnT + kCB * lp;                             // kCB x kLC: LC[t][c] = L_JJ[c][t], c > t
+  __shared__ float s_red[32];
+  __shared__ float s_rinv[kCB];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  float md = 0.f;
+  for (int i = tid; i < l; i += blockDim.x) md = fmaxf(md, G[static_cast<int64_t>(i) * l + i]);
+  md = warp_max_o(md);
+  if (lane == 0) s_red[warp] = md;
+  __syncthreads();
+  if (warp == 0) {
+    float v = lane < nw ? s_red[lane] : 0.f;
+    v = warp_max_o(v);
+    if (lane == 0) s_red[0] = v;
+  }
+  __syncthreads();
+  const float shift = shift_rel * s_red[0];
+  {  // G (row-major, l % 4 == 0) into the packed lower triangle: 8 float4 loads in flight per thread
+    const int nq = l * l / 4, lq4 = l / 4;
+    const float4* G4 = reinterpret_cast<const float4*>(G);
+    for (int q0 = tid; q0 < nq; q0 += 8 * blockDim.x) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q < nq) v[u] = G4[q];
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * blockDim.x;
+        if (q >= nq) break;
+        const int i = q / lq4, j = 4 * (q - i * lq4);
+        const float e4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+          if (j + t <= i) P[opidx(i, j + t)] = e4[t] + (i == j + t ? shift : 0.f);
+      }
+    }
+  }
+  for (int e = tid; e < kCB * lp; e += blockDim.x) PnT[e] = 0.f;
+  __syncthreads();
+
+  for (int j0 = 0; j0 < l; j0 += kCB) {
+    const int w = min(kCB, l - j0);
+    if (warp == 0) {
+      float a[kCB];
+#pragma unroll
+      for (int c = 0; c < kCB; ++c)
+        a[c] = lane < w ? (c <= lane ? P[opidx(j0 + lane, j0 + c)] : 0.f) : (c == lane ? 1.f : 0.f);
+#pragma unroll
+      for (int k = 0; k < kCB; ++k) {
+        float piv = __shfl_sync(0xffffffffu, a[k], k);
+        if (!(piv > 0.f)) {
+          if (lane == 0) set_status(status, LRAMM_ERR_NUMERIC);
+          piv = FLT_MIN * 1024.f;
+        }
+        const float inv = rsqrtf(piv);
+        const float lk = lane == k ? piv * inv : a[k] * inv;
+        a[k] = lk;
+        if (lane == k) s_rinv[k] = inv;
+#pragma unroll
+        for (int c = k + 1; c < kCB; ++c) a[c] = fmaf(-lk, __shfl_sync(0xffffffffu, lk, c), a[c]);
+      }
+#pragma unroll
+      for (int c = 0; c < kCB; ++c) {
+        if (lane < w && c <= lane) P[opidx(j0 + lane, j0 + c)] = a[c];
+        LC[c * kLC + lane] = (lane < w && c < lane) ? a[c] : 0.f;
+      }
+    }
+    __syncthreads();
+    const int r0 = j0 + kCB;   // first row below the diagonal block
+    const int n2 = l - r0;
+    if (n2 <= 0) break;
+    // (b) rows below: x L_JJ^T = a, right-looking in registers
+    if (tid < n2) {
+      const int row = r0 + tid;
+      float a[kCB];
+#pragma unroll
+      for (int t = 0; t < kCB; ++t) a[t] = P[opidx(row, j0 + t)];
+#pragma unroll
+      for (int t = 0; t < kCB; ++t) {
+        const float x = a[t] * s_rinv[t];
+        a[t] = x;
+#pragma unroll
+        for (int c4 = ((t + 1) / 4) * 4; c4 < kCB; c4 += 4) {
+          const float4 lv = *reinterpret_cast<const float4*>(LC + t * kLC + c4);
+          if (c4 + 0 > t) a[c4 + 0] = fmaf(-x, lv.x, a[c4 + 0]);
+          if (c4 + 1 > t) a[c4 + 1] = fmaf(-x, lv.y, a[c4 + 1]);
+          if (c4 + 2 > t) a[c4 + 2] = fmaf(-x, lv.z, a[c4 + 2]);
+          if (c4 + 3 > t) a[c4 + 3] = fmaf(-x, lv.w, a[c4 + 3]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kCB; ++t) {
+        P[opidx(row, j0 + t)] = a[t];
+        PnT[t * lp + tid] = a[t];
+      }
+    }
+    __syncthreads();
+    // (c) trailing update, rows/cols r0 .. l-1, lower triangle, 4 x 4 tiles
+    {
+      const int nb4 = (n2 + 3) / 4;
+      const int ntile = nb4 * (nb4 + 1) / 2;
+      for (int t = tid; t < ntile; t += blockDim.x) {
+        int bi = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while (bi * (bi + 1) / 2 > t) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bc = t - bi * (bi + 1) / 2;
+        float acc[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < kCB; ++k) {
+          const float4 av = *reinterpret_cast<const float4*>(PnT + k * lp + 4 * bi);
+          const float4 bv = *reinterpret_cast<const float4*>(PnT + k * lp + 4 * bc);
+          const float a4[4] = {av.x, av.y, av.z, av.w};
+          const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a4[u], b4[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int i = r0 + 4 * bi + u, c = r0 + 4 * bc + v;
+            if (i < l && c <= i) P[opidx(i, c)] -= acc[u][v];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  {
+    const int nq = l * l / 4, lq4 = l / 4;
+    float4* L4 = reinterpret_cast<float4*>(Lo);
+    for (int q = tid; q < nq; q += blockDim.x) {
+      const int i = q / lq4, j = 4 * (q - i * lq4);
+      float e4[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) e4[t] = j + t <= i ? P[opidx(i, j + t)] : 0.f;
+      L4[q] = make_float4(e4[0], e4[1], e4[2], e4[3]);
+    }
+  }
+  // inverses of the diagonal blocks: column `lane` of L_JJ^-1 by forward
+  // substitution, L_JJ read from shared memory (one element for all lanes)
+  const int nb = (l + kCB - 1) / kCB;
+  for (int J = warp; J < nb; J += nw) {
+    const int j0 = J * kCB, w = min(kCB, l - j0);
+    float x[kCB];
+#pragma unroll
+    for (int i = 0; i < kCB; ++i) {
+      const float* Li = P + opidx(j0 + min(i, w - 1), j0);
+      const float rinv = i < w ? 1.0f / Li[i] : 1.0f;
+      float acc = 0.f;
+#pragma unroll
+      for (int t = 0; t < i; ++t) acc = fmaf(i < w ? Li[t] : 0.f, x[t], acc);
+      x[i] = lane < i ? -acc * rinv : (lane == i ? rinv : 0.f);
+    }
+    float* xg = Xd + static_cast<int64_t>(J) * kCB * kCB;
+#pragma unroll
+    for (int i = 0; i < kCB; ++i) xg[i * kCB + lane] = (i < w && lane < w) ? x[i] : 0.f;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Q = Y L^-T for 64 rows of one problem per CTA, by 32-column panels:
+//   T_J = Y_J - Q_<J L_J,<J^T        (4 rows x 2 columns per thread, K in float4 steps)
+//   Q_J = T_J X_JJ^T,  X_JJ = L_JJ^-1 from chol3_kernel (1 row x 8 columns per thread)
+// The 64 rows stay in shared memory; the rows of L that panel J+1 needs and
+// X_J+1 are fetched with cp.async while panel J is computed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Stage rows c0 .. c0+w-1 of L (columns 0 .. c0) and X_J = L_JJ^-1.  One warp
+// per row of L, lanes over float4 columns; 16-byte copies need l % 4 == 0
+// (checked by the launcher).
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void trsm3_stage_L(const float* __restrict__ L, int l, int lqL, int J, float* Ls, int tid) {
+  const int c0 = J * kCB, w = min(kCB, l - c0);
+  const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  for (int c = warp; c < w; c += nw) {
+    const float* src = L + static_cast<int64_t>(c0 + c) * l;
+    for (int k4 = lane; k4 < c0 / 4; k4 += 32) cp_async16(Ls + c * lqL + 4 * k4, src + 4 * k4);
+  }
+}
+
+__device__ __forceinline__ void trsm3_stage_X(const float* __restrict__ Xd, int J, float* Xs, int tid) {
+  const float* xg = Xd + static_cast<int64_t>(J) * kCB * kCB;
+  for (int e4 = tid; e4 < kCB * kCB / 4; e4 += blockDim.x) {
+    const int i = e4 >> 3, c4 = e4 & 7;
+    cp_async16(Xs + i * kLC + 4 * c4, xg + 4 * e4);
+  }
+}
+
+constexpr int kR3 = 64;
+
+__global__ void __launch_bounds__(256) trsm3_kernel(TrsmBatch tb, int l, int lqQ, int lqL) {
+  const TrsmProb& tp = tb.p[blockIdx.y];
+  const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kR3;
+  if (r0 >= tp.rows) return;
+  const int nrows = static_cast<int>(tp.rows - r0 < kR3 ? tp.rows - r0 : kR3);
+  extern __shared__ float4 t3_smem4[];
+  float* Qs = reinterpret_cast<float*>(t3_smem4);       // kR3 x lqQ
+  float* Ls = Qs + kR3 * lqQ;                            // kCB x lqL
+  float* Xb[2] = {Ls + kCB * lqL, Ls + kCB * lqL + kCB * kLC};
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float* __restrict__ Y = tp.Y;
+  // rows of L beyond a partial last panel read as zero
+  for (int e = tid; e < kCB * lqL; e += blockDim.x) Ls[e] = 0.f;
+  {  // the 64 rows: every load of a thread issued before its stores
+    const int q4 = lqQ / 4, nq = kR3 * q4;
+    constexpr int kU = 8;
+    for (int q0 = tid; q0 < nq; q0 += kU * 256) {
+      float4 v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int q = q0 + u * 256;
+        const int r = q / q4, c4 = q - r * q4;
+        v[u] = (q < nq && r < nrows && 4 * c4 < l) ? *reinterpret_cast<const float4*>(Y + (r0 + r) * l + 4 * c4)
+                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int q = q0 + u * 256;
+        if (q < nq) {
+          const int r = q / q4, c4 = q - r * q4;
+          *reinterpret_cast<float4*>(Qs + r * lqQ + 4 * c4) = v[u];
+        }
+      }
+    }
+  }
+  const int np = (l + kCB - 1) / kCB;
+  trsm3_stage_X(tp.Xd, 0, Xb[0], tid);
+  cp_async_commit();
+  const int ty = tid >> 4, tx = tid & 15;     // update: rows 4ty..4ty+3, columns tx, tx+16
+  const int dr = tid >> 2, dg = tid & 3;      // diagonal: row dr, columns dg, dg+4, .., dg+28
+  for (int J = 0; J < np; ++J) {
+    const int c0 = J * kCB;
+    float* Xs = Xb[J & 1];
+    cp_async_wait_all();
+    __syncthreads();
+    if (c0 > 0) {
+      float acc[4][2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
+      for (int k = 0; k < c0; k += 4) {
+        float4 a4[4], b4[2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a4[u] = *reinterpret_cast<const float4*>(Qs + (4 * ty + u) * lqQ + k);
+#pragma unroll
+        for (int v = 0; v < 2; ++v) b4[v] = *reinterpret_cast<const float4*>(Ls + (tx + 16 * v) * lqL + k);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            acc[u][v] = fmaf(a4[u].x, b4[v].x, acc[u][v]);
+            acc[u][v] = fmaf(a4[u].y, b4[v].y, acc[u][v]);
+            acc[u][v] = fmaf(a4[u].z, b4[v].z, acc[u][v]);
+            acc[u][v] = fmaf(a4[u].w, b4[v].w, acc[u][v]);
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 2; ++v)
+          if (c0 + tx + 16 * v < l) Qs[(4 * ty + u) * lqQ + c0 + tx + 16 * v] -= acc[u][v];
+    }
+    __syncthreads();
+    // L rows and X for the next panel arrive while this panel's diagonal block is solved
+    if (J + 1 < np) {
+      trsm3_stage_L(tp.L, l, lqL, J + 1, Ls, tid);
+      trsm3_stage_X(tp.Xd, J + 1, Xb[(J + 1) & 1], tid);
+    }
+    cp_async_commit();
+    {
+      float trow[kCB];
+#pragma unroll
+      for (int t4 = 0; t4 < kCB / 4; ++t4) {
+        const float4 v4 = *reinterpret_cast<const float4*>(Qs + dr * lqQ + c0 + 4 * t4);
+        trow[4 * t4] = v4.x;
+        trow[4 * t4 + 1] = v4.y;
+        trow[4 * t4 + 2] = v4.z;
+        trow[4 * t4 + 3] = v4.w;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = 4 * cc + dg;   // the four dg of a warp read rows of X one stride apart: no bank conflict
+        float v = 0.f;   // X_JJ is lower triangular (zero above the diagonal and beyond w)
+#pragma unroll
+        for (int t4 = 0; t4 < kCB / 4; ++t4) {
+          const float4 x4 = *reinterpret_cast<const float4*>(Xs + c * kLC + 4 * t4);
+          v = fmaf(trow[4 * t4], x4.x, v);
+          v = fmaf(trow[4 * t4 + 1], x4.y, v);
+          v = fmaf(trow[4 * t4 + 2], x4.z, v);
+          v = fmaf(trow[4 * t4 + 3], x4.w, v);
+        }
+        if (c0 + c < l) Qs[dr * lqQ + c0 + c] = v;
+      }
+    }
+  }
+  __syncthreads();
+  for (int r = warp; r < nrows; r += 8) {
+    float4* dst = reinterpret_cast<float4*>(tp.Q + (r0 + r) * l);
+    const float4* src = reinterpret_cast<const float4*>(Qs + r * lqQ);
+    for (int c4 = lane; 4 * c4 < l; c4 += 32) dst[c4] = src[c4];
+  }
+}
+
 }  // namespace
 
 size_t gram_part_floats(int l) {
@@ -313,9 +688,14 @@ lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s) {
   if (rps < 64) rps = 64;
   splits = static_cast<int>(ceil_div(rows, rps));
   if (static_cast<size_t>(gb.n) * splits * ntiles > 2 * 320) return LRAMM_ERR_UNSUPPORTED;
-  gram_partial_kernel<<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
+  bool vec = l % 4 == 0;
+  for (int i = 0; i < gb.n; ++i) vec = vec && (reinterpret_cast<uintptr_t>(gb.p[i].Y) & 15) == 0;
+  if (vec)
+    gram_partial_kernel<true><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
+  else
+    gram_partial_kernel<false><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
   LRAMM_TRY(last_launch());
-  int64_t g = ceil_div(static_cast<int64_t>(l) * l * gb.n, 256);
+  int64_t g = ceil_div(static_cast<int64_t>(ntiles) * kGT * kGT * gb.n, 256);
   if (g > 152 * 8) g = 152 * 8;
   gram_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(gb, l, ntiles, splits, part);
   return last_launch();
@@ -341,6 +721,40 @@ lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s) {
   int64_t rows = 0;
   for (int i = 0; i < bt.n; ++i) rows = bt.p[i].rows > rows ? bt.p[i].rows : rows;
   trsm_panel_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kTR)), bt.n), 256, smem, s>>>(bt, l, lq);
+  return last_launch();
+}
+
+size_t chol3_smem(int l) {
+  const size_t np = static_cast<size_t>(l) * (l + 1) / 2;
+  const size_t lp = round_up(l, 4) + 4;
+  return sizeof(float) * (round_up(np, 4) + kCB * lp + kCB * kLC);
+}
+
+bool chol3_supported(int l) { return l >= 4 && l % 4 == 0 && l - kCB <= 256 && chol3_smem(l) <= static_cast<size_t>(kSmemMaxO); }
+
+lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s) {
+  if (!chol3_supported(l)) return LRAMM_ERR_UNSUPPORTED;
+  const size_t smem = chol3_smem(l);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  chol3_kernel<<<cb.n, 512, smem, s>>>(cb, l, shift_rel, status);
+  return last_launch();
+}
+
+lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s) {
+  // float4 staging: rows of Y, Q and L start on 16-byte boundaries
+  if (l % 4 != 0) return LRAMM_ERR_UNSUPPORTED;
+  for (int i = 0; i < tb.n; ++i)
+    if ((reinterpret_cast<uintptr_t>(tb.p[i].Y) | reinterpret_cast<uintptr_t>(tb.p[i].Q) |
+         reinterpret_cast<uintptr_t>(tb.p[i].L) | reinterpret_cast<uintptr_t>(tb.p[i].Xd)) & 15)
+      return LRAMM_ERR_UNSUPPORTED;
+  const int lqQ = static_cast<int>(round_up(l, kCB)) + 4;   // panel writes reach round_up(l, 32)
+  const int lqL = static_cast<int>(round_up(l > kCB ? l - kCB : 4, kCB)) + 4;
+  const size_t smem = sizeof(float) * (static_cast<size_t>(kR3) * lqQ + static_cast<size_t>(kCB) * lqL + 2 * kCB * kLC);
+  if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(trsm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  int64_t rows = 0;
+  for (int i = 0; i < tb.n; ++i) rows = tb.p[i].rows > rows ? tb.p[i].rows : rows;
+  trsm3_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kR3)), tb.n), 256, smem, s>>>(tb, l, lqQ, lqL);
   return last_launch();
 }
 

@@ -1,0 +1,337 @@
+// The integer factor products of the quantised chain (Algorithm 2 inside
+// Algorithm 3: E1 = QM(V^T W), E2 = QM(E1 Z~), E3 = QM(U~ E2)) on the
+// 5th-generation tensor cores.  INT8 codes are held as BF16 values (every
+// integer of magnitude <= 127 is exact in BF16) and multiplied with
+// tcgen05.mma kind::f16, FP32 accumulation in TMEM.  A product of two codes
+// is at most 127^2 = 16129, so a sum of at most 1024 of them stays below
+// 2^24 and every partial sum is an integer FP32 represents exactly: each CTA
+// sums at most 1024 products (16 K blocks of 64), so its accumulator holds
+// the exact integer.
+//
+//   out[i][j] = sum_k L[i][k] R[j][k]      (L: M x K codes, R: N x K codes, both K-major)
+//
+// One chunk of K (the usual case, K <= 1024): the epilogue dequantises in
+// the reference order fp32(fp32(acc) * fp32(sL[i] * sR[j])), applies
+// alpha and beta C and writes D.  Several chunks: each CTA writes its exact
+// partial sums and a reduction kernel adds them as 32-bit integers (fixed
+// order) before the same epilogue.
+//
+// Warp roles per CTA (192 threads): warp 0 issues TMA loads of 128 x 64 and
+// BN x 64 code tiles (128-byte swizzle) into a ring of shared-memory stages;
+// one thread of warp 1 issues the MMAs (M = 128, N = BN <= 256, K = 16 per
+// instruction); warps 2..5 read the accumulator back with tcgen05.ld (TMEM
+// lane = output row) and run the epilogue.  All waits are bounded; on expiry
+// the kernel latches LRAMM_ERR_TIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include "tc_common.cuh"
+
+namespace lramm {
+namespace {
+
+using namespace tc;
+
+constexpr int kQM = 128;         // output rows per CTA = TMEM lanes
+constexpr int kQK = 64;          // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int kQThreads = 192;
+constexpr int kQMaxStages = 8;
+constexpr int kQChunkBlocks = 16;  // 16 x 64 = 1024 products per exact FP32 partial
+
+struct QtcParams {
+  int64_t M, N;
+  int kblocks, kb_per_chunk, chunks;
+  int bn, stages;
+  uint32_t a_bytes, b_bytes, tmem_cols;
+  int per_row;
+  const float* sL;
+  const float* sR;
+  float alpha, beta;
+  const float* C;
+  int64_t ldc;
+  float* D;
+  int64_t ldd;
+  float* part;   // chunks > 1: chunks x M x N exact partial sums
+  int* status;
+};
+
+// kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16
+// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
+// 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kQThreads, 2)
+qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR, QtcParams p) {
+  extern __shared__ uint8_t q_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q_smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + static_cast<size_t>(p.stages) * p.a_bytes;
+  __shared__ __align__(8) uint64_t full_bar[kQMaxStages], empty_bar[kQMaxStages], tmem_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  __shared__ float sR_sh[256];
+  __shared__ float tr_sh[4][32 * 33];
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * p.bn;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.y) * kQM;
+  const int chunk = blockIdx.z;
+  const int kb0 = chunk * p.kb_per_chunk;
+  const int kb1 = min(p.kblocks, kb0 + p.kb_per_chunk);
+  const int nkb = kb1 - kb0;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tmem_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t tx_bytes = p.a_bytes + p.b_bytes;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (i >= p.stages && !mbar_wait(&empty_bar[s], ((i / p.stages) & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], tx_bytes);
+      const int k0 = (kb0 + i) * kQK;
+      tma_load_2d(sA + static_cast<size_t>(s) * p.a_bytes, &tmL, &full_bar[s], k0, static_cast<int>(m0));
+      tma_load_2d(sB + static_cast<size_t>(s) * p.b_bytes, &tmR, &full_bar[s], k0, static_cast<int>(n0));
+      ++issued;
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      const int first = issued > p.stages ? issued - p.stages : 0;
+      for (int i = first; i < issued; ++i) {
+        volatile int zero = 0;
+        mbar_wait(&full_bar[i % p.stages], (i / p.stages) & 1, &zero);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t idesc = idesc_bf16(kQM, p.bn);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(sA + static_cast<size_t>(s) * p.a_bytes);
+      const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * p.b_bytes);
+#pragma unroll
+      for (int kk = 0; kk < kQK / 16; ++kk)  // 16 BF16 (32 bytes) of K per instruction
+        mma_bf16(tmem, kmajor_sw128_desc(a_base + kk * 32), kmajor_sw128_desc(b_base + kk * 32), idesc,
+                 (i > 0 || kk > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&tmem_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lanes 32q .. 32q+31 are rows m0 + 32q + lane
+    const int q = warp & 3;
+    const int et = threadIdx.x - 64;   // 0 .. 127
+    if (p.chunks == 1) {
+      for (int j = et; j < p.bn; j += 128) {
+        const int64_t col = n0 + j;
+        sR_sh[j] = col < p.N ? (p.per_row ? p.sR[col] : p.sR[0]) : 0.f;
+      }
+    }
+    epi_bar();
+    volatile int zero = 0;  // wait for the MMAs even after an abort: they read shared memory
+    const bool ok = mbar_wait(&tmem_bar, 0, &zero);
+    tc_fence_after();
+    // Each 32 x 32 block (rows = this warp's TMEM lanes) is transposed through
+    // shared memory so that a store instruction writes 32 consecutive
+    // columns of one row (128 bytes).
+    float* T = tr_sh[q];
+    const int64_t rbase = m0 + q * 32;
+    const float sl_own = (p.chunks == 1 && rbase + lane < p.M) ? (p.per_row ? p.sL[rbase + lane] : p.sL[0]) : 0.f;
+    for (int c0 = 0; c0 < p.bn; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+      __syncwarp();
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) T[lane * 33 + jj] = v[jj];
+      __syncwarp();
+      const int64_t col = n0 + c0 + lane;
+      const bool col_ok = ok && col < p.N;
+      const float sr = p.chunks == 1 ? sR_sh[c0 + lane] : 0.f;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const float x = T[r * 33 + lane];
+        const float sl = __shfl_sync(0xffffffffu, sl_own, r);
+        const int64_t row = rbase + r;
+        if (!col_ok || row >= p.M) continue;
+        if (p.chunks > 1) {
+          p.part[(static_cast<int64_t>(chunk) * p.M + row) * p.N + col] = x;
+        } else {
+          float o = __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl, sr)));
+          if (p.beta != 0.f) o = fmaf(p.beta, p.C[row * p.ldc + col], o);
+          p.D[row * p.ldd + col] = o;
+        }
+      }
+    }
+    if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// D = dequantised sum over chunks: tot = sum_c int(part[c]) (exact, fixed
+// order), then fp32(fp32(tot) * fp32(sL * sR)), alpha and beta C.
+__global__ void qgemm_tc_reduce_kernel(QtcParams p) {
+  const int64_t total = p.M * p.N;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / p.N, j = e - i * p.N;
+    int tot = 0;
+    for (int c = 0; c < p.chunks; ++c) tot += __float2int_rn(p.part[static_cast<int64_t>(c) * total + e]);
+    const float sp = __fmul_rn(p.per_row ? p.sL[i] : p.sL[0], p.per_row ? p.sR[j] : p.sR[0]);
+    float o = __fmul_rn(p.alpha, __fmul_rn(static_cast<float>(tot), sp));
+    if (p.beta != 0.f) o = fmaf(p.beta, p.C[i * p.ldc + j], o);
+    p.D[i * p.ldd + j] = o;
+  }
+}
+
+constexpr int kQSmemBudget = 232448 - 4096;  // opt-in maximum minus alignment slack and static shared memory
+
+struct QtcShape {
+  int kblocks, kb_per_chunk, chunks, bn;
+  int64_t mtiles, ntiles;
+};
+
+QtcShape qtc_shape(int64_t M, int64_t N, int64_t K) {
+  QtcShape sh{};
+  sh.kblocks = static_cast<int>(ceil_div(K, kQK));
+  sh.bn = static_cast<int>(N >= 256 ? 256 : round_up(N, 16));
+  // short K and a wide output (E3: m x n, K = r): 128-column tiles with a
+  // two-stage ring, so that two or three CTAs share an SM and one CTA's
+  // epilogue (the HBM-bound part) overlaps another's loads and MMAs
+  if (N >= 1024 && K <= 512) sh.bn = 128;
+  sh.mtiles = ceil_div(M, kQM);
+  sh.ntiles = ceil_div(N, sh.bn);
+  const int64_t tiles = sh.mtiles * sh.ntiles;
+  int kpc = kQChunkBlocks;
+  if (tiles < 64) {  // few output tiles: split K further for parallelism (at least 4 blocks per CTA)
+    const int64_t want = ceil_div(sh.kblocks * tiles, 128);
+    kpc = static_cast<int>(want < 4 ? 4 : (want > kQChunkBlocks ? kQChunkBlocks : want));
+  }
+  if (kpc > sh.kblocks) kpc = sh.kblocks;
+  if (kpc < 1) kpc = 1;
+  sh.kb_per_chunk = kpc;
+  sh.chunks = static_cast<int>(ceil_div(sh.kblocks, kpc));
+  return sh;
+}
+
+}  // namespace
+
+bool qgemm_tc_supported(int prec, const void* L, const void* R, int64_t ldl, int64_t ldr, int64_t M, int64_t N,
+                        int64_t K) {
+  if (prec != LRAMM_P_INT8) return false;
+  if (M <= 0 || N <= 0 || K <= 0 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return false;
+  // TMA: 16-byte aligned bases and row pitches
+  return (reinterpret_cast<uintptr_t>(L) % 16) == 0 && (reinterpret_cast<uintptr_t>(R) % 16) == 0 && ldl % 8 == 0 &&
+         ldr % 8 == 0 && ldl >= K && ldr >= K;
+}
+
+size_t qgemm_tc_part_floats(int64_t M, int64_t N, int64_t K) {
+  const QtcShape sh = qtc_shape(M, N, K);
+  return sh.chunks > 1 ? static_cast<size_t>(sh.chunks) * M * N : 0;
+}
+
+lramm_status qgemm_tc(const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl, int64_t ldr,
+                      int per_row, const float* sL, const float* sR, float alpha, float beta, const float* C,
+                      int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats, int* status,
+                      cudaStream_t s) {
+  if (!qgemm_tc_supported(LRAMM_P_INT8, L, R, ldl, ldr, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
+  const QtcShape sh = qtc_shape(M, N, K);
+  if (sh.chunks > 1 && (!part || part_floats < static_cast<size_t>(sh.chunks) * M * N)) return LRAMM_ERR_WORKSPACE;
+  if (sh.mtiles > 65535 || sh.chunks > 65535) return LRAMM_ERR_UNSUPPORTED;
+  QtcParams p{};
+  p.M = M;
+  p.N = N;
+  p.kblocks = sh.kblocks;
+  p.kb_per_chunk = sh.kb_per_chunk;
+  p.chunks = sh.chunks;
+  p.bn = sh.bn;
+  p.a_bytes = kQM * kQK * 2;
+  p.b_bytes = static_cast<uint32_t>(sh.bn) * kQK * 2;
+  p.stages = static_cast<int>((kQSmemBudget - 1024) / (p.a_bytes + p.b_bytes));
+  if (p.stages > kQMaxStages) p.stages = kQMaxStages;
+  if (p.stages > sh.kb_per_chunk) p.stages = sh.kb_per_chunk < 2 ? 2 : sh.kb_per_chunk;
+  if (sh.kb_per_chunk <= 8 && sh.bn <= 128) p.stages = 2;
+  uint32_t tc = 32;
+  while (tc < static_cast<uint32_t>(sh.bn)) tc <<= 1;
+  p.tmem_cols = tc;
+  p.per_row = per_row;
+  p.sL = sL;
+  p.sR = sR;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.C = C;
+  p.ldc = ldc;
+  p.D = D;
+  p.ldd = ldd;
+  p.part = part;
+  p.status = status;
+
+  CUtensorMap mL, mR;
+  if (!make_map_2d(&mL, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L, K, M, ldl * 2, kQK, kQM, CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  if (!make_map_2d(&mR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R, K, N, ldr * 2, kQK, static_cast<uint32_t>(sh.bn),
+                   CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  qgemm_tc_kernel<<<dim3(static_cast<unsigned>(sh.ntiles), static_cast<unsigned>(sh.mtiles),
+                         static_cast<unsigned>(sh.chunks)),
+                    kQThreads, smem, s>>>(mL, mR, p);
+  LRAMM_TRY(last_launch());
+  if (sh.chunks > 1) {
+    int64_t g = ceil_div(M * N, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    qgemm_tc_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(p);
+    LRAMM_TRY(last_launch());
+  }
+  return LRAMM_OK;
+}
+
+}  // namespace lramm

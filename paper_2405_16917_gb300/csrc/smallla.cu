@@ -395,25 +395,42 @@ __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], flo
     be = fmaf(ym[u], ym[u], be);
     ga = fmaf(xm[u], ym[u], ga);
   }
-  al = warp_sum(al);
-  be = warp_sum(be);
-  ga = warp_sum(ga);
-  if (lane == 0) {
-    s_part[grp][wig][0] = al;
-    s_part[grp][wig][1] = be;
-    s_part[grp][wig][2] = ga;
+  // Three warp sums with six shuffles: the halves of the warp trade (al, be)
+  // and then (that, ga) so that each lane carries one quantity; the totals
+  // end in lanes 0 (al), 8 (ga) and 16 (be).
+  {
+    const bool hi16 = lane & 16, hi8 = lane & 8;
+    float v = hi16 ? be : al;
+    const float u = hi16 ? al : be;
+    v += __shfl_xor_sync(0xffffffffu, u, 16);
+    ga += __shfl_xor_sync(0xffffffffu, ga, 16);
+    float x = hi8 ? ga : v;
+    const float y = hi8 ? v : ga;
+    x += __shfl_xor_sync(0xffffffffu, y, 8);
+    x += __shfl_xor_sync(0xffffffffu, x, 4);
+    x += __shfl_xor_sync(0xffffffffu, x, 2);
+    x += __shfl_xor_sync(0xffffffffu, x, 1);
+    if (lane == 0) s_part[grp][wig][0] = x;
+    if (lane == 16) s_part[grp][wig][1] = x;
+    if (lane == 8) s_part[grp][wig][2] = x;
   }
   group_bar(1 + grp);
   al = s_part[grp][0][0] + s_part[grp][1][0];
   be = s_part[grp][0][1] + s_part[grp][1][1];
   ga = s_part[grp][0][2] + s_part[grp][1][2];
-  if (!(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
-  const float zeta = (be - al) / (2.0f * ga);
-  const float tt = fabsf(zeta) > 1e18f ? 0.5f / zeta
-                                       : copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
-  const float c = 1.0f / sqrtf(fmaf(tt, tt, 1.0f));
+  // Threshold and angle in fast arithmetic: the angle only has to be close
+  // (an inexact one leaves a small inner product for the next sweep); the
+  // rotation stays orthogonal to working precision because s and c come
+  // from the same t and the tau form below depends on c only through s^2.
+  const float nab = al * rsqrtf(al) * (be * rsqrtf(be));   // sqrt(al) sqrt(be); NaN for a zero column: no rotation
+  if (!(fabsf(ga) > tol * nab)) return false;
+  const float zeta = __fdividef(be - al, 2.0f * ga);
+  const float az = fabsf(zeta);
+  const float q = fmaf(zeta, zeta, 1.0f);
+  const float tt = az > 1e18f ? __fdividef(0.5f, zeta) : copysignf(__fdividef(1.0f, az + q * rsqrtf(q)), zeta);
+  const float c = rsqrtf(fmaf(tt, tt, 1.0f));
   const float s = c * tt;
-  const float tau = s / (1.0f + c);
+  const float tau = __fdividef(s, 1.0f + c);
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
     const float x = xm[u], y = ym[u];
@@ -427,27 +444,94 @@ __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], flo
 }
 
 template <int RP>
-__device__ __forceinline__ void jc2_load(const float* __restrict__ col, int ls, int l, int p, float (&m)[RP],
-                                         float (&v)[RP]) {
+__device__ __forceinline__ void jc2_load(const float* __restrict__ col, int ls, int p, float (&m)[RP], float (&v)[RP]) {
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
-    const int i = p + 64 * u;
-    m[u] = i < l ? col[i] : 0.f;
-    v[u] = i < l ? col[ls + i] : 0.f;
+    m[u] = col[p + 64 * u];
+    v[u] = col[ls + p + 64 * u];
   }
 }
 
 template <int RP>
-__device__ __forceinline__ void jc2_store(float* __restrict__ col, int ls, int l, int p, const float (&m)[RP],
+__device__ __forceinline__ void jc2_store(float* __restrict__ col, int ls, int p, const float (&m)[RP],
                                           const float (&v)[RP]) {
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
-    const int i = p + 64 * u;
-    if (i < l) {
-      col[i] = m[u];
-      col[ls + i] = v[u];
-    }
+    col[p + 64 * u] = m[u];
+    col[ls + p + 64 * u] = v[u];
   }
+}
+
+// Physical buffers of cluster rank `rank` after e moves, four per CTA:
+// top T, bottom B and the landing buffers FL / FR that blocks pushed by the
+// left / right neighbour arrive in (-1: none).  A landing buffer is always
+// the buffer this CTA last pushed to that same neighbour, so the neighbour
+// can only write it after it has received (hence finished reading) it.
+//   middle CTAs: (T, B, FL, FR) -> (FL, FR, B, T)
+//   CTA 0:       T fixed, (B, FR) -> (FR, B)
+//   last CTA:    (T, B, FL) -> (FL, T, B)   (its old top becomes its bottom in place)
+__device__ __forceinline__ void jc5_bufs(int rank, int C, int e, int& t, int& b, int& fl, int& fr) {
+  if (rank == 0) {
+    t = 0;
+    b = (e & 1) ? 2 : 1;
+    fr = (e & 1) ? 1 : 2;
+    fl = -1;
+    return;
+  }
+  fr = -1;
+  if (rank == C - 1) {
+    const int m = e % 3;
+    if (m == 0) { t = 0; b = 1; fl = 2; }
+    else if (m == 1) { t = 2; b = 0; fl = 1; }
+    else { t = 1; b = 2; fl = 0; }
+    return;
+  }
+  switch (e & 3) {
+    case 0: t = 0; b = 1; fl = 2; fr = 3; break;
+    case 1: t = 2; b = 3; fl = 1; fr = 0; break;
+    case 2: t = 1; b = 0; fl = 3; fr = 2; break;
+    default: t = 3; b = 2; fl = 0; fr = 1; break;
+  }
+}
+
+__device__ __forceinline__ uint32_t jc_smem_u32(const void* ptr) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ uint32_t jc_mapa(uint32_t saddr, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void jc_mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(jc_smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void jc_mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(jc_smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bounded wait on a phase parity; false when the limit expires.
+__device__ __forceinline__ bool jc_mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 22); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(jc_smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// Bulk copy of `bytes` from this CTA's shared memory into CTA `rank`'s, the
+// arrival counted on that CTA's mbarrier (same offset in its shared memory).
+__device__ __forceinline__ void jc_push(const float* src, float* dst_local_view, uint64_t* bar_local_view, int rank,
+                                        uint32_t bytes) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          jc_mapa(jc_smem_u32(dst_local_view), rank)),
+      "r"(jc_smem_u32(src)), "r"(bytes), "r"(jc_mapa(jc_smem_u32(bar_local_view), rank))
+      : "memory");
 }
 
 template <int RP>
@@ -467,11 +551,21 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   __shared__ int s_flags[16];
   __shared__ int s_ids[32];
   __shared__ int s_rot;
+  __shared__ __align__(8) uint64_t rx_bar[2];   // incoming blocks of even / odd moves
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = warp >> 1, wig = warp & 1, p = tid & 63;
   const int nslots = 2 * C;
 
   if (tid < nslots) s_ids[tid] = tid;
+  const uint32_t blk_bytes = static_cast<uint32_t>(bufsz * sizeof(float));
+  const uint32_t rx_bytes = ((rank >= 1) + (rank <= C - 2)) * blk_bytes;
+  if (tid == 0) {
+    jc_mbar_init(&rx_bar[0]);
+    jc_mbar_init(&rx_bar[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (C > 1) jc_mbar_expect(&rx_bar[0], rx_bytes);   // move 0
+  }
+  bool failed = false;
   for (int half = 0; half < 2; ++half) {
     float* buf = sm + half * bufsz;
     const int blk = 2 * rank + half;
@@ -495,8 +589,8 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int br = 0; br < 2 * C - 1; ++br) {
-      int bt_, bb_, bf_;
-      jc_bufs(rank, e, bt_, bb_, bf_);
+      int bt_, bb_, bfl, bfr;
+      jc5_bufs(rank, C, e, bt_, bb_, bfl, bfr);
       float* topb = sm + bt_ * bufsz;
       float* botb = sm + bb_ * bufsz;
       if (br == 0) {  // pairs inside each block, circle method on b (+1 dummy) columns
@@ -524,11 +618,11 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
             float xm[RP], xv[RP], ym[RP], yv[RP];
             float* cx = base + (int64_t)x * cs;
             float* cy = base + (int64_t)y * cs;
-            jc2_load<RP>(cx, ls, l, p, xm, xv);
-            jc2_load<RP>(cy, ls, l, p, ym, yv);
+            jc2_load<RP>(cx, ls, p, xm, xv);
+            jc2_load<RP>(cy, ls, p, ym, yv);
             if (jc2_rotate<RP>(xm, xv, ym, yv, tol, grp, wig, lane, s_part)) {
-              jc2_store<RP>(cx, ls, l, p, xm, xv);
-              jc2_store<RP>(cy, ls, l, p, ym, yv);
+              jc2_store<RP>(cx, ls, p, xm, xv);
+              jc2_store<RP>(cy, ls, p, ym, yv);
               if (p == 0) s_rot = 1;
             }
           }
@@ -538,42 +632,46 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
       {  // top column grp against bottom column (grp + j) mod b, top held in registers
         float tm[RP], tv[RP];
         float* tcol = topb + (int64_t)grp * cs;
-        jc2_load<RP>(tcol, ls, l, p, tm, tv);
+        jc2_load<RP>(tcol, ls, p, tm, tv);
         bool trot = false;
         for (int j = 0; j < b; ++j) {
           int k = grp + j;
           if (k >= b) k -= b;
           float* bcol = botb + (int64_t)k * cs;
           float bm[RP], bv[RP];
-          jc2_load<RP>(bcol, ls, l, p, bm, bv);
+          jc2_load<RP>(bcol, ls, p, bm, bv);
           if (jc2_rotate<RP>(tm, tv, bm, bv, tol, grp, wig, lane, s_part)) {
-            jc2_store<RP>(bcol, ls, l, p, bm, bv);
+            jc2_store<RP>(bcol, ls, p, bm, bv);
             trot = true;
           }
           __syncthreads();
         }
         if (trot) {
-          jc2_store<RP>(tcol, ls, l, p, tm, tv);
+          jc2_store<RP>(tcol, ls, p, tm, tv);
           if (p == 0) s_rot = 1;
         }
       }
       if (C > 1) {
-        cluster.sync();
-        if (rank >= 1) {
-          int st, sb, sf;
-          jc_bufs(rank - 1, e, st, sb, sf);
-          const float4* src =
-              cluster.map_shared_rank(reinterpret_cast<float4*>(sm + (rank == 1 ? sb : st) * bufsz), rank - 1);
-          float4* dst = reinterpret_cast<float4*>(sm + bf_ * bufsz);
-          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
-        }
-        cluster.sync();
-        if (rank <= C - 2) {
-          int st, sb, sf;
-          jc_bufs(rank + 1, e, st, sb, sf);
-          const float4* src = cluster.map_shared_rank(reinterpret_cast<float4*>(sm + sb * bufsz), rank + 1);
-          float4* dst = reinterpret_cast<float4*>(sm + (rank == 0 ? bb_ : bt_) * bufsz);
-          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        // Move: push the outgoing blocks into the neighbours' landing buffers
+        // (bulk copies through distributed shared memory, counted on their
+        // mbarriers) and wait for the incoming ones.  No cluster barrier.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && !failed) {
+          // after a timeout nothing more is armed, pushed or awaited: the
+          // neighbours' waits expire in turn and every CTA runs to the end
+          jc_mbar_expect(&rx_bar[(e + 1) & 1], rx_bytes);   // next move; its previous phase is complete
+          if (rank >= 1) {  // bottom -> left neighbour's right landing buffer
+            int t2, b2, l2, r2;
+            jc5_bufs(rank - 1, C, e, t2, b2, l2, r2);
+            jc_push(sm + bb_ * bufsz, sm + r2 * bufsz, &rx_bar[e & 1], rank - 1, blk_bytes);
+          }
+          if (rank <= C - 2) {  // top (CTA 0: bottom) -> right neighbour's left landing buffer
+            int t2, b2, l2, r2;
+            jc5_bufs(rank + 1, C, e, t2, b2, l2, r2);
+            jc_push(sm + (rank == 0 ? bb_ : bt_) * bufsz, sm + l2 * bufsz, &rx_bar[e & 1], rank + 1, blk_bytes);
+          }
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
         if (tid == 0) {
           int nid[32];
@@ -584,24 +682,30 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
           for (int c = 0; c <= C - 2; ++c) nid[2 * c + 1] = s_ids[2 * c + 3];
           for (int q = 0; q < nslots; ++q) s_ids[q] = nid[q];
         }
-        cluster.sync();
+        if (!failed && !jc_mbar_wait(&rx_bar[e & 1], (e >> 1) & 1)) {
+          failed = true;
+          set_status(status, LRAMM_ERR_TIMEOUT);
+        }
+        failed = __syncthreads_or(failed);   // one decision for the whole CTA
         ++e;
-      } else {
-        __syncthreads();
       }
+      __syncthreads();
     }
+    // convergence: every CTA's rotation flag for the sweep, one cluster barrier
     __syncthreads();
     if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rot;
     cluster.sync();
     int any = 0;
     for (int c = 0; c < C; ++c) any |= s_flags[c];
-    cluster.sync();
     if (!any) break;
   }
   if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
   if (tid == 0 && rank == 0 && status) status[1 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
-  int bt_, bb_, bf_;
-  jc_bufs(rank, e, bt_, bb_, bf_);
+  // no CTA leaves while a bulk copy it issued may still be writing a peer
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  cluster.sync();
+  int bt_, bb_, bfl, bfr;
+  jc5_bufs(rank, C, e, bt_, bb_, bfl, bfr);
   for (int hf = 0; hf < 2; ++hf) {
     const float* buf = sm + (hf == 0 ? bt_ : bb_) * bufsz;
     const int blk = s_ids[2 * rank + hf];
@@ -668,13 +772,13 @@ int jacobi_max_l() {
 }
 
 static bool jacobi2_shape(int l, int& C, int& b, int& ls, int& rp, size_t& smem) {
-  ls = (int)round_up(l, 4);
   C = (int)ceil_div(l, 16);
   if (C < 1) C = 1;
   if (C > 16) C = 16;
   b = (int)ceil_div(l, 2 * C);
   rp = (int)ceil_div(l, 64);
-  smem = sizeof(float) * 3 * (size_t)b * 2 * ls;
+  ls = 64 * rp;  // rows per column part, zero padded: every thread owns exactly rp rows
+  smem = sizeof(float) * 4 * (size_t)b * 2 * ls;
   return b <= 10 && rp <= 5 && smem <= (size_t)kSmemMax;  // 64 b <= 640 threads
 }
 

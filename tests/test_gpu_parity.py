@@ -230,9 +230,12 @@ def test_rsvd_matches_oracle(L, m, k, r, p, q, which):
     assert np.abs(V.T @ V - np.eye(r)).max() < tol
 
 
-@pytest.mark.parametrize("m,k,r,p,q", [(900, 800, 200, 16, 1), (1100, 1024, 256, 16, 2)])
+@pytest.mark.parametrize("m,k,r,p,q", [(900, 800, 200, 16, 1), (1100, 1024, 256, 16, 2), (1100, 1024, 272, 16, 1),
+                                       (1100, 1024, 300, 20, 1)])
 def test_rsvd_wide_sketch_matches_oracle(L, m, k, r, p, q):
-    """l = 216 and 272: the small SVD runs on 4- and 5-CTA clusters."""
+    """l = 216, 272, 288, 320: the small SVD runs on 14- and 16-CTA clusters;
+    l = 288 is the largest blocked-Cholesky case, l = 320 takes the
+    column-panel Cholesky."""
     X = workloads.lowrank(m, k, workloads.spectrum("poly1", min(m, k)), 600 + m).astype(np.float32)
     plan = L.Plan(m, m, k, r, p, q, seed=7)
     ws = plan.workspace()

@@ -1,0 +1,99 @@
+"""The tensor-core INT8 QM product (tcgen05, codes as BF16) against the oracle.
+
+The integer sum must be exact (FP32 partials of at most 1024 products are
+exact integers; longer K is split and added as 32-bit integers), so with
+unit scales the output is fp32(exact sum), compared bit for bit; with real
+scales the dequantised value is fp32(fp32(acc) * fp32(sL * sR)) as the
+oracle computes it.
+"""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2405_16917_gb300 as L
+    L.load()
+    return L
+
+
+def np_(t):
+    return t.detach().cpu().numpy()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def codes(vals):
+    return dev(vals.astype(np.float32)).to(torch.bfloat16)
+
+
+def ones(n):
+    return torch.ones(n, dtype=torch.float32, device="cuda")
+
+
+# (M, N, K): ragged tiles, K not a multiple of the 64-wide stage, one and several
+# K chunks, the shapes of E1 (r x r, K = k), E2 (n x r, K = r) and E3 (m x n, K = r)
+SHAPES = [(70, 45, 48), (129, 65, 4096), (64, 200, 1040), (1, 1, 16), (300, 260, 256), (256, 256, 4096),
+          (4096, 256, 256), (1000, 1100, 272), (128, 4096, 2048)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+def test_integer_sum_exact(L, M, N, K):
+    rng = np.random.default_rng(M * 7 + N * 3 + K)
+    a = rng.integers(-127, 128, (M, K))
+    b = rng.integers(-127, 128, (N, K))
+    D = np_(L.qgemm_tc(codes(a), codes(b), ones(M), ones(N)))
+    exact = oracle.quant.code_product(a, b.T)
+    assert np.array_equal(D, exact.astype(np.float32))
+
+
+@pytest.mark.parametrize("K", [1024, 1040, 4096, 16384])
+def test_worst_case_codes(L, K):
+    """All-extreme codes: |acc| up to 127^2 K, far above 2^24 for K > 1024."""
+    a = np.full((3, K), 127.0)
+    a[1] = -127.0
+    a[2, ::2] = -127.0
+    b = np.full((2, K), 127.0)
+    b[1, 1::2] = -127.0
+    D = np_(L.qgemm_tc(codes(a), codes(b), ones(3), ones(2)))
+    assert np.array_equal(D, oracle.quant.code_product(a, b.T).astype(np.float32))
+
+
+@pytest.mark.parametrize("per_row", [True, False])
+@pytest.mark.parametrize("M,K,N", [(150, 200, 90), (4096, 256, 300), (256, 4096, 256)])
+def test_dequantised_matches_oracle(L, per_row, M, K, N):
+    rng = np.random.default_rng(M + K + N + per_row)
+    Lm = (rng.standard_normal((M, K)) * np.exp(rng.uniform(-2, 2, (M, 1)))).astype(np.float32)
+    R = (rng.standard_normal((K, N)) * np.exp(rng.uniform(-2, 2, (1, N)))).astype(np.float32)
+    Kp = K + (-K) % 16
+    cL, sL = L.quantize(dev(Lm), 1, per_row, ldcodes=Kp)
+    cR, sR = L.quantize(dev(np.ascontiguousarray(R.T)), 1, per_row, ldcodes=Kp)
+    D = np_(L.qgemm_tc(cL, cR, sL, sR, per_row=per_row))
+    ref = oracle.quant.qm(Lm, R, 1, 0 if per_row else 1)
+    assert np.array_equal(D, ref)
+
+
+def test_alpha_beta(L):
+    """D = alpha QM + beta C: one FP32 multiply and one FMA after the dequantisation."""
+    rng = np.random.default_rng(5)
+    M, K, N = 300, 256, 280
+    Lm = rng.standard_normal((M, K)).astype(np.float32)
+    R = rng.standard_normal((K, N)).astype(np.float32)
+    C = rng.standard_normal((M, N)).astype(np.float32)
+    cL, sL = L.quantize(dev(Lm), 1, True, ldcodes=K)
+    cR, sR = L.quantize(dev(np.ascontiguousarray(R.T)), 1, True, ldcodes=K)
+    D = np_(L.qgemm_tc(cL, cR, sL, sR, alpha=0.75, beta=-1.5, C=dev(C)))
+    qm = oracle.quant.qm(Lm, R, 1, 0)
+    v = (np.float32(0.75) * qm).astype(np.float32)
+    ref = np.float64(-1.5) * C.astype(np.float64) + v.astype(np.float64)   # exact FMA, one rounding below
+    assert np.all(np.abs(D - ref) <= 2.0 ** -24 * np.abs(ref) + 1e-30)
