@@ -508,9 +508,11 @@ __device__ __forceinline__ void jc_mbar_init(uint64_t* bar) {
 __device__ __forceinline__ void jc_mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(jc_smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait on a phase parity; false when the limit expires.
+// Bounded wait on a phase parity (about half a second of SM clocks); false
+// when the limit expires.
 __device__ __forceinline__ bool jc_mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (uint32_t it = 0; it < (1u << 22); ++it) {
+  const long long t0 = clock64();
+  while (clock64() - t0 < (1ll << 30)) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"

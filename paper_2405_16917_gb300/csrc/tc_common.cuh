@@ -11,7 +11,10 @@
 namespace lramm {
 namespace tc {
 
-constexpr uint32_t kWaitLimit = 1u << 26;
+// Wait budget in SM clock cycles (about half a second at 2 GHz): a try_wait
+// may suspend the thread for a system-dependent time, so the limit is on
+// elapsed clocks, not on iterations.
+constexpr long long kWaitCycles = 1ll << 30;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -40,11 +43,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 // Bounded wait for the phase with the given parity; false on expiry or abort.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 255u && *abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
   }
-  return false;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1) {
