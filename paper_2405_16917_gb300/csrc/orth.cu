@@ -123,26 +123,134 @@ gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_pe
     *reinterpret_cast<float4*>(dst + (ty * 4 + i) * kGT + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
 }
 
+// Partial Gram of one lower 64 x 64 tile over a slice of rows, 64 threads
+// each owning an 8 x 8 block: four float4 shared-memory reads feed 64 FMAs.
+// Rows arrive through a register-prefetched double buffer (8 float4 global
+// loads per thread per 16 rows).  Plain FP32 FMA chains over the slice (a
+// few hundred rows); the slices are added in FP64 by the reduction.
+// Needs l % 4 == 0 and 16-byte aligned rows.
+__global__ void __launch_bounds__(64)
+gram_partial8_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_per_split, float* __restrict__ part) {
+  const GramProb& gp = gb.p[blockIdx.z];
+  const float* __restrict__ Y = gp.Y;
+  const int64_t rows = gp.rows;
+  int ti, tj;
+  tile_of(blockIdx.x, ti, tj);
+  const int64_t k0 = static_cast<int64_t>(blockIdx.y) * rows_per_split;
+  const int64_t k1 = min(rows, k0 + rows_per_split);
+  const int m0 = ti * kGT, n0 = tj * kGT;
+  __shared__ __align__(16) float As[2][16][kGT];
+  __shared__ __align__(16) float Bs[2][16][kGT];
+  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  // loader: 16 rows x 16 float4 per operand = 256 float4 = 4 per thread
+  float4 ra[4], rb[4];
+  auto fetch = [&](int64_t kb) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = tid + 64 * u, kk = q >> 4, c4 = (q & 15) * 4;
+      const int64_t gk = kb + kk;
+      const float* yr = Y + gk * l;
+      const bool rok = gk < k1;
+      ra[u] = (rok && m0 + c4 < l) ? *reinterpret_cast<const float4*>(yr + m0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+      rb[u] = (rok && n0 + c4 < l) ? *reinterpret_cast<const float4*>(yr + n0 + c4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int q = tid + 64 * u, kk = q >> 4, c4 = (q & 15) * 4;
+      *reinterpret_cast<float4*>(&As[buf][kk][c4]) = ra[u];
+      *reinterpret_cast<float4*>(&Bs[buf][kk][c4]) = rb[u];
+    }
+  };
+  if (k0 < k1) {
+    fetch(k0);
+    stash(0);
+  }
+  __syncthreads();
+  int cur = 0;
+  for (int64_t kb = k0; kb < k1; kb += 16) {
+    const bool more = kb + 16 < k1;
+    if (more) fetch(kb + 16);
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 8]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 8 + 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 8]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 8 + 4]);
+      const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    if (more) stash(cur ^ 1);
+    __syncthreads();
+    cur ^= 1;
+  }
+  float* dst = part + ((static_cast<int64_t>(blockIdx.z) * splits + blockIdx.y) * ntiles + blockIdx.x) * kGT * kGT;
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    float* rowp = dst + (ty * 8 + i) * kGT + tx * 8;
+    *reinterpret_cast<float4*>(rowp) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(rowp + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+  }
+}
+
 // G = sum over slices (FP64, fixed order) of the lower-tile partials; the
 // transposed entry of an off-diagonal tile is written from the same sum, and
 // a diagonal tile holds both triangles computed from identical products, so
-// G is exactly symmetric.  Consecutive threads read consecutive partials.
+// G is exactly symmetric.  Each thread adds four consecutive elements of a
+// tile row (float4 reads of the partials, four slices in flight).
 __global__ void gram_reduce_kernel(GramBatch gb, int l, int ntiles, int splits, const float* __restrict__ part) {
-  const int64_t per = static_cast<int64_t>(ntiles) * kGT * kGT;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < per * gb.n;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int side = static_cast<int>(e / per);
-    const int64_t rem = e - side * per;
-    const int tile = static_cast<int>(rem >> 12), idx = static_cast<int>(rem & 4095);
+  const int64_t per4 = static_cast<int64_t>(ntiles) * kGT * kGT / 4;
+  const int64_t tile_stride4 = static_cast<int64_t>(ntiles) * kGT * kGT / 4;   // between slices
+  const float4* part4 = reinterpret_cast<const float4*>(part);
+  for (int64_t e4 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e4 < per4 * gb.n;
+       e4 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int side = static_cast<int>(e4 / per4);
+    const int64_t rem4 = e4 - side * per4;
+    const int tile = static_cast<int>(rem4 >> 10), idx = static_cast<int>(rem4 & 1023) * 4;
     int ti, tj;
     tile_of(tile, ti, tj);
     const int i = ti * kGT + (idx >> 6), j = tj * kGT + (idx & 63);
     if (i >= l || j >= l) continue;
-    double s = 0.0;
-    for (int sp = 0; sp < splits; ++sp) s += part[((static_cast<int64_t>(side) * splits + sp) * ntiles + tile) * kGT * kGT + idx];
+    const float4* src = part4 + static_cast<int64_t>(side) * splits * tile_stride4 + rem4;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int sp = 0;
+    for (; sp + 4 <= splits; sp += 4) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = src[static_cast<int64_t>(sp + u) * tile_stride4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        s0 += v[u].x;
+        s1 += v[u].y;
+        s2 += v[u].z;
+        s3 += v[u].w;
+      }
+    }
+    for (; sp < splits; ++sp) {
+      const float4 v = src[static_cast<int64_t>(sp) * tile_stride4];
+      s0 += v.x;
+      s1 += v.y;
+      s2 += v.z;
+      s3 += v.w;
+    }
     float* G = gb.p[side].G;
-    G[static_cast<int64_t>(i) * l + j] = static_cast<float>(s);
-    if (ti != tj) G[static_cast<int64_t>(j) * l + i] = static_cast<float>(s);
+    const double sv[4] = {s0, s1, s2, s3};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (j + t >= l) break;
+      G[static_cast<int64_t>(i) * l + j + t] = static_cast<float>(sv[t]);
+      if (ti != tj) G[static_cast<int64_t>(j + t) * l + i] = static_cast<float>(sv[t]);
+    }
   }
 }
 
@@ -681,21 +789,23 @@ lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s) {
   const int ntiles = nt * (nt + 1) / 2;
   int64_t rows = 0;
   for (int i = 0; i < gb.n; ++i) rows = gb.p[i].rows > rows ? gb.p[i].rows : rows;
-  int splits = static_cast<int>((2 * 152 + ntiles - 1) / ntiles);
+  bool vec = l % 4 == 0;
+  for (int i = 0; i < gb.n; ++i) vec = vec && (reinterpret_cast<uintptr_t>(gb.p[i].Y) & 15) == 0;
+  // 64-thread CTAs (8 x 8 per thread) run several per SM: aim at ~6 per SM
+  const int want = vec ? 6 * 152 : 2 * 152;
+  int splits = static_cast<int>((want / gb.n + ntiles - 1) / ntiles);
   if (splits > 320 / ntiles) splits = 320 / ntiles;
   if (splits < 1) splits = 1;
   int64_t rps = ceil_div(ceil_div(rows, splits), 16) * 16;
   if (rps < 64) rps = 64;
   splits = static_cast<int>(ceil_div(rows, rps));
   if (static_cast<size_t>(gb.n) * splits * ntiles > 2 * 320) return LRAMM_ERR_UNSUPPORTED;
-  bool vec = l % 4 == 0;
-  for (int i = 0; i < gb.n; ++i) vec = vec && (reinterpret_cast<uintptr_t>(gb.p[i].Y) & 15) == 0;
   if (vec)
-    gram_partial_kernel<true><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
+    gram_partial8_kernel<<<dim3(ntiles, splits, gb.n), 64, 0, s>>>(gb, l, ntiles, splits, rps, part);
   else
     gram_partial_kernel<false><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
   LRAMM_TRY(last_launch());
-  int64_t g = ceil_div(static_cast<int64_t>(ntiles) * kGT * kGT * gb.n, 256);
+  int64_t g = ceil_div(static_cast<int64_t>(ntiles) * kGT * kGT / 4 * gb.n, 256);
   if (g > 152 * 8) g = 152 * 8;
   gram_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(gb, l, ntiles, splits, part);
   return last_launch();

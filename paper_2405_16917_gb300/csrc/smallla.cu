@@ -122,17 +122,20 @@ __global__ void __launch_bounds__(1024) trsm_rows_kernel(SmallBatch bt, int l) {
 }
 
 // Sort columns by descending norm (sigma) and write the rank-r outputs.
-__global__ void __launch_bounds__(1024) svd_finalize_kernel(FinalBatch fb, int l, int r) {
-  const FinalProb& fp = fb.p[blockIdx.x];
+// blockIdx.y = problem; blockIdx.x = a slice of 32 output rows.  Every CTA
+// recomputes the l norms and the ranking (l^2 work, cheap) so that the
+// row-major S1 / S2 rows can be written coalesced (consecutive threads,
+// consecutive output columns p).  Ties are broken by column index.
+constexpr int kFinRows = 32;
+
+__global__ void __launch_bounds__(256) svd_finalize_kernel(FinalBatch fb, int l, int r) {
+  const FinalProb& fp = fb.p[blockIdx.y];
   const float* __restrict__ M = fp.M;
   const float* __restrict__ V = fp.V;
-  float* __restrict__ sig = fp.sig;
-  float* __restrict__ S1 = fp.S1;
-  float* __restrict__ S2 = fp.S2;
-  const int s1_sigma = fp.s1_sigma, s2_sigma = fp.s2_sigma;
   extern __shared__ float sm[];
-  float* nrm = sm;                               // l
-  int* pos = reinterpret_cast<int*>(sm + l);     // l
+  float* nrm = sm;                                  // l
+  int* pos = reinterpret_cast<int*>(sm + l);        // l
+  int* inv = pos + l;                               // r: column holding rank p
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   for (int j = warp; j < l; j += nw) {
     float s = 0.f;
@@ -149,19 +152,20 @@ __global__ void __launch_bounds__(1024) svd_finalize_kernel(FinalBatch fb, int l
       rank += (u > v) || (u == v && i < j);
     }
     pos[j] = rank;
+    if (rank < r) inv[rank] = j;
   }
   __syncthreads();
-  for (int j = warp; j < l; j += nw) {
-    const int p = pos[j];
-    if (p >= r) continue;
+  if (blockIdx.x == 0)
+    for (int p = tid; p < r; p += blockDim.x) fp.sig[p] = nrm[inv[p]];
+  const int i0 = blockIdx.x * kFinRows, i1 = min(l, i0 + kFinRows);
+  for (int e = tid; e < (i1 - i0) * r; e += blockDim.x) {
+    const int i = i0 + e / r, p = e - (e / r) * r;
+    const int j = inv[p];
     const float sj = nrm[j];
-    if (lane == 0) sig[p] = sj;
-    const float u_scale = s1_sigma ? 1.0f : (sj > 0.f ? 1.0f / sj : 0.f);
-    const float v_scale = s2_sigma ? sj : 1.0f;
-    for (int i = lane; i < l; i += 32) {
-      S1[(int64_t)i * r + p] = M[(int64_t)j * l + i] * u_scale;
-      S2[(int64_t)i * r + p] = V[(int64_t)j * l + i] * v_scale;
-    }
+    const float u_scale = fp.s1_sigma ? 1.0f : (sj > 0.f ? 1.0f / sj : 0.f);
+    const float v_scale = fp.s2_sigma ? sj : 1.0f;
+    fp.S1[(int64_t)i * r + p] = M[(int64_t)j * l + i] * u_scale;
+    fp.S2[(int64_t)i * r + p] = V[(int64_t)j * l + i] * v_scale;
   }
 }
 
@@ -385,7 +389,7 @@ __device__ __forceinline__ void group_bar(int id) {
   asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
 }
 
-template <int RP>
+template <int RP, int GW>
 __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], float (&ym)[RP], float (&yv)[RP],
                                            float tol, int grp, int wig, int lane, float (*s_part)[2][4]) {
   float al = 0.f, be = 0.f, ga = 0.f;
@@ -410,14 +414,22 @@ __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], flo
     x += __shfl_xor_sync(0xffffffffu, x, 4);
     x += __shfl_xor_sync(0xffffffffu, x, 2);
     x += __shfl_xor_sync(0xffffffffu, x, 1);
-    if (lane == 0) s_part[grp][wig][0] = x;
-    if (lane == 16) s_part[grp][wig][1] = x;
-    if (lane == 8) s_part[grp][wig][2] = x;
+    if (GW == 1) {  // one warp per pair: broadcast the three totals
+      al = __shfl_sync(0xffffffffu, x, 0);
+      be = __shfl_sync(0xffffffffu, x, 16);
+      ga = __shfl_sync(0xffffffffu, x, 8);
+    } else {
+      if (lane == 0) s_part[grp][wig][0] = x;
+      if (lane == 16) s_part[grp][wig][1] = x;
+      if (lane == 8) s_part[grp][wig][2] = x;
+    }
   }
-  group_bar(1 + grp);
-  al = s_part[grp][0][0] + s_part[grp][1][0];
-  be = s_part[grp][0][1] + s_part[grp][1][1];
-  ga = s_part[grp][0][2] + s_part[grp][1][2];
+  if (GW == 2) {  // two warps per pair: add the warps' totals (same order everywhere)
+    group_bar(1 + grp);
+    al = s_part[grp][0][0] + s_part[grp][1][0];
+    be = s_part[grp][0][1] + s_part[grp][1][1];
+    ga = s_part[grp][0][2] + s_part[grp][1][2];
+  }
   // Threshold and angle in fast arithmetic: the angle only has to be close
   // (an inexact one leaves a small inner product for the next sweep); the
   // rotation stays orthogonal to working precision because s and c come
@@ -443,22 +455,22 @@ __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], flo
   return true;
 }
 
-template <int RP>
+template <int RP, int GW>
 __device__ __forceinline__ void jc2_load(const float* __restrict__ col, int ls, int p, float (&m)[RP], float (&v)[RP]) {
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
-    m[u] = col[p + 64 * u];
-    v[u] = col[ls + p + 64 * u];
+    m[u] = col[p + 32 * GW * u];
+    v[u] = col[ls + p + 32 * GW * u];
   }
 }
 
-template <int RP>
+template <int RP, int GW>
 __device__ __forceinline__ void jc2_store(float* __restrict__ col, int ls, int p, const float (&m)[RP],
                                           const float (&v)[RP]) {
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
-    col[p + 64 * u] = m[u];
-    col[ls + p + 64 * u] = v[u];
+    col[p + 32 * GW * u] = m[u];
+    col[ls + p + 32 * GW * u] = v[u];
   }
 }
 
@@ -536,7 +548,7 @@ __device__ __forceinline__ void jc_push(const float* src, float* dst_local_view,
       : "memory");
 }
 
-template <int RP>
+template <int RP, int GW>
 __global__ void __launch_bounds__(640)
 jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float tol, int* status) {
   cg::cluster_group cluster = cg::this_cluster();
@@ -555,7 +567,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   __shared__ int s_rot;
   __shared__ __align__(8) uint64_t rx_bar[2];   // incoming blocks of even / odd moves
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int grp = warp >> 1, wig = warp & 1, p = tid & 63;
+  const int grp = warp / GW, wig = warp % GW, p = tid & (32 * GW - 1);
   const int nslots = 2 * C;
 
   if (tid < nslots) s_ids[tid] = tid;
@@ -620,11 +632,11 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
             float xm[RP], xv[RP], ym[RP], yv[RP];
             float* cx = base + (int64_t)x * cs;
             float* cy = base + (int64_t)y * cs;
-            jc2_load<RP>(cx, ls, p, xm, xv);
-            jc2_load<RP>(cy, ls, p, ym, yv);
-            if (jc2_rotate<RP>(xm, xv, ym, yv, tol, grp, wig, lane, s_part)) {
-              jc2_store<RP>(cx, ls, p, xm, xv);
-              jc2_store<RP>(cy, ls, p, ym, yv);
+            jc2_load<RP, GW>(cx, ls, p, xm, xv);
+            jc2_load<RP, GW>(cy, ls, p, ym, yv);
+            if (jc2_rotate<RP, GW>(xm, xv, ym, yv, tol, grp, wig, lane, s_part)) {
+              jc2_store<RP, GW>(cx, ls, p, xm, xv);
+              jc2_store<RP, GW>(cy, ls, p, ym, yv);
               if (p == 0) s_rot = 1;
             }
           }
@@ -634,22 +646,22 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
       {  // top column grp against bottom column (grp + j) mod b, top held in registers
         float tm[RP], tv[RP];
         float* tcol = topb + (int64_t)grp * cs;
-        jc2_load<RP>(tcol, ls, p, tm, tv);
+        jc2_load<RP, GW>(tcol, ls, p, tm, tv);
         bool trot = false;
         for (int j = 0; j < b; ++j) {
           int k = grp + j;
           if (k >= b) k -= b;
           float* bcol = botb + (int64_t)k * cs;
           float bm[RP], bv[RP];
-          jc2_load<RP>(bcol, ls, p, bm, bv);
-          if (jc2_rotate<RP>(tm, tv, bm, bv, tol, grp, wig, lane, s_part)) {
-            jc2_store<RP>(bcol, ls, p, bm, bv);
+          jc2_load<RP, GW>(bcol, ls, p, bm, bv);
+          if (jc2_rotate<RP, GW>(tm, tv, bm, bv, tol, grp, wig, lane, s_part)) {
+            jc2_store<RP, GW>(bcol, ls, p, bm, bv);
             trot = true;
           }
           __syncthreads();
         }
         if (trot) {
-          jc2_store<RP>(tcol, ls, p, tm, tv);
+          jc2_store<RP, GW>(tcol, ls, p, tm, tv);
           if (p == 0) s_rot = 1;
         }
       }
@@ -726,6 +738,8 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
 // Opt-in shared memory per block on sm_100-class GPUs (227 KB), minus the
 // static shared memory the kernels declare themselves.
 static const int kSmemMax = 232448 - 1024;
+// Warps per column pair of the cluster Jacobi (measured on GB300 at l = 272).
+static const int kJacobiWarpsPerPair = 1;
 
 lramm_status launch_chol(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s) {
   const size_t smem = sizeof(float) * (size_t)l * (l + 1) / 2;
@@ -773,27 +787,30 @@ int jacobi_max_l() {
   return best;
 }
 
-static bool jacobi2_shape(int l, int& C, int& b, int& ls, int& rp, size_t& smem) {
+// Cluster shape: C = min(16, ceil(l/16)) CTAs, blocks of b columns, GW warps
+// per column pair (64 b or 32 b threads), RP rows of a column per thread
+// (columns zero padded to 32 GW RP rows).
+static bool jacobi2_shape(int l, int gw, int& C, int& b, int& ls, int& rp, size_t& smem) {
   C = (int)ceil_div(l, 16);
   if (C < 1) C = 1;
   if (C > 16) C = 16;
   b = (int)ceil_div(l, 2 * C);
-  rp = (int)ceil_div(l, 64);
-  ls = 64 * rp;  // rows per column part, zero padded: every thread owns exactly rp rows
+  rp = (int)ceil_div(l, 32 * gw);
+  ls = 32 * gw * rp;
   smem = sizeof(float) * 4 * (size_t)b * 2 * ls;
-  return b <= 10 && rp <= 5 && smem <= (size_t)kSmemMax;  // 64 b <= 640 threads
+  return b <= 10 && rp <= (gw == 2 ? 5 : 10) && smem <= (size_t)kSmemMax;
 }
 
-template <int RP>
+template <int RP, int GW>
 static lramm_status launch_jacobi2_rp(JacobiBatch jb, int l, int ls, int C, int b, size_t smem, int max_sweeps,
                                       float tol, int* status, cudaStream_t s, bool& launched) {
   launched = false;
-  auto kern = jacobi_pair2_kernel<RP>;
+  auto kern = jacobi_pair2_kernel<RP, GW>;
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   if (C > 8) LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
-  cfg.blockDim = dim3((unsigned)(64 * b), 1, 1);
+  cfg.blockDim = dim3((unsigned)(32 * GW * b), 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
@@ -811,23 +828,35 @@ static lramm_status launch_jacobi2_rp(JacobiBatch jb, int l, int ls, int C, int 
   return last_launch();
 }
 
+// The cluster Jacobi with gw warps per column pair (1 or 2); `done` is
+// false when the shape is not available (the caller falls back).
+lramm_status launch_jacobi_gw(JacobiBatch jb, int l, int gw, int max_sweeps, int* status, cudaStream_t s, bool& done) {
+  done = false;
+  int C2, b2, ls2, rp;
+  size_t smem2;
+  if (!jacobi2_shape(l, gw, C2, b2, ls2, rp, smem2)) return LRAMM_OK;
+  const float tol2 = 4.0f * sqrtf((float)l) * 0x1p-24f;
+#define JC_CASE(R, G) \
+  case R: return launch_jacobi2_rp<R, G>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done);
+  if (gw == 2) {
+    switch (rp) {
+      JC_CASE(1, 2) JC_CASE(2, 2) JC_CASE(3, 2) JC_CASE(4, 2) JC_CASE(5, 2)
+      default: return LRAMM_OK;
+    }
+  }
+  switch (rp) {
+    JC_CASE(1, 1) JC_CASE(2, 1) JC_CASE(3, 1) JC_CASE(4, 1) JC_CASE(5, 1)
+    JC_CASE(6, 1) JC_CASE(7, 1) JC_CASE(8, 1) JC_CASE(9, 1) JC_CASE(10, 1)
+    default: return LRAMM_OK;
+  }
+#undef JC_CASE
+}
+
 lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s) {
   {
-    int C2, b2, ls2, rp;
-    size_t smem2;
-    if (jacobi2_shape(l, C2, b2, ls2, rp, smem2)) {
-      const float tol2 = 4.0f * sqrtf((float)l) * 0x1p-24f;
-      bool done = false;
-      lramm_status st2 = LRAMM_OK;
-      switch (rp) {
-        case 1: st2 = launch_jacobi2_rp<1>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
-        case 2: st2 = launch_jacobi2_rp<2>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
-        case 3: st2 = launch_jacobi2_rp<3>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
-        case 4: st2 = launch_jacobi2_rp<4>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
-        default: st2 = launch_jacobi2_rp<5>(jb, l, ls2, C2, b2, smem2, max_sweeps, tol2, status, s, done); break;
-      }
-      if (st2 != LRAMM_OK || done) return st2;
-    }
+    bool done = false;
+    LRAMM_TRY(launch_jacobi_gw(jb, l, kJacobiWarpsPerPair, max_sweeps, status, s, done));
+    if (done) return LRAMM_OK;
   }
   int C, b, ls;
   size_t smem;
@@ -853,8 +882,8 @@ lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, c
 }
 
 lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s) {
-  const size_t smem = sizeof(float) * 2 * (size_t)l;
-  svd_finalize_kernel<<<fb.n, 1024, smem, s>>>(fb, l, r);
+  const size_t smem = sizeof(float) * (2 * (size_t)l + (size_t)r);
+  svd_finalize_kernel<<<dim3((unsigned)ceil_div(l, kFinRows), fb.n), 256, smem, s>>>(fb, l, r);
   return last_launch();
 }
 
