@@ -124,7 +124,10 @@ gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_pe
 }
 
 // Partial Gram of one lower 64 x 64 tile over a slice of rows, 64 threads
-// each owning an 8 x 8 block: four float4 shared-memory reads feed 64 FMAs.
+// each owning an 8 x 8 block -- rows {4ty..4ty+3, 32+4ty..32+4ty+3} x the
+// same split of columns by tx, so that each float4 read of a warp covers one
+// contiguous 64- or 128-byte span (no bank conflicts): four float4 reads
+// feed 64 FMAs.
 // Rows arrive through a register-prefetched double buffer (8 float4 global
 // loads per thread per 16 rows).  Plain FP32 FMA chains over the slice (a
 // few hundred rows); the slices are added in FP64 by the reduction.
@@ -179,10 +182,10 @@ gram_partial8_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_p
     if (more) fetch(kb + 16);
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 8]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 8 + 4]);
-      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 8]);
-      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 8 + 4]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[cur][kk][32 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4*>(&Bs[cur][kk][32 + tx * 4]);
       const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
       const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -197,20 +200,21 @@ gram_partial8_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_p
   float* dst = part + ((static_cast<int64_t>(blockIdx.z) * splits + blockIdx.y) * ntiles + blockIdx.x) * kGT * kGT;
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    float* rowp = dst + (ty * 8 + i) * kGT + tx * 8;
-    *reinterpret_cast<float4*>(rowp) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    *reinterpret_cast<float4*>(rowp + 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    float* rowp = dst + (i < 4 ? ty * 4 + i : 32 + ty * 4 + i - 4) * kGT;
+    *reinterpret_cast<float4*>(rowp + tx * 4) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+    *reinterpret_cast<float4*>(rowp + 32 + tx * 4) = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
   }
 }
 
-// G = sum over slices (FP64, fixed order) of the lower-tile partials; the
-// transposed entry of an off-diagonal tile is written from the same sum, and
-// a diagonal tile holds both triangles computed from identical products, so
-// G is exactly symmetric.  Each thread adds four consecutive elements of a
-// tile row (float4 reads of the partials, four slices in flight).
+// G = sum over slices of the lower-tile partials, in slice order with Kahan
+// compensation (FP32; error ~2u of the sum of magnitudes); the transposed
+// entry of an off-diagonal tile is written from the same sum, and a diagonal
+// tile holds both triangles computed from identical products, so G is
+// exactly symmetric.  Each thread adds four consecutive elements of a tile
+// row (float4 reads of the partials, four slices in flight).
 __global__ void gram_reduce_kernel(GramBatch gb, int l, int ntiles, int splits, const float* __restrict__ part) {
   const int64_t per4 = static_cast<int64_t>(ntiles) * kGT * kGT / 4;
-  const int64_t tile_stride4 = static_cast<int64_t>(ntiles) * kGT * kGT / 4;   // between slices
+  const int64_t tile_stride4 = per4;   // between slices
   const float4* part4 = reinterpret_cast<const float4*>(part);
   for (int64_t e4 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e4 < per4 * gb.n;
        e4 += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -222,34 +226,32 @@ __global__ void gram_reduce_kernel(GramBatch gb, int l, int ntiles, int splits, 
     const int i = ti * kGT + (idx >> 6), j = tj * kGT + (idx & 63);
     if (i >= l || j >= l) continue;
     const float4* src = part4 + static_cast<int64_t>(side) * splits * tile_stride4 + rem4;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    float sum[4] = {0.f, 0.f, 0.f, 0.f}, cmp[4] = {0.f, 0.f, 0.f, 0.f};
+    auto add = [&](const float4& v) {
+      const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const float y = x[t] - cmp[t];
+        const float u = sum[t] + y;
+        cmp[t] = (u - sum[t]) - y;
+        sum[t] = u;
+      }
+    };
     int sp = 0;
     for (; sp + 4 <= splits; sp += 4) {
       float4 v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) v[u] = src[static_cast<int64_t>(sp + u) * tile_stride4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        s0 += v[u].x;
-        s1 += v[u].y;
-        s2 += v[u].z;
-        s3 += v[u].w;
-      }
+      for (int u = 0; u < 4; ++u) add(v[u]);
     }
-    for (; sp < splits; ++sp) {
-      const float4 v = src[static_cast<int64_t>(sp) * tile_stride4];
-      s0 += v.x;
-      s1 += v.y;
-      s2 += v.z;
-      s3 += v.w;
-    }
+    for (; sp < splits; ++sp) add(src[static_cast<int64_t>(sp) * tile_stride4]);
     float* G = gb.p[side].G;
-    const double sv[4] = {s0, s1, s2, s3};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       if (j + t >= l) break;
-      G[static_cast<int64_t>(i) * l + j + t] = static_cast<float>(sv[t]);
-      if (ti != tj) G[static_cast<int64_t>(j + t) * l + i] = static_cast<float>(sv[t]);
+      G[static_cast<int64_t>(i) * l + j + t] = sum[t];
+      if (ti != tj) G[static_cast<int64_t>(j + t) * l + i] = sum[t];
     }
   }
 }
@@ -805,9 +807,8 @@ lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s) {
   else
     gram_partial_kernel<false><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
   LRAMM_TRY(last_launch());
-  int64_t g = ceil_div(static_cast<int64_t>(ntiles) * kGT * kGT / 4 * gb.n, 256);
-  if (g > 152 * 8) g = 152 * 8;
-  gram_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(gb, l, ntiles, splits, part);
+  const int64_t g = ceil_div(static_cast<int64_t>(ntiles) * kGT * kGT / 4 * gb.n, 64);
+  gram_reduce_kernel<<<static_cast<unsigned>(g), 64, 0, s>>>(gb, l, ntiles, splits, part);
   return last_launch();
 }
 
