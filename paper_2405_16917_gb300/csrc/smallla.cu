@@ -517,12 +517,6 @@ __device__ __forceinline__ uint32_t jc_mapa(uint32_t saddr, int rank) {
 __device__ __forceinline__ void jc_mbar_init(uint64_t* bar) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(jc_smem_u32(bar)) : "memory");
 }
-__device__ __forceinline__ void jc_mbar_init_count(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(jc_smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void jc_mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(jc_smem_u32(bar)) : "memory");
-}
 __device__ __forceinline__ void jc_mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(jc_smem_u32(bar)), "r"(bytes) : "memory");
 }
@@ -567,8 +561,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   float* sm = reinterpret_cast<float*>(jc2_smem4);
   const int cs = 2 * ls;                      // floats per column: M part, then V part
   const int64_t bufsz = (int64_t)b * cs;      // floats per b-column buffer
-  __shared__ float s_part[2][16][2][4];   // double-buffered by round parity
-  __shared__ __align__(8) uint64_t col_bar[16];
+  __shared__ float s_part[16][2][4];
   __shared__ int s_flags[16];
   __shared__ int s_ids[32];
   __shared__ int s_rot;
@@ -583,12 +576,10 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   if (tid == 0) {
     jc_mbar_init(&rx_bar[0]);
     jc_mbar_init(&rx_bar[1]);
-    for (int c = 0; c < b; ++c) jc_mbar_init_count(&col_bar[c], 32 * GW);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     if (C > 1) jc_mbar_expect(&rx_bar[0], rx_bytes);   // move 0
   }
   bool failed = false;
-  uint32_t col_phase = 0;   // completed phases of every col_bar at the start of a block round
   for (int half = 0; half < 2; ++half) {
     float* buf = sm + half * bufsz;
     const int blk = 2 * rank + half;
@@ -643,7 +634,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
             float* cy = base + (int64_t)y * cs;
             jc2_load<RP, GW>(cx, ls, p, xm, xv);
             jc2_load<RP, GW>(cy, ls, p, ym, yv);
-            if (jc2_rotate<RP, GW>(xm, xv, ym, yv, tol, grp, wig, lane, s_part[0])) {
+            if (jc2_rotate<RP, GW>(xm, xv, ym, yv, tol, grp, wig, lane, s_part)) {
               jc2_store<RP, GW>(cx, ls, p, xm, xv);
               jc2_store<RP, GW>(cy, ls, p, ym, yv);
               if (p == 0) s_rot = 1;
@@ -657,28 +648,18 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
         float* tcol = topb + (int64_t)grp * cs;
         jc2_load<RP, GW>(tcol, ls, p, tm, tv);
         bool trot = false;
-        // Bottom column k is handed from group g+1 (round j-1) to group g
-        // (round j) through its mbarrier: every thread of the group that
-        // processed it arrives once per round, so its phase count advances
-        // by one per round and no CTA-wide barrier is needed inside a block
-        // round.  (Each column is processed exactly once per round.)
         for (int j = 0; j < b; ++j) {
           int k = grp + j;
           if (k >= b) k -= b;
-          if (j > 0 && !failed && !jc_mbar_wait(&col_bar[k], (col_phase + j - 1) & 1u)) {
-            failed = true;
-            set_status(status, LRAMM_ERR_TIMEOUT);
-          }
           float* bcol = botb + (int64_t)k * cs;
           float bm[RP], bv[RP];
           jc2_load<RP, GW>(bcol, ls, p, bm, bv);
-          if (jc2_rotate<RP, GW>(tm, tv, bm, bv, tol, grp, wig, lane, s_part[j & 1])) {
+          if (jc2_rotate<RP, GW>(tm, tv, bm, bv, tol, grp, wig, lane, s_part)) {
             jc2_store<RP, GW>(bcol, ls, p, bm, bv);
             trot = true;
           }
-          jc_mbar_arrive(&col_bar[k]);
+          __syncthreads();
         }
-        col_phase += b;
         if (trot) {
           jc2_store<RP, GW>(tcol, ls, p, tm, tv);
           if (p == 0) s_rot = 1;
