@@ -124,6 +124,19 @@ def kernel_work(kind, cfg, l, variant):
     return (None, None)
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# the ncu captures summarised under profiles/ (lramm_4096, the kernels as
+# they are in this tree); None where no capture of the current kernel exists.
+MEASURED_TRAFFIC = {
+    "lramm_4096": {"svd": 642304, "chol": 702464, "trsm": 9308672, "gram": 8941312 + 7308288,
+                   "sketch": 71634688 + 2668544, "e3": 4260352 + 8458752},
+}
+
+
+def measured_traffic(workload, kind):
+    return MEASURED_TRAFFIC.get(workload, {}).get(kind)
+
+
 def jacobi_work(l, sweeps):
     """Algorithmic FP32 flops of one launch of the one-sided Jacobi SVD (both
     operands): per sweep every one of the l(l-1)/2 column pairs forms three
@@ -351,7 +364,8 @@ def run_lramm(args):
         roof = {"bound": "alu", "achieved": jf / avg_s / 1e12,
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
                 "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
-                "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz", "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz",
+                "traffic": measured_traffic(args.workload, "svd"),
                 "algorithmic_flops_per_launch": jf,
                 "note": "one-sided Jacobi, sequential rounds of column-pair rotations on 2 x 16-CTA clusters"}
         roof["frac"] = roof["achieved"] / roof["peak"]
@@ -371,7 +385,8 @@ def run_lramm(args):
             continue
         kroofs[kn] = {"bound": "hbm", "achieved": kb / ks / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                       "frac": kb / ks / 1e9 / pk["hbm_gbs"], "avg_launch_ms": ks * 1e3,
-                      "launches_per_step": kc / args.steps, "algorithmic_bytes_per_launch": kb}
+                      "launches_per_step": kc / args.steps, "algorithmic_bytes_per_launch": kb,
+                      "traffic": measured_traffic(args.workload, kn)}
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
