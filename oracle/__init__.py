@@ -11,5 +11,6 @@ Modules:
              Dequantization), e4m3 rounding, QM (Algorithm 2)
   lramm   -- randomized SVD (Sec. 2.2, Algorithm 1, power iterations) and
              LRAMM (Algorithm 3), exact product, relative Frobenius error
+  rf      -- the range-finder form C ~ (X Q)(Q^T W) and its gradients
 """
-from . import philox, quant, lramm  # noqa: F401
+from . import philox, quant, lramm, rf  # noqa: F401

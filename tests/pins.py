@@ -376,3 +376,63 @@ def pin_lramm_bit_ordering(lr, wl, quant):
         err[name] = lr.rel_fro(lr.chain(Ut, V, W, Zt, pr), Cx)
     assert err["884"] < err["444"] and err["844"] < err["444"], err
     assert err["888"] <= min(err.values()) + 1e-12, err
+
+
+# ---------------------------------------------------------------- range-finder form (oracle/rf.py)
+def _rf_case(seed, m=7, k=10, n=9):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m, k))
+    W = rng.standard_normal((k, n))
+    G = rng.standard_normal((m, n))
+    return X, W, G
+
+
+def pin_qr_adjoint_fd(rf, seed=31, h=1e-6):
+    """d/dY <dQ, Q(Y)> by central differences against qr_adjoint."""
+    rng = np.random.default_rng(seed)
+    Y = rng.standard_normal((11, 4))
+    dQ = rng.standard_normal((11, 4))
+    Q, R = rf.qr_pos(Y)
+    g = rf.qr_adjoint(Q, R, dQ)
+    for _ in range(4):
+        E = rng.standard_normal(Y.shape)
+        fd = (np.sum(dQ * rf.qr_pos(Y + h * E)[0]) - np.sum(dQ * rf.qr_pos(Y - h * E)[0])) / (2 * h)
+        assert abs(fd - np.sum(g * E)) <= 1e-7 * (1.0 + abs(fd)), (fd, np.sum(g * E))
+
+
+def pin_rf_gradients_fd(rf, seed=32, h=1e-6):
+    """Directional derivatives of L(X, W) = <G, X Q(W) Q(W)^T W> by central
+    differences (Omega fixed) against rf_backward, q = 0, 1, 2."""
+    X, W, G = _rf_case(seed)
+    rng = np.random.default_rng(seed + 1)
+    for q in (0, 1, 2):
+        dX, dW = rf.rf_backward(X, W, G, 3, 2, q, 7)
+
+        def L(Xv, Wv):
+            return np.sum(G * rf.rf_forward(Xv, Wv, 3, 2, q, 7))
+        for _ in range(3):
+            EX = rng.standard_normal(X.shape)
+            EW = rng.standard_normal(W.shape)
+            fdx = (L(X + h * EX, W) - L(X - h * EX, W)) / (2 * h)
+            fdw = (L(X, W + h * EW) - L(X, W - h * EW)) / (2 * h)
+            assert abs(fdx - np.sum(dX * EX)) <= 1e-6 * (1.0 + abs(fdx)), (q, fdx, np.sum(dX * EX))
+            assert abs(fdw - np.sum(dW * EW)) <= 1e-6 * (1.0 + abs(fdw)), (q, fdw, np.sum(dW * EW))
+
+
+def pin_rf_exact_rank(rf, seed=33):
+    """W of rank <= l: Q Q^T W = W, so the range-finder product is X W exactly."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((20, 30))
+    W = rng.standard_normal((30, 4)) @ rng.standard_normal((4, 25))
+    for q in (0, 1):
+        C = rf.rf_forward(X, W, 4, 2, q, 7)
+        assert np.linalg.norm(C - X @ W) <= 1e-12 * np.linalg.norm(X @ W)
+    T, P, Q = rf.rf_factors(X, W, 4, 2, 1, 7)
+    assert np.abs(Q.T @ Q - np.eye(6)).max() <= 1e-13
+
+
+def pin_copyltu(rf, seed=34):
+    M = np.random.default_rng(seed).standard_normal((5, 5))
+    S = rf.copyltu(M)
+    assert np.array_equal(S, S.T)
+    assert np.array_equal(np.tril(S), np.tril(M))

@@ -181,3 +181,65 @@ def test_chain_transposed_e1_caught(monkeypatch):
     monkeypatch.setattr(Lr, "chain", bad_chain)
     with pytest.raises(AssertionError):
         pins.pin_lramm_factor_identity(Lr, workloads, Qn)
+
+
+# ---------------------------------------------------------------- range-finder form
+from oracle import rf as Rf
+
+
+def _qr_adjoint_variant(kind):
+    def f(Q, R, dQ):
+        M = -dQ.T @ Q
+        if kind == "no_copyltu":
+            B = dQ
+        elif kind == "upper":
+            B = dQ + Q @ (np.triu(M) + np.triu(M, 1).T)
+        else:  # sign of M
+            B = dQ - Q @ Rf.copyltu(M)
+        return np.linalg.solve(R, B.T).T
+    return f
+
+
+@pytest.mark.parametrize("kind", ["no_copyltu", "upper", "sign"])
+def test_qr_adjoint_mutations_caught(monkeypatch, kind):
+    monkeypatch.setattr(Rf, "qr_adjoint", _qr_adjoint_variant(kind))
+    with pytest.raises(AssertionError):
+        pins.pin_qr_adjoint_fd(Rf)
+
+
+def test_rf_backward_missing_direct_term_caught(monkeypatch):
+    orig = Rf.rf_backward
+
+    def bad(X, W, G, r, p, q, seed, alpha=1.0):
+        dX, dW = orig(X, W, G, r, p, q, seed, alpha)
+        Q, _ = Rf.range_finder_chain(W, r + p, q, seed)
+        return dX, dW - Q @ ((X @ Q).T @ (alpha * G))    # drop dW's term through P = Q^T W
+    monkeypatch.setattr(Rf, "rf_backward", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_rf_gradients_fd(Rf)
+
+
+def test_rf_backward_missing_dq_term_caught(monkeypatch):
+    """dQ without the W dP^T term (the dependence of P = Q^T W on Q)."""
+    src_qr_adjoint = Rf.qr_adjoint
+
+    def bad(X, W, G, r, p, q, seed, alpha=1.0):
+        X = np.asarray(X, dtype=float); W = np.asarray(W, dtype=float); G = alpha * np.asarray(G, dtype=float)
+        Q, ch = Rf.range_finder_chain(W, r + p, q, seed)
+        T = X @ Q; P = Q.T @ W
+        dT = G @ P.T; dP = T.T @ G
+        dX = dT @ Q.T
+        dW = Q @ dP
+        dQ = X.T @ dT                      # missing + W @ dP.T
+        Qprev = [ch["Q0"]] + [st[2] for st in ch["steps"][:-1]]
+        for (Z, Rp, Qi, Ri), Qp in zip(reversed(ch["steps"]), reversed(Qprev)):
+            dY = src_qr_adjoint(Qi, Ri, dQ)
+            dW += dY @ Z.T
+            dYp = src_qr_adjoint(Z, Rp, W.T @ dY)
+            dW += Qp @ dYp.T
+            dQ = W @ dYp
+        dW += src_qr_adjoint(ch["Q0"], ch["R0"], dQ) @ ch["Om"].T
+        return dX, dW
+    monkeypatch.setattr(Rf, "rf_backward", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_rf_gradients_fd(Rf)

@@ -81,3 +81,20 @@ def test_lramm_factor_identity():
 
 def test_lramm_bit_width_ordering():
     pins.pin_lramm_bit_ordering(oracle.lramm, workloads, oracle.quant)
+
+
+# ---------------------------------------------------------------- range-finder form
+def test_rf_qr_adjoint_matches_finite_differences():
+    pins.pin_qr_adjoint_fd(oracle.rf)
+
+
+def test_rf_gradients_match_finite_differences():
+    pins.pin_rf_gradients_fd(oracle.rf)
+
+
+def test_rf_exact_rank_product():
+    pins.pin_rf_exact_rank(oracle.rf)
+
+
+def test_rf_copyltu():
+    pins.pin_copyltu(oracle.rf)
