@@ -230,6 +230,35 @@ LRAMM_API lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int
                          const float* C, int64_t ldc, void* D, int64_t ldd,
                          int32_t out_kind, void* stream);
 
+/* Range-finder form of LRAMM as a linear layer: the two-stage randomized
+ * scheme of Sec. 2.2 applied to the right operand.  C ~ X W is computed as
+ * (X Q)(Q^T W): Q (k x l, l = r + p) is the orthonormal basis of the sketch
+ * W Omega (Omega n x l, Philox stream 1 of the plan's seed) after q power
+ * iterations (text after Eq. (rsvderror_z)), every product re-orthonormalised
+ * by CholeskyQR; T = X Q (m x l), P = Q^T W (l x n), and
+ *   C = alpha * QM(T P, d) + beta * C      (Algorithm 2, d = prec[2], plan scale)
+ * or alpha T P + beta C when prec[2] is LRAMM_P_F32.  X: m x k of a_type,
+ * stride lda; W: k x n of b_type, stride ldb; C: m x n FP32, stride ldc, read
+ * when beta != 0 and written.  The plan's r, p, q, seed, prec[2], scale,
+ * sketch, alpha and beta apply; ws as for lramm_matmul.  Asynchronous on
+ * `stream`; device-side errors latch in the status word. */
+LRAMM_API lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, float* C, void* ws,
+                                        size_t ws_bytes, void* stream);
+
+/* Gradients of L = <G, C> for the range-finder form, with Omega fixed and the
+ * quantiser passed straight through (the gradients of alpha X Q Q^T W):
+ *   dT = alpha G P^T, dP = alpha T^T G, dX = dT Q^T, dW = Q dP + the path
+ *   through Q: dQ = X^T dT + W dP^T carried back through every thin QR
+ *   Y = Q R by dY = (dQ + Q copyltu(M)) R^-T, M = -dQ^T Q, and through every
+ *   product of the power chain (W Z: dW += dY Z^T; W^T Q: dW += Q dY^T; the
+ *   sketch W Omega: dW += dY Omega^T).
+ * The range finder is recomputed (no state is kept from lramm_rf_forward).
+ * G: m x n FP32 (stride ldc); dX: m x k FP32 (dense, stride k); dW: k x n
+ * FP32 (dense, stride n).  W must be FP32 (else LRAMM_ERR_UNSUPPORTED).  ws as
+ * for lramm_matmul. */
+LRAMM_API lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, const float* G,
+                                         float* dX, float* dW, void* ws, size_t ws_bytes, void* stream);
+
 /* The INT8 QM product of Algorithm 2 on the tensor cores (tcgen05.mma
  * kind::f16; the INT8 codes lramm_quantize writes as bfloat16 values are
  * exact BF16 operands):

@@ -56,6 +56,8 @@ _SIGS = {
     "lramm_quantize": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _VP, _VP]),
     "lramm_qgemm": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _I32, _VP, _VP, _F, _F,
                            _VP, _I64, _VP, _I64, _I32, _VP]),
+    "lramm_rf_forward": (_I32, [_VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
+    "lramm_rf_backward": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "lramm_qgemm_tc": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _VP, _VP, _F, _F, _VP, _I64, _VP, _I64,
                               _VP, ctypes.c_size_t, _VP]),
     "lramm_qgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
@@ -187,6 +189,60 @@ def matmul(plan, A, B, C=None, out=None, ws=None, stream=None):
     _check(load().lramm_matmul(plan.handle, _ptr(A), _ptr(B), _ptr(C), _ptr(out), _ptr(ws),
                                ws.numel(), _stream(stream)), "lramm_matmul")
     return out
+
+
+def rf_forward(plan, X, W, C=None, ws=None, stream=None):
+    """Range-finder form: C = alpha * QM((X Q)(Q^T W)) + beta * C; returns C (m x n FP32)."""
+    torch = _torch()
+    _need_cuda(X, W, C)
+    d = plan.desc
+    if C is None:
+        C = torch.zeros((d.m, d.ldc), dtype=torch.float32, device=X.device)[:, : d.n]
+    if ws is None:
+        ws = plan.workspace(X.device)
+    _check(load().lramm_rf_forward(plan.handle, _ptr(X), _ptr(W), _ptr(C), _ptr(ws), ws.numel(), _stream(stream)),
+           "lramm_rf_forward")
+    return C
+
+
+def rf_backward(plan, X, W, G, ws=None, stream=None):
+    """Gradients (dX, dW) of <G, C> for the range-finder form (straight-through quantisers)."""
+    torch = _torch()
+    _need_cuda(X, W, G)
+    d = plan.desc
+    dX = torch.empty((d.m, d.k), dtype=torch.float32, device=X.device)
+    dW = torch.empty((d.k, d.n), dtype=torch.float32, device=X.device)
+    if ws is None:
+        ws = plan.workspace(X.device)
+    _check(load().lramm_rf_backward(plan.handle, _ptr(X), _ptr(W), _ptr(G), _ptr(dX), _ptr(dW), _ptr(ws),
+                                    ws.numel(), _stream(stream)), "lramm_rf_backward")
+    return dX, dW
+
+
+def _rf_function():
+    """torch.autograd.Function of the range-finder form: forward and the
+    hand-written backward both run in the library."""
+    torch = _torch()
+
+    class RangeFinderMatmul(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, W, plan):
+            ctx.plan = plan
+            ctx.save_for_backward(X, W)
+            return rf_forward(plan, X.contiguous(), W.contiguous())
+
+        @staticmethod
+        def backward(ctx, G):
+            X, W = ctx.saved_tensors
+            dX, dW = rf_backward(ctx.plan, X.contiguous(), W.contiguous(), G.contiguous().float())
+            return dX.to(X.dtype), dW.to(W.dtype), None
+
+    return RangeFinderMatmul
+
+
+def rf_matmul(X, W, plan):
+    """Differentiable C ~ X W in the range-finder form (autograd through the library's backward)."""
+    return _rf_function().apply(X, W, plan)
 
 
 def rsvd(plan, which, X, ws=None, stream=None):

@@ -55,6 +55,13 @@ struct lramm_plan_s {
   size_t amax;
   size_t part, gpart, qpart;
   size_t qpart_floats;
+  // range-finder form: codes / scales of T and P^T; the range-finder chain
+  // kept for the backward (Q_0..Q_q, Z_1..Z_q, the Cholesky factors of every
+  // orthonormalisation) and its temporaries
+  int64_t lp;
+  size_t cT, cP, sT, sP;
+  size_t bq, bz, bl;
+  size_t tdT, tdP, tdQ, tdZ, tB, tY, tY2, tM, tMc, tI, tLi;
   size_t total;
 };
 
@@ -142,8 +149,31 @@ void layout(lramm_plan_s* P) {
     size_t q = qgemm_tc_part_floats(r, r, P->kp);
     q = std::max(q, qgemm_tc_part_floats(d.n, r, P->rp));
     q = std::max(q, qgemm_tc_part_floats(d.m, d.n, P->rp));
+    q = std::max(q, qgemm_tc_part_floats(d.m, d.n, round_up(l, 16)));
     P->qpart_floats = q;
     P->qpart = b.take(sizeof(float) * (q > 0 ? q : 4));
+  }
+  {  // range-finder form
+    const int64_t kk = d.k, nn = d.n, mm = d.m, qq = d.q, mx = std::max(kk, nn);
+    P->lp = round_up(l, 16);
+    P->cT = b.take(cb * mm * P->lp);
+    P->cP = b.take(cb * nn * P->lp);
+    P->sT = b.take(sizeof(float) * mm);
+    P->sP = b.take(sizeof(float) * nn);
+    P->bq = b.take(sizeof(float) * (qq + 1) * kk * l);
+    P->bz = b.take(sizeof(float) * std::max<int64_t>(qq, 1) * nn * l);
+    P->bl = b.take(sizeof(float) * (2 * qq + 1) * 2 * l * l);
+    P->tdT = b.take(sizeof(float) * mm * l);
+    P->tdP = b.take(sizeof(float) * nn * l);
+    P->tdQ = b.take(sizeof(float) * kk * l);
+    P->tdZ = b.take(sizeof(float) * nn * l);
+    P->tB = b.take(sizeof(float) * mx * l);
+    P->tY = b.take(sizeof(float) * mx * l);
+    P->tY2 = b.take(sizeof(float) * mx * l);
+    P->tM = b.take(sizeof(float) * l * l);
+    P->tMc = b.take(sizeof(float) * l * l);
+    P->tI = b.take(sizeof(float) * l * l);
+    P->tLi = b.take(sizeof(float) * l * l);
   }
   P->total = b.off;
 }
@@ -315,6 +345,101 @@ SideRun side_run(const lramm_plan_s* P, int which, const void* X) {
   const lramm_desc& d = P->d;
   return SideRun{X, which == 0 ? d.lda : d.ldb, (which == 0 ? d.a_type : d.b_type) == LRAMM_BF16,
                  &P->side[which]};
+}
+
+// ---------------------------------------------------------------------------
+// Range-finder form (the two-stage scheme of Sec. 2.2 applied to the right
+// operand W, k x n): Q (k x l) = orth of the sketch W Omega (Philox stream 1)
+// after q power iterations, each product re-orthonormalised.  With `keep`
+// the chain the backward needs is stored: Q_0..Q_q in bq, Z_1..Z_q in bz and
+// the Cholesky factors of orthonormalisation o (o = 0 for Y_0; 2i-1 for
+// Y'_i = W^T Q_{i-1}; 2i for Y_i = W Z_i) in bl[o] = {L1, L2}.  On exit Q is
+// in the side's R0.
+float* bl_slot(lramm_plan_s* P, void* ws, int o, int which) {
+  const int64_t l = P->l;
+  return at<float>(ws, P->bl) + ((int64_t)o * 2 + which) * l * l;
+}
+
+lramm_status range_finder_side(lramm_plan_s* P, const SideRun& sd, void* ws, bool keep, cudaStream_t s) {
+  const lramm_desc& d = P->d;
+  const int l = P->l;
+  const SideLayout& S = *sd.S;
+  int* st = at<int>(ws, 0);
+  float* R0 = at<float>(ws, S.R0);
+  float* R1 = at<float>(ws, S.R1);
+  float* C0 = at<float>(ws, S.C0);
+  float* C1 = at<float>(ws, S.C1);
+  const size_t ll = sizeof(float) * l * l;
+  auto keep_L = [&](int o, int passes) -> lramm_status {
+    if (!keep) return LRAMM_OK;
+    LRAMM_CUDA_TRY(cudaMemcpyAsync(bl_slot(P, ws, o, 0), at<float>(ws, S.L1), ll, cudaMemcpyDeviceToDevice, s));
+    if (passes == 2)
+      LRAMM_CUDA_TRY(cudaMemcpyAsync(bl_slot(P, ws, o, 1), at<float>(ws, S.L2), ll, cudaMemcpyDeviceToDevice, s));
+    return LRAMM_OK;
+  };
+  float* Om = at<float>(ws, S.omega);
+  TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, 1u, S.cols, l, Om, l, s));
+  TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, Om, R0, s));
+  const int p0 = d.q > 0 ? 1 : 2;
+  float* src[1] = {R0};
+  float* tmp[1] = {R1};
+  int64_t rows[1] = {S.rows}, cols[1] = {S.cols};
+  LRAMM_TRY(orth_sides(P, ws, &sd, 1, src, tmp, src, rows, p0, false, st, s));
+  LRAMM_TRY(keep_L(0, p0));
+  if (keep)
+    LRAMM_CUDA_TRY(cudaMemcpyAsync(at<float>(ws, P->bq), R0, sizeof(float) * S.rows * l, cudaMemcpyDeviceToDevice, s));
+  for (int it = 0; it < d.q; ++it) {
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 1, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, R0, C0, s));
+    float* csrc[1] = {C0};
+    float* ctmp[1] = {C1};
+    LRAMM_TRY(orth_sides(P, ws, &sd, 1, csrc, ctmp, csrc, cols, 1, false, st, s));
+    LRAMM_TRY(keep_L(2 * it + 1, 1));
+    if (keep)
+      LRAMM_CUDA_TRY(cudaMemcpyAsync(at<float>(ws, P->bz) + (int64_t)it * S.cols * l, C0, sizeof(float) * S.cols * l,
+                                     cudaMemcpyDeviceToDevice, s));
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, C0, R0, s));
+    const int pi = it == d.q - 1 ? 2 : 1;
+    LRAMM_TRY(orth_sides(P, ws, &sd, 1, src, tmp, src, rows, pi, false, st, s));
+    LRAMM_TRY(keep_L(2 * it + 2, pi));
+    if (keep)
+      LRAMM_CUDA_TRY(cudaMemcpyAsync(at<float>(ws, P->bq) + (int64_t)(it + 1) * S.rows * l, R0,
+                                     sizeof(float) * S.rows * l, cudaMemcpyDeviceToDevice, s));
+  }
+  return LRAMM_OK;
+}
+
+// Right-multiplication by L^-1 (L lower triangular, l x l): out = X L^-1
+// (rows x l), through L^-T = I L^-T (the panel triangular solve on the
+// identity) and one product.
+lramm_status mul_linv(lramm_plan_s* P, void* ws, const float* L, const float* X, int64_t rows, float* out,
+                      cudaStream_t s) {
+  const int l = P->l;
+  float* I = at<float>(ws, P->tI);
+  float* LiT = at<float>(ws, P->tLi);
+  LRAMM_TRY(launch_identity(I, l, s));
+  SmallBatch tb{};
+  tb.n = 1;
+  tb.p[0] = SmallProb{I, LiT, L, l};
+  LRAMM_TRY(launch_trsm_panel(tb, l, s));
+  return sgemm(0, 1, rows, l, l, 1.f, X, l, 0, LiT, l, 0.f, out, l, s);
+}
+
+// Adjoint of the thin QR Y = Q R (R = L1^T, or L2^T L1^T after two
+// CholeskyQR passes) for a loss that sees Y only through Q:
+// dY = (dQ + Q copyltu(M)) R^-T, M = -dQ^T Q; R^-T = L1^-1 or L2^-1 L1^-1.
+// dQ (rows x l) is overwritten.
+lramm_status qr_adjoint(lramm_plan_s* P, void* ws, const float* Q, int64_t rows, const float* L1, const float* L2,
+                        float* dQ, float* dY, cudaStream_t s) {
+  const int l = P->l;
+  float* M = at<float>(ws, P->tM);
+  float* Mc = at<float>(ws, P->tMc);
+  LRAMM_TRY(sgemm(1, 0, l, l, rows, -1.f, dQ, l, 0, Q, l, 0.f, M, l, s));
+  LRAMM_TRY(launch_copyltu(M, Mc, l, s));
+  LRAMM_TRY(sgemm(0, 0, rows, l, l, 1.f, Q, l, 0, Mc, l, 1.f, dQ, l, s));
+  if (!L2) return mul_linv(P, ws, L1, dQ, rows, dY, s);
+  float* T2 = at<float>(ws, P->tY2);
+  LRAMM_TRY(mul_linv(P, ws, L2, dQ, rows, T2, s));
+  return mul_linv(P, ws, L1, T2, rows, dY, s);
 }
 
 // One QM product on codes: the tensor-core kernel for INT8 codes (exact
@@ -603,6 +728,93 @@ lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, in
   if (out_kind == 0 && (!sL || !sR || (beta != 0.f && (!C || ldc < N)))) return LRAMM_ERR_INVALID_ARG;
   return qgemm(L, Rt, M, N, K, ldl, ldr, prec, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, out_kind,
                static_cast<cudaStream_t>(stream));
+}
+
+lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, float* C, void* ws, size_t ws_bytes,
+                              void* stream) {
+  if (!plan || !X || !W || !C) return LRAMM_ERR_INVALID_ARG;
+  LRAMM_TRY(check_ws(plan, ws, ws_bytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const lramm_desc& d = plan->d;
+  const int l = plan->l;
+  plan->used = 0;
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  const SideRun sx = side_run(plan, 0, X), sw = side_run(plan, 1, W);
+  LRAMM_TRY(range_finder_side(plan, sw, ws, false, s));
+  const float* Q = at<float>(ws, sw.S->R0);
+  float* T = at<float>(ws, sx.S->R0);   // m x l
+  float* Pt = at<float>(ws, sw.S->C0);  // n x l = (Q^T W)^T
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, X, d.m, d.k, d.lda, sx.xbf, Q, T, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, d.k, d.n, d.ldb, sw.xbf, Q, Pt, s));
+  if (d.prec[2] == LRAMM_P_F32) {
+    TIMED(plan, LRAMM_K_E3, s, sgemm(0, 1, d.m, d.n, l, d.alpha, T, l, 0, Pt, l, d.beta, C, d.ldc, s));
+    return LRAMM_OK;
+  }
+  const int per_row = d.scale == LRAMM_S_ROWCOL;
+  unsigned int* am = at<unsigned int>(ws, plan->amax);
+  void* cT = at<void>(ws, plan->cT);
+  void* cP = at<void>(ws, plan->cP);
+  float* sT = at<float>(ws, plan->sT);
+  float* sP = at<float>(ws, plan->sP);
+  TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(T, d.m, l, l, d.prec[2], per_row, cT, plan->lp, sT, am, s));
+  TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(Pt, d.n, l, l, d.prec[2], per_row, cP, plan->lp, sP, am, s));
+  TIMED(plan, LRAMM_K_E3, s, qm_product(plan, ws, cT, cP, d.m, d.n, plan->lp, plan->lp, plan->lp, d.prec[2], per_row,
+                                       sT, sP, d.alpha, d.beta, C, d.ldc, C, d.ldc, s));
+  return LRAMM_OK;
+}
+
+lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, const float* G, float* dX,
+                               float* dW, void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || !X || !W || !G || !dX || !dW) return LRAMM_ERR_INVALID_ARG;
+  const lramm_desc& d = plan->d;
+  if (d.b_type != LRAMM_F32) return LRAMM_ERR_UNSUPPORTED;
+  LRAMM_TRY(check_ws(plan, ws, ws_bytes));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int l = plan->l;
+  const int64_t m = d.m, n = d.n, k = d.k;
+  plan->used = 0;
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  const SideRun sx = side_run(plan, 0, X), sw = side_run(plan, 1, W);
+  LRAMM_TRY(range_finder_side(plan, sw, ws, true, s));
+  auto Qi = [&](int i) { return at<float>(ws, plan->bq) + (int64_t)i * k * l; };
+  auto Zi = [&](int i) { return at<float>(ws, plan->bz) + (int64_t)(i - 1) * n * l; };
+  const float* Q = Qi(d.q);
+  float* T = at<float>(ws, sx.S->R0);   // m x l
+  float* Pt = at<float>(ws, sw.S->C0);  // n x l
+  float* dT = at<float>(ws, plan->tdT);
+  float* dPt = at<float>(ws, plan->tdP);
+  float* dQ = at<float>(ws, plan->tdQ);
+  float* dZ = at<float>(ws, plan->tdZ);
+  float* dY = at<float>(ws, plan->tY);
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, X, m, k, d.lda, sx.xbf, Q, T, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, k, n, d.ldb, sw.xbf, Q, Pt, s));
+  // dT = alpha G P^T (m x l), dP^T = alpha G^T T (n x l)
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, G, m, n, d.ldc, 0, Pt, dT, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, G, m, n, d.ldc, 0, T, dPt, s));
+  LRAMM_TRY(launch_scale(dT, m * l, d.alpha, s));
+  LRAMM_TRY(launch_scale(dPt, n * l, d.alpha, s));
+  // dX = dT Q^T (m x k);  dW = Q dP (k x n)
+  LRAMM_TRY(sgemm(0, 1, m, k, l, 1.f, dT, l, 0, Q, l, 0.f, dX, k, s));
+  LRAMM_TRY(sgemm(0, 1, k, n, l, 1.f, Q, l, 0, dPt, l, 0.f, dW, n, s));
+  // dQ = X^T dT + W dP^T (k x l)
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, X, m, k, d.lda, sx.xbf, dT, dQ, s));
+  LRAMM_TRY(sgemm(0, 0, k, l, n, 1.f, W, d.ldb, 0, dPt, l, 1.f, dQ, l, s));
+  // back through the power iterations (Omega fixed)
+  for (int i = d.q; i >= 1; --i) {
+    const int o = 2 * i;                 // Y_i = W Z_i, Q_i = orth(Y_i)
+    const bool two = i == d.q;           // the last basis took two CholeskyQR passes
+    LRAMM_TRY(qr_adjoint(plan, ws, Qi(i), k, bl_slot(plan, ws, o, 0), two ? bl_slot(plan, ws, o, 1) : nullptr, dQ,
+                         dY, s));
+    LRAMM_TRY(sgemm(0, 1, k, n, l, 1.f, dY, l, 0, Zi(i), l, 1.f, dW, n, s));     // dW += dY Z_i^T
+    TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, k, n, d.ldb, sw.xbf, dY, dZ, s));   // dZ = W^T dY
+    LRAMM_TRY(qr_adjoint(plan, ws, Zi(i), n, bl_slot(plan, ws, o - 1, 0), nullptr, dZ, dY, s));   // dY' (n x l)
+    LRAMM_TRY(sgemm(0, 1, k, n, l, 1.f, Qi(i - 1), l, 0, dY, l, 1.f, dW, n, s));   // dW += Q_{i-1} dY'^T
+    TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, W, k, n, d.ldb, sw.xbf, dY, dQ, s));   // dQ = W dY'
+  }
+  LRAMM_TRY(qr_adjoint(plan, ws, Qi(0), k, bl_slot(plan, ws, 0, 0), d.q == 0 ? bl_slot(plan, ws, 0, 1) : nullptr, dQ,
+                       dY, s));
+  const float* Om = at<float>(ws, sw.S->omega);
+  return sgemm(0, 1, k, n, l, 1.f, dY, l, 0, Om, l, 1.f, dW, n, s);   // dW += dY_0 Omega^T
 }
 
 size_t lramm_qgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K) {

@@ -159,6 +159,11 @@ size_t gram_part_floats(int l);
 lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s);
 lramm_status launch_chol2(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s);
 lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s);
+// Range-finder backward helpers: out = copyltu(M) (lower triangle mirrored),
+// I = identity (l x l), x *= a.
+lramm_status launch_copyltu(const float* M, float* out, int l, cudaStream_t s);
+lramm_status launch_identity(float* I, int l, cudaStream_t s);
+lramm_status launch_scale(float* x, int64_t n, float a, cudaStream_t s);
 // Largest l the small-SVD kernels accept.
 int jacobi_max_l();
 

@@ -887,4 +887,46 @@ lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s) {
   return last_launch();
 }
 
+
+// ---------------------------------------------------------------------------
+// Small helpers of the range-finder backward.
+// out = the symmetric matrix holding M's lower triangle (diagonal included)
+// on both sides: out[i][j] = M[max(i,j)][min(i,j)].
+__global__ void copyltu_kernel(const float* __restrict__ M, float* __restrict__ out, int l) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)l * l;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / l), j = (int)(e - (int64_t)i * l);
+    out[e] = i >= j ? M[e] : M[(int64_t)j * l + i];
+  }
+}
+__global__ void identity_kernel(float* __restrict__ I, int l) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)l * l;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / l), j = (int)(e - (int64_t)i * l);
+    I[e] = i == j ? 1.f : 0.f;
+  }
+}
+__global__ void scale_kernel(float* __restrict__ x, int64_t n, float a) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    x[e] *= a;
+}
+
+static unsigned small_grid(int64_t n) {
+  int64_t g = ceil_div(n, 256);
+  return (unsigned)(g < 1 ? 1 : (g > 1216 ? 1216 : g));
+}
+lramm_status launch_copyltu(const float* M, float* out, int l, cudaStream_t s) {
+  copyltu_kernel<<<small_grid((int64_t)l * l), 256, 0, s>>>(M, out, l);
+  return last_launch();
+}
+lramm_status launch_identity(float* I, int l, cudaStream_t s) {
+  identity_kernel<<<small_grid((int64_t)l * l), 256, 0, s>>>(I, l);
+  return last_launch();
+}
+lramm_status launch_scale(float* x, int64_t n, float a, cudaStream_t s) {
+  if (n <= 0) return LRAMM_OK;
+  scale_kernel<<<small_grid(n), 256, 0, s>>>(x, n, a);
+  return last_launch();
+}
+
 }  // namespace lramm
