@@ -26,12 +26,18 @@ void note_cuda_error(cudaError_t e, const char* where) {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kMaxL = 320;
+constexpr int kMaxL = 576;   // the SVD form stops earlier, at jacobi_max_l()
+
+// Largest l of the small SVD (the SVD form); the range-finder form needs none.
+int svd_max_l() {
+  static const int v = jacobi_max_l();
+  return v;
+}
 constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of every CholeskyQR pass
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, CS;
 };
 
 }  // namespace
@@ -94,6 +100,10 @@ lramm_status validate(const lramm_desc* d) {
   if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_BF16) return LRAMM_ERR_INVALID_ARG;
   if (d->max_sweeps < 0 || (d->flags & ~LRAMM_FLAG_TIMING) != 0) return LRAMM_ERR_INVALID_ARG;
   if (l > kMaxL) return LRAMM_ERR_UNSUPPORTED;
+  // orthonormalisation: blocked Cholesky (l <= 288), two-level beyond
+  // (l % 4 == 0), the column-panel Cholesky while its triangle fits
+  if (!chol3_supported((int)l) && !chol_split_supported((int)l) && l * (l + 1) / 2 * 4 > 231424)
+    return LRAMM_ERR_UNSUPPORTED;
   return LRAMM_OK;
 }
 
@@ -115,6 +125,7 @@ void layout(lramm_plan_s* P) {
     S.L1 = b.take(sizeof(float) * l * l);
     S.L2 = b.take(sizeof(float) * l * l);
     S.Xd = b.take(sizeof(float) * ceil_div(l, 32) * 32 * 32);
+    S.CS = chol_split_supported((int)l) ? b.take(sizeof(float) * chol_split_scratch_floats((int)l)) : 0;
     S.R = b.take(sizeof(float) * l * l);
     S.Vj = b.take(sizeof(float) * l * l);
     S.sig = b.take(sizeof(float) * l);
@@ -270,6 +281,11 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
     TIMED(P, LRAMM_K_GRAM, s, launch_gram(gb, l, at<float>(ws, P->gpart), s));
     if (chol3_supported(l) && l % 4 == 0) {  // blocked Cholesky + panel solve with inverted diagonal blocks
       TIMED(P, LRAMM_K_CHOL, s, launch_chol3(cb3, l, kCholShift, st, s));
+      TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
+    } else if (chol_split_supported(l)) {  // two-level Cholesky, same panel solve
+      SplitScratch sc{};
+      for (int i = 0; i < ns; ++i) sc.w[i] = at<float>(ws, sd[i].S->CS);
+      TIMED(P, LRAMM_K_CHOL, s, launch_chol_split(cb3, sc, l, kCholShift, st, s));
       TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
     } else {
       TIMED(P, LRAMM_K_CHOL, s, launch_chol2(cb, l, kCholShift, st, s));
@@ -578,6 +594,7 @@ lramm_status lramm_workspace_size(lramm_plan_t plan, size_t* bytes) {
 lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* U, float* S, float* V,
                         void* ws, size_t ws_bytes, void* stream) {
   if (!plan || (which != 0 && which != 1) || !X || !U || !S || !V) return LRAMM_ERR_INVALID_ARG;
+  if (plan->l > svd_max_l()) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const SideLayout& Sd = plan->side[which];
@@ -610,6 +627,7 @@ lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const
                           void* ws, size_t ws_bytes, void* stream) {
   if (!plan || !A || !B || !D) return LRAMM_ERR_INVALID_ARG;
   if (plan->d.beta != 0.f && !C) return LRAMM_ERR_INVALID_ARG;
+  if (plan->l > svd_max_l()) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const lramm_desc& d = plan->d;

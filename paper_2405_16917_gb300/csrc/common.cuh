@@ -155,6 +155,14 @@ struct TrsmBatch {
 bool chol3_supported(int l);
 lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s);
 lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s);
+// Two-level Cholesky for 288 < l <= 576 (l % 4 == 0) on chol3 / trsm3 /
+// sgemm; scratch: chol_split_scratch_floats(l) floats per problem.
+struct SplitScratch {
+  float* w[2];
+};
+bool chol_split_supported(int l);
+size_t chol_split_scratch_floats(int l);
+lramm_status launch_chol_split(CholBatch cb, SplitScratch sc, int l, float shift_rel, int* status, cudaStream_t s);
 size_t gram_part_floats(int l);
 lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s);
 lramm_status launch_chol2(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s);

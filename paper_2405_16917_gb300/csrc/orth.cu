@@ -451,6 +451,11 @@ __global__ void __launch_bounds__(256) trsm_panel_kernel(SmallBatch bt, int l, i
 constexpr int kCB = 32;
 constexpr int kLC = kCB + 4;   // row stride of the column-major copy of L_JJ
 
+__host__ __device__ inline int chol_split_h_dev(int l) {
+  const int h = ((l + 1) / 2 + kCB - 1) / kCB * kCB;
+  return h < 288 ? h : 288;
+}
+
 __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, float shift_rel, int* status) {
   const CholProb& cp = cb.p[blockIdx.x];
   const float* __restrict__ G = cp.G;
@@ -866,6 +871,115 @@ lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s) {
   int64_t rows = 0;
   for (int i = 0; i < tb.n; ++i) rows = tb.p[i].rows > rows ? tb.p[i].rows : rows;
   trsm3_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kR3)), tb.n), 256, smem, s>>>(tb, l, lqQ, lqL);
+  return last_launch();
+}
+
+
+// ---------------------------------------------------------------------------
+// Cholesky of Grams too large for one CTA's shared memory (chol3_kernel
+// stops at l = 288), two-level with h = min(288, round_up(l/2, 32)):
+//   G + shift I = [G11 G21^T; G21 G22],  L11 = chol(G11),  L21 = G21 L11^-T,
+//   L22 = chol(G22 - L21 L21^T),  L = [L11 0; L21 L22].
+// The shift comes from the whole matrix's diagonal before the split.  h is a
+// multiple of 32, so the inverted 32 x 32 diagonal blocks of L11 and L22 are
+// those of L, in order, and the panel solve of the tall sketch runs on L
+// unchanged.  Scratch per problem (2 l^2 floats):
+//   G11 h x h | G21 m x h | S m x m | L11 h x h | L21 m x h | L22 m x m, m = l - h.
+// ---------------------------------------------------------------------------
+int chol_split_h(int l) { return chol_split_h_dev(l); }
+
+bool chol_split_supported(int l) {
+  if (l % 4 != 0 || l <= 288) return false;
+  const int h = chol_split_h(l), m = l - h;
+  return m >= 4 && chol3_supported(h) && chol3_supported(m);
+}
+
+size_t chol_split_scratch_floats(int l) { return 2 * static_cast<size_t>(l) * l; }
+
+struct SplitPtrs {
+  float *G11, *G21, *S, *L11, *L21, *L22;
+};
+
+__host__ __device__ inline SplitPtrs split_ptrs(float* w, int l) {
+  const int64_t h = chol_split_h_dev(l), m = l - h;
+  SplitPtrs p;
+  p.G11 = w;
+  p.G21 = p.G11 + h * h;
+  p.S = p.G21 + m * h;
+  p.L11 = p.S + m * m;
+  p.L21 = p.L11 + h * h;
+  p.L22 = p.L21 + m * h;
+  return p;
+}
+
+__global__ void __launch_bounds__(256) chol_split_prep_kernel(CholBatch cb, SplitScratch sc, int l, float shift_rel) {
+  const CholProb& cp = cb.p[blockIdx.y];
+  const float* __restrict__ G = cp.G;
+  __shared__ float s_red[8];
+  float md = 0.f;
+  for (int i = threadIdx.x; i < l; i += blockDim.x) md = fmaxf(md, G[static_cast<int64_t>(i) * l + i]);
+  md = warp_max_o(md);
+  if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = md;
+  __syncthreads();
+  float mx = 0.f;
+#pragma unroll
+  for (int w = 0; w < 8; ++w) mx = fmaxf(mx, s_red[w]);
+  const float shift = shift_rel * mx;
+  const int h = chol_split_h_dev(l), m = l - h;
+  const SplitPtrs sp = split_ptrs(sc.w[blockIdx.y], l);
+  const int64_t n = static_cast<int64_t>(l) * l;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(e / l), j = static_cast<int>(e - static_cast<int64_t>(i) * l);
+    const float v = G[e] + (i == j ? shift : 0.f);
+    if (i < h) {
+      if (j < h) sp.G11[i * h + j] = v;
+    } else if (j < h) {
+      sp.G21[(i - h) * h + j] = v;
+    } else {
+      sp.S[(i - h) * m + (j - h)] = v;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) chol_split_assemble_kernel(CholBatch cb, SplitScratch sc, int l) {
+  float* __restrict__ Lo = cb.p[blockIdx.y].L;
+  const int h = chol_split_h_dev(l), m = l - h;
+  const SplitPtrs sp = split_ptrs(sc.w[blockIdx.y], l);
+  const int64_t n = static_cast<int64_t>(l) * l;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(e / l), j = static_cast<int>(e - static_cast<int64_t>(i) * l);
+    float v;
+    if (i < h) v = j < h ? sp.L11[i * h + j] : 0.f;
+    else v = j < h ? sp.L21[(i - h) * h + j] : sp.L22[(i - h) * m + (j - h)];
+    Lo[e] = v;
+  }
+}
+
+lramm_status launch_chol_split(CholBatch cb, SplitScratch sc, int l, float shift_rel, int* status, cudaStream_t s) {
+  if (!chol_split_supported(l)) return LRAMM_ERR_UNSUPPORTED;
+  const int h = chol_split_h(l), m = l - h;
+  const dim3 grid(static_cast<unsigned>(ceil_div(static_cast<int64_t>(l) * l, 256 * 8)), cb.n);
+  chol_split_prep_kernel<<<grid, 256, 0, s>>>(cb, sc, l, shift_rel);
+  LRAMM_TRY(last_launch());
+  CholBatch c1{}, c2{};
+  TrsmBatch t1{};
+  c1.n = c2.n = t1.n = cb.n;
+  for (int i = 0; i < cb.n; ++i) {
+    const SplitPtrs sp = split_ptrs(sc.w[i], l);
+    c1.p[i] = CholProb{sp.G11, sp.L11, cb.p[i].Xd};
+    t1.p[i] = TrsmProb{sp.G21, sp.L21, sp.L11, cb.p[i].Xd, m};
+    c2.p[i] = CholProb{sp.S, sp.L22, cb.p[i].Xd + static_cast<int64_t>(h / kCB) * kCB * kCB};
+  }
+  LRAMM_TRY(launch_chol3(c1, h, 0.f, status, s));
+  LRAMM_TRY(launch_trsm3(t1, h, s));
+  for (int i = 0; i < cb.n; ++i) {
+    const SplitPtrs sp = split_ptrs(sc.w[i], l);
+    LRAMM_TRY(sgemm(0, 1, m, m, h, -1.f, sp.L21, h, 0, sp.L21, h, 1.f, sp.S, m, s));   // S = G22 - L21 L21^T
+  }
+  LRAMM_TRY(launch_chol3(c2, m, 0.f, status, s));
+  chol_split_assemble_kernel<<<grid, 256, 0, s>>>(cb, sc, l);
   return last_launch();
 }
 

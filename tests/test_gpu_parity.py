@@ -231,11 +231,12 @@ def test_rsvd_matches_oracle(L, m, k, r, p, q, which):
 
 
 @pytest.mark.parametrize("m,k,r,p,q", [(900, 800, 200, 16, 1), (1100, 1024, 256, 16, 2), (1100, 1024, 272, 16, 1),
-                                       (1100, 1024, 300, 20, 1)])
+                                       (1100, 1024, 300, 20, 1), (1300, 1100, 380, 20, 1), (1500, 1300, 512, 32, 1)])
 def test_rsvd_wide_sketch_matches_oracle(L, m, k, r, p, q):
-    """l = 216, 272, 288, 320: the small SVD runs on 14- and 16-CTA clusters;
-    l = 288 is the largest blocked-Cholesky case, l = 320 takes the
-    column-panel Cholesky."""
+    """l = 216, 272, 288, 320, 400, 544: the small SVD runs on 14- and 16-CTA
+    clusters; l = 288 is the largest single-CTA blocked Cholesky, l = 320
+    takes the column-panel Cholesky, l = 400 and 544 the two-level
+    Cholesky (blocks of 224 + 176 and 288 + 256)."""
     X = workloads.lowrank(m, k, workloads.spectrum("poly1", min(m, k)), 600 + m).astype(np.float32)
     plan = L.Plan(m, m, k, r, p, q, seed=7)
     ws = plan.workspace()

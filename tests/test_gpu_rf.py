@@ -32,20 +32,29 @@ def dev(x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-def _case(m, k, n, seed):
+def _case(m, k, n, seed, spectrum="exp32"):
     rng = np.random.default_rng(seed)
     X = rng.standard_normal((m, k)).astype(np.float32)
-    W = workloads.lowrank(k, n, workloads.spectrum("exp32", min(k, n)), seed + 1).astype(np.float32)
+    W = workloads.lowrank(k, n, workloads.spectrum(spectrum, min(k, n)), seed + 1).astype(np.float32)
     G = rng.standard_normal((m, n)).astype(np.float32)
     return X, W, G
 
 
-SHAPES = [(96, 80, 112, 10, 4, 0), (200, 160, 150, 12, 4, 1), (128, 256, 192, 20, 8, 2), (64, 300, 257, 28, 4, 1)]
+SHAPES = [(96, 80, 112, 10, 4, 0), (200, 160, 150, 12, 4, 1), (128, 256, 192, 20, 8, 2), (64, 300, 257, 28, 4, 1),
+          (512, 900, 1000, 380, 20, 1)]
+
+
+def _spectrum(l):
+    """exp(-i/32) for the small sketches; for l = 400 the linear-layer weight's
+    spectrum exp(-i/128) + 1e-3 (with exp(-i/32), sigma_400 / sigma_0 = 4e-6:
+    the sketch is numerically rank-deficient in FP32 and CholeskyQR breaks
+    down)."""
+    return "exp128" if l > 64 else "exp32"
 
 
 @pytest.mark.parametrize("m,k,n,r,p,q", SHAPES)
 def test_rf_forward_fp32(L, m, k, n, r, p, q):
-    X, W, _ = _case(m, k, n, m + k + n)
+    X, W, _ = _case(m, k, n, m + k + n, _spectrum(r + p))
     plan = L.Plan(m, n, k, r, p, q, seed=7, prec=(0, 0, 0))
     ws = plan.workspace()
     C = L.rf_forward(plan, dev(X), dev(W), ws=ws).cpu().numpy().astype(np.float64)
@@ -56,7 +65,7 @@ def test_rf_forward_fp32(L, m, k, n, r, p, q):
 
 @pytest.mark.parametrize("m,k,n,r,p,q", SHAPES)
 def test_rf_backward_fp32(L, m, k, n, r, p, q):
-    X, W, G = _case(m, k, n, 3 * m + k)
+    X, W, G = _case(m, k, n, 3 * m + k, _spectrum(r + p))
     plan = L.Plan(m, n, k, r, p, q, seed=7, prec=(0, 0, 0))
     ws = plan.workspace()
     dX, dW = (t.cpu().numpy().astype(np.float64) for t in L.rf_backward(plan, dev(X), dev(W), dev(G), ws=ws))
