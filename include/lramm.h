@@ -116,7 +116,9 @@ typedef enum {
   LRAMM_K_E2 = 11,        /* QM E2                                            */
   LRAMM_K_E3 = 12,        /* QM E3 with the alpha/beta epilogue               */
   LRAMM_K_OTHER = 13,
-  LRAMM_K_COUNT = 14
+  LRAMM_K_BWD = 14,       /* range-finder backward: products with G, X, W, Q  */
+  LRAMM_K_ADJOINT = 15,   /* range-finder backward: thin-QR adjoints          */
+  LRAMM_K_COUNT = 16
 } lramm_kernel_kind;
 
 typedef struct lramm_plan_s* lramm_plan_t;
@@ -259,27 +261,45 @@ LRAMM_API lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const 
 LRAMM_API lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, const float* G,
                                          float* dX, float* dW, void* ws, size_t ws_bytes, void* stream);
 
-/* The INT8 QM product of Algorithm 2 on the tensor cores (tcgen05.mma
- * kind::f16; the INT8 codes lramm_quantize writes as bfloat16 values are
- * exact BF16 operands):
- *   acc(i,j) = sum_t L(i,t) Rt(j,t), L M x K (stride ldl), Rt N x K (stride ldr),
- *   summed exactly (each CTA adds at most 1024 products in FP32, where every
- *   partial sum is an exact integer; longer K is split across CTAs and the
- *   partials are added as 32-bit integers), then
+/* The QM product of Algorithm 2 on the tensor cores, on the codes
+ * lramm_quantize writes:
+ *   prec LRAMM_P_INT8: codes as bfloat16 values (exact BF16 operands),
+ *     tcgen05.mma kind::f16; each CTA adds at most 1024 products in FP32,
+ *     where every partial sum is an exact integer; longer K is split across
+ *     CTAs and the partials are added as 32-bit integers: exact.
+ *   prec LRAMM_P_INT4: codes as FP8 e4m3 bytes (|c| <= 7 are exact e4m3
+ *     values), kind::f8f6f4; FP32 sums of products <= 49: exact for
+ *     K < 342000 (larger K: LRAMM_ERR_UNSUPPORTED).
+ *   prec LRAMM_P_E4M3: e4m3 codes, kind::f8f6f4; FP32 sums.
+ *   acc(i,j) = sum_t L(i,t) Rt(j,t), L M x K (stride ldl), Rt N x K (stride ldr), then
  *   D(i,j) = alpha * fp32( fp32(acc) * fp32(sL[i or 0] * sR[j or 0]) ) + beta * C(i,j)
  * (FP32, stride ldd), as lramm_qgemm with out_kind 0.  per_row as in
- * lramm_qgemm.  K a multiple of 16; L and Rt 16-byte aligned with ldl, ldr
- * multiples of 8 (else LRAMM_ERR_UNSUPPORTED).  ws: device buffer of
- * lramm_qgemm_tc_ws_bytes(M, N, K) bytes, 256-byte aligned (first word: the
- * status word, LRAMM_ERR_TIMEOUT if a bounded wait expired; then the
- * split-K partials).  Asynchronous on `stream`. */
-LRAMM_API lramm_status lramm_qgemm_tc(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K,
+ * lramm_qgemm.  K a multiple of 16; L and Rt 16-byte aligned with row
+ * pitches (ldl, ldr times the code size) multiples of 16 bytes (else
+ * LRAMM_ERR_UNSUPPORTED).  ws: device buffer of
+ * lramm_qgemm_tc_ws_bytes(prec, M, N, K) bytes, 256-byte aligned (first
+ * word: the status word, LRAMM_ERR_TIMEOUT if a bounded wait expired; then
+ * the split-K partials).  Asynchronous on `stream`. */
+LRAMM_API lramm_status lramm_qgemm_tc(int32_t prec, const void* L, const void* Rt, int64_t M, int64_t N, int64_t K,
                                       int64_t ldl, int64_t ldr, int32_t per_row, const float* sL,
                                       const float* sR, float alpha, float beta, const float* C, int64_t ldc,
                                       float* D, int64_t ldd, void* ws, size_t ws_bytes, void* stream);
 
 /* Bytes of workspace lramm_qgemm_tc needs for an M x N x K product. */
-LRAMM_API size_t lramm_qgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K);
+LRAMM_API size_t lramm_qgemm_tc_ws_bytes(int32_t prec, int64_t M, int64_t N, int64_t K);
+
+/* C = alpha A B^T + beta C on the tensor cores with FP32 operands rounded
+ * to TF32 (tcgen05.mma kind::tf32, FP32 accumulation): the dense products
+ * with the l-column factors of the range-finder backward (dX = dT Q^T,
+ * dW = Q dP + ...).  A: M x K (stride lda), B: N x K (stride ldb), C: M x N
+ * (stride ldc), all FP32 row-major, C updated in place.  A and B 16-byte
+ * aligned, lda and ldb multiples of 4 (else LRAMM_ERR_UNSUPPORTED).  ws:
+ * lramm_tgemm_tc_ws_bytes(M, N, K) bytes, 256-byte aligned (status word,
+ * then split-K partials).  Asynchronous on `stream`. */
+LRAMM_API lramm_status lramm_tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda,
+                                      const float* B, int64_t ldb, float beta, float* C, int64_t ldc, void* ws,
+                                      size_t ws_bytes, void* stream);
+LRAMM_API size_t lramm_tgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K);
 
 /* The products of an operand with an l-column matrix that the range finder
  * runs (Sec. 2.2 sketch Y = X Omega, the power-iteration products, and the

@@ -58,9 +58,11 @@ _SIGS = {
                            _VP, _I64, _VP, _I64, _I32, _VP]),
     "lramm_rf_forward": (_I32, [_VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
     "lramm_rf_backward": (_I32, [_VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]),
-    "lramm_qgemm_tc": (_I32, [_VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _VP, _VP, _F, _F, _VP, _I64, _VP, _I64,
-                              _VP, ctypes.c_size_t, _VP]),
-    "lramm_qgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
+    "lramm_qgemm_tc": (_I32, [_I32, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _VP, _VP, _F, _F, _VP, _I64, _VP,
+                              _I64, _VP, ctypes.c_size_t, _VP]),
+    "lramm_qgemm_tc_ws_bytes": (ctypes.c_size_t, [_I32, _I64, _I64, _I64]),
+    "lramm_tgemm_tc": (_I32, [_I64, _I64, _I64, _F, _VP, _I64, _VP, _I64, _F, _VP, _I64, _VP, ctypes.c_size_t, _VP]),
+    "lramm_tgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
     "lramm_sketch_product": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _I32, _VP, ctypes.c_size_t,
                                     _VP]),
@@ -72,7 +74,7 @@ _SIGS = {
 }
 
 FLAG_TIMING = 1
-K_COUNT = 14
+K_COUNT = 16
 
 
 def load(path=LIB_PATH):
@@ -361,20 +363,40 @@ def quantize_noalloc(X, prec, per_row=False, ldcodes=None, codes=None, scales=No
     return codes, scales
 
 
-def qgemm_tc(Lc, Rc, sL, sR, per_row=True, alpha=1.0, beta=0.0, C=None, ws=None):
-    """INT8 QM product on the tensor cores (codes as lramm_quantize writes them, K-major)."""
+def qgemm_tc(Lc, Rc, sL, sR, per_row=True, alpha=1.0, beta=0.0, C=None, ws=None, prec=None):
+    """QM product on the tensor cores (codes as lramm_quantize writes them,
+    K-major): INT8 codes (bfloat16) by default for bfloat16 codes, E4M3 for
+    byte codes unless prec says INT4."""
     torch = _torch()
     _need_cuda(Lc, Rc, C)
+    if prec is None:
+        prec = P_INT8 if Lc.dtype == torch.bfloat16 else P_E4M3
     M, K = Lc.shape
     N = Rc.shape[0]
     out = torch.empty((M, N), dtype=torch.float32, device=Lc.device)
-    need = load().lramm_qgemm_tc_ws_bytes(M, N, K)
+    need = load().lramm_qgemm_tc_ws_bytes(prec, M, N, K)
     if ws is None or ws.numel() < need:
         ws = torch.zeros(need, dtype=torch.uint8, device=Lc.device)
-    _check(load().lramm_qgemm_tc(_ptr(Lc), _ptr(Rc), M, N, K, Lc.stride(0), Rc.stride(0), int(per_row),
+    _check(load().lramm_qgemm_tc(prec, _ptr(Lc), _ptr(Rc), M, N, K, Lc.stride(0), Rc.stride(0), int(per_row),
                                  _ptr(sL), _ptr(sR), alpha, beta, _ptr(C), C.stride(0) if C is not None else 0,
                                  _ptr(out), N, _ptr(ws), ws.numel(), _stream()), "lramm_qgemm_tc")
     return out
+
+
+def tgemm_tc(A, B, alpha=1.0, beta=0.0, C=None, ws=None):
+    """C = alpha A B^T + beta C on the tensor cores (FP32 operands as TF32); returns C."""
+    torch = _torch()
+    _need_cuda(A, B, C)
+    M, K = A.shape
+    N = B.shape[0]
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float32, device=A.device)
+    need = load().lramm_tgemm_tc_ws_bytes(M, N, K)
+    if ws is None or ws.numel() < need:
+        ws = torch.zeros(need, dtype=torch.uint8, device=A.device)
+    _check(load().lramm_tgemm_tc(M, N, K, alpha, _ptr(A), A.stride(0), _ptr(B), B.stride(0), beta, _ptr(C),
+                                 C.stride(0), _ptr(ws), ws.numel(), _stream()), "lramm_tgemm_tc")
+    return C
 
 
 def qgemm(Lc, Rc, prec, sL=None, sR=None, per_row=True, alpha=1.0, beta=0.0, C=None, raw=False):

@@ -157,10 +157,17 @@ void layout(lramm_plan_s* P) {
   P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
   P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
   {  // split-K partials of the tensor-core code products (E1 with long K)
-    size_t q = qgemm_tc_part_floats(r, r, P->kp);
-    q = std::max(q, qgemm_tc_part_floats(d.n, r, P->rp));
-    q = std::max(q, qgemm_tc_part_floats(d.m, d.n, P->rp));
-    q = std::max(q, qgemm_tc_part_floats(d.m, d.n, round_up(l, 16)));
+    auto qp = [](int prec, int64_t M, int64_t N, int64_t K) -> size_t {
+      return prec == LRAMM_P_F32 ? 0 : qgemm_tc_part_floats(prec, M, N, K);
+    };
+    size_t q = qp(d.prec[0], r, r, P->kp);
+    q = std::max(q, qp(d.prec[1], d.n, r, P->rp));
+    q = std::max(q, qp(d.prec[2], d.m, d.n, P->rp));
+    q = std::max(q, qp(d.prec[2], d.m, d.n, round_up(l, 16)));
+    // TF32 products of the range-finder form (K = l)
+    q = std::max(q, tgemm_tc_part_floats(d.m, d.n, l));
+    q = std::max(q, tgemm_tc_part_floats(d.m, d.k, l));
+    q = std::max(q, tgemm_tc_part_floats(d.k, d.n, l));
     P->qpart_floats = q;
     P->qpart = b.take(sizeof(float) * (q > 0 ? q : 4));
   }
@@ -458,13 +465,25 @@ lramm_status qr_adjoint(lramm_plan_s* P, void* ws, const float* Q, int64_t rows,
   return mul_linv(P, ws, L1, T2, rows, dY, s);
 }
 
-// One QM product on codes: the tensor-core kernel for INT8 codes (exact
-// integer sums, fused dequantisation), the SIMT kernel otherwise.
+// C = alpha A B^T + beta C (A: M x K, B: N x K, rows K-contiguous): TF32
+// tensor cores when the plan runs its operand products in TF32, FP32 SIMT
+// otherwise.
+lramm_status nt_product(lramm_plan_s* P, void* ws, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                        int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, cudaStream_t s) {
+  if (P->d.sketch == LRAMM_SKETCH_TF32 && tgemm_tc_supported(A, B, lda, ldb, M, N, K))
+    return tgemm_tc(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, at<float>(ws, P->qpart), P->qpart_floats,
+                    at<int>(ws, 0), s);
+  return sgemm(0, 1, M, N, K, alpha, A, lda, 0, B, ldb, beta, C, ldc, s);
+}
+
+// One QM product on codes: the tensor-core kernel (INT8 codes as BF16, INT4 /
+// E4M3 codes as FP8; fused dequantisation), the SIMT kernel where the
+// operands do not meet its alignment rules.
 lramm_status qm_product(lramm_plan_s* P, void* ws, const void* L, const void* R, int64_t M, int64_t N, int64_t K,
                         int64_t ldl, int64_t ldr, int prec, int per_row, const float* sL, const float* sR, float alpha,
                         float beta, const float* C, int64_t ldc, float* D, int64_t ldd, cudaStream_t s) {
   if (qgemm_tc_supported(prec, L, R, ldl, ldr, M, N, K))
-    return qgemm_tc(L, R, M, N, K, ldl, ldr, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, at<float>(ws, P->qpart),
+    return qgemm_tc(prec, L, R, M, N, K, ldl, ldr, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, at<float>(ws, P->qpart),
                     P->qpart_floats, at<int>(ws, 0), s);
   return qgemm(L, R, M, N, K, ldl, ldr, prec, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, 0, s);
 }
@@ -581,7 +600,8 @@ lramm_status lramm_timing_read(lramm_plan_t plan, float* ms, int32_t* launches) 
 
 const char* lramm_kernel_kind_name(int32_t kind) {
   static const char* names[LRAMM_K_COUNT] = {"omega", "sketch", "gram", "chol", "trsm", "rfactor", "svd",
-                                             "svdsort", "assemble", "quant", "e1", "e2", "e3", "other"};
+                                             "svdsort", "assemble", "quant", "e1", "e2", "e3", "other",
+                                             "backward", "qr_adjoint"};
   return (kind >= 0 && kind < LRAMM_K_COUNT) ? names[kind] : "unknown";
 }
 
@@ -765,7 +785,7 @@ lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, f
   TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, X, d.m, d.k, d.lda, sx.xbf, Q, T, s));
   TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, d.k, d.n, d.ldb, sw.xbf, Q, Pt, s));
   if (d.prec[2] == LRAMM_P_F32) {
-    TIMED(plan, LRAMM_K_E3, s, sgemm(0, 1, d.m, d.n, l, d.alpha, T, l, 0, Pt, l, d.beta, C, d.ldc, s));
+    TIMED(plan, LRAMM_K_E3, s, nt_product(plan, ws, d.m, d.n, l, d.alpha, T, l, Pt, l, d.beta, C, d.ldc, s));
     return LRAMM_OK;
   }
   const int per_row = d.scale == LRAMM_S_ROWCOL;
@@ -809,53 +829,78 @@ lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, 
   // dT = alpha G P^T (m x l), dP^T = alpha G^T T (n x l)
   TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, G, m, n, d.ldc, 0, Pt, dT, s));
   TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, G, m, n, d.ldc, 0, T, dPt, s));
-  LRAMM_TRY(launch_scale(dT, m * l, d.alpha, s));
-  LRAMM_TRY(launch_scale(dPt, n * l, d.alpha, s));
+  TIMED(plan, LRAMM_K_BWD, s, launch_scale(dT, m * l, d.alpha, s));
+  TIMED(plan, LRAMM_K_BWD, s, launch_scale(dPt, n * l, d.alpha, s));
   // dX = dT Q^T (m x k);  dW = Q dP (k x n)
-  LRAMM_TRY(sgemm(0, 1, m, k, l, 1.f, dT, l, 0, Q, l, 0.f, dX, k, s));
-  LRAMM_TRY(sgemm(0, 1, k, n, l, 1.f, Q, l, 0, dPt, l, 0.f, dW, n, s));
+  TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, m, k, l, 1.f, dT, l, Q, l, 0.f, dX, k, s));
+  TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, Q, l, dPt, l, 0.f, dW, n, s));
   // dQ = X^T dT + W dP^T (k x l)
   TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, X, m, k, d.lda, sx.xbf, dT, dQ, s));
-  LRAMM_TRY(sgemm(0, 0, k, l, n, 1.f, W, d.ldb, 0, dPt, l, 1.f, dQ, l, s));
+  float* tmp = at<float>(ws, plan->tB);
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, W, k, n, d.ldb, sw.xbf, dPt, tmp, s));
+  TIMED(plan, LRAMM_K_BWD, s, launch_axpy(dQ, tmp, k * l, 1.f, s));
   // back through the power iterations (Omega fixed)
   for (int i = d.q; i >= 1; --i) {
     const int o = 2 * i;                 // Y_i = W Z_i, Q_i = orth(Y_i)
     const bool two = i == d.q;           // the last basis took two CholeskyQR passes
-    LRAMM_TRY(qr_adjoint(plan, ws, Qi(i), k, bl_slot(plan, ws, o, 0), two ? bl_slot(plan, ws, o, 1) : nullptr, dQ,
-                         dY, s));
-    LRAMM_TRY(sgemm(0, 1, k, n, l, 1.f, dY, l, 0, Zi(i), l, 1.f, dW, n, s));     // dW += dY Z_i^T
+    TIMED(plan, LRAMM_K_ADJOINT, s,
+          qr_adjoint(plan, ws, Qi(i), k, bl_slot(plan, ws, o, 0), two ? bl_slot(plan, ws, o, 1) : nullptr, dQ, dY, s));
+    TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, dY, l, Zi(i), l, 1.f, dW, n, s));   // dW += dY Z_i^T
     TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, k, n, d.ldb, sw.xbf, dY, dZ, s));   // dZ = W^T dY
-    LRAMM_TRY(qr_adjoint(plan, ws, Zi(i), n, bl_slot(plan, ws, o - 1, 0), nullptr, dZ, dY, s));   // dY' (n x l)
-    LRAMM_TRY(sgemm(0, 1, k, n, l, 1.f, Qi(i - 1), l, 0, dY, l, 1.f, dW, n, s));   // dW += Q_{i-1} dY'^T
+    TIMED(plan, LRAMM_K_ADJOINT, s, qr_adjoint(plan, ws, Zi(i), n, bl_slot(plan, ws, o - 1, 0), nullptr, dZ, dY, s));
+    TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, Qi(i - 1), l, dY, l, 1.f, dW, n, s));  // dW += Q_{i-1} dY'^T
     TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, W, k, n, d.ldb, sw.xbf, dY, dQ, s));   // dQ = W dY'
   }
-  LRAMM_TRY(qr_adjoint(plan, ws, Qi(0), k, bl_slot(plan, ws, 0, 0), d.q == 0 ? bl_slot(plan, ws, 0, 1) : nullptr, dQ,
-                       dY, s));
+  TIMED(plan, LRAMM_K_ADJOINT, s,
+        qr_adjoint(plan, ws, Qi(0), k, bl_slot(plan, ws, 0, 0), d.q == 0 ? bl_slot(plan, ws, 0, 1) : nullptr, dQ, dY, s));
   const float* Om = at<float>(ws, sw.S->omega);
-  return sgemm(0, 1, k, n, l, 1.f, dY, l, 0, Om, l, 1.f, dW, n, s);   // dW += dY_0 Omega^T
+  TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, dY, l, Om, l, 1.f, dW, n, s));   // dW += dY_0 Omega^T
+  return LRAMM_OK;
 }
 
-size_t lramm_qgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K) {
-  if (M <= 0 || N <= 0 || K <= 0) return kAlign;
-  return kAlign + sizeof(float) * qgemm_tc_part_floats(M, N, K);
+size_t lramm_qgemm_tc_ws_bytes(int32_t prec, int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0 || (prec != LRAMM_P_INT8 && prec != LRAMM_P_INT4 && prec != LRAMM_P_E4M3))
+    return kAlign;
+  return kAlign + sizeof(float) * qgemm_tc_part_floats(prec, M, N, K);
 }
 
-lramm_status lramm_qgemm_tc(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
+lramm_status lramm_qgemm_tc(int32_t prec, const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
                             int64_t ldr, int32_t per_row, const float* sL, const float* sR, float alpha, float beta,
                             const float* C, int64_t ldc, float* D, int64_t ldd, void* ws, size_t ws_bytes,
                             void* stream) {
+  if (prec != LRAMM_P_INT8 && prec != LRAMM_P_INT4 && prec != LRAMM_P_E4M3) return LRAMM_ERR_INVALID_ARG;
   if (M < 0 || N < 0 || K < 0 || K % 16 || ldl < K || ldr < K || ldd < N) return LRAMM_ERR_INVALID_ARG;
   if (M == 0 || N == 0) return LRAMM_OK;
   if (!L || !Rt || !D || !sL || !sR || (beta != 0.f && (!C || ldc < N))) return LRAMM_ERR_INVALID_ARG;
-  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) || ws_bytes < lramm_qgemm_tc_ws_bytes(M, N, K))
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) || ws_bytes < lramm_qgemm_tc_ws_bytes(prec, M, N, K))
     return LRAMM_ERR_WORKSPACE;
-  if (!qgemm_tc_supported(LRAMM_P_INT8, L, Rt, ldl, ldr, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
+  if (!qgemm_tc_supported(prec, L, Rt, ldl, ldr, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int* st = static_cast<int*>(ws);
   LRAMM_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int) * 4, s));
   float* part = reinterpret_cast<float*>(static_cast<char*>(ws) + kAlign);
-  return qgemm_tc(L, Rt, M, N, K, ldl, ldr, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, part,
+  return qgemm_tc(prec, L, Rt, M, N, K, ldl, ldr, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, part,
                   (ws_bytes - kAlign) / sizeof(float), st, s);
+}
+
+size_t lramm_tgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K) {
+  if (M <= 0 || N <= 0 || K <= 0) return kAlign;
+  return kAlign + sizeof(float) * tgemm_tc_part_floats(M, N, K);
+}
+
+lramm_status lramm_tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda, const float* B,
+                            int64_t ldb, float beta, float* C, int64_t ldc, void* ws, size_t ws_bytes, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || lda < K || ldb < K || ldc < N) return LRAMM_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return LRAMM_OK;
+  if (!A || !B || !C) return LRAMM_ERR_INVALID_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) || ws_bytes < lramm_tgemm_tc_ws_bytes(M, N, K))
+    return LRAMM_ERR_WORKSPACE;
+  if (K == 0 || !tgemm_tc_supported(A, B, lda, ldb, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* st = static_cast<int*>(ws);
+  LRAMM_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int) * 4, s));
+  float* part = reinterpret_cast<float*>(static_cast<char*>(ws) + kAlign);
+  return tgemm_tc(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, part, (ws_bytes - kAlign) / sizeof(float), st, s);
 }
 
 }  // extern "C"

@@ -172,17 +172,25 @@ lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s);
 lramm_status launch_copyltu(const float* M, float* out, int l, cudaStream_t s);
 lramm_status launch_identity(float* I, int l, cudaStream_t s);
 lramm_status launch_scale(float* x, int64_t n, float a, cudaStream_t s);
+lramm_status launch_axpy(float* y, const float* x, int64_t n, float a, cudaStream_t s);   // y += a x
 // Largest l the small-SVD kernels accept.
 int jacobi_max_l();
 
-// qgemm_tc.cu -- INT8 code products on the tensor cores (codes as BF16,
-// exact integer sums), fused dequantisation epilogue.
+// qgemm_tc.cu -- code products on the tensor cores: INT8 codes as BF16
+// (exact integer sums), INT4 / E4M3 codes as FP8 e4m3; fused dequantisation
+// epilogue.  tgemm_tc: C = alpha A B^T + beta C with FP32 operands as TF32
+// (A: M x K, B: N x K, both K-major).
 bool qgemm_tc_supported(int prec, const void* L, const void* R, int64_t ldl, int64_t ldr, int64_t M, int64_t N,
                         int64_t K);
-size_t qgemm_tc_part_floats(int64_t M, int64_t N, int64_t K);
-lramm_status qgemm_tc(const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl, int64_t ldr,
-                      int per_row, const float* sL, const float* sR, float alpha, float beta, const float* C,
-                      int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats, int* status,
+size_t qgemm_tc_part_floats(int prec, int64_t M, int64_t N, int64_t K);
+lramm_status qgemm_tc(int prec, const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                      int64_t ldr, int per_row, const float* sL, const float* sR, float alpha, float beta,
+                      const float* C, int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats,
+                      int* status, cudaStream_t s);
+bool tgemm_tc_supported(const float* A, const float* B, int64_t lda, int64_t ldb, int64_t M, int64_t N, int64_t K);
+size_t tgemm_tc_part_floats(int64_t M, int64_t N, int64_t K);
+lramm_status tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda, const float* B,
+                      int64_t ldb, float beta, float* C, int64_t ldc, float* part, size_t part_floats, int* status,
                       cudaStream_t s);
 // sketch_tc.cu -- X B / X^T B on the tensor cores (TF32, FP32 accumulate)
 bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void* B);

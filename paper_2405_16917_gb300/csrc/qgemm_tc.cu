@@ -1,28 +1,32 @@
-// The integer factor products of the quantised chain (Algorithm 2 inside
-// Algorithm 3: E1 = QM(V^T W), E2 = QM(E1 Z~), E3 = QM(U~ E2)) on the
-// 5th-generation tensor cores.  INT8 codes are held as BF16 values (every
-// integer of magnitude <= 127 is exact in BF16) and multiplied with
-// tcgen05.mma kind::f16, FP32 accumulation in TMEM.  A product of two codes
-// is at most 127^2 = 16129, so a sum of at most 1024 of them stays below
-// 2^24 and every partial sum is an integer FP32 represents exactly: each CTA
-// sums at most 1024 products (16 K blocks of 64), so its accumulator holds
-// the exact integer.
+// Products on the 5th-generation tensor cores, FP32 accumulation in TMEM:
 //
-//   out[i][j] = sum_k L[i][k] R[j][k]      (L: M x K codes, R: N x K codes, both K-major)
+//   acc[i][j] = sum_k L[i][k] R[j][k]      (L: M x K, R: N x K, both K-major)
 //
-// One chunk of K (the usual case, K <= 1024): the epilogue dequantises in
-// the reference order fp32(fp32(acc) * fp32(sL[i] * sR[j])), applies
-// alpha and beta C and writes D.  Several chunks: each CTA writes its exact
-// partial sums and a reduction kernel adds them as 32-bit integers (fixed
-// order) before the same epilogue.
+// in three operand kinds:
+//  * BF16 codes (INT8 factors of Algorithm 2 / 3): every integer of
+//    magnitude <= 127 is exact in BF16; tcgen05.mma kind::f16.  A product
+//    of two codes is at most 127^2 = 16129, so a sum of at most 1024 of
+//    them stays below 2^24: each CTA sums at most 1024 products (16 K blocks
+//    of 64), its accumulator holds the exact integer, and longer K is split
+//    across CTAs whose partials are added as 32-bit integers.
+//  * FP8 e4m3 codes (E4M3 factors, and INT4 factors, whose integer codes
+//    |c| <= 7 are exact e4m3 values); kind::f8f6f4.  INT4 sums are exact
+//    (|sum| <= 49 K < 2^24 for K < 342,000); e4m3 sums are FP32 sums.
+//  * FP32 operands as TF32 (the dense products of the range-finder
+//    backward); kind::tf32, no scales.
 //
-// Warp roles per CTA (192 threads): warp 0 issues TMA loads of 128 x 64 and
-// BN x 64 code tiles (128-byte swizzle) into a ring of shared-memory stages;
-// one thread of warp 1 issues the MMAs (M = 128, N = BN <= 256, K = 16 per
-// instruction); warps 2..5 read the accumulator back with tcgen05.ld (TMEM
-// lane = output row) and run the epilogue.  All waits are bounded; on expiry
-// the kernel latches LRAMM_ERR_TIMEOUT, drains its own copies and MMAs,
-// frees TMEM and returns.
+// Epilogue, codes: the reference dequantisation order
+// fp32(fp32(acc) * fp32(sL[i] * sR[j])), then alpha and beta C; TF32:
+// alpha acc + beta C.  Several K chunks: each CTA writes its partial sums
+// and a reduction kernel adds them in a fixed order before the epilogue.
+//
+// Warp roles per CTA (192 threads): warp 0 issues TMA loads of 128 x 128-byte
+// and BN x 128-byte K tiles (128-byte swizzle) into a ring of shared-memory
+// stages; one thread of warp 1 issues the MMAs (M = 128, N = BN <= 256, 32
+// bytes of K per instruction); warps 2..5 read the accumulator back with
+// tcgen05.ld (TMEM lane = output row) and run the epilogue.  All waits are
+// bounded; on expiry the kernel latches LRAMM_ERR_TIMEOUT, drains its own
+// copies and MMAs, frees TMEM and returns.
 #include "tc_common.cuh"
 
 namespace lramm {
@@ -31,10 +35,14 @@ namespace {
 using namespace tc;
 
 constexpr int kQM = 128;         // output rows per CTA = TMEM lanes
-constexpr int kQK = 64;          // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int kQKB = 128;        // K bytes per stage: one 128-byte swizzle row
 constexpr int kQThreads = 192;
 constexpr int kQMaxStages = 8;
-constexpr int kQChunkBlocks = 16;  // 16 x 64 = 1024 products per exact FP32 partial
+constexpr int kQChunkBlocks = 16;  // BF16 codes: 16 x 64 = 1024 products per exact FP32 partial
+
+enum { kKindBF16 = 0, kKindFP8 = 1, kKindTF32 = 2 };
+
+__host__ __device__ constexpr int kind_elem_bytes(int kind) { return kind == kKindBF16 ? 2 : (kind == kKindFP8 ? 1 : 4); }
 
 struct QtcParams {
   int64_t M, N;
@@ -49,32 +57,54 @@ struct QtcParams {
   int64_t ldc;
   float* D;
   int64_t ldd;
-  float* part;   // chunks > 1: chunks x M x N exact partial sums
+  float* part;   // chunks > 1: chunks x M x N partial sums
+  int scaled;    // codes: dequantise with sL, sR; TF32: no scales
   int* status;
 };
 
-// kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16
-// (bits 7-9 and 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
-// 17, M >> 4 at bit 24.
-__device__ __forceinline__ uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+// Instruction descriptor: D F32 (bits 4-5 = 1); A and B formats at bits
+// 7-9 and 10-12 (kind::f16: BF16 = 1; kind::f8f6f4: E4M3 = 0; kind::tf32:
+// TF32 = 2); both K-major (bits 15, 16 = 0); N >> 3 at bit 17, M >> 4 at
+// bit 24.
+template <int KIND>
+__device__ __forceinline__ uint32_t idesc_kind(int M, int N) {
+  const uint32_t fmt = KIND == kKindBF16 ? 1u : (KIND == kKindFP8 ? 0u : 2u);
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+template <int KIND>
+__device__ __forceinline__ void mma_kind(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+  if (KIND == kKindBF16)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else if (KIND == kKindFP8)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
+template <int KIND>
 __global__ void __launch_bounds__(kQThreads, 2)
 qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR, QtcParams p) {
+  constexpr int kStageK = kQKB / kind_elem_bytes(KIND);   // K elements per stage
   extern __shared__ uint8_t q_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q_smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
@@ -126,7 +156,7 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
         break;
       }
       mbar_expect_tx(&full_bar[s], tx_bytes);
-      const int k0 = (kb0 + i) * kQK;
+      const int k0 = (kb0 + i) * kStageK;
       tma_load_2d(sA + static_cast<size_t>(s) * p.a_bytes, &tmL, &full_bar[s], k0, static_cast<int>(m0));
       tma_load_2d(sB + static_cast<size_t>(s) * p.b_bytes, &tmR, &full_bar[s], k0, static_cast<int>(n0));
       ++issued;
@@ -142,7 +172,7 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    const uint32_t idesc = idesc_bf16(kQM, p.bn);
+    const uint32_t idesc = idesc_kind<KIND>(kQM, p.bn);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
       if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
@@ -154,9 +184,9 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
       const uint32_t a_base = smem_u32(sA + static_cast<size_t>(s) * p.a_bytes);
       const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * p.b_bytes);
 #pragma unroll
-      for (int kk = 0; kk < kQK / 16; ++kk)  // 16 BF16 (32 bytes) of K per instruction
-        mma_bf16(tmem, kmajor_sw128_desc(a_base + kk * 32), kmajor_sw128_desc(b_base + kk * 32), idesc,
-                 (i > 0 || kk > 0) ? 1u : 0u);
+      for (int kk = 0; kk < kQKB / 32; ++kk)  // 32 bytes of K per instruction
+        mma_kind<KIND>(tmem, kmajor_sw128_desc(a_base + kk * 32), kmajor_sw128_desc(b_base + kk * 32), idesc,
+                       (i > 0 || kk > 0) ? 1u : 0u);
       mma_commit(&empty_bar[s]);
     }
     mma_commit(&tmem_bar);
@@ -167,7 +197,7 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
     if (p.chunks == 1) {
       for (int j = et; j < p.bn; j += 128) {
         const int64_t col = n0 + j;
-        sR_sh[j] = col < p.N ? (p.per_row ? p.sR[col] : p.sR[0]) : 0.f;
+        sR_sh[j] = col < p.N ? (!p.scaled ? 1.f : (p.per_row ? p.sR[col] : p.sR[0])) : 0.f;
       }
     }
     epi_bar();
@@ -179,7 +209,9 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
     // columns of one row (128 bytes).
     float* T = tr_sh[q];
     const int64_t rbase = m0 + q * 32;
-    const float sl_own = (p.chunks == 1 && rbase + lane < p.M) ? (p.per_row ? p.sL[rbase + lane] : p.sL[0]) : 0.f;
+    const float sl_own = (p.chunks == 1 && rbase + lane < p.M)
+                             ? (!p.scaled ? 1.f : (p.per_row ? p.sL[rbase + lane] : p.sL[0]))
+                             : 0.f;
     for (int c0 = 0; c0 < p.bn; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
@@ -199,7 +231,7 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
         if (p.chunks > 1) {
           p.part[(static_cast<int64_t>(chunk) * p.M + row) * p.N + col] = x;
         } else {
-          float o = __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl, sr)));
+          float o = p.scaled ? __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl, sr))) : __fmul_rn(p.alpha, x);
           if (p.beta != 0.f) o = fmaf(p.beta, p.C[row * p.ldc + col], o);
           p.D[row * p.ldd + col] = o;
         }
@@ -215,17 +247,32 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
   }
 }
 
-// D = dequantised sum over chunks: tot = sum_c int(part[c]) (exact, fixed
-// order), then fp32(fp32(tot) * fp32(sL * sR)), alpha and beta C.
+// D = dequantised sum over chunks: tot = sum_c part[c] in a fixed order (as
+// 32-bit integers for BF16 codes, whose total may pass 2^24; in FP32
+// otherwise), then fp32(fp32(tot) * fp32(sL * sR)) (or tot unscaled), alpha
+// and beta C.
+template <bool INT_SUM>
 __global__ void qgemm_tc_reduce_kernel(QtcParams p) {
   const int64_t total = p.M * p.N;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int64_t i = e / p.N, j = e - i * p.N;
-    int tot = 0;
-    for (int c = 0; c < p.chunks; ++c) tot += __float2int_rn(p.part[static_cast<int64_t>(c) * total + e]);
-    const float sp = __fmul_rn(p.per_row ? p.sL[i] : p.sL[0], p.per_row ? p.sR[j] : p.sR[0]);
-    float o = __fmul_rn(p.alpha, __fmul_rn(static_cast<float>(tot), sp));
+    float totf;
+    if (INT_SUM) {
+      int tot = 0;
+      for (int c = 0; c < p.chunks; ++c) tot += __float2int_rn(p.part[static_cast<int64_t>(c) * total + e]);
+      totf = static_cast<float>(tot);
+    } else {
+      totf = 0.f;
+      for (int c = 0; c < p.chunks; ++c) totf += p.part[static_cast<int64_t>(c) * total + e];
+    }
+    float o;
+    if (p.scaled) {
+      const float sp = __fmul_rn(p.per_row ? p.sL[i] : p.sL[0], p.per_row ? p.sR[j] : p.sR[0]);
+      o = __fmul_rn(p.alpha, __fmul_rn(totf, sp));
+    } else {
+      o = __fmul_rn(p.alpha, totf);
+    }
     if (p.beta != 0.f) o = fmaf(p.beta, p.C[i * p.ldc + j], o);
     p.D[i * p.ldd + j] = o;
   }
@@ -234,73 +281,137 @@ __global__ void qgemm_tc_reduce_kernel(QtcParams p) {
 constexpr int kQSmemBudget = 232448 - 4096;  // opt-in maximum minus alignment slack and static shared memory
 
 struct QtcShape {
-  int kblocks, kb_per_chunk, chunks, bn;
+  int kblocks, kb_per_chunk, chunks, bn, stages;
   int64_t mtiles, ntiles;
 };
 
-QtcShape qtc_shape(int64_t M, int64_t N, int64_t K) {
+QtcShape qtc_shape(int kind, int64_t M, int64_t N, int64_t K) {
   QtcShape sh{};
-  sh.kblocks = static_cast<int>(ceil_div(K, kQK));
+  const int stage_k = kQKB / kind_elem_bytes(kind);
+  sh.kblocks = static_cast<int>(ceil_div(K, stage_k));
   sh.bn = static_cast<int>(N >= 256 ? 256 : round_up(N, 16));
-  // short K and a wide output (E3: m x n, K = r): 128-column tiles with a
-  // two-stage ring, so that two or three CTAs share an SM and one CTA's
-  // epilogue (the HBM-bound part) overlaps another's loads and MMAs
-  if (N >= 1024 && K <= 512) sh.bn = 128;
+  // short K and a wide output (E3: m x n, K = r; the rank-l updates of the
+  // range-finder backward): 128-column tiles with a short ring, so that two
+  // or three CTAs share an SM and one CTA's epilogue (the HBM-bound part)
+  // overlaps another's loads and MMAs
+  const bool wide = N >= 1024 && K * kind_elem_bytes(kind) <= 2048;
+  if (wide) sh.bn = 128;
   sh.mtiles = ceil_div(M, kQM);
   sh.ntiles = ceil_div(N, sh.bn);
   const int64_t tiles = sh.mtiles * sh.ntiles;
-  int kpc = kQChunkBlocks;
+  // chunk limit: exactness for BF16 codes, none otherwise
+  const int cap = kind == kKindBF16 ? kQChunkBlocks : sh.kblocks;
+  int kpc = cap;
   if (tiles < 64) {  // few output tiles: split K further for parallelism (at least 4 blocks per CTA)
-    const int64_t want = ceil_div(sh.kblocks * tiles, 128);
-    kpc = static_cast<int>(want < 4 ? 4 : (want > kQChunkBlocks ? kQChunkBlocks : want));
+    const int64_t want = ceil_div(static_cast<int64_t>(sh.kblocks) * tiles, 128);
+    kpc = static_cast<int>(want < 4 ? 4 : (want > cap ? cap : want));
   }
   if (kpc > sh.kblocks) kpc = sh.kblocks;
   if (kpc < 1) kpc = 1;
   sh.kb_per_chunk = kpc;
   sh.chunks = static_cast<int>(ceil_div(sh.kblocks, kpc));
+  const int stage_bytes = (kQM + sh.bn) * kQKB;
+  int st = (kQSmemBudget - 1024) / stage_bytes;
+  if (st > kQMaxStages) st = kQMaxStages;
+  if (st > sh.kb_per_chunk) st = sh.kb_per_chunk;
+  if (st < 2) st = 2;
+  // a 2-stage ring (32 KB per stage at BN = 128) leaves room for two CTAs
+  // per SM next to the epilogue's 17 KB of static shared memory
+  if (wide || (sh.kb_per_chunk <= 8 && sh.bn <= 128)) st = 2;
+  sh.stages = st;
   return sh;
 }
 
-}  // namespace
+int prec_kind(int prec) { return prec == LRAMM_P_INT8 ? kKindBF16 : kKindFP8; }
 
-bool qgemm_tc_supported(int prec, const void* L, const void* R, int64_t ldl, int64_t ldr, int64_t M, int64_t N,
-                        int64_t K) {
-  if (prec != LRAMM_P_INT8) return false;
+bool tc_operands_ok(int kind, const void* L, const void* R, int64_t ldl, int64_t ldr, int64_t M, int64_t N,
+                    int64_t K) {
   if (M <= 0 || N <= 0 || K <= 0 || M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return false;
+  const int eb = kind_elem_bytes(kind);
   // TMA: 16-byte aligned bases and row pitches
-  return (reinterpret_cast<uintptr_t>(L) % 16) == 0 && (reinterpret_cast<uintptr_t>(R) % 16) == 0 && ldl % 8 == 0 &&
-         ldr % 8 == 0 && ldl >= K && ldr >= K;
+  return (reinterpret_cast<uintptr_t>(L) % 16) == 0 && (reinterpret_cast<uintptr_t>(R) % 16) == 0 &&
+         (ldl * eb) % 16 == 0 && (ldr * eb) % 16 == 0 && ldl >= K && ldr >= K;
 }
 
-size_t qgemm_tc_part_floats(int64_t M, int64_t N, int64_t K) {
-  const QtcShape sh = qtc_shape(M, N, K);
-  return sh.chunks > 1 ? static_cast<size_t>(sh.chunks) * M * N : 0;
-}
-
-lramm_status qgemm_tc(const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl, int64_t ldr,
-                      int per_row, const float* sL, const float* sR, float alpha, float beta, const float* C,
-                      int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats, int* status,
-                      cudaStream_t s) {
-  if (!qgemm_tc_supported(LRAMM_P_INT8, L, R, ldl, ldr, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
-  const QtcShape sh = qtc_shape(M, N, K);
-  if (sh.chunks > 1 && (!part || part_floats < static_cast<size_t>(sh.chunks) * M * N)) return LRAMM_ERR_WORKSPACE;
+lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                       int64_t ldr, QtcParams p, cudaStream_t s) {
+  const QtcShape sh = qtc_shape(kind, M, N, K);
+  if (sh.chunks > 1 && (!p.part)) return LRAMM_ERR_WORKSPACE;
   if (sh.mtiles > 65535 || sh.chunks > 65535) return LRAMM_ERR_UNSUPPORTED;
-  QtcParams p{};
   p.M = M;
   p.N = N;
   p.kblocks = sh.kblocks;
   p.kb_per_chunk = sh.kb_per_chunk;
   p.chunks = sh.chunks;
   p.bn = sh.bn;
-  p.a_bytes = kQM * kQK * 2;
-  p.b_bytes = static_cast<uint32_t>(sh.bn) * kQK * 2;
-  p.stages = static_cast<int>((kQSmemBudget - 1024) / (p.a_bytes + p.b_bytes));
-  if (p.stages > kQMaxStages) p.stages = kQMaxStages;
-  if (p.stages > sh.kb_per_chunk) p.stages = sh.kb_per_chunk < 2 ? 2 : sh.kb_per_chunk;
-  if (sh.kb_per_chunk <= 8 && sh.bn <= 128) p.stages = 2;
+  p.a_bytes = kQM * kQKB;
+  p.b_bytes = static_cast<uint32_t>(sh.bn) * kQKB;
+  p.stages = sh.stages;
   uint32_t tc = 32;
   while (tc < static_cast<uint32_t>(sh.bn)) tc <<= 1;
   p.tmem_cols = tc;
+  const int eb = kind_elem_bytes(kind);
+  const CUtensorMapDataType dt = kind == kKindBF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : kind == kKindFP8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                                    : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const uint32_t box_k = static_cast<uint32_t>(kQKB / eb);
+  CUtensorMap mL, mR;
+  if (!make_map_2d(&mL, dt, L, K, M, ldl * eb, box_k, kQM, CU_TENSOR_MAP_SWIZZLE_128B)) return LRAMM_ERR_CUDA;
+  if (!make_map_2d(&mR, dt, R, K, N, ldr * eb, box_k, static_cast<uint32_t>(sh.bn), CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
+  const dim3 grid(static_cast<unsigned>(sh.ntiles), static_cast<unsigned>(sh.mtiles), static_cast<unsigned>(sh.chunks));
+  switch (kind) {
+    case kKindBF16:
+      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      qgemm_tc_kernel<kKindBF16><<<grid, kQThreads, smem, s>>>(mL, mR, p);
+      break;
+    case kKindFP8:
+      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      qgemm_tc_kernel<kKindFP8><<<grid, kQThreads, smem, s>>>(mL, mR, p);
+      break;
+    default:
+      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem));
+      qgemm_tc_kernel<kKindTF32><<<grid, kQThreads, smem, s>>>(mL, mR, p);
+      break;
+  }
+  LRAMM_TRY(last_launch());
+  if (sh.chunks > 1) {
+    int64_t g = ceil_div(M * N, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    if (kind == kKindBF16)
+      qgemm_tc_reduce_kernel<true><<<static_cast<unsigned>(g), 256, 0, s>>>(p);
+    else
+      qgemm_tc_reduce_kernel<false><<<static_cast<unsigned>(g), 256, 0, s>>>(p);
+    LRAMM_TRY(last_launch());
+  }
+  return LRAMM_OK;
+}
+
+}  // namespace
+
+bool qgemm_tc_supported(int prec, const void* L, const void* R, int64_t ldl, int64_t ldr, int64_t M, int64_t N,
+                        int64_t K) {
+  if (prec != LRAMM_P_INT8 && prec != LRAMM_P_INT4 && prec != LRAMM_P_E4M3) return false;
+  if (prec == LRAMM_P_INT4 && K >= 342000) return false;   // exact FP32 sums of products <= 49
+  return tc_operands_ok(prec_kind(prec), L, R, ldl, ldr, M, N, K);
+}
+
+size_t qgemm_tc_part_floats(int prec, int64_t M, int64_t N, int64_t K) {
+  const QtcShape sh = qtc_shape(prec_kind(prec), M, N, K);
+  return sh.chunks > 1 ? static_cast<size_t>(sh.chunks) * M * N : 0;
+}
+
+lramm_status qgemm_tc(int prec, const void* L, const void* R, int64_t M, int64_t N, int64_t K, int64_t ldl,
+                      int64_t ldr, int per_row, const float* sL, const float* sR, float alpha, float beta,
+                      const float* C, int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats,
+                      int* status, cudaStream_t s) {
+  if (!qgemm_tc_supported(prec, L, R, ldl, ldr, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
+  if (part_floats < qgemm_tc_part_floats(prec, M, N, K)) return LRAMM_ERR_WORKSPACE;
+  QtcParams p{};
   p.per_row = per_row;
   p.sL = sL;
   p.sR = sR;
@@ -311,27 +422,37 @@ lramm_status qgemm_tc(const void* L, const void* R, int64_t M, int64_t N, int64_
   p.D = D;
   p.ldd = ldd;
   p.part = part;
+  p.scaled = 1;
   p.status = status;
+  return launch_tc(prec_kind(prec), L, R, M, N, K, ldl, ldr, p, s);
+}
 
-  CUtensorMap mL, mR;
-  if (!make_map_2d(&mL, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L, K, M, ldl * 2, kQK, kQM, CU_TENSOR_MAP_SWIZZLE_128B))
-    return LRAMM_ERR_CUDA;
-  if (!make_map_2d(&mR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R, K, N, ldr * 2, kQK, static_cast<uint32_t>(sh.bn),
-                   CU_TENSOR_MAP_SWIZZLE_128B))
-    return LRAMM_ERR_CUDA;
-  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  qgemm_tc_kernel<<<dim3(static_cast<unsigned>(sh.ntiles), static_cast<unsigned>(sh.mtiles),
-                         static_cast<unsigned>(sh.chunks)),
-                    kQThreads, smem, s>>>(mL, mR, p);
-  LRAMM_TRY(last_launch());
-  if (sh.chunks > 1) {
-    int64_t g = ceil_div(M * N, 256);
-    if (g > 152 * 8) g = 152 * 8;
-    qgemm_tc_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(p);
-    LRAMM_TRY(last_launch());
-  }
-  return LRAMM_OK;
+bool tgemm_tc_supported(const float* A, const float* B, int64_t lda, int64_t ldb, int64_t M, int64_t N, int64_t K) {
+  return tc_operands_ok(kKindTF32, A, B, lda, ldb, M, N, K);
+}
+
+size_t tgemm_tc_part_floats(int64_t M, int64_t N, int64_t K) {
+  const QtcShape sh = qtc_shape(kKindTF32, M, N, K);
+  return sh.chunks > 1 ? static_cast<size_t>(sh.chunks) * M * N : 0;
+}
+
+lramm_status tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda, const float* B,
+                      int64_t ldb, float beta, float* C, int64_t ldc, float* part, size_t part_floats, int* status,
+                      cudaStream_t s) {
+  if (!tgemm_tc_supported(A, B, lda, ldb, M, N, K)) return LRAMM_ERR_UNSUPPORTED;
+  if (part_floats < tgemm_tc_part_floats(M, N, K)) return LRAMM_ERR_WORKSPACE;
+  QtcParams p{};
+  p.per_row = 0;
+  p.alpha = alpha;
+  p.beta = beta;
+  p.C = C;
+  p.ldc = ldc;
+  p.D = C;
+  p.ldd = ldc;
+  p.part = part;
+  p.scaled = 0;
+  p.status = status;
+  return launch_tc(kKindTF32, A, B, M, N, K, lda, ldb, p, s);
 }
 
 }  // namespace lramm

@@ -911,6 +911,11 @@ __global__ void scale_kernel(float* __restrict__ x, int64_t n, float a) {
     x[e] *= a;
 }
 
+__global__ void axpy_kernel(float* __restrict__ y, const float* __restrict__ x, int64_t n, float a) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    y[e] = fmaf(a, x[e], y[e]);
+}
+
 static unsigned small_grid(int64_t n) {
   int64_t g = ceil_div(n, 256);
   return (unsigned)(g < 1 ? 1 : (g > 1216 ? 1216 : g));
@@ -926,6 +931,12 @@ lramm_status launch_identity(float* I, int l, cudaStream_t s) {
 lramm_status launch_scale(float* x, int64_t n, float a, cudaStream_t s) {
   if (n <= 0) return LRAMM_OK;
   scale_kernel<<<small_grid(n), 256, 0, s>>>(x, n, a);
+  return last_launch();
+}
+
+lramm_status launch_axpy(float* y, const float* x, int64_t n, float a, cudaStream_t s) {
+  if (n <= 0) return LRAMM_OK;
+  axpy_kernel<<<small_grid(n), 256, 0, s>>>(y, x, n, a);
   return last_launch();
 }
 

@@ -85,11 +85,15 @@ def test_calls_reject_bad_arguments_without_gpu_work(L):
     assert lib.lramm_matmul(p.handle, fake, fake, nul, fake, ctypes.c_void_p(300), p.ws_bytes, nul) == 3
     assert lib.lramm_qgemm(fake, fake, 4, 4, 17, 17, 17, 1, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, 0,
                            nul) == 1                                                   # K % 16
-    assert lib.lramm_qgemm_tc(fake, fake, 4, 4, 17, 17, 17, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, fake, 4096,
+    assert lib.lramm_qgemm_tc(1, fake, fake, 4, 4, 17, 17, 17, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, fake, 4096,
                               nul) == 1                                                # K % 16
-    assert lib.lramm_qgemm_tc(fake, fake, 4, 4, 16, 16, 16, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, nul, 0,
+    assert lib.lramm_qgemm_tc(1, fake, fake, 4, 4, 16, 16, 16, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, nul, 0,
                               nul) == 3                                                # no workspace
-    assert lib.lramm_qgemm_tc_ws_bytes(256, 256, 4096) > lib.lramm_qgemm_tc_ws_bytes(256, 256, 256)
+    assert lib.lramm_qgemm_tc(0, fake, fake, 4, 4, 16, 16, 16, 1, fake, fake, 1.0, 0.0, nul, 0, fake, 4, fake, 4096,
+                              nul) == 1                                                # F32 is not a code
+    assert lib.lramm_qgemm_tc_ws_bytes(1, 256, 256, 4096) > lib.lramm_qgemm_tc_ws_bytes(1, 256, 256, 256)
+    assert lib.lramm_tgemm_tc(4, 4, 8, 1.0, fake, 4, fake, 8, 0.0, fake, 4, fake, 4096, nul) == 1   # lda < K
+    assert lib.lramm_tgemm_tc(4, 4, 8, 1.0, fake, 8, fake, 8, 0.0, fake, 4, nul, 0, nul) == 3       # no workspace
     assert lib.lramm_quantize(fake, 4, 8, 8, 0, 1, fake, 8, fake, nul, nul) == 1      # F32 is not a code
     assert lib.lramm_philox_words(1, 0, 4, ctypes.c_void_p(4), nul) == 1               # misaligned
     assert lib.lramm_status_str(5).decode().startswith("non-positive")

@@ -1,10 +1,13 @@
-"""The tensor-core INT8 QM product (tcgen05, codes as BF16) against the oracle.
+"""The tensor-core QM products (tcgen05) against the oracle.
 
-The integer sum must be exact (FP32 partials of at most 1024 products are
-exact integers; longer K is split and added as 32-bit integers), so with
-unit scales the output is fp32(exact sum), compared bit for bit; with real
-scales the dequantised value is fp32(fp32(acc) * fp32(sL * sR)) as the
-oracle computes it.
+INT8 codes as BF16 (kind::f16): the integer sum must be exact (FP32
+partials of at most 1024 products are exact integers; longer K is split and
+added as 32-bit integers), so with unit scales the output is fp32(exact
+sum), compared bit for bit; with real scales the dequantised value is
+fp32(fp32(acc) * fp32(sL * sR)) as the oracle computes it.  INT4 codes as
+e4m3 bytes (kind::f8f6f4): exact in the same sense.  E4M3 codes: FP32
+accumulation, within the FP32 summation bound.  FP32 operands as TF32
+(kind::tf32): within the TF32 rounding bound.
 """
 import numpy as np
 import pytest
@@ -97,3 +100,79 @@ def test_alpha_beta(L):
     v = (np.float32(0.75) * qm).astype(np.float32)
     ref = np.float64(-1.5) * C.astype(np.float64) + v.astype(np.float64)   # exact FMA, one rounding below
     assert np.all(np.abs(D - ref) <= 2.0 ** -24 * np.abs(ref) + 1e-30)
+
+
+# ---------------------------------------------------------------- FP8 kinds
+from tests import pins  # noqa: E402
+
+
+def e4m3(vals):
+    return dev(np.asarray(vals, dtype=np.float32)).to(torch.float8_e4m3fn)
+
+
+FP8_SHAPES = [(70, 45, 48), (129, 65, 4096), (1, 1, 16), (300, 260, 400), (4096, 256, 128), (1000, 1100, 400),
+              (256, 256, 8192)]
+
+
+@pytest.mark.parametrize("M,N,K", FP8_SHAPES)
+def test_int4_codes_exact(L, M, N, K):
+    """INT4 codes |c| <= 7 are exact e4m3 values; sums of products <= 49 are exact in FP32."""
+    rng = np.random.default_rng(M + 3 * N + 5 * K)
+    a = rng.integers(-7, 8, (M, K))
+    b = rng.integers(-7, 8, (N, K))
+    D = np_(L.qgemm_tc(e4m3(a), e4m3(b), ones(M), ones(N), prec=L.P_INT4))
+    assert np.array_equal(D, oracle.quant.code_product(a, b.T).astype(np.float32))
+
+
+def test_int4_worst_case(L):
+    K = 65536
+    a = np.full((2, K), 7.0)
+    a[1, ::2] = -7.0
+    b = np.full((2, K), -7.0)
+    D = np_(L.qgemm_tc(e4m3(a), e4m3(b), ones(2), ones(2), prec=L.P_INT4))
+    assert np.array_equal(D, oracle.quant.code_product(a, b.T).astype(np.float32))
+
+
+@pytest.mark.parametrize("M,N,K", [(96, 80, 2048), (300, 260, 400), (1000, 1100, 400)])
+def test_e4m3_codes_within_fp32_sum_bound(L, M, N, K):
+    rng = np.random.default_rng(M + N + K)
+    grid = pins.e4m3_decode_all()
+    a = rng.choice(grid, (M, K))
+    b = rng.choice(grid, (N, K))
+    D = np_(L.qgemm_tc(e4m3(a), e4m3(b), ones(M), ones(N), prec=L.P_E4M3)).astype(np.float64)
+    ref = oracle.quant.code_product(a, b.T)
+    mag = np.abs(a) @ np.abs(b).T
+    assert np.all(np.abs(D - ref) <= K * 2.0 ** -24 * mag + 2.0 ** -24 * np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", [2, 3])
+@pytest.mark.parametrize("per_row", [True, False])
+def test_fp8_dequantised_matches_oracle(L, prec, per_row):
+    rng = np.random.default_rng(30 + prec + per_row)
+    M, K, N = 300, 400, 280
+    Lm = (rng.standard_normal((M, K)) * np.exp(rng.uniform(-2, 2, (M, 1)))).astype(np.float32)
+    R = (rng.standard_normal((K, N)) * np.exp(rng.uniform(-2, 2, (1, N)))).astype(np.float32)
+    cL, sL = L.quantize(dev(Lm), prec, per_row, ldcodes=K)
+    cR, sR = L.quantize(dev(np.ascontiguousarray(R.T)), prec, per_row, ldcodes=K)
+    D = np_(L.qgemm_tc(cL, cR, sL, sR, per_row=per_row, prec=prec))
+    ref = oracle.quant.qm(Lm, R, prec, 0 if per_row else 1)
+    if prec == 2:
+        assert np.array_equal(D, ref)
+    else:
+        assert oracle.lramm.rel_fro(D, ref) < 1e-6
+
+
+# ---------------------------------------------------------------- TF32 products
+@pytest.mark.parametrize("M,N,K", [(70, 45, 40), (512, 1000, 400), (4096, 4096, 400), (64, 64, 4096), (1, 300, 8)])
+@pytest.mark.parametrize("beta", [0.0, 1.0])
+def test_tgemm_within_tf32_bound(L, M, N, K, beta):
+    """C = alpha A B^T + beta C with operands as TF32 (10 explicit mantissa
+    bits): |error| <= 2^-9 (|A| |B|^T) + FP32 summation, elementwise."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    C0 = rng.standard_normal((M, N)).astype(np.float32)
+    C = L.tgemm_tc(dev(A), dev(B), alpha=0.5, beta=beta, C=dev(C0.copy()))
+    ref = 0.5 * (A.astype(np.float64) @ B.astype(np.float64).T) + beta * C0
+    mag = 0.5 * (np.abs(A).astype(np.float64) @ np.abs(B).astype(np.float64).T) + abs(beta) * np.abs(C0)
+    assert np.all(np.abs(np_(C) - ref) <= (2.0 ** -9 + K * 2.0 ** -23) * mag)
