@@ -83,7 +83,8 @@ typedef struct lramm_desc {
   int64_t lda, ldb, ldc;  /* row strides of A, B and of C / D (elements)         */
   int32_t a_type, b_type; /* lramm_dtype of A and B                              */
   int32_t r;              /* target rank, 1 <= r                                 */
-  int32_t p;              /* oversampling: l = r + p sketch columns, l <= 320,
+  int32_t p;              /* oversampling: l = r + p sketch columns, l <= 576
+                             (the SVD form: l <= 544, the small SVD's limit),
                              l <= min(m, k) and l <= min(k, n)                   */
   int32_t q;              /* power iterations, 0 <= q <= 16                      */
   uint64_t seed;          /* Philox4x32-10 key; Omega_A is stream 0, Omega_B 1   */
@@ -307,18 +308,24 @@ LRAMM_API size_t lramm_tgemm_tc_ws_bytes(int64_t M, int64_t N, int64_t K);
  *   transpose = 0: out = X B    (X rows x cols, B cols x l, out rows x l)
  *   transpose = 1: out = X^T B  (B rows x l, out cols x l)
  * X has row stride ldx and type x_type; B and out are dense row-major FP32.
- * sketch = LRAMM_SKETCH_F32: FP32 SIMT product (compensated accumulation);
- * LRAMM_SKETCH_TF32: tcgen05 tensor cores, TF32 inputs, FP32 accumulation
- * (needs FP32 X, l and ldx divisible by 4, 16-byte aligned X and B, l <= 512,
- * else LRAMM_ERR_UNSUPPORTED) with ws of lramm_sketch_ws_bytes(l) bytes for
- * split-K partials (256-byte aligned; its first word is the status word). */
+ * sketch = LRAMM_SKETCH_F32: FP32 SIMT product (compensated accumulation).
+ * LRAMM_SKETCH_TF32 / LRAMM_SKETCH_BF16, tcgen05 tensor cores, FP32
+ * accumulation:
+ *   FP32 X: TF32 inputs (kind::tf32; l and ldx divisible by 4, l <= 512);
+ *   BF16 X: X exact (kind::f16), B split into BF16 parts B_hi + B_lo (TF32
+ *     mode, 16 significant bits of B) or rounded to B_hi (BF16 mode); l
+ *     divisible by 4, ldx by 8, any l (blocks of <= 512 columns).
+ * X and B 16-byte aligned, else LRAMM_ERR_UNSUPPORTED.  ws:
+ * lramm_sketch_ws_bytes(rows, cols, l) bytes, 256-byte aligned (status word,
+ * split-K partials, the BF16 parts of B). */
 LRAMM_API lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t cols, int64_t ldx,
                                             int32_t x_type, int32_t transpose, const float* B, int64_t l,
                                             float* out, int32_t sketch, void* ws, size_t ws_bytes,
                                             void* stream);
 
-/* Bytes of workspace lramm_sketch_product needs for an l-column product. */
-LRAMM_API size_t lramm_sketch_ws_bytes(int64_t l);
+/* Bytes of workspace lramm_sketch_product needs for an l-column product of a
+ * rows x cols operand. */
+LRAMM_API size_t lramm_sketch_ws_bytes(int64_t rows, int64_t cols, int64_t l);
 
 /* Bytes of workspace lramm_quantize needs in per-tensor mode. */
 LRAMM_API size_t lramm_quant_ws_bytes(void);

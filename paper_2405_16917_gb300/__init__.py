@@ -66,7 +66,7 @@ _SIGS = {
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
     "lramm_sketch_product": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _I32, _VP, ctypes.c_size_t,
                                     _VP]),
-    "lramm_sketch_ws_bytes": (ctypes.c_size_t, [_I64]),
+    "lramm_sketch_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
     "lramm_quantize_noalloc": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _VP]),
     "lramm_noalloc_scratch_bytes": (ctypes.c_size_t, []),
     "lramm_timing_read": (_I32, [_VP, ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32)]),
@@ -314,7 +314,7 @@ def sketch_product(X, B, transpose=False, sketch=SKETCH_TF32):
     l = B.shape[1]
     out = torch.empty((cols if transpose else rows, l), dtype=torch.float32, device=X.device)
     lib = load()
-    ws = torch.zeros(lib.lramm_sketch_ws_bytes(l), dtype=torch.uint8, device=X.device)
+    ws = torch.zeros(lib.lramm_sketch_ws_bytes(rows, cols, l), dtype=torch.uint8, device=X.device)
     _check(lib.lramm_sketch_product(_ptr(X), rows, cols, X.stride(0), _dtype_code(X), int(transpose), _ptr(B), l,
                                     _ptr(out), sketch, _ptr(ws), ws.numel(), _stream()), "lramm_sketch_product")
     st = int(ws[:4].view(torch.int32).item())

@@ -60,6 +60,7 @@ struct lramm_plan_s {
   size_t sV, sW, sE1, sZ, sU, sE2;
   size_t amax;
   size_t part, gpart, qpart;
+  size_t bsplit, bsplit_bytes;   // BF16 parts of the l-column operand (BF16 A or B)
   size_t qpart_floats;
   // range-finder form: codes / scales of T and P^T; the range-finder chain
   // kept for the backward (Q_0..Q_q, Z_1..Z_q, the Cholesky factors of every
@@ -156,6 +157,10 @@ void layout(lramm_plan_s* P) {
   P->amax = b.take(kAlign);
   P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
   P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
+  P->bsplit_bytes = (d.a_type == LRAMM_BF16 || d.b_type == LRAMM_BF16)
+                        ? sketch_bf_split_bytes(std::max(d.m, std::max(d.k, d.n)), (int)l)
+                        : 0;
+  P->bsplit = P->bsplit_bytes ? b.take(P->bsplit_bytes) : 0;
   {  // split-K partials of the tensor-core code products (E1 with long K)
     auto qp = [](int prec, int64_t M, int64_t N, int64_t K) -> size_t {
       return prec == LRAMM_P_F32 ? 0 : qgemm_tc_part_floats(prec, M, N, K);
@@ -240,7 +245,11 @@ lramm_status check_ws(const lramm_plan_s* P, void* ws, size_t ws_bytes) {
 lramm_status x_product(lramm_plan_s* P, void* ws, int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx,
                        int xbf, const float* B, float* out, cudaStream_t s) {
   const int l = P->l;
-  if (P->d.sketch == LRAMM_SKETCH_TF32 && sketch_tc_supported(xbf, ldx, l, X, B))
+  const int sk = P->d.sketch;
+  if (xbf && sk != LRAMM_SKETCH_F32 && P->bsplit_bytes && sketch_bf_supported(ldx, l, X, B))
+    return sketch_bf(a_mn, X, rows, cols, ldx, B, l, sk == LRAMM_SKETCH_TF32 ? 2 : 1, out, at<float>(ws, P->part),
+                     sketch_tc_part_floats(l), at<void>(ws, P->bsplit), P->bsplit_bytes, at<int>(ws, 0), s);
+  if (sk != LRAMM_SKETCH_F32 && sketch_tc_supported(xbf, ldx, l, X, B))
     return sketch_tc(a_mn, X, rows, cols, ldx, xbf, B, l, out, at<float>(ws, P->part),
                      sketch_tc_part_floats(l), at<int>(ws, 0), s);
   if (a_mn) return sgemm(1, 0, cols, l, rows, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
@@ -431,9 +440,20 @@ lramm_status range_finder_side(lramm_plan_s* P, const SideRun& sd, void* ws, boo
   return LRAMM_OK;
 }
 
+// C = alpha A B^T + beta C (A: M x K, B: N x K, rows K-contiguous): TF32
+// tensor cores when the plan runs its operand products in TF32, FP32 SIMT
+// otherwise.
+lramm_status nt_product(lramm_plan_s* P, void* ws, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                        int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, cudaStream_t s) {
+  if (P->d.sketch != LRAMM_SKETCH_F32 && tgemm_tc_supported(A, B, lda, ldb, M, N, K))
+    return tgemm_tc(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, at<float>(ws, P->qpart), P->qpart_floats,
+                    at<int>(ws, 0), s);
+  return sgemm(0, 1, M, N, K, alpha, A, lda, 0, B, ldb, beta, C, ldc, s);
+}
+
 // Right-multiplication by L^-1 (L lower triangular, l x l): out = X L^-1
 // (rows x l), through L^-T = I L^-T (the panel triangular solve on the
-// identity) and one product.
+// identity) and one product X (L^-T)^T.
 lramm_status mul_linv(lramm_plan_s* P, void* ws, const float* L, const float* X, int64_t rows, float* out,
                       cudaStream_t s) {
   const int l = P->l;
@@ -444,7 +464,7 @@ lramm_status mul_linv(lramm_plan_s* P, void* ws, const float* L, const float* X,
   tb.n = 1;
   tb.p[0] = SmallProb{I, LiT, L, l};
   LRAMM_TRY(launch_trsm_panel(tb, l, s));
-  return sgemm(0, 1, rows, l, l, 1.f, X, l, 0, LiT, l, 0.f, out, l, s);
+  return nt_product(P, ws, rows, l, l, 1.f, X, l, LiT, l, 0.f, out, l, s);
 }
 
 // Adjoint of the thin QR Y = Q R (R = L1^T, or L2^T L1^T after two
@@ -456,24 +476,14 @@ lramm_status qr_adjoint(lramm_plan_s* P, void* ws, const float* Q, int64_t rows,
   const int l = P->l;
   float* M = at<float>(ws, P->tM);
   float* Mc = at<float>(ws, P->tMc);
-  LRAMM_TRY(sgemm(1, 0, l, l, rows, -1.f, dQ, l, 0, Q, l, 0.f, M, l, s));
+  LRAMM_TRY(x_product(P, ws, 1, dQ, rows, l, l, 0, Q, M, s));   // M = dQ^T Q
   LRAMM_TRY(launch_copyltu(M, Mc, l, s));
-  LRAMM_TRY(sgemm(0, 0, rows, l, l, 1.f, Q, l, 0, Mc, l, 1.f, dQ, l, s));
+  // dQ += Q copyltu(-M); copyltu(M) is symmetric, so it serves as the N x K operand
+  LRAMM_TRY(nt_product(P, ws, rows, l, l, -1.f, Q, l, Mc, l, 1.f, dQ, l, s));
   if (!L2) return mul_linv(P, ws, L1, dQ, rows, dY, s);
   float* T2 = at<float>(ws, P->tY2);
   LRAMM_TRY(mul_linv(P, ws, L2, dQ, rows, T2, s));
   return mul_linv(P, ws, L1, T2, rows, dY, s);
-}
-
-// C = alpha A B^T + beta C (A: M x K, B: N x K, rows K-contiguous): TF32
-// tensor cores when the plan runs its operand products in TF32, FP32 SIMT
-// otherwise.
-lramm_status nt_product(lramm_plan_s* P, void* ws, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
-                        int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc, cudaStream_t s) {
-  if (P->d.sketch == LRAMM_SKETCH_TF32 && tgemm_tc_supported(A, B, lda, ldb, M, N, K))
-    return tgemm_tc(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, at<float>(ws, P->qpart), P->qpart_floats,
-                    at<int>(ws, 0), s);
-  return sgemm(0, 1, M, N, K, alpha, A, lda, 0, B, ldb, beta, C, ldc, s);
 }
 
 // One QM product on codes: the tensor-core kernel (INT8 codes as BF16, INT4 /
@@ -709,8 +719,9 @@ lramm_status lramm_gaussian(uint64_t seed, uint32_t stream_id, int64_t rows, int
 
 size_t lramm_quant_ws_bytes(void) { return kAlign; }
 
-size_t lramm_sketch_ws_bytes(int64_t l) {
-  return l < 1 ? 0 : kAlign + sizeof(float) * sketch_tc_part_floats((int)l);
+size_t lramm_sketch_ws_bytes(int64_t rows, int64_t cols, int64_t l) {
+  if (l < 1 || rows < 1 || cols < 1) return 0;
+  return kAlign + sizeof(float) * sketch_tc_part_floats((int)l) + sketch_bf_split_bytes(std::max(rows, cols), (int)l);
 }
 
 lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t cols, int64_t ldx, int32_t x_type,
@@ -718,15 +729,22 @@ lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t cols, int
                                   void* ws, size_t ws_bytes, void* stream) {
   if (rows < 1 || cols < 1 || ldx < cols || l < 1 || l > 4096 || !X || !B || !out) return LRAMM_ERR_INVALID_ARG;
   if ((x_type != LRAMM_F32 && x_type != LRAMM_BF16) || (transpose != 0 && transpose != 1)) return LRAMM_ERR_INVALID_ARG;
-  if (sketch != LRAMM_SKETCH_F32 && sketch != LRAMM_SKETCH_TF32) return LRAMM_ERR_INVALID_ARG;
+  if (sketch < LRAMM_SKETCH_F32 || sketch > LRAMM_SKETCH_BF16) return LRAMM_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int xbf = x_type == LRAMM_BF16;
-  if (sketch == LRAMM_SKETCH_TF32) {
-    if (!sketch_tc_supported(xbf, ldx, (int)l, X, B)) return LRAMM_ERR_UNSUPPORTED;
-    if (!ws || ws_bytes < lramm_sketch_ws_bytes(l) || reinterpret_cast<uintptr_t>(ws) % kAlign)
+  if (sketch != LRAMM_SKETCH_F32) {
+    if (!ws || ws_bytes < lramm_sketch_ws_bytes(rows, cols, l) || reinterpret_cast<uintptr_t>(ws) % kAlign)
       return LRAMM_ERR_WORKSPACE;
-    return sketch_tc(transpose, X, rows, cols, ldx, xbf, B, (int)l, out, at<float>(ws, kAlign),
-                     sketch_tc_part_floats((int)l), at<int>(ws, 0), s);
+    float* part = at<float>(ws, kAlign);
+    const size_t pf = sketch_tc_part_floats((int)l);
+    if (xbf) {
+      if (!sketch_bf_supported(ldx, (int)l, X, B)) return LRAMM_ERR_UNSUPPORTED;
+      void* split = at<void>(ws, kAlign + sizeof(float) * pf);
+      return sketch_bf(transpose, X, rows, cols, ldx, B, (int)l, sketch == LRAMM_SKETCH_TF32 ? 2 : 1, out, part, pf,
+                       split, sketch_bf_split_bytes(std::max(rows, cols), (int)l), at<int>(ws, 0), s);
+    }
+    if (!sketch_tc_supported(xbf, ldx, (int)l, X, B)) return LRAMM_ERR_UNSUPPORTED;
+    return sketch_tc(transpose, X, rows, cols, ldx, xbf, B, (int)l, out, part, pf, at<int>(ws, 0), s);
   }
   if (transpose) return sgemm(1, 0, cols, l, rows, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
   return sgemm(0, 0, rows, l, cols, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);

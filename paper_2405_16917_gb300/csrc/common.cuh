@@ -195,6 +195,13 @@ lramm_status tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float*
 // sketch_tc.cu -- X B / X^T B on the tensor cores (TF32, FP32 accumulate)
 bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void* B);
 size_t sketch_tc_part_floats(int l);
+// BF16 X: B split into BF16 parts (nb = 2: hi + lo; 1: hi only), kind::f16;
+// split: sketch_bf_split_bytes(K, l) bytes of scratch for the parts.
+bool sketch_bf_supported(int64_t ldx, int l, const void* X, const void* B);
+size_t sketch_bf_split_bytes(int64_t K, int l);
+lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, const float* B, int l,
+                       int nb, float* out, float* part, size_t part_floats, void* split, size_t split_bytes,
+                       int* status, cudaStream_t s);
 lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, int xbf, const float* B,
                        int l, float* out, float* part, size_t part_floats, int* status, cudaStream_t s);
 

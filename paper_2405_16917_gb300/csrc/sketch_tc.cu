@@ -18,6 +18,16 @@
 // Every mbarrier wait is bounded; on expiry the kernel latches
 // LRAMM_ERR_TIMEOUT, stops issuing, waits (bounded) for its own copies and
 // MMAs in flight, frees its TMEM and returns.
+//
+// BF16 operands X (sketch_bf_kernel): X is read as stored (BF16, exact
+// tensor-core operands, kind::f16) and B is split once into BF16 parts
+// B = B_hi + B_lo (B_hi = bf16(B), B_lo = bf16(B - B_hi), 16 significant
+// bits together) with two MMAs per K step, or rounded to B_hi alone (one
+// MMA, the LRAMM_SKETCH_BF16 arithmetic).  Stages of 32 K: X K-major with
+// the 64-byte swizzle (a_mn = 0) or MN-major with the 128-byte swizzle
+// (a_mn = 1), B parts MN-major with the 128-byte swizzle in 64-column
+// chunks.  l > 512 (more than the 512 TMEM columns) is split into column
+// blocks of at most 512, one grid slice each.
 #include "tc_common.cuh"
 
 namespace lramm {
@@ -201,6 +211,203 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------------------
+// BF16 X (see the file comment).
+constexpr int kFK = 32;        // K per stage (BF16)
+constexpr int kFAtom = 64;     // BF16 elements per 128-byte MN row
+constexpr int kFChunk = kFAtom * kFK * 2;   // bytes of one 64-column x 32-K chunk
+
+struct BfParams {
+  int64_t M, K;
+  int l, lout;          // columns of this launch's output block, row stride of out
+  int npad;             // B parts' padded width (multiple of 64)
+  int ncols, n1, n2;    // columns per CTA (<= 512), MMA widths (n1 <= 256)
+  int nb;               // B parts: 1 (B_hi) or 2 (B_hi + B_lo)
+  int a_mn;
+  int64_t kblocks;
+  int kb_per_split;
+  int stages;
+  uint32_t a_bytes, b_bytes, tmem_cols;
+  float* out;
+  int* status;
+};
+
+// K-major, 64-byte swizzle (layout type 4): rows of 32 BF16 along K, 8-row
+// atoms 512 bytes apart; a K step of 16 advances 32 bytes in the row.
+__device__ __forceinline__ uint64_t kmajor64_desc(uint32_t saddr) { return smem_desc(saddr, 16, 512, 4); }
+// MN-major, 128-byte swizzle (type 2): K rows of 64 BF16 along MN, 8-row
+// atoms 1024 bytes apart (SBO), 64-column chunks kFChunk bytes apart (LBO);
+// a K step of 16 rows advances 2048 bytes.
+__device__ __forceinline__ uint64_t mnmajor_bf_desc(uint32_t saddr) { return smem_desc(saddr, kFChunk, 1024, 2); }
+
+__device__ __forceinline__ uint32_t idesc_bf(int M, int N, int a_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (static_cast<uint32_t>(a_mn) << 15) | (1u << 16) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+sketch_bf_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmBh,
+                 const __grid_constant__ CUtensorMap tmBl, BfParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + static_cast<size_t>(p.stages) * p.a_bytes;
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kBM;
+  const int split = blockIdx.y;
+  const int c0 = blockIdx.z * p.ncols;              // first output column of this CTA
+  const int ncols = min(p.ncols, p.l - c0);
+  const int64_t kb0 = static_cast<int64_t>(split) * p.kb_per_split;
+  const int64_t kb1 = min(p.kblocks, kb0 + p.kb_per_split);
+  const int nkb = static_cast<int>(kb1 - kb0);
+  const int nchunks = (ncols + kFAtom - 1) / kFAtom;
+  const int n1 = ncols <= 256 ? ((ncols + 15) / 16) * 16 : 256;
+  const int n2 = ncols <= 256 ? 0 : ((ncols - 256 + 15) / 16) * 16;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tmem_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t part_bytes = static_cast<uint32_t>(nchunks) * kFChunk;   // one B part of one stage
+  const uint32_t tx_bytes = p.a_bytes + static_cast<uint32_t>(p.nb) * part_bytes;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (i >= p.stages && !mbar_wait(&empty_bar[s], ((i / p.stages) & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], tx_bytes);
+      const int k0 = static_cast<int>((kb0 + i) * kFK);
+      uint8_t* a_dst = sA + static_cast<size_t>(s) * p.a_bytes;
+      if (p.a_mn) {
+        for (int j = 0; j < kBM / kFAtom; ++j)
+          tma_load_2d(a_dst + j * kFChunk, &tmX, &full_bar[s], static_cast<int>(m0) + j * kFAtom, k0);
+      } else {
+        tma_load_2d(a_dst, &tmX, &full_bar[s], k0, static_cast<int>(m0));
+      }
+      uint8_t* b_dst = sB + static_cast<size_t>(s) * p.b_bytes;
+      for (int j = 0; j < nchunks; ++j) {
+        tma_load_2d(b_dst + j * kFChunk, &tmBh, &full_bar[s], c0 + j * kFAtom, k0);
+        if (p.nb > 1) tma_load_2d(b_dst + part_bytes + j * kFChunk, &tmBl, &full_bar[s], c0 + j * kFAtom, k0);
+      }
+      ++issued;
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      const int first = issued > p.stages ? issued - p.stages : 0;
+      for (int i = first; i < issued; ++i) {
+        volatile int zero = 0;
+        mbar_wait(&full_bar[i % p.stages], (i / p.stages) & 1, &zero);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t id1 = idesc_bf(kBM, n1, p.a_mn);
+    const uint32_t id2 = n2 ? idesc_bf(kBM, n2, p.a_mn) : 0u;
+    const uint32_t seg2 = static_cast<uint32_t>(256 / kFAtom) * kFChunk;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(sA + static_cast<size_t>(s) * p.a_bytes);
+      const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * p.b_bytes);
+#pragma unroll
+      for (int kk = 0; kk < kFK / 16; ++kk) {  // 16 BF16 of K per instruction
+        const uint64_t ad = p.a_mn ? mnmajor_bf_desc(a_base + kk * 2048) : kmajor64_desc(a_base + kk * 32);
+        const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
+        for (int b = 0; b < p.nb; ++b) {
+          const uint32_t bb = b_base + b * part_bytes + kk * 2048;
+          mma_bf(tmem, ad, mnmajor_bf_desc(bb), id1, (acc | b) ? 1u : 0u);
+          if (n2) mma_bf(tmem + 256, ad, mnmajor_bf_desc(bb + seg2), id2, (acc | b) ? 1u : 0u);
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&tmem_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lanes 32q .. 32q+31 are rows m0 + 32q + lane
+    const int q = warp & 3;
+    volatile int zero = 0;
+    const bool ok = mbar_wait(&tmem_bar, 0, &zero);
+    tc_fence_after();
+    const int64_t row = m0 + q * 32 + lane;
+    float* dst = p.out + (static_cast<int64_t>(split) * p.M + row) * p.lout + c0;
+    for (int cc = 0; cc < ncols; cc += 32) {
+      float v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(cc), v);
+      if (!ok) continue;
+      if (row < p.M) {
+        const int nv = min(32, ncols - cc);  // multiple of 4
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          if (j < nv) *reinterpret_cast<float4*>(dst + cc + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+    }
+    if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// B (K x l FP32, row-major) -> B_hi, B_lo (K x npad BF16, zero padded).
+__global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l, int npad, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo) {
+  const int64_t n = K * npad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t k = e / npad;
+    const int j = static_cast<int>(e - k * npad);
+    const float b = j < l ? B[k * l + j] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(b);
+    hi[e] = h;
+    if (lo) lo[e] = __float2bfloat16_rn(b - __bfloat162float(h));
+  }
+}
+
 // out = sum over splits of part[s] (fixed order), n4 float4 per split.
 __global__ void split_reduce_kernel(const float4* __restrict__ part, int splits, int64_t n4, float4* __restrict__ out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
@@ -232,6 +439,86 @@ bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void*
 }
 
 size_t sketch_tc_part_floats(int l) { return static_cast<size_t>(152) * kBM * l; }
+
+bool sketch_bf_supported(int64_t ldx, int l, const void* X, const void* B) {
+  return l % 4 == 0 && l >= 4 && ldx % 8 == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0 &&
+         (reinterpret_cast<uintptr_t>(B) % 16) == 0;
+}
+
+size_t sketch_bf_split_bytes(int64_t K, int l) { return 2 * sizeof(__nv_bfloat16) * K * round_up(l, kFAtom) + 256; }
+
+lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, const float* B, int l,
+                       int nb, float* out, float* part, size_t part_floats, void* split, size_t split_bytes,
+                       int* status, cudaStream_t s) {
+  if (!sketch_bf_supported(ldx, l, X, B) || (nb != 1 && nb != 2)) return LRAMM_ERR_UNSUPPORTED;
+  const int64_t M = a_mn ? cols : rows, K = a_mn ? rows : cols;
+  if (M <= 0 || K <= 0) return LRAMM_OK;
+  if (M > INT32_MAX || K > INT32_MAX) return LRAMM_ERR_UNSUPPORTED;
+  if (split_bytes < sketch_bf_split_bytes(K, l)) return LRAMM_ERR_WORKSPACE;
+  BfParams p{};
+  p.M = M;
+  p.K = K;
+  p.l = l;
+  p.lout = l;
+  p.npad = static_cast<int>(round_up(l, kFAtom));
+  const int nslices = static_cast<int>(ceil_div(l, 512));
+  p.ncols = static_cast<int>(round_up(ceil_div(l, nslices), kFAtom));   // multiple of 64, <= 512
+  p.nb = nb;
+  p.a_mn = a_mn;
+  p.kblocks = ceil_div(K, kFK);
+  p.a_bytes = kBM * kFK * 2;
+  p.b_bytes = static_cast<uint32_t>(nb) * static_cast<uint32_t>(p.ncols / kFAtom) * kFChunk;
+  p.stages = static_cast<int>((kSmemBudget - 1024) / (p.a_bytes + p.b_bytes));
+  if (p.stages > kMaxStages) p.stages = kMaxStages;
+  if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
+  uint32_t tc = 32;
+  while (tc < static_cast<uint32_t>(p.ncols)) tc <<= 1;
+  p.tmem_cols = tc;
+  p.status = status;
+  const int64_t mtiles = ceil_div(M, kBM);
+  int64_t splits = 152 / (mtiles * nslices);
+  if (splits > p.kblocks / 8) splits = p.kblocks / 8;
+  if (splits < 1) splits = 1;
+  while (splits > 1 && static_cast<size_t>(splits) * M * l > part_floats) --splits;
+  p.kb_per_split = static_cast<int>(ceil_div(p.kblocks, splits));
+  splits = ceil_div(p.kblocks, p.kb_per_split);
+  p.out = splits > 1 ? part : out;
+
+  // B parts (K x npad BF16 each)
+  __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>((reinterpret_cast<uintptr_t>(split) + 255) & ~uintptr_t(255));
+  __nv_bfloat16* lo = nb > 1 ? hi + K * p.npad : nullptr;
+  {
+    int64_t g = ceil_div(K * p.npad, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    split_bf16_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(B, K, l, p.npad, hi, lo);
+    LRAMM_TRY(last_launch());
+  }
+  CUtensorMap mX, mBh, mBl;
+  if (!make_map_2d(&mX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, X, cols, rows, ldx * 2, a_mn ? kFAtom : kFK,
+                   a_mn ? kFK : kBM, a_mn ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B))
+    return LRAMM_ERR_CUDA;
+  if (!make_map_2d(&mBh, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, hi, p.npad, K, static_cast<uint64_t>(p.npad) * 2, kFAtom,
+                   kFK, CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  if (!make_map_2d(&mBl, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, nb > 1 ? lo : hi, p.npad, K,
+                   static_cast<uint64_t>(p.npad) * 2, kFAtom, kFK, CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(sketch_bf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  sketch_bf_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits), static_cast<unsigned>(nslices)),
+                     kThreads, smem, s>>>(mX, mBh, mBl, p);
+  LRAMM_TRY(last_launch());
+  if (splits > 1) {
+    const int64_t n4 = M * l / 4;
+    int64_t g = ceil_div(n4, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    split_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
+                                                                  static_cast<int>(splits), n4,
+                                                                  reinterpret_cast<float4*>(out));
+    LRAMM_TRY(last_launch());
+  }
+  return LRAMM_OK;
+}
 
 lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, int xbf, const float* B,
                        int l, float* out, float* part, size_t part_floats, int* status, cudaStream_t s) {

@@ -75,3 +75,29 @@ def test_rsvd_with_tf32_sketch(L):
     Uo, so, Vo = oracle.lramm.rsvd(X, r, p, q, 7, 0)
     err = oracle.lramm.rel_fro((U * S) @ V.T, (Uo * so) @ Vo.T)
     assert err < 4 * 2.0 ** -10, err
+
+
+BF_SHAPES = [(4096, 4096, 272), (700, 520, 64), (130, 1000, 8), (1000, 136, 144), (513, 2056, 400), (600, 1200, 544),
+             (256, 256, 1100)]
+
+
+@pytest.mark.parametrize("rows,cols,l", BF_SHAPES)
+@pytest.mark.parametrize("transpose", [0, 1])
+@pytest.mark.parametrize("sketch", ["tf32", "bf16"])
+def test_sketch_product_bf16_operand(L, rows, cols, l, transpose, sketch):
+    """BF16 X is exact on the tensor cores; B enters as B_hi + B_lo (TF32
+    mode: |B - B_hi - B_lo| <= 2^-16 |B|) or as B_hi (BF16 mode: 2^-9 |B|).
+    l = 544 and 1100 run in column blocks of at most 512."""
+    rng = np.random.default_rng(rows + 5 * cols + 11 * l + transpose)
+    Xb = torch.from_numpy(rng.standard_normal((rows, cols)).astype(np.float32)).to(torch.bfloat16)
+    X = Xb.float().numpy().astype(np.float64)
+    B = rng.standard_normal((rows if transpose else cols, l)).astype(np.float32)
+    mode = L.SKETCH_TF32 if sketch == "tf32" else L.SKETCH_BF16
+    out = L.sketch_product(Xb.cuda(), torch.from_numpy(B).cuda(), transpose=bool(transpose),
+                           sketch=mode).cpu().numpy().astype(np.float64)
+    Xd = X.T if transpose else X
+    ref = Xd @ B.astype(np.float64)
+    mag = np.abs(Xd) @ np.abs(B.astype(np.float64))
+    K = Xd.shape[1]
+    rel = 2.0 ** -15 if sketch == "tf32" else 2.0 ** -8
+    assert np.all(np.abs(out - ref) <= (rel + K * 2.0 ** -23) * mag), np.max(np.abs(out - ref) / mag)
