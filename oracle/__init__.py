@@ -12,5 +12,7 @@ Modules:
   lramm   -- randomized SVD (Sec. 2.2, Algorithm 1, power iterations) and
              LRAMM (Algorithm 3), exact product, relative Frobenius error
   rf      -- the range-finder form C ~ (X Q)(Q^T W) and its gradients
+  mixed   -- MXFP4 (e2m1, 32-element block scales), split-precision
+             residuals and the lead / tail E3 of the mixed 4/8-bit chain
 """
-from . import philox, quant, lramm, rf  # noqa: F401
+from . import philox, quant, lramm, rf, mixed  # noqa: F401

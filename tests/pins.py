@@ -436,3 +436,147 @@ def pin_copyltu(rf, seed=34):
     S = rf.copyltu(M)
     assert np.array_equal(S, S.T)
     assert np.array_equal(np.tril(S), np.tril(M))
+
+
+# --------------------------------------------------------------------------
+# MXFP4, split-precision residuals, lead / tail E3
+# --------------------------------------------------------------------------
+def e2m1_decode_all():
+    """All 16 e2m1 codes from the bit fields (1 sign, 2 exponent bits with
+    bias 1, 1 mantissa bit): (value, mantissa bit)."""
+    out = []
+    for code in range(16):
+        sgn = -1.0 if code & 8 else 1.0
+        e = (code >> 1) & 3
+        m = code & 1
+        v = (m / 2.0) if e == 0 else (1.0 + m / 2.0) * 2.0 ** (e - 1)
+        out.append((sgn * v, m))
+    return out
+
+
+def pin_e2m1(mixed):
+    """Every representable value maps to itself; every midpoint of two
+    neighbours goes to the one whose mantissa bit is 0; nudged midpoints go
+    to the nearer one; magnitudes above 6 saturate; brute-force nearest-even
+    on random values."""
+    grid = sorted({v for v, _ in e2m1_decode_all() if v >= 0})
+    assert grid == [0.0, 0.5, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0]
+    mant = {abs(v): m for v, m in e2m1_decode_all()}
+    g = np.array(grid)
+    assert np.array_equal(mixed.round_e2m1(g), g) and np.array_equal(mixed.round_e2m1(-g), -g)
+    for lo, hi in zip(grid[:-1], grid[1:]):
+        mid = (lo + hi) / 2.0
+        want = lo if mant[lo] == 0 else hi
+        assert mixed.round_e2m1(np.array([mid]))[0] == want, (lo, hi)
+        assert mixed.round_e2m1(np.array([mid * (1 + 1e-9)]))[0] == hi
+        assert mixed.round_e2m1(np.array([mid * (1 - 1e-9)]))[0] == lo
+    assert mixed.round_e2m1(np.array([7.9, 100.0, -6.5]))[0] == 6.0
+    rng = np.random.default_rng(41)
+    v = rng.uniform(-6, 6, 5000)
+    got = mixed.round_e2m1(v)
+    d = np.abs(np.abs(v)[:, None] - g[None, :])
+    best = g[np.argmin(d, axis=1)]
+    assert np.array_equal(np.abs(got), best) and np.all(np.sign(got[got != 0]) == np.sign(v[got != 0]))
+
+
+def pin_mx_scale_rule(mixed):
+    """e = ceil(log2(amax / 6)): amax / 2^e lies in (3, 6] (no element
+    saturates, the block's largest element uses the top binade), checked on
+    random magnitudes and the power-of-two edges; a zero block gets -127."""
+    rng = np.random.default_rng(42)
+    amax = np.exp(rng.uniform(-30, 30, 20000)).astype(np.float32)
+    edges = np.array([6.0, 3.0, 12.0, 1.5, 6.0 * 2.0 ** -20, 3.0 * 2.0 ** 10, 6.0000005, 2.9999998],
+                     dtype=np.float32)
+    amax = np.concatenate([amax, edges])
+    e = mixed.mx_exponent(amax)
+    ratio = amax.astype(np.float64) / np.exp2(e.astype(np.float64))
+    assert np.all(ratio > 3.0) and np.all(ratio <= 6.0 * (1 + 2.0 ** -23))
+    assert np.array_equal(mixed.mx_exponent(np.array([6.0, 3.0, 12.0], np.float32)), [0, -1, 1])
+    assert mixed.mx_exponent(np.array([0.0], np.float32))[0] == -127
+
+
+def pin_mxfp4_quantise(mixed, seed=43):
+    """Block quantisation: |x - deq| <= half the grid step at |x| / 2^e
+    times 2^e (<= 2^e overall), codes on the grid, block scales from each
+    block's own amax (a large value in one block does not coarsen its
+    neighbours), K tails shorter than a block."""
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((9, 77)) * np.exp(rng.uniform(-5, 5, (9, 77)))).astype(np.float32)
+    X[2, 40] = 1e6
+    c, e = mixed.quantize_mxfp4(X)
+    assert c.shape == X.shape and e.shape == (9, 3)
+    grid = np.array([0.0, 0.5, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0])
+    assert np.all(np.isin(np.abs(c), grid))
+    deq = mixed.dequantize_mxfp4(c, e)
+    scale = np.repeat(np.exp2(e.astype(np.float64)), 32, axis=1)[:, :77]
+    y = np.abs(X) / scale
+    half_step = np.where(y < 2, 0.25, np.where(y < 4, 0.5, 1.0))
+    assert np.all(np.abs(X - deq) <= half_step * scale * (1 + 1e-12))
+    for b in range(3):
+        blk = X[:, 32 * b:32 * (b + 1)]
+        assert np.array_equal(e[:, b], mixed.mx_exponent(np.max(np.abs(blk), axis=1)))
+
+
+def pin_mx_product_bruteforce(mixed, seed=44):
+    """The block-scaled product equals a Python loop over K of the
+    dequantised elements (exact dyadic arithmetic), K tail included."""
+    rng = np.random.default_rng(seed)
+    L = (rng.standard_normal((3, 70)) * np.exp(rng.uniform(-3, 3, (3, 70)))).astype(np.float32)
+    R = (rng.standard_normal((70, 4)) * np.exp(rng.uniform(-3, 3, (70, 4)))).astype(np.float32)
+    cl, el = mixed.quantize_mxfp4(L)
+    cr, er = mixed.quantize_mxfp4(R.T)
+    got = mixed.mx_product(cl, el, cr, er)
+    for i in range(3):
+        for j in range(4):
+            want = 0.0
+            for k in range(70):
+                want += (cl[i, k] * 2.0 ** int(el[i, k // 32])) * (cr[j, k] * 2.0 ** int(er[j, k // 32]))
+            assert got[i, j] == want, (i, j, got[i, j], want)
+    assert np.array_equal(mixed.qm_mxfp4(L, R), got.astype(np.float32))
+
+
+def pin_hilo_residual(mixed, quant, seed=45):
+    """The split-precision pair reconstructs x to half a lo step: |x -
+    deq(hi) - deq(lo)| <= (1/2 + eps) s_lo + FP32 rounding; the residual's
+    scale is at most about s_hi / (2 D)."""
+    rng = np.random.default_rng(seed)
+    X = (rng.standard_normal((33, 64)) * np.exp(rng.uniform(-3, 3, (33, 1)))).astype(np.float32)
+    for prec, D in ((quant.PREC_INT8, 127.0), (quant.PREC_INT4, 7.0)):
+        for axis in (1, 0, None):
+            (ch, sh), (cl, sl) = mixed.quantize_hilo(X, prec, axis)
+            rec = quant.dequantize(ch, sh, axis).astype(np.float64) + quant.dequantize(cl, sl, axis)
+            sb = sl[:, None] if axis == 1 else (sl[None, :] if axis == 0 else sl[0])
+            xb = np.abs(X).max(axis=1, keepdims=True) if axis == 1 else (
+                np.abs(X).max(axis=0, keepdims=True) if axis == 0 else np.abs(X).max())
+            assert np.all(np.abs(X - rec) <= (0.5 + 1e-5) * sb + 2.0 ** -23 * xb)
+            assert np.all(sl <= (0.5 + 1e-5) * sh / D + 2.0 ** -23 * np.asarray(sh) * D)
+
+
+def pin_lead_tail(mixed, quant, seed=46):
+    """Reductions and accuracy of the lead / tail E3:
+    lead = 0 is the plain QM in the tail precision; lead = r without
+    residual is the plain QM in the lead precision; each residual term
+    shrinks the lead block's error against the FP64 product (the split
+    error is a small fraction of the unsplit one)."""
+    rng = np.random.default_rng(seed)
+    m, r, n = 40, 24, 36
+    Ut = (rng.standard_normal((m, r)) * np.exp(-np.arange(r) / 6.0)).astype(np.float32)
+    E2 = rng.standard_normal((r, n)).astype(np.float32)
+    for tail in (quant.PREC_INT4, mixed.PREC_MXFP4):
+        got = mixed.e3_lead_tail(Ut, E2, tail, 0, quant.PREC_INT8, 2)
+        assert np.array_equal(got, mixed.qm_any(Ut, E2, tail, quant.SCALE_ROWCOL).astype(np.float64))
+    got = mixed.e3_lead_tail(Ut, E2, quant.PREC_INT4, r, quant.PREC_INT8, 0)
+    assert np.array_equal(got, quant.qm(Ut, E2, quant.PREC_INT8).astype(np.float64))
+    exact = Ut.astype(np.float64) @ E2.astype(np.float64)
+    errs = [np.linalg.norm(mixed.e3_lead_tail(Ut, E2, quant.PREC_INT4, r, quant.PREC_INT8, s) - exact)
+            for s in (0, 1, 2)]
+    assert errs[1] < 0.6 * errs[0] and errs[2] < 0.05 * errs[0], errs
+    # split = 2 leaves only the lo.lo term and the lo roundings: ~ (s_lo / 2)-sized errors
+    (uh, suh), (ul, sul) = mixed.quantize_hilo(Ut, quant.PREC_INT8, 1)
+    (eh, seh), (el, sel) = mixed.quantize_hilo(E2, quant.PREC_INT8, 0)
+    du = Ut.astype(np.float64) - quant.dequantize(uh, suh, 1) - quant.dequantize(ul, sul, 1)
+    de = E2.astype(np.float64) - quant.dequantize(eh, seh, 0) - quant.dequantize(el, sel, 0)
+    lolo = quant.dequantize(ul, sul, 1).astype(np.float64) @ quant.dequantize(el, sel, 0)
+    bound = (np.abs(du) @ np.abs(E2) + np.abs(Ut) @ np.abs(de) + np.abs(lolo) + np.abs(du) @ np.abs(de))
+    full = mixed.e3_lead_tail(Ut, E2, quant.PREC_INT4, r, quant.PREC_INT8, 2)
+    assert np.all(np.abs(full - exact) <= bound * (1 + 1e-4) + 1e-6 * np.abs(exact).max())

@@ -243,3 +243,66 @@ def test_rf_backward_missing_dq_term_caught(monkeypatch):
     monkeypatch.setattr(Rf, "rf_backward", bad)
     with pytest.raises(AssertionError):
         pins.pin_rf_gradients_fd(Rf)
+
+
+# ---------------------------------------------------------------- MXFP4, residuals, lead / tail
+from oracle import mixed as Mx  # noqa: E402
+
+
+def test_e2m1_ties_away_caught(monkeypatch):
+    def bad(v):
+        v = np.asarray(v, dtype=np.float64)
+        a = np.abs(v)
+        with np.errstate(divide="ignore"):
+            e = np.clip(np.floor(np.log2(np.where(a > 0, a, 1.0))), 0, 2)
+        q = np.exp2(e - 1)
+        return np.sign(v) * np.minimum(np.floor(a / q + 0.5) * q, 6.0)     # ties away from zero
+    monkeypatch.setattr(Mx, "round_e2m1", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_e2m1(Mx)
+
+
+def test_mx_floor_exponent_caught(monkeypatch):
+    def bad(amax):
+        amax = np.asarray(amax, dtype=np.float32)
+        y = (amax / np.float32(6.0)).astype(np.float32)
+        m, E = np.frexp(y.astype(np.float64))
+        e = np.where(amax > 0, E - 1, -127)                                # floor(log2 y)
+        return np.clip(e, -127, 127).astype(np.int64)
+    monkeypatch.setattr(Mx, "mx_exponent", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_mx_scale_rule(Mx)
+
+
+def test_mx_product_wrong_block_scale_caught(monkeypatch):
+    good = Mx.mx_product
+
+    def bad(cl, el, cr, er):
+        return good(cl, el, cr, np.roll(er, 1, axis=1))                   # right scales one block off
+    monkeypatch.setattr(Mx, "mx_product", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_mx_product_bruteforce(Mx)
+
+
+def test_hilo_without_residual_caught(monkeypatch):
+    def bad(X, prec, axis):
+        X = np.asarray(X, dtype=np.float32)
+        c_hi, _, s_hi = Qn.quantize(X, prec, axis)
+        c_lo, _, s_lo = Qn.quantize(X, prec, axis)                         # quantises x again, not x - deq(hi)
+        return (c_hi, s_hi), (c_lo, s_lo)
+    monkeypatch.setattr(Mx, "quantize_hilo", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_hilo_residual(Mx, Qn)
+
+
+def test_lead_tail_missing_residual_term_caught(monkeypatch):
+    good = Mx._qm_codes
+    calls = {"n": 0}
+
+    def bad(cl, sl, cr, sr, ax_l, ax_r):
+        calls["n"] += 1
+        out = good(cl, sl, cr, sr, ax_l, ax_r)
+        return out * 0 if calls["n"] % 3 == 2 else out                     # the lo.hi term lost
+    monkeypatch.setattr(Mx, "_qm_codes", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_lead_tail(Mx, Qn)

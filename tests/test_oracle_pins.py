@@ -98,3 +98,28 @@ def test_rf_exact_rank_product():
 
 def test_rf_copyltu():
     pins.pin_copyltu(oracle.rf)
+
+
+# ---------------------------------------------------------------- MXFP4, residuals, lead / tail
+def test_e2m1_grid_and_rounding():
+    pins.pin_e2m1(oracle.mixed)
+
+
+def test_mx_scale_rule():
+    pins.pin_mx_scale_rule(oracle.mixed)
+
+
+def test_mxfp4_quantiser():
+    pins.pin_mxfp4_quantise(oracle.mixed)
+
+
+def test_mx_product_bruteforce():
+    pins.pin_mx_product_bruteforce(oracle.mixed)
+
+
+def test_hilo_residual():
+    pins.pin_hilo_residual(oracle.mixed, oracle.quant)
+
+
+def test_lead_tail_e3():
+    pins.pin_lead_tail(oracle.mixed, oracle.quant)
