@@ -63,8 +63,12 @@ typedef enum { LRAMM_F32 = 0, LRAMM_BF16 = 1 } lramm_dtype;
  *   F32  : no quantisation, FP32 product (the "plain LRAMM" of Sec. 4.2)
  *   INT8 : N = 8 bits, codes in [-127, 127], exact integer product
  *   INT4 : N = 4 bits, codes in [-7, 7], exact integer product
- *   E4M3 : FP8 e4m3 codes with lambda = 448 / a_max, FP32 accumulation  */
-typedef enum { LRAMM_P_F32 = 0, LRAMM_P_INT8 = 1, LRAMM_P_INT4 = 2, LRAMM_P_E4M3 = 3 } lramm_prec;
+ *   E4M3 : FP8 e4m3 codes with lambda = 448 / a_max, FP32 accumulation
+ *   MXFP4: e2m1 elements, one power-of-two scale 2^e per 32 consecutive
+ *          elements along K, e = ceil(log2(a_max / 6)) (OCP MX e2m1 with this
+ *          scale rule); exact block sums, FP32 sum over blocks.  The scale
+ *          groups of lramm_scale do not apply to MXFP4 operands.          */
+typedef enum { LRAMM_P_F32 = 0, LRAMM_P_INT8 = 1, LRAMM_P_INT4 = 2, LRAMM_P_E4M3 = 3, LRAMM_P_MXFP4 = 4 } lramm_prec;
 
 /* Scale groups of the quantiser (a_max of Eq. (get_lambda)):
  *   ROWCOL: left operand one scale per row, right operand one per column
@@ -94,6 +98,17 @@ typedef struct lramm_desc {
   float alpha, beta;      /* D = alpha E3 + beta C                               */
   int32_t max_sweeps;     /* Jacobi sweep cap, 0 selects the default (40)        */
   int32_t flags;          /* LRAMM_FLAG_* bits; other bits must be 0             */
+  /* Mixed precision inside E3 = QM(U~ E2): the first `lead` rank directions
+   * (the largest singular values) in lead_prec (INT8, INT4 or E4M3), the
+   * remaining r - lead in prec[2]:
+   *   E3 = QM(U~_l^hi, E2_l^hi) [+ QM(U~_l^lo, E2_l^hi)] [+ QM(U~_l^hi, E2_l^lo)]
+   *        + QM(U~_t, E2_t)
+   * where x^lo is the quantised residual x - deq(x^hi) (its own scales);
+   * lead_split = 0, 1 or 2 selects the bracketed terms in order.  lead = 0
+   * disables the split (lead_prec and lead_split are then ignored). */
+  int32_t lead;
+  int32_t lead_prec;
+  int32_t lead_split;
 } lramm_desc;
 
 /* flags: record a CUDA event pair around every kernel launch of a call, on
@@ -322,6 +337,26 @@ LRAMM_API lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t
                                             int32_t x_type, int32_t transpose, const float* B, int64_t l,
                                             float* out, int32_t sketch, void* ws, size_t ws_bytes,
                                             void* stream);
+
+/* MXFP4 quantiser (lramm_prec LRAMM_P_MXFP4) of the rows of X (rows x cols,
+ * stride ldx, FP32): per row and per 32 consecutive elements, e = ceil(log2(
+ * fp32(a_max / 6))) clamped to [-127, 127] (-127 for a zero block), element
+ * = x 2^-e rounded to nearest-even on the e2m1 grid.  codes: rows x ldcodes
+ * int8 holding twice the e2m1 value (integers in [-12, 12]), zero beyond
+ * cols; exps: rows x (ldcodes / 32) int8.  ldcodes a multiple of 32,
+ * >= cols.  Asynchronous on `stream`. */
+LRAMM_API lramm_status lramm_quantize_mx(const float* X, int64_t rows, int64_t cols, int64_t ldx, int8_t* codes,
+                                         int64_t ldcodes, int8_t* exps, void* stream);
+
+/* Block-scaled QM product on MXFP4 codes as lramm_quantize_mx writes them:
+ *   acc(i,j) = sum_b 2^(eL[i,b] + eR[j,b] - 2) sum_{t in block b} L(i,t) Rt(j,t)
+ * (exact block sums, FP32 sum over blocks in block order), D = alpha acc +
+ * beta C (FP32, strides ldc, ldd).  L M x K (stride ldl), Rt N x K (stride
+ * ldr), exps M x K/32 and N x K/32; K a multiple of 32, ldl and ldr
+ * multiples of 16, code bases 16-byte aligned. */
+LRAMM_API lramm_status lramm_qgemm_mx(const int8_t* L, const int8_t* Le, const int8_t* Rt, const int8_t* Re,
+                                      int64_t M, int64_t N, int64_t K, int64_t ldl, int64_t ldr, float alpha,
+                                      float beta, const float* C, int64_t ldc, float* D, int64_t ldd, void* stream);
 
 /* Bytes of workspace lramm_sketch_product needs for an l-column product of a
  * rows x cols operand. */

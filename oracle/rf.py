@@ -26,6 +26,7 @@ to Q; the sketch Y0 = W Omega adds dY0 Omega^T.
 """
 import numpy as np
 
+from . import mixed
 from . import philox
 from . import quant
 
@@ -87,7 +88,7 @@ def rf_forward(X, W, r, p, q, seed, prec=quant.PREC_F32, scale=quant.SCALE_ROWCO
     if prec == quant.PREC_F32:
         D = T @ P
     else:
-        D = quant.qm(T.astype(np.float32), P.astype(np.float32), prec, scale).astype(F64)
+        D = mixed.qm_any(T.astype(np.float32), P.astype(np.float32), prec, scale).astype(F64)
     D = alpha * D
     if beta != 0.0:
         D = D + beta * np.asarray(C, dtype=F64)

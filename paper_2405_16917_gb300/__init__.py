@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "liblramm.so")
 
 F32, BF16 = 0, 1
-P_F32, P_INT8, P_INT4, P_E4M3 = 0, 1, 2, 3
+P_F32, P_INT8, P_INT4, P_E4M3, P_MXFP4 = 0, 1, 2, 3, 4
 S_ROWCOL, S_TENSOR = 0, 1
 SKETCH_F32, SKETCH_TF32, SKETCH_BF16 = 0, 1, 2
 
@@ -35,7 +35,8 @@ class Desc(ctypes.Structure):
                 ("seed", ctypes.c_uint64), ("prec", ctypes.c_int32 * 3),
                 ("scale", ctypes.c_int32), ("sketch", ctypes.c_int32),
                 ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
-                ("max_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("max_sweeps", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("lead", ctypes.c_int32), ("lead_prec", ctypes.c_int32), ("lead_split", ctypes.c_int32)]
 
 
 _VP, _I64, _I32, _U64, _U32, _F = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64,
@@ -63,6 +64,8 @@ _SIGS = {
     "lramm_qgemm_tc_ws_bytes": (ctypes.c_size_t, [_I32, _I64, _I64, _I64]),
     "lramm_tgemm_tc": (_I32, [_I64, _I64, _I64, _F, _VP, _I64, _VP, _I64, _F, _VP, _I64, _VP, ctypes.c_size_t, _VP]),
     "lramm_tgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
+    "lramm_quantize_mx": (_I32, [_VP, _I64, _I64, _I64, _VP, _I64, _VP, _VP]),
+    "lramm_qgemm_mx": (_I32, [_VP, _VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _F, _F, _VP, _I64, _VP, _I64, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
     "lramm_sketch_product": (_I32, [_VP, _I64, _I64, _I64, _I32, _I32, _VP, _I64, _VP, _I32, _VP, ctypes.c_size_t,
                                     _VP]),
@@ -136,7 +139,7 @@ class Plan:
 
     def __init__(self, m, n, k, r, p, q, seed=7, prec=(P_INT8, P_INT8, P_INT8), scale=S_ROWCOL,
                  sketch=SKETCH_F32, alpha=1.0, beta=0.0, a_type=F32, b_type=F32, lda=None, ldb=None,
-                 ldc=None, max_sweeps=0, timing=False):
+                 ldc=None, max_sweeps=0, timing=False, lead=0, lead_prec=P_INT8, lead_split=0):
         lib = load()
         d = Desc()
         d.m, d.n, d.k = m, n, k
@@ -150,6 +153,7 @@ class Plan:
         d.scale, d.sketch = scale, sketch
         d.alpha, d.beta = alpha, beta
         d.max_sweeps, d.flags = max_sweeps, (FLAG_TIMING if timing else 0)
+        d.lead, d.lead_prec, d.lead_split = lead, lead_prec, lead_split
         self.desc = d
         h = ctypes.c_void_p()
         _check(lib.lramm_plan_create(ctypes.byref(d), ctypes.byref(h)), "lramm_plan_create")
@@ -380,6 +384,32 @@ def qgemm_tc(Lc, Rc, sL, sR, per_row=True, alpha=1.0, beta=0.0, C=None, ws=None,
     _check(load().lramm_qgemm_tc(prec, _ptr(Lc), _ptr(Rc), M, N, K, Lc.stride(0), Rc.stride(0), int(per_row),
                                  _ptr(sL), _ptr(sR), alpha, beta, _ptr(C), C.stride(0) if C is not None else 0,
                                  _ptr(out), N, _ptr(ws), ws.numel(), _stream()), "lramm_qgemm_tc")
+    return out
+
+
+def quantize_mx(X, ldcodes=None):
+    """MXFP4 codes (int8, twice the e2m1 value) and block exponents (int8) of the rows of X."""
+    torch = _torch()
+    _need_cuda(X)
+    rows, cols = X.shape
+    ldc = ldcodes if ldcodes is not None else -(-cols // 32) * 32
+    codes = torch.empty((rows, ldc), dtype=torch.int8, device=X.device)
+    exps = torch.empty((rows, ldc // 32), dtype=torch.int8, device=X.device)
+    _check(load().lramm_quantize_mx(_ptr(X), rows, cols, X.stride(0), _ptr(codes), ldc, _ptr(exps), _stream()),
+           "lramm_quantize_mx")
+    return codes, exps
+
+
+def qgemm_mx(Lc, Le, Rc, Re, alpha=1.0, beta=0.0, C=None):
+    """Block-scaled QM on MXFP4 codes (K-major, K a multiple of 32)."""
+    torch = _torch()
+    _need_cuda(Lc, Rc, C)
+    M, K = Lc.shape
+    N = Rc.shape[0]
+    out = torch.empty((M, N), dtype=torch.float32, device=Lc.device)
+    _check(load().lramm_qgemm_mx(_ptr(Lc), _ptr(Le), _ptr(Rc), _ptr(Re), M, N, K, Lc.stride(0), Rc.stride(0), alpha,
+                                 beta, _ptr(C), C.stride(0) if C is not None else 0, _ptr(out), N, _stream()),
+           "lramm_qgemm_mx")
     return out
 
 

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblramm.so")
-SOURCES = ["api.cu", "philox.cu", "gemm_simt.cu", "smallla.cu", "quant.cu", "sketch_tc.cu", "orth.cu", "qgemm_tc.cu"]
+SOURCES = ["api.cu", "philox.cu", "gemm_simt.cu", "smallla.cu", "quant.cu", "sketch_tc.cu", "orth.cu", "qgemm_tc.cu", "mx.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]

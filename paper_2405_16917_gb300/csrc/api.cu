@@ -61,6 +61,11 @@ struct lramm_plan_s {
   size_t amax;
   size_t part, gpart, qpart;
   size_t bsplit, bsplit_bytes;   // BF16 parts of the l-column operand (BF16 A or B)
+  // MXFP4 block exponents of the chain operands; the lead / tail E3 buffers
+  size_t xV, xW, xZ, xE1, xU, xE2;
+  int64_t lq;
+  size_t cUh, cUl, cEh, cEl, sUh, sUl, sEh, sEl, tres;
+  size_t xT, xP;
   size_t qpart_floats;
   // range-finder form: codes / scales of T and P^T; the range-finder chain
   // kept for the backward (Q_0..Q_q, Z_1..Z_q, the Cholesky factors of every
@@ -83,7 +88,7 @@ struct Bump {
   }
 };
 
-bool valid_prec(int p) { return p >= LRAMM_P_F32 && p <= LRAMM_P_E4M3; }
+bool valid_prec(int p) { return p >= LRAMM_P_F32 && p <= LRAMM_P_MXFP4; }
 
 lramm_status validate(const lramm_desc* d) {
   if (!d) return LRAMM_ERR_INVALID_ARG;
@@ -100,6 +105,9 @@ lramm_status validate(const lramm_desc* d) {
   if (d->scale != LRAMM_S_ROWCOL && d->scale != LRAMM_S_TENSOR) return LRAMM_ERR_INVALID_ARG;
   if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_BF16) return LRAMM_ERR_INVALID_ARG;
   if (d->max_sweeps < 0 || (d->flags & ~LRAMM_FLAG_TIMING) != 0) return LRAMM_ERR_INVALID_ARG;
+  if (d->lead < 0 || d->lead > d->r || d->lead_split < 0 || d->lead_split > 2) return LRAMM_ERR_INVALID_ARG;
+  if (d->lead > 0 && d->lead_prec != LRAMM_P_INT8 && d->lead_prec != LRAMM_P_INT4 && d->lead_prec != LRAMM_P_E4M3)
+    return LRAMM_ERR_INVALID_ARG;
   if (l > kMaxL) return LRAMM_ERR_UNSUPPORTED;
   // orthonormalisation: blocked Cholesky (l <= 288), two-level beyond
   // (l % 4 == 0), the column-panel Cholesky while its triangle fits
@@ -133,8 +141,8 @@ void layout(lramm_plan_s* P) {
     S.S1 = b.take(sizeof(float) * l * r);
     S.S2 = b.take(sizeof(float) * l * r);
   }
-  P->kp = round_up(d.k, 16);
-  P->rp = round_up(r, 16);
+  P->kp = round_up(d.k, 32);   // code rows padded to whole 32-blocks (MXFP4) and 16-K MMA steps
+  P->rp = round_up(r, 32);
   P->Ut = b.take(sizeof(float) * d.m * r);
   P->Vt = b.take(sizeof(float) * r * d.k);
   P->Wt = b.take(sizeof(float) * r * d.k);
@@ -155,6 +163,24 @@ void layout(lramm_plan_s* P) {
   P->sU = b.take(sizeof(float) * d.m);
   P->sE2 = b.take(sizeof(float) * d.n);
   P->amax = b.take(kAlign);
+  P->xV = b.take(r * (P->kp / 32));
+  P->xW = b.take(r * (P->kp / 32));
+  P->xE1 = b.take(r * (P->rp / 32));
+  P->xZ = b.take(d.n * (P->rp / 32));
+  P->xU = b.take(d.m * (P->rp / 32));
+  P->xE2 = b.take(d.n * (P->rp / 32));
+  P->lq = round_up(d.lead > 0 ? d.lead : 1, 32);
+  if (d.lead > 0) {
+    P->cUh = b.take(cb * d.m * P->lq);
+    P->cUl = b.take(cb * d.m * P->lq);
+    P->cEh = b.take(cb * d.n * P->lq);
+    P->cEl = b.take(cb * d.n * P->lq);
+    P->sUh = b.take(sizeof(float) * d.m);
+    P->sUl = b.take(sizeof(float) * d.m);
+    P->sEh = b.take(sizeof(float) * d.n);
+    P->sEl = b.take(sizeof(float) * d.n);
+    P->tres = b.take(sizeof(float) * std::max(d.m, d.n) * d.lead);
+  }
   P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
   P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
   P->bsplit_bytes = (d.a_type == LRAMM_BF16 || d.b_type == LRAMM_BF16)
@@ -163,12 +189,13 @@ void layout(lramm_plan_s* P) {
   P->bsplit = P->bsplit_bytes ? b.take(P->bsplit_bytes) : 0;
   {  // split-K partials of the tensor-core code products (E1 with long K)
     auto qp = [](int prec, int64_t M, int64_t N, int64_t K) -> size_t {
-      return prec == LRAMM_P_F32 ? 0 : qgemm_tc_part_floats(prec, M, N, K);
+      return (prec == LRAMM_P_F32 || prec == LRAMM_P_MXFP4) ? 0 : qgemm_tc_part_floats(prec, M, N, K);
     };
     size_t q = qp(d.prec[0], r, r, P->kp);
     q = std::max(q, qp(d.prec[1], d.n, r, P->rp));
     q = std::max(q, qp(d.prec[2], d.m, d.n, P->rp));
-    q = std::max(q, qp(d.prec[2], d.m, d.n, round_up(l, 16)));
+    q = std::max(q, qp(d.prec[2], d.m, d.n, round_up(l, 32)));
+    if (d.lead > 0) q = std::max(q, qp(d.lead_prec, d.m, d.n, round_up(d.lead, 32)));
     // TF32 products of the range-finder form (K = l)
     q = std::max(q, tgemm_tc_part_floats(d.m, d.n, l));
     q = std::max(q, tgemm_tc_part_floats(d.m, d.k, l));
@@ -178,9 +205,11 @@ void layout(lramm_plan_s* P) {
   }
   {  // range-finder form
     const int64_t kk = d.k, nn = d.n, mm = d.m, qq = d.q, mx = std::max(kk, nn);
-    P->lp = round_up(l, 16);
+    P->lp = round_up(l, 32);
     P->cT = b.take(cb * mm * P->lp);
     P->cP = b.take(cb * nn * P->lp);
+    P->xT = b.take(mm * (P->lp / 32));
+    P->xP = b.take(nn * (P->lp / 32));
     P->sT = b.take(sizeof(float) * mm);
     P->sP = b.take(sizeof(float) * nn);
     P->bq = b.take(sizeof(float) * (qq + 1) * kk * l);
@@ -498,51 +527,111 @@ lramm_status qm_product(lramm_plan_s* P, void* ws, const void* L, const void* R,
   return qgemm(L, R, M, N, K, ldl, ldr, prec, per_row, sL, sR, alpha, beta, C, ldc, D, ldd, 0, s);
 }
 
+// The codes of one QM operand: container (ld = K padded to 32), scales (per
+// row or one) and, for MXFP4, block exponents.
+struct QOp {
+  void* c;
+  float* s;
+  int8_t* x;
+};
+
+lramm_status quant_op(lramm_plan_s* P, void* ws, const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
+                      const QOp& op, int64_t ldq, cudaStream_t s) {
+  if (prec == LRAMM_P_MXFP4) return quantize_mx(X, rows, cols, ldx, static_cast<int8_t*>(op.c), ldq, op.x, s);
+  return quantize_rows(X, rows, cols, ldx, prec, P->d.scale == LRAMM_S_ROWCOL, op.c, ldq, op.s,
+                       at<unsigned int>(ws, P->amax), s);
+}
+
+lramm_status qm_op(lramm_plan_s* P, void* ws, const QOp& L, const QOp& R, int64_t M, int64_t N, int64_t Kq, int prec,
+                   float alpha, float beta, const float* C, int64_t ldc, float* D, int64_t ldd, cudaStream_t s) {
+  if (prec == LRAMM_P_MXFP4)
+    return qgemm_mx(static_cast<const int8_t*>(L.c), L.x, static_cast<const int8_t*>(R.c), R.x, M, N, Kq, Kq, Kq,
+                    alpha, beta, C, ldc, D, ldd, s);
+  return qm_product(P, ws, L.c, R.c, M, N, Kq, Kq, Kq, prec, P->d.scale == LRAMM_S_ROWCOL, L.s, R.s, alpha, beta, C,
+                    ldc, D, ldd, s);
+}
+
+// E3 with the lead / tail split: the first `lead` rank directions in
+// lead_prec with split-precision residuals, the rest in prec[2]; the terms
+// accumulate into D (the first one carries beta C).
+lramm_status e3_lead_tail(lramm_plan_s* P, const float* Ut, const float* E2t, const float* C, float* D, void* ws,
+                          cudaStream_t s) {
+  const lramm_desc& d = P->d;
+  const int64_t r = d.r, lead = d.lead, tail = r - lead, lq = P->lq, tq = round_up(tail > 0 ? tail : 1, 32);
+  const int lp = d.lead_prec, per_row = d.scale == LRAMM_S_ROWCOL;
+  const QOp uh{at<void>(ws, P->cUh), at<float>(ws, P->sUh), nullptr};
+  const QOp ul{at<void>(ws, P->cUl), at<float>(ws, P->sUl), nullptr};
+  const QOp eh{at<void>(ws, P->cEh), at<float>(ws, P->sEh), nullptr};
+  const QOp el{at<void>(ws, P->cEl), at<float>(ws, P->sEl), nullptr};
+  float* tres = at<float>(ws, P->tres);
+  TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut, d.m, lead, r, lp, uh, lq, s));
+  TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E2t, d.n, lead, r, lp, eh, lq, s));
+  TIMED(P, LRAMM_K_E3, s, qm_op(P, ws, uh, eh, d.m, d.n, lq, lp, d.alpha, d.beta, C, d.ldc, D, d.ldc, s));
+  if (d.lead_split >= 1) {   // + QM(U~_l^lo, E2_l^hi)
+    TIMED(P, LRAMM_K_QUANT, s, residual_rows(Ut, d.m, lead, r, lp, uh.c, lq, uh.s, per_row, tres, lead, s));
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, tres, d.m, lead, lead, lp, ul, lq, s));
+    TIMED(P, LRAMM_K_E3, s, qm_op(P, ws, ul, eh, d.m, d.n, lq, lp, d.alpha, 1.f, D, d.ldc, D, d.ldc, s));
+  }
+  if (d.lead_split >= 2) {   // + QM(U~_l^hi, E2_l^lo)
+    TIMED(P, LRAMM_K_QUANT, s, residual_rows(E2t, d.n, lead, r, lp, eh.c, lq, eh.s, per_row, tres, lead, s));
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, tres, d.n, lead, lead, lp, el, lq, s));
+    TIMED(P, LRAMM_K_E3, s, qm_op(P, ws, uh, el, d.m, d.n, lq, lp, d.alpha, 1.f, D, d.ldc, D, d.ldc, s));
+  }
+  if (tail > 0) {
+    if (d.prec[2] == LRAMM_P_F32) {
+      TIMED(P, LRAMM_K_E3, s, sgemm(0, 1, d.m, d.n, tail, d.alpha, Ut + lead, r, 0, E2t + lead, r, 1.f, D, d.ldc, s));
+    } else {
+      const QOp ut{at<void>(ws, P->cU), at<float>(ws, P->sU), at<int8_t>(ws, P->xU)};
+      const QOp et{at<void>(ws, P->cE2), at<float>(ws, P->sE2), at<int8_t>(ws, P->xE2)};
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut + lead, d.m, tail, r, d.prec[2], ut, tq, s));
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E2t + lead, d.n, tail, r, d.prec[2], et, tq, s));
+      TIMED(P, LRAMM_K_E3, s, qm_op(P, ws, ut, et, d.m, d.n, tq, d.prec[2], d.alpha, 1.f, D, d.ldc, D, d.ldc, s));
+    }
+  }
+  return LRAMM_OK;
+}
+
 lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const float* Wt,
                         const float* Zt, const float* C, float* D, void* ws, cudaStream_t s) {
   const lramm_desc& d = P->d;
   const int64_t r = d.r, kp = P->kp, rp = P->rp;
-  const int per_row = d.scale == LRAMM_S_ROWCOL;
-  unsigned int* am = at<unsigned int>(ws, P->amax);
   float* E1 = at<float>(ws, P->E1);
   float* E2t = at<float>(ws, P->E2t);
   // E1 = QM(V^T W, d1): r x r, K = k
   if (d.prec[0] == LRAMM_P_F32) {
     TIMED(P, LRAMM_K_E1, s, sgemm(0, 1, r, r, d.k, 1.f, Vt, d.k, 0, Wt, d.k, 0.f, E1, r, s));
   } else {
-    void* cV = at<void>(ws, P->cV);
-    void* cW = at<void>(ws, P->cW);
-    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Vt, r, d.k, d.k, d.prec[0], per_row, cV, kp, at<float>(ws, P->sV), am, s));
-    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Wt, r, d.k, d.k, d.prec[0], per_row, cW, kp, at<float>(ws, P->sW), am, s));
-    TIMED(P, LRAMM_K_E1, s, qm_product(P, ws, cV, cW, r, r, kp, kp, kp, d.prec[0], per_row, at<float>(ws, P->sV),
-                                       at<float>(ws, P->sW), 1.f, 0.f, nullptr, 0, E1, r, s));
+    const QOp v{at<void>(ws, P->cV), at<float>(ws, P->sV), at<int8_t>(ws, P->xV)};
+    const QOp w{at<void>(ws, P->cW), at<float>(ws, P->sW), at<int8_t>(ws, P->xW)};
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Vt, r, d.k, d.k, d.prec[0], v, kp, s));
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Wt, r, d.k, d.k, d.prec[0], w, kp, s));
+    TIMED(P, LRAMM_K_E1, s, qm_op(P, ws, v, w, r, r, kp, d.prec[0], 1.f, 0.f, nullptr, 0, E1, r, s));
   }
   // E2 = QM(E1 Z~, d2), computed transposed: E2^T = Z~^T E1^T (n x r, K = r)
   if (d.prec[1] == LRAMM_P_F32) {
     TIMED(P, LRAMM_K_E2, s, sgemm(0, 1, d.n, r, r, 1.f, Zt, r, 0, E1, r, 0.f, E2t, r, s));
   } else {
-    void* cZ = at<void>(ws, P->cZ);
-    void* cE1 = at<void>(ws, P->cE1);
-    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Zt, d.n, r, r, d.prec[1], per_row, cZ, rp, at<float>(ws, P->sZ), am, s));
-    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(E1, r, r, r, d.prec[1], per_row, cE1, rp, at<float>(ws, P->sE1), am, s));
-    TIMED(P, LRAMM_K_E2, s, qm_product(P, ws, cZ, cE1, d.n, r, rp, rp, rp, d.prec[1], per_row, at<float>(ws, P->sZ),
-                                       at<float>(ws, P->sE1), 1.f, 0.f, nullptr, 0, E2t, r, s));
+    const QOp z{at<void>(ws, P->cZ), at<float>(ws, P->sZ), at<int8_t>(ws, P->xZ)};
+    const QOp e1{at<void>(ws, P->cE1), at<float>(ws, P->sE1), at<int8_t>(ws, P->xE1)};
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Zt, d.n, r, r, d.prec[1], z, rp, s));
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E1, r, r, r, d.prec[1], e1, rp, s));
+    TIMED(P, LRAMM_K_E2, s, qm_op(P, ws, z, e1, d.n, r, rp, d.prec[1], 1.f, 0.f, nullptr, 0, E2t, r, s));
   }
   // E3 = QM(U~ E2, d3); D = alpha E3 + beta C  (m x n, K = r)
   const float beta = d.beta;
   if (beta != 0.f && !C) return LRAMM_ERR_INVALID_ARG;
+  if (d.lead > 0) return e3_lead_tail(P, Ut, E2t, C, D, ws, s);
   if (d.prec[2] == LRAMM_P_F32) {
     if (beta != 0.f && C != D)
       LRAMM_CUDA_TRY(cudaMemcpy2DAsync(D, sizeof(float) * d.ldc, C, sizeof(float) * d.ldc,
                                        sizeof(float) * d.n, d.m, cudaMemcpyDeviceToDevice, s));
     TIMED(P, LRAMM_K_E3, s, sgemm(0, 1, d.m, d.n, r, d.alpha, Ut, r, 0, E2t, r, beta, D, d.ldc, s));
   } else {
-    void* cU = at<void>(ws, P->cU);
-    void* cE2 = at<void>(ws, P->cE2);
-    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(Ut, d.m, r, r, d.prec[2], per_row, cU, rp, at<float>(ws, P->sU), am, s));
-    TIMED(P, LRAMM_K_QUANT, s, quantize_rows(E2t, d.n, r, r, d.prec[2], per_row, cE2, rp, at<float>(ws, P->sE2), am, s));
-    TIMED(P, LRAMM_K_E3, s, qm_product(P, ws, cU, cE2, d.m, d.n, rp, rp, rp, d.prec[2], per_row, at<float>(ws, P->sU),
-                                       at<float>(ws, P->sE2), d.alpha, beta, C, d.ldc, D, d.ldc, s));
+    const QOp u{at<void>(ws, P->cU), at<float>(ws, P->sU), at<int8_t>(ws, P->xU)};
+    const QOp e2{at<void>(ws, P->cE2), at<float>(ws, P->sE2), at<int8_t>(ws, P->xE2)};
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut, d.m, r, r, d.prec[2], u, rp, s));
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E2t, d.n, r, r, d.prec[2], e2, rp, s));
+    TIMED(P, LRAMM_K_E3, s, qm_op(P, ws, u, e2, d.m, d.n, rp, d.prec[2], d.alpha, beta, C, d.ldc, D, d.ldc, s));
   }
   return LRAMM_OK;
 }
@@ -806,16 +895,12 @@ lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, f
     TIMED(plan, LRAMM_K_E3, s, nt_product(plan, ws, d.m, d.n, l, d.alpha, T, l, Pt, l, d.beta, C, d.ldc, s));
     return LRAMM_OK;
   }
-  const int per_row = d.scale == LRAMM_S_ROWCOL;
-  unsigned int* am = at<unsigned int>(ws, plan->amax);
-  void* cT = at<void>(ws, plan->cT);
-  void* cP = at<void>(ws, plan->cP);
-  float* sT = at<float>(ws, plan->sT);
-  float* sP = at<float>(ws, plan->sP);
-  TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(T, d.m, l, l, d.prec[2], per_row, cT, plan->lp, sT, am, s));
-  TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(Pt, d.n, l, l, d.prec[2], per_row, cP, plan->lp, sP, am, s));
-  TIMED(plan, LRAMM_K_E3, s, qm_product(plan, ws, cT, cP, d.m, d.n, plan->lp, plan->lp, plan->lp, d.prec[2], per_row,
-                                       sT, sP, d.alpha, d.beta, C, d.ldc, C, d.ldc, s));
+  const QOp ct{at<void>(ws, plan->cT), at<float>(ws, plan->sT), at<int8_t>(ws, plan->xT)};
+  const QOp cp{at<void>(ws, plan->cP), at<float>(ws, plan->sP), at<int8_t>(ws, plan->xP)};
+  TIMED(plan, LRAMM_K_QUANT, s, quant_op(plan, ws, T, d.m, l, l, d.prec[2], ct, plan->lp, s));
+  TIMED(plan, LRAMM_K_QUANT, s, quant_op(plan, ws, Pt, d.n, l, l, d.prec[2], cp, plan->lp, s));
+  TIMED(plan, LRAMM_K_E3, s, qm_op(plan, ws, ct, cp, d.m, d.n, plan->lp, d.prec[2], d.alpha, d.beta, C, d.ldc, C,
+                                  d.ldc, s));
   return LRAMM_OK;
 }
 
@@ -919,6 +1004,22 @@ lramm_status lramm_tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const 
   LRAMM_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int) * 4, s));
   float* part = reinterpret_cast<float*>(static_cast<char*>(ws) + kAlign);
   return tgemm_tc(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, part, (ws_bytes - kAlign) / sizeof(float), st, s);
+}
+
+lramm_status lramm_quantize_mx(const float* X, int64_t rows, int64_t cols, int64_t ldx, int8_t* codes,
+                               int64_t ldcodes, int8_t* exps, void* stream) {
+  if (rows < 0 || cols < 0 || ldx < cols || ldcodes < cols || ldcodes % 32) return LRAMM_ERR_INVALID_ARG;
+  if (rows > 0 && (!X || !codes || !exps)) return LRAMM_ERR_INVALID_ARG;
+  return quantize_mx(X, rows, cols, ldx, codes, ldcodes, exps, static_cast<cudaStream_t>(stream));
+}
+
+lramm_status lramm_qgemm_mx(const int8_t* L, const int8_t* Le, const int8_t* Rt, const int8_t* Re, int64_t M,
+                            int64_t N, int64_t K, int64_t ldl, int64_t ldr, float alpha, float beta, const float* C,
+                            int64_t ldc, float* D, int64_t ldd, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || K % 32 || ldl < K || ldr < K || ldd < N) return LRAMM_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return LRAMM_OK;
+  if (!L || !Le || !Rt || !Re || !D || (beta != 0.f && (!C || ldc < N))) return LRAMM_ERR_INVALID_ARG;
+  return qgemm_mx(L, Le, Rt, Re, M, N, K, ldl, ldr, alpha, beta, C, ldc, D, ldd, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -213,6 +213,18 @@ lramm_status quantize_rows_noalloc(const float* X, int64_t rows, int64_t cols, i
                                    int per_row, void* codes, int64_t ldcodes, float* scales,
                                    cudaStream_t s);
 size_t noalloc_scratch_bytes();
+
+// mx.cu -- MXFP4 operands (unpacked codes: int8 = 2 x e2m1 value; int8 block
+// exponents, one per 32 codes along K), the block-scaled QM product, and the
+// residual r = x - c s of a quantised factor.
+lramm_status quantize_mx(const float* X, int64_t rows, int64_t cols, int64_t ldx, int8_t* codes, int64_t ldc,
+                         int8_t* exps, cudaStream_t s);
+lramm_status qgemm_mx(const int8_t* Lc, const int8_t* Le, const int8_t* Rc, const int8_t* Re, int64_t M, int64_t N,
+                      int64_t K, int64_t ldl, int64_t ldr, float alpha, float beta, const float* C, int64_t ldc,
+                      float* D, int64_t ldd, cudaStream_t s);
+lramm_status residual_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, const void* codes,
+                           int64_t ldcodes, const float* scales, int per_row, float* out, int64_t ldo,
+                           cudaStream_t s);
 lramm_status qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
                    int64_t ldr, int prec, int per_row, const float* sL, const float* sR, float alpha,
                    float beta, const float* C, int64_t ldc, void* D, int64_t ldd, int out_kind,
