@@ -35,8 +35,12 @@ import numpy as np  # noqa: E402
 import workloads  # noqa: E402
 
 METRIC = "effective TFLOP/s (2mnk/t) at stated rel. Frobenius error vs dense BF16 GEMM"
-VARIANTS = {"int8": (1, 1, 1), "fp32": (0, 0, 0), "e4m3": (3, 3, 3), "884": (1, 1, 2)}
-DTYPES = {"int8": "f32+int8", "fp32": "f32", "e4m3": "f32+e4m3", "884": "f32+int8+int4"}
+VARIANTS = {"int8": (1, 1, 1), "fp32": (0, 0, 0), "e4m3": (3, 3, 3), "884": (1, 1, 2),
+            "lead64_mxfp4": (1, 1, 4), "lead64_int4": (1, 1, 2)}
+DTYPES = {"int8": "f32+int8", "fp32": "f32", "e4m3": "f32+e4m3", "884": "f32+int8+int4",
+          "lead64_mxfp4": "int8+mxfp4", "lead64_int4": "int8+int4"}
+# E3 lead / tail split (lead rank directions, lead precision, residual terms)
+LEADS = {"lead64_mxfp4": (64, 1, 2), "lead64_int4": (64, 1, 2)}
 FLUSH_BYTES = 256 << 20
 
 
@@ -156,10 +160,14 @@ def fp32_alu_peak_tflops(sm_mhz):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_step(A, B, cfg, prec):
+def cpu_oracle_step(A, B, cfg, prec, lead=None):
     import oracle
     t0 = time.perf_counter()
-    oracle.lramm.lramm(A, B, cfg["r"], cfg["p"], cfg["q"], workloads.SEED_SKETCH, prec)
+    if lead:
+        fac = oracle.lramm.factors(A, B, cfg["r"], cfg["p"], cfg["q"], workloads.SEED_SKETCH)
+        oracle.mixed.chain_lead_tail(*fac, prec, min(lead[0], cfg["r"]), lead[1], lead[2])
+    else:
+        oracle.lramm.lramm(A, B, cfg["r"], cfg["p"], cfg["q"], workloads.SEED_SKETCH, prec)
     return time.perf_counter() - t0
 
 
@@ -217,7 +225,7 @@ def run_reference(args):
     else:
         A, B, c = cpu_sample(args.workload)
         flops = 2.0 * c["m"] * c["n"] * c["k"]
-        step = lambda: cpu_oracle_step(A, B, c, prec)  # noqa: E731
+        step = lambda: cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))  # noqa: E731
         what = "oracle LRAMM"
     for _ in range(args.warmup):
         step()
@@ -260,8 +268,9 @@ def run_lramm(args):
     a_type = L.BF16 if A.dtype == torch.bfloat16 else L.F32
     sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
     sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
+    lead = LEADS.get(args.variant, (0, 1, 0))
     plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
-                  sketch=sketch, timing=True)
+                  sketch=sketch, timing=True, lead=lead[0], lead_prec=lead[1], lead_split=lead[2])
     ws = plan.workspace(dev)
     D = torch.empty((m, n), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -433,7 +442,7 @@ def run_lramm(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Ac, Bc, cs = cpu_sample(args.workload)
-        t_cpu = cpu_oracle_step(Ac, Bc, cs, prec)
+        t_cpu = cpu_oracle_step(Ac, Bc, cs, prec, LEADS.get(args.variant))
         cpu = {"value": 2.0 * cs["m"] * cs["n"] * cs["k"] / t_cpu / 1e12, "unit": "TFLOP/s",
                "cores": cores_used(), "kind": "oracle",
                "sample": "one oracle LRAMM step at m=%d n=%d k=%d r=%d p=%d q=%d, %.1f s"
@@ -447,6 +456,7 @@ def run_lramm(args):
             "vs_baseline": None, "dtype": DTYPES[args.variant], "data": "synthetic",
             "config": {"workload": args.workload, "m": m, "n": n, "k": k, "r": r, "p": p, "q": q,
                        "variant": args.variant, "operands": cfg["dtype"], "spectrum": cfg["spectrum"],
+                       "lead": {"directions": lead[0], "prec": lead[1], "residual_terms": lead[2]} if lead[0] else None,
                        "sketch": sketch_name, "scale": "rowcol",
                        "jacobi_sweeps": info[1:3], "l2": "flushed: 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
