@@ -59,6 +59,7 @@ struct QtcParams {
   int64_t ldd;
   float* part;   // chunks > 1: chunks x M x N partial sums
   int scaled;    // codes: dequantise with sL, sR; TF32: no scales
+  int tma_store; // one chunk, beta = 0, D a valid TMA target: 32 x 32 blocks stored by TMA
   int* status;
 };
 
@@ -103,7 +104,8 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 
 template <int KIND>
 __global__ void __launch_bounds__(kQThreads, 2)
-qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR, QtcParams p) {
+qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
+                const __grid_constant__ CUtensorMap tmD, QtcParams p) {
   constexpr int kStageK = kQKB / kind_elem_bytes(KIND);   // K elements per stage
   extern __shared__ uint8_t q_smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q_smem_raw) + 1023) & ~uintptr_t(1023));
@@ -204,37 +206,80 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
     volatile int zero = 0;  // wait for the MMAs even after an abort: they read shared memory
     const bool ok = mbar_wait(&tmem_bar, 0, &zero);
     tc_fence_after();
-    // Each 32 x 32 block (rows = this warp's TMEM lanes) is transposed through
-    // shared memory so that a store instruction writes 32 consecutive
-    // columns of one row (128 bytes).
-    float* T = tr_sh[q];
     const int64_t rbase = m0 + q * 32;
     const float sl_own = (p.chunks == 1 && rbase + lane < p.M)
                              ? (!p.scaled ? 1.f : (p.per_row ? p.sL[rbase + lane] : p.sL[0]))
                              : 0.f;
-    for (int c0 = 0; c0 < p.bn; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
-      __syncwarp();
-#pragma unroll
-      for (int jj = 0; jj < 32; ++jj) T[lane * 33 + jj] = v[jj];
-      __syncwarp();
-      const int64_t col = n0 + c0 + lane;
-      const bool col_ok = ok && col < p.N;
-      const float sr = p.chunks == 1 ? sR_sh[c0 + lane] : 0.f;
-#pragma unroll 4
-      for (int r = 0; r < 32; ++r) {
-        const float x = T[r * 33 + lane];
-        const float sl = __shfl_sync(0xffffffffu, sl_own, r);
-        const int64_t row = rbase + r;
-        if (!col_ok || row >= p.M) continue;
-        if (p.chunks > 1) {
-          p.part[(static_cast<int64_t>(chunk) * p.M + row) * p.N + col] = x;
-        } else {
-          float o = p.scaled ? __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl, sr))) : __fmul_rn(p.alpha, x);
-          if (p.beta != 0.f) o = fmaf(p.beta, p.C[row * p.ldc + col], o);
-          p.D[row * p.ldd + col] = o;
+    if (p.tma_store) {
+      // Each lane owns one output row of the block: the dequantised values go
+      // to a staging block in the 128-byte swizzled layout (16-byte chunk c
+      // of row r at chunk position c ^ (r mod 8)) and one lane stores the
+      // block with a TMA bulk copy; two staging blocks per warp alternate.
+      // The blocks live in the operand ring (at least 2 x 16 KB of A tiles),
+      // free once the accumulator is complete: every copy into the ring was
+      // consumed by an MMA before tmem_bar arrived.
+      for (int c0 = 0, nb = 0; c0 < p.bn; c0 += 32, ++nb) {
+        float v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+        float* stg = reinterpret_cast<float*>(sA) + (q * 2 + (nb & 1)) * 1024;
+        if (nb >= 2) {   // this staging block's previous store has finished reading it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
         }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float sr = sR_sh[c0 + 4 * c + e];
+            o[e] = p.scaled ? __fmul_rn(p.alpha, __fmul_rn(v[4 * c + e], __fmul_rn(sl_own, sr)))
+                            : __fmul_rn(p.alpha, v[4 * c + e]);
+          }
+          *reinterpret_cast<float4*>(stg + lane * 32 + ((c ^ (lane & 7)) << 2)) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0 && ok && rbase < p.M && n0 + c0 < p.N) {   // TMA clips the block at M and N
+          asm volatile(
+              "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                  reinterpret_cast<uint64_t>(&tmD)),
+              "r"(static_cast<int>(n0 + c0)), "r"(static_cast<int>(rbase)), "r"(smem_u32(stg))
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      }
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      __syncwarp();
+    } else {
+      // Each 32 x 32 block (rows = this warp's TMEM lanes) is transposed
+      // through shared memory so that a store instruction writes 32
+      // consecutive columns of one row (128 bytes).
+      float* T = tr_sh[q];
+      for (int c0 = 0; c0 < p.bn; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) T[lane * 33 + jj] = v[jj];
+        __syncwarp();
+        const int64_t col = n0 + c0 + lane;
+        const bool col_ok = ok && col < p.N;
+        const float sr = p.chunks == 1 ? sR_sh[c0 + lane] : 0.f;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const float x = T[r * 33 + lane];
+          const float sl = __shfl_sync(0xffffffffu, sl_own, r);
+          const int64_t row = rbase + r;
+          if (!col_ok || row >= p.M) continue;
+          if (p.chunks > 1) {
+            p.part[(static_cast<int64_t>(chunk) * p.M + row) * p.N + col] = x;
+          } else {
+            float o = p.scaled ? __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl, sr))) : __fmul_rn(p.alpha, x);
+            if (p.beta != 0.f) o = fmaf(p.beta, p.C[row * p.ldc + col], o);
+            p.D[row * p.ldd + col] = o;
+          }
+        }
+        __syncwarp();
       }
     }
     if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
@@ -359,23 +404,32 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
   if (!make_map_2d(&mL, dt, L, K, M, ldl * eb, box_k, kQM, CU_TENSOR_MAP_SWIZZLE_128B)) return LRAMM_ERR_CUDA;
   if (!make_map_2d(&mR, dt, R, K, N, ldr * eb, box_k, static_cast<uint32_t>(sh.bn), CU_TENSOR_MAP_SWIZZLE_128B))
     return LRAMM_ERR_CUDA;
+  // TMA stores of the output: one K chunk, no beta C term, D 16-byte aligned
+  // with a row pitch that is a multiple of 16 bytes
+  CUtensorMap mD;
+  p.tma_store = sh.chunks == 1 && p.beta == 0.f && p.stages * p.a_bytes >= 8 * 4096 &&
+                (reinterpret_cast<uintptr_t>(p.D) % 16) == 0 &&
+                (p.ldd * 4) % 16 == 0 && p.ldd >= N &&
+                make_map_2d(&mD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.D, N, M, p.ldd * 4, 32, 32,
+                            CU_TENSOR_MAP_SWIZZLE_128B);
+  if (!p.tma_store) mD = mL;   // unused
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
   const dim3 grid(static_cast<unsigned>(sh.ntiles), static_cast<unsigned>(sh.mtiles), static_cast<unsigned>(sh.chunks));
   switch (kind) {
     case kKindBF16:
       LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-      qgemm_tc_kernel<kKindBF16><<<grid, kQThreads, smem, s>>>(mL, mR, p);
+      qgemm_tc_kernel<kKindBF16><<<grid, kQThreads, smem, s>>>(mL, mR, mD, p);
       break;
     case kKindFP8:
       LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-      qgemm_tc_kernel<kKindFP8><<<grid, kQThreads, smem, s>>>(mL, mR, p);
+      qgemm_tc_kernel<kKindFP8><<<grid, kQThreads, smem, s>>>(mL, mR, mD, p);
       break;
     default:
       LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
-      qgemm_tc_kernel<kKindTF32><<<grid, kQThreads, smem, s>>>(mL, mR, p);
+      qgemm_tc_kernel<kKindTF32><<<grid, kQThreads, smem, s>>>(mL, mR, mD, p);
       break;
   }
   LRAMM_TRY(last_launch());
