@@ -138,7 +138,7 @@ def kernel_work(kind, cfg, l, variant):
 # they are in this tree); None where no capture of the current kernel exists.
 MEASURED_TRAFFIC = {
     "lramm_4096": {"svd": 642304, "chol": 702464, "trsm": 9308672, "gram": 8941312 + 7308288,
-                   "sketch": 71634688 + 2668544, "e3": 4260352 + 8458752},
+                   "sketch": 71634688 + 2668544},
 }
 
 

@@ -37,7 +37,7 @@ constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of eve
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, CS;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, CS, GS;
 };
 
 }  // namespace
@@ -59,7 +59,7 @@ struct lramm_plan_s {
   size_t cV, cW, cE1, cZ, cU, cE2;
   size_t sV, sW, sE1, sZ, sU, sE2;
   size_t amax;
-  size_t part, gpart, qpart;
+  size_t part, gpart, qpart, gtpart;
   size_t bsplit, bsplit_bytes;   // BF16 parts of the l-column operand (BF16 A or B)
   // MXFP4 block exponents of the chain operands; the lead / tail E3 buffers
   size_t xV, xW, xZ, xE1, xU, xE2;
@@ -135,6 +135,9 @@ void layout(lramm_plan_s* P) {
     S.L2 = b.take(sizeof(float) * l * l);
     S.Xd = b.take(sizeof(float) * ceil_div(l, 32) * 32 * 32);
     S.CS = chol_split_supported((int)l) ? b.take(sizeof(float) * chol_split_scratch_floats((int)l)) : 0;
+    S.GS = (d.sketch != LRAMM_SKETCH_F32 && gram_tc_supported((int)l))
+               ? b.take(sizeof(float) * gram_tc_scratch_floats(std::max(S.rows, S.cols), (int)l))
+               : 0;
     S.R = b.take(sizeof(float) * l * l);
     S.Vj = b.take(sizeof(float) * l * l);
     S.sig = b.take(sizeof(float) * l);
@@ -183,6 +186,9 @@ void layout(lramm_plan_s* P) {
   }
   P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
   P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
+  P->gtpart = d.sketch != LRAMM_SKETCH_F32 && gram_tc_supported((int)l)
+                  ? b.take(sizeof(float) * gram_tc_part_floats((int)l))
+                  : 0;
   P->bsplit_bytes = (d.a_type == LRAMM_BF16 || d.b_type == LRAMM_BF16)
                         ? sketch_bf_split_bytes(std::max(d.m, std::max(d.k, d.n)), (int)l)
                         : 0;
@@ -323,7 +329,32 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
       cb3.p[i] = CholProb{G, Lf, Xd};
       tb3.p[i] = TrsmProb{in[i], out[i], Lf, Xd, rows[i]};
     }
-    TIMED(P, LRAMM_K_GRAM, s, launch_gram(gb, l, at<float>(ws, P->gpart), s));
+    // Grams of tall sketches (>= 16384 rows) in split TF32 on the tensor cores
+    // when the products already run in TF32; the rest on the SIMT kernel
+    bool tc[2] = {false, false};
+    GramBatch gs{};
+    for (int i = 0; i < ns; ++i) {
+      tc[i] = P->gtpart && rows[i] >= 16384;
+      if (!tc[i]) gs.p[gs.n++] = gb.p[i];
+    }
+    for (int i = 0; i < ns; ++i)
+      if (tc[i]) {
+        const float* Yi[1] = {in[i]};
+        float* Gi[1] = {at<float>(ws, sd[i].S->G)};
+        float* scr[1] = {at<float>(ws, sd[i].S->GS)};
+        lramm_status gst = LRAMM_OK;
+        TIMED(P, LRAMM_K_GRAM, s,
+              (gst = gram_tc(1, Yi, &rows[i], Gi, l, scr, at<float>(ws, P->gtpart), gram_tc_part_floats(l), st, s)) ==
+                      LRAMM_ERR_UNSUPPORTED
+                  ? [&] {
+                      GramBatch g1{};
+                      g1.n = 1;
+                      g1.p[0] = gb.p[i];
+                      return launch_gram(g1, l, at<float>(ws, P->gpart), s);
+                    }()
+                  : gst);
+      }
+    if (gs.n) TIMED(P, LRAMM_K_GRAM, s, launch_gram(gs, l, at<float>(ws, P->gpart), s));
     if (chol3_supported(l) && l % 4 == 0) {  // blocked Cholesky + panel solve with inverted diagonal blocks
       TIMED(P, LRAMM_K_CHOL, s, launch_chol3(cb3, l, kCholShift, st, s));
       TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));

@@ -408,6 +408,168 @@ __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Gram G = Y^T Y of the CholeskyQR passes in split TF32 (three MMAs per K
+// step): Y = Y_hi + Y_lo with Y_hi = Y truncated to TF32 (exactly
+// representable) and Y_lo = Y - Y_hi (exact in FP32, 13 significant bits),
+// G ~ Y_hi^T Y_hi + Y_hi^T Y_lo + Y_lo^T Y_hi (the dropped Y_lo^T Y_lo term
+// and the TF32 rounding of Y_lo are ~2^-21 relative).  Both operands are
+// MN-major views of the same staged K x W tiles (W = l rounded up to 128):
+// the A operand of output row block mt is the tile's columns 128 mt ...
+// One CTA per (row block of G, K range), one launch per problem; split-K
+// partials are added by split_reduce_kernel.
+struct GramTcParams {
+  int l, W, n1, n2;
+  int64_t rows, kblocks;
+  int kb_per_split;
+  int stages;
+  uint32_t part_bytes, tmem_cols;
+  float* out;   // splits x l x l (or l x l when not split)
+  int splits;
+  int* status;
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmL, GramTcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mt = blockIdx.x, split = blockIdx.y;
+  const int64_t kb0 = static_cast<int64_t>(split) * p.kb_per_split;
+  const int64_t kb1 = min(p.kblocks, kb0 + p.kb_per_split);
+  const int nkb = static_cast<int>(kb1 - kb0);   // >= 1: the host sizes the splits to the K range
+  const int natoms = p.W / kAtom;
+  const uint32_t stage_bytes = 2 * p.part_bytes;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tmem_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (i >= p.stages && !mbar_wait(&empty_bar[s], ((i / p.stages) & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], stage_bytes);
+      const int k0 = static_cast<int>((kb0 + i) * kBK);
+      uint8_t* dst = smem + static_cast<size_t>(s) * stage_bytes;
+      for (int j = 0; j < natoms; ++j) {
+        tma_load_2d(dst + j * (kAtom * kBK * 4), &tmH, &full_bar[s], j * kAtom, k0);
+        tma_load_2d(dst + p.part_bytes + j * (kAtom * kBK * 4), &tmL, &full_bar[s], j * kAtom, k0);
+      }
+      ++issued;
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      const int first = issued > p.stages ? issued - p.stages : 0;
+      for (int i = first; i < issued; ++i) {
+        volatile int zero = 0;
+        mbar_wait(&full_bar[i % p.stages], (i / p.stages) & 1, &zero);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t id1 = idesc_tf32(kBM, p.n1, 1, 1);
+    const uint32_t id2 = p.n2 ? idesc_tf32(kBM, p.n2, 1, 1) : 0u;
+    const uint32_t seg2 = static_cast<uint32_t>(256 / kAtom) * (kAtom * kBK * 4);
+    const uint32_t aoff = static_cast<uint32_t>(mt * (kBM / kAtom)) * (kAtom * kBK * 4);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t hi = smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
+      const uint32_t lo = hi + p.part_bytes;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {
+        const uint32_t ko = kk * 1024;
+        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
+        // (A, B) = (hi, hi), (hi, lo), (lo, hi)
+        mma_tf32(tmem, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + ko), id1, acc0);
+        mma_tf32(tmem, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + ko), id1, 1u);
+        mma_tf32(tmem, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + ko), id1, 1u);
+        if (p.n2) {
+          mma_tf32(tmem + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, acc0);
+          mma_tf32(tmem + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + seg2 + ko), id2, 1u);
+          mma_tf32(tmem + 256, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, 1u);
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&tmem_bar);
+  } else if (warp >= 2) {
+    const int q = warp & 3;
+    volatile int zero = 0;
+    const bool ok = mbar_wait(&tmem_bar, 0, &zero);
+    tc_fence_after();
+    const int row = mt * kBM + q * 32 + lane;
+    float* dst = p.out + (static_cast<int64_t>(p.splits > 1 ? split : 0) * p.l + row) * p.l;
+    for (int c0 = 0; c0 < p.l; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+      if (!ok) continue;
+      if (row < p.l) {
+        const int nv = min(32, p.l - c0);
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          if (j < nv) *reinterpret_cast<float4*>(dst + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+    }
+    if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// Y (rows x l) -> Y_hi, Y_lo (rows x W, zero beyond l; W = l rounded up to
+// 32): Y_hi keeps the top
+// 19 bits of each FP32 word (sign, exponent, 10 mantissa bits), Y_lo = Y - Y_hi.
+__global__ void split_tf32_kernel(const float* __restrict__ Y, int64_t rows, int l, int W, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  const int64_t n = rows * W;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t r = e / W;
+    const int j = static_cast<int>(e - r * W);
+    const float y = j < l ? Y[r * l + j] : 0.f;
+    const float h = __uint_as_float(__float_as_uint(y) & 0xFFFFE000u);
+    hi[e] = h;
+    lo[e] = y - h;
+  }
+}
+
 // out = sum over splits of part[s] (fixed order), n4 float4 per split.
 __global__ void split_reduce_kernel(const float4* __restrict__ part, int splits, int64_t n4, float4* __restrict__ out) {
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
@@ -584,6 +746,78 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
                                                                   static_cast<int>(splits), n4,
                                                                   reinterpret_cast<float4*>(out));
     LRAMM_TRY(last_launch());
+  }
+  return LRAMM_OK;
+}
+
+// Gram on the tensor cores (split TF32) for one or two problems.
+static int gram_tc_width(int l) { return static_cast<int>(round_up(l, kBM)); }   // staged tile width
+static int gram_tc_ld(int l) { return static_cast<int>(round_up(l, kAtom)); }     // Y_hi / Y_lo row length
+
+size_t gram_tc_scratch_floats(int64_t rows, int l) { return 2 * static_cast<size_t>(rows) * gram_tc_ld(l) + 64; }
+
+size_t gram_tc_part_floats(int l) { return static_cast<size_t>(152) * l * l; }
+
+bool gram_tc_supported(int l) { return l >= 4 && l % 4 == 0 && l <= 512; }
+
+lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* const* scratch,
+                     float* part, size_t part_floats, int* status, cudaStream_t s) {
+  if (!gram_tc_supported(l) || n < 1 || n > 2) return LRAMM_ERR_UNSUPPORTED;
+  GramTcParams p{};
+  p.l = l;
+  p.W = gram_tc_width(l);
+  p.n1 = l <= 256 ? static_cast<int>(round_up(l, 16)) : 256;
+  p.n2 = l <= 256 ? 0 : static_cast<int>(round_up(l - 256, 16));
+  p.part_bytes = static_cast<uint32_t>(p.W) * kBK * 4;
+  p.stages = static_cast<int>((kSmemBudget - 1024) / (2 * p.part_bytes));
+  if (p.stages > kMaxStages) p.stages = kMaxStages;
+  if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
+  uint32_t tc = 32;
+  while (tc < static_cast<uint32_t>(p.n1 + p.n2)) tc <<= 1;
+  p.tmem_cols = tc;
+  p.status = status;
+  const int mtiles = static_cast<int>(ceil_div(l, kBM));
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * 2 * p.part_bytes;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  for (int i = 0; i < n; ++i) {
+    if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
+    p.rows = rows[i];
+    p.kblocks = ceil_div(rows[i], kBK);
+    int64_t splits = 152 / mtiles;
+    if (splits > p.kblocks / 8) splits = p.kblocks / 8;
+    if (splits < 1) splits = 1;
+    while (splits > 1 && static_cast<size_t>(splits) * l * l > part_floats) --splits;
+    p.kb_per_split = static_cast<int>(ceil_div(p.kblocks, splits));
+    splits = ceil_div(p.kblocks, p.kb_per_split);   // every CTA has at least one K block
+    p.splits = static_cast<int>(splits);
+    p.out = splits > 1 ? part : G[i];
+    // Y_hi / Y_lo rows of ld = l rounded to 32; the tile atoms beyond ld are
+    // loaded out of range (x a multiple of 32) and arrive as zeros
+    const int ld = gram_tc_ld(l);
+    float* hi = scratch[i];
+    float* lo = hi + static_cast<size_t>(rows[i]) * ld;
+    int64_t g = ceil_div(rows[i] * ld, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    split_tf32_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(Y[i], rows[i], l, ld, hi, lo);
+    LRAMM_TRY(last_launch());
+    CUtensorMap mh, ml;
+    if (!make_map_f32(&mh, hi, ld, rows[i], static_cast<uint64_t>(ld) * 4, kAtom, kBK,
+                      CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
+        !make_map_f32(&ml, lo, ld, rows[i], static_cast<uint64_t>(ld) * 4, kAtom, kBK,
+                      CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
+      return LRAMM_ERR_CUDA;
+    gram_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(mh, ml,
+                                                                                                              p);
+    LRAMM_TRY(last_launch());
+    if (splits > 1) {
+      const int64_t n4 = static_cast<int64_t>(l) * l / 4;
+      int64_t g2 = ceil_div(n4, 256);
+      if (g2 > 152 * 8) g2 = 152 * 8;
+      split_reduce_kernel<<<static_cast<unsigned>(g2), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
+                                                                     static_cast<int>(splits), n4,
+                                                                     reinterpret_cast<float4*>(G[i]));
+      LRAMM_TRY(last_launch());
+    }
   }
   return LRAMM_OK;
 }

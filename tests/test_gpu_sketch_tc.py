@@ -101,3 +101,21 @@ def test_sketch_product_bf16_operand(L, rows, cols, l, transpose, sketch):
     K = Xd.shape[1]
     rel = 2.0 ** -15 if sketch == "tf32" else 2.0 ** -8
     assert np.all(np.abs(out - ref) <= (rel + K * 2.0 ** -23) * mag), np.max(np.abs(out - ref) / mag)
+
+
+@pytest.mark.parametrize("m,k,r,p,q", [(16384, 600, 128, 16, 2), (20000, 500, 60, 4, 0), (16400, 700, 256, 16, 1),
+                                       (4096, 1000, 128, 16, 2)])
+def test_rsvd_tf32_split_gram(L, m, k, r, p, q):
+    """TF32 mode runs the CholeskyQR Grams of tall sketches (>= 16384 rows) in
+    split TF32 on the tensor cores (l = 144, 64, 272; K tails): orthogonality
+    to working precision after the two final passes, and the rank-r product
+    within a few TF32 roundings."""
+    X = workloads.lowrank(m, k, workloads.spectrum("poly1", min(m, k)), 88 + m).astype(np.float32)
+    plan = L.Plan(m, m, k, r, p, q, seed=7, sketch=L.SKETCH_TF32)
+    ws = plan.workspace()
+    U, S, V = (t.cpu().numpy() for t in L.rsvd(plan, 0, torch.from_numpy(X).cuda(), ws=ws))
+    assert L.status_read(ws) == 0
+    Uo, so, Vo = oracle.lramm.rsvd(X, r, p, q, 7, 0)
+    assert oracle.lramm.rel_fro((U * S) @ V.T, (Uo * so) @ Vo.T) < 4 * 2.0 ** -10
+    tol = 4.0 * np.sqrt(max(m, k) * (r + p)) * 2.0 ** -24
+    assert np.abs(U.T @ U - np.eye(r)).max() < 4 * tol
