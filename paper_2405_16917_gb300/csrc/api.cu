@@ -38,6 +38,7 @@ constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of eve
 struct SideLayout {
   int64_t rows, cols;
   size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, CS, GS;
+  size_t part, gpart, gtpart, bsplit;   // this operand's split-K partials and BF16 parts (own stream)
 };
 
 }  // namespace
@@ -59,8 +60,12 @@ struct lramm_plan_s {
   size_t cV, cW, cE1, cZ, cU, cE2;
   size_t sV, sW, sE1, sZ, sU, sE2;
   size_t amax;
-  size_t part, gpart, qpart, gtpart;
-  size_t bsplit, bsplit_bytes;   // BF16 parts of the l-column operand (BF16 A or B)
+  size_t qpart;
+  size_t bsplit_bytes;           // BF16 parts of the l-column operand (BF16 A or B), per side
+  // second stream and fork / join events: the two operands' RSVDs overlap
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int dev = -1;
   // MXFP4 block exponents of the chain operands; the lead / tail E3 buffers
   size_t xV, xW, xZ, xE1, xU, xE2;
   int64_t lq;
@@ -184,15 +189,18 @@ void layout(lramm_plan_s* P) {
     P->sEl = b.take(sizeof(float) * d.n);
     P->tres = b.take(sizeof(float) * std::max(d.m, d.n) * d.lead);
   }
-  P->part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
-  P->gpart = b.take(sizeof(float) * gram_part_floats((int)l));
-  P->gtpart = d.sketch != LRAMM_SKETCH_F32 && gram_tc_supported((int)l)
-                  ? b.take(sizeof(float) * gram_tc_part_floats((int)l))
-                  : 0;
   P->bsplit_bytes = (d.a_type == LRAMM_BF16 || d.b_type == LRAMM_BF16)
                         ? sketch_bf_split_bytes(std::max(d.m, std::max(d.k, d.n)), (int)l)
                         : 0;
-  P->bsplit = P->bsplit_bytes ? b.take(P->bsplit_bytes) : 0;
+  for (int sd = 0; sd < 2; ++sd) {   // per operand: the two RSVDs run on two streams
+    SideLayout& S = P->side[sd];
+    S.part = b.take(sizeof(float) * sketch_tc_part_floats((int)l));
+    S.gpart = b.take(sizeof(float) * gram_part_floats((int)l));
+    S.gtpart = d.sketch != LRAMM_SKETCH_F32 && gram_tc_supported((int)l)
+                   ? b.take(sizeof(float) * gram_tc_part_floats((int)l))
+                   : 0;
+    S.bsplit = P->bsplit_bytes ? b.take(P->bsplit_bytes) : 0;
+  }
   {  // split-K partials of the tensor-core code products (E1 with long K)
     auto qp = [](int prec, int64_t M, int64_t N, int64_t K) -> size_t {
       return (prec == LRAMM_P_F32 || prec == LRAMM_P_MXFP4) ? 0 : qgemm_tc_part_floats(prec, M, N, K);
@@ -277,15 +285,15 @@ lramm_status check_ws(const lramm_plan_s* P, void* ws, size_t ws_bytes) {
 // cores in TF32 when the plan asks for a TF32 sketch and the shapes allow
 // (TMA needs l and the row stride of X divisible by 4, 16-byte aligned
 // bases), else the FP32 SIMT product.
-lramm_status x_product(lramm_plan_s* P, void* ws, int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx,
-                       int xbf, const float* B, float* out, cudaStream_t s) {
+lramm_status x_product(lramm_plan_s* P, void* ws, const SideLayout& S, int a_mn, const void* X, int64_t rows,
+                       int64_t cols, int64_t ldx, int xbf, const float* B, float* out, cudaStream_t s) {
   const int l = P->l;
   const int sk = P->d.sketch;
   if (xbf && sk != LRAMM_SKETCH_F32 && P->bsplit_bytes && sketch_bf_supported(ldx, l, X, B))
-    return sketch_bf(a_mn, X, rows, cols, ldx, B, l, sk == LRAMM_SKETCH_TF32 ? 2 : 1, out, at<float>(ws, P->part),
-                     sketch_tc_part_floats(l), at<void>(ws, P->bsplit), P->bsplit_bytes, at<int>(ws, 0), s);
+    return sketch_bf(a_mn, X, rows, cols, ldx, B, l, sk == LRAMM_SKETCH_TF32 ? 2 : 1, out, at<float>(ws, S.part),
+                     sketch_tc_part_floats(l), at<void>(ws, S.bsplit), P->bsplit_bytes, at<int>(ws, 0), s);
   if (sk != LRAMM_SKETCH_F32 && sketch_tc_supported(xbf, ldx, l, X, B))
-    return sketch_tc(a_mn, X, rows, cols, ldx, xbf, B, l, out, at<float>(ws, P->part),
+    return sketch_tc(a_mn, X, rows, cols, ldx, xbf, B, l, out, at<float>(ws, S.part),
                      sketch_tc_part_floats(l), at<int>(ws, 0), s);
   if (a_mn) return sgemm(1, 0, cols, l, rows, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
   return sgemm(0, 0, rows, l, cols, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
@@ -334,7 +342,7 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
     bool tc[2] = {false, false};
     GramBatch gs{};
     for (int i = 0; i < ns; ++i) {
-      tc[i] = P->gtpart && rows[i] >= 16384;
+      tc[i] = sd[i].S->gtpart && rows[i] >= 16384;
       if (!tc[i]) gs.p[gs.n++] = gb.p[i];
     }
     for (int i = 0; i < ns; ++i)
@@ -344,17 +352,18 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
         float* scr[1] = {at<float>(ws, sd[i].S->GS)};
         lramm_status gst = LRAMM_OK;
         TIMED(P, LRAMM_K_GRAM, s,
-              (gst = gram_tc(1, Yi, &rows[i], Gi, l, scr, at<float>(ws, P->gtpart), gram_tc_part_floats(l), st, s)) ==
+              (gst = gram_tc(1, Yi, &rows[i], Gi, l, scr, at<float>(ws, sd[i].S->gtpart), gram_tc_part_floats(l), st,
+                             s)) ==
                       LRAMM_ERR_UNSUPPORTED
                   ? [&] {
                       GramBatch g1{};
                       g1.n = 1;
                       g1.p[0] = gb.p[i];
-                      return launch_gram(g1, l, at<float>(ws, P->gpart), s);
+                      return launch_gram(g1, l, at<float>(ws, sd[i].S->gpart), s);
                     }()
                   : gst);
       }
-    if (gs.n) TIMED(P, LRAMM_K_GRAM, s, launch_gram(gs, l, at<float>(ws, P->gpart), s));
+    if (gs.n) TIMED(P, LRAMM_K_GRAM, s, launch_gram(gs, l, at<float>(ws, sd[0].S->gpart), s));
     if (chol3_supported(l) && l % 4 == 0) {  // blocked Cholesky + panel solve with inverted diagonal blocks
       TIMED(P, LRAMM_K_CHOL, s, launch_chol3(cb3, l, kCholShift, st, s));
       TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
@@ -403,24 +412,25 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
     cols[i] = S.cols;
     float* Om = at<float>(ws, S.omega);
     TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, (uint32_t)which[i], S.cols, l, Om, l, s));
-    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s));
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s));
   }
   LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, d.q > 0 ? 1 : 2, false, st, s));  // Q
   for (int it = 0; it < d.q; ++it) {
     for (int i = 0; i < ns; ++i)
-      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));
+      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));
     LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 1, false, st, s));  // Z^ (span only)
     for (int i = 0; i < ns; ++i)
-      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, C0[i], R0[i], s));
+      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 0, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, C0[i], R0[i], s));
     LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, it == d.q - 1 ? 2 : 1, false, st, s));
   }
   for (int i = 0; i < ns; ++i)
-    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));  // B^T
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));  // B^T
   LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 2, true, st, s));  // B^T = P R
   // R row-major is R^T column-major: one-sided Jacobi on R^T = U_s S V_s^T.
   JacobiBatch jb{};
   FinalBatch fb{};
   jb.n = fb.n = ns;
+  jb.info0 = ns == 1 ? which[0] : 0;
   for (int i = 0; i < ns; ++i) {
     const SideLayout& S = *sd[i].S;
     jb.M[i] = at<float>(ws, S.R);
@@ -430,6 +440,25 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
   }
   TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s));
   TIMED(P, LRAMM_K_SVDSORT, s, launch_svd_finalize(fb, l, d.r, s));
+  return LRAMM_OK;
+}
+
+// The plan's second stream and fork / join events, made on first use on the
+// calling thread's current device (remade if the device changes).
+lramm_status ensure_streams(lramm_plan_s* P) {
+  int dev = 0;
+  LRAMM_CUDA_TRY(cudaGetDevice(&dev));
+  if (P->s2 && P->dev == dev) return LRAMM_OK;
+  if (P->s2) {
+    cudaStreamDestroy(P->s2);
+    cudaEventDestroy(P->ev_fork);
+    cudaEventDestroy(P->ev_join);
+    P->s2 = nullptr;
+  }
+  LRAMM_CUDA_TRY(cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking));
+  LRAMM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+  LRAMM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  P->dev = dev;
   return LRAMM_OK;
 }
 
@@ -471,7 +500,7 @@ lramm_status range_finder_side(lramm_plan_s* P, const SideRun& sd, void* ws, boo
   };
   float* Om = at<float>(ws, S.omega);
   TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, 1u, S.cols, l, Om, l, s));
-  TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, Om, R0, s));
+  TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd.S, 0, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, Om, R0, s));
   const int p0 = d.q > 0 ? 1 : 2;
   float* src[1] = {R0};
   float* tmp[1] = {R1};
@@ -481,7 +510,7 @@ lramm_status range_finder_side(lramm_plan_s* P, const SideRun& sd, void* ws, boo
   if (keep)
     LRAMM_CUDA_TRY(cudaMemcpyAsync(at<float>(ws, P->bq), R0, sizeof(float) * S.rows * l, cudaMemcpyDeviceToDevice, s));
   for (int it = 0; it < d.q; ++it) {
-    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 1, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, R0, C0, s));
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd.S, 1, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, R0, C0, s));
     float* csrc[1] = {C0};
     float* ctmp[1] = {C1};
     LRAMM_TRY(orth_sides(P, ws, &sd, 1, csrc, ctmp, csrc, cols, 1, false, st, s));
@@ -489,7 +518,7 @@ lramm_status range_finder_side(lramm_plan_s* P, const SideRun& sd, void* ws, boo
     if (keep)
       LRAMM_CUDA_TRY(cudaMemcpyAsync(at<float>(ws, P->bz) + (int64_t)it * S.cols * l, C0, sizeof(float) * S.cols * l,
                                      cudaMemcpyDeviceToDevice, s));
-    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, 0, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, C0, R0, s));
+    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd.S, 0, sd.X, S.rows, S.cols, sd.ldx, sd.xbf, C0, R0, s));
     const int pi = it == d.q - 1 ? 2 : 1;
     LRAMM_TRY(orth_sides(P, ws, &sd, 1, src, tmp, src, rows, pi, false, st, s));
     LRAMM_TRY(keep_L(2 * it + 2, pi));
@@ -536,7 +565,7 @@ lramm_status qr_adjoint(lramm_plan_s* P, void* ws, const float* Q, int64_t rows,
   const int l = P->l;
   float* M = at<float>(ws, P->tM);
   float* Mc = at<float>(ws, P->tMc);
-  LRAMM_TRY(x_product(P, ws, 1, dQ, rows, l, l, 0, Q, M, s));   // M = dQ^T Q
+  LRAMM_TRY(x_product(P, ws, P->side[1], 1, dQ, rows, l, l, 0, Q, M, s));   // M = dQ^T Q
   LRAMM_TRY(launch_copyltu(M, Mc, l, s));
   // dQ += Q copyltu(-M); copyltu(M) is symmetric, so it serves as the N x K operand
   LRAMM_TRY(nt_product(P, ws, rows, l, l, -1.f, Q, l, Mc, l, 1.f, dQ, l, s));
@@ -702,11 +731,18 @@ lramm_status lramm_plan_create(const lramm_desc* desc, lramm_plan_t* out) {
 }
 
 lramm_status lramm_plan_destroy(lramm_plan_t plan) {
-  if (plan)
+  if (plan) {
     for (TimerRec& r : plan->recs) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
     }
+    if (plan->s2) {
+      cudaStreamSynchronize(plan->s2);
+      cudaStreamDestroy(plan->s2);
+      cudaEventDestroy(plan->ev_fork);
+      cudaEventDestroy(plan->ev_join);
+    }
+  }
   delete plan;
   return LRAMM_OK;
 }
@@ -793,16 +829,37 @@ lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const
   const SideLayout& SB = plan->side[1];
   const SideRun sd[2] = {side_run(plan, 0, A), side_run(plan, 1, B)};
   const int which[2] = {0, 1}, s1s[2] = {1, 0}, s2s[2] = {0, 1};
-  LRAMM_TRY(rsvd_sides(plan, sd, which, 2, ws, s1s, s2s, s));
-  TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(0, 0, d.m, r, l, 1.f, at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, 0.f, Ut, r, s));
-  TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SA.S2), r, 0, at<float>(ws, SA.C0), l, 0.f, Vt, d.k, s));
+  // The two operands' RSVDs are independent: A on the caller's stream, B on
+  // the plan's second stream, so that one operand's latency-bound small
+  // algebra (a few CTAs) runs beside the other's HBM-bound products.
+  LRAMM_TRY(ensure_streams(plan));
+  cudaStream_t s2 = plan->s2;
+  LRAMM_CUDA_TRY(cudaEventRecord(plan->ev_fork, s));
+  LRAMM_CUDA_TRY(cudaStreamWaitEvent(s2, plan->ev_fork, 0));
+  auto side_a = [&]() -> lramm_status {
+    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s));
+    TIMED(plan, LRAMM_K_ASSEMBLE, s,
+          sgemm(0, 0, d.m, r, l, 1.f, at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, 0.f, Ut, r, s));
+    TIMED(plan, LRAMM_K_ASSEMBLE, s,
+          sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SA.S2), r, 0, at<float>(ws, SA.C0), l, 0.f, Vt, d.k, s));
+    return LRAMM_OK;
+  };
   // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)
-  TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SB.S1), r, 0, at<float>(ws, SB.R0), l, 0.f, Wt, d.k, s));
-  TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(0, 0, d.n, r, l, 1.f, at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, 0.f, Zt, r, s));
+  auto side_b = [&]() -> lramm_status {
+    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2));
+    TIMED(plan, LRAMM_K_ASSEMBLE, s2,
+          sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SB.S1), r, 0, at<float>(ws, SB.R0), l, 0.f, Wt, d.k, s2));
+    TIMED(plan, LRAMM_K_ASSEMBLE, s2,
+          sgemm(0, 0, d.n, r, l, 1.f, at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, 0.f, Zt, r, s2));
+    return LRAMM_OK;
+  };
+  const lramm_status st_a = side_a();
+  const lramm_status st_b = side_b();
+  // join (also after an error: nothing of this call may still run on s2 once it returns to s's order)
+  LRAMM_CUDA_TRY(cudaEventRecord(plan->ev_join, s2));
+  LRAMM_CUDA_TRY(cudaStreamWaitEvent(s, plan->ev_join, 0));
+  LRAMM_TRY(st_a);
+  LRAMM_TRY(st_b);
   return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
 }
 
@@ -920,8 +977,8 @@ lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, f
   const float* Q = at<float>(ws, sw.S->R0);
   float* T = at<float>(ws, sx.S->R0);   // m x l
   float* Pt = at<float>(ws, sw.S->C0);  // n x l = (Q^T W)^T
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, X, d.m, d.k, d.lda, sx.xbf, Q, T, s));
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, d.k, d.n, d.ldb, sw.xbf, Q, Pt, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sx.S, 0, X, d.m, d.k, d.lda, sx.xbf, Q, T, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 1, W, d.k, d.n, d.ldb, sw.xbf, Q, Pt, s));
   if (d.prec[2] == LRAMM_P_F32) {
     TIMED(plan, LRAMM_K_E3, s, nt_product(plan, ws, d.m, d.n, l, d.alpha, T, l, Pt, l, d.beta, C, d.ldc, s));
     return LRAMM_OK;
@@ -958,20 +1015,20 @@ lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, 
   float* dQ = at<float>(ws, plan->tdQ);
   float* dZ = at<float>(ws, plan->tdZ);
   float* dY = at<float>(ws, plan->tY);
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, X, m, k, d.lda, sx.xbf, Q, T, s));
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, k, n, d.ldb, sw.xbf, Q, Pt, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sx.S, 0, X, m, k, d.lda, sx.xbf, Q, T, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 1, W, k, n, d.ldb, sw.xbf, Q, Pt, s));
   // dT = alpha G P^T (m x l), dP^T = alpha G^T T (n x l)
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, G, m, n, d.ldc, 0, Pt, dT, s));
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, G, m, n, d.ldc, 0, T, dPt, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 0, G, m, n, d.ldc, 0, Pt, dT, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 1, G, m, n, d.ldc, 0, T, dPt, s));
   TIMED(plan, LRAMM_K_BWD, s, launch_scale(dT, m * l, d.alpha, s));
   TIMED(plan, LRAMM_K_BWD, s, launch_scale(dPt, n * l, d.alpha, s));
   // dX = dT Q^T (m x k);  dW = Q dP (k x n)
   TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, m, k, l, 1.f, dT, l, Q, l, 0.f, dX, k, s));
   TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, Q, l, dPt, l, 0.f, dW, n, s));
   // dQ = X^T dT + W dP^T (k x l)
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, X, m, k, d.lda, sx.xbf, dT, dQ, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sx.S, 1, X, m, k, d.lda, sx.xbf, dT, dQ, s));
   float* tmp = at<float>(ws, plan->tB);
-  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, W, k, n, d.ldb, sw.xbf, dPt, tmp, s));
+  TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 0, W, k, n, d.ldb, sw.xbf, dPt, tmp, s));
   TIMED(plan, LRAMM_K_BWD, s, launch_axpy(dQ, tmp, k * l, 1.f, s));
   // back through the power iterations (Omega fixed)
   for (int i = d.q; i >= 1; --i) {
@@ -980,10 +1037,10 @@ lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, 
     TIMED(plan, LRAMM_K_ADJOINT, s,
           qr_adjoint(plan, ws, Qi(i), k, bl_slot(plan, ws, o, 0), two ? bl_slot(plan, ws, o, 1) : nullptr, dQ, dY, s));
     TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, dY, l, Zi(i), l, 1.f, dW, n, s));   // dW += dY Z_i^T
-    TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 1, W, k, n, d.ldb, sw.xbf, dY, dZ, s));   // dZ = W^T dY
+    TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 1, W, k, n, d.ldb, sw.xbf, dY, dZ, s));   // dZ = W^T dY
     TIMED(plan, LRAMM_K_ADJOINT, s, qr_adjoint(plan, ws, Zi(i), n, bl_slot(plan, ws, o - 1, 0), nullptr, dZ, dY, s));
     TIMED(plan, LRAMM_K_BWD, s, nt_product(plan, ws, k, n, l, 1.f, Qi(i - 1), l, dY, l, 1.f, dW, n, s));  // dW += Q_{i-1} dY'^T
-    TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, 0, W, k, n, d.ldb, sw.xbf, dY, dQ, s));   // dQ = W dY'
+    TIMED(plan, LRAMM_K_SKETCH, s, x_product(plan, ws, *sw.S, 0, W, k, n, d.ldb, sw.xbf, dY, dQ, s));   // dQ = W dY'
   }
   TIMED(plan, LRAMM_K_ADJOINT, s,
         qr_adjoint(plan, ws, Qi(0), k, bl_slot(plan, ws, 0, 0), d.q == 0 ? bl_slot(plan, ws, 0, 1) : nullptr, dQ, dY, s));

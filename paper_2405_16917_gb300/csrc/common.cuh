@@ -101,6 +101,7 @@ struct JacobiBatch {
   float* M[2];  // l x l column-major: in R^T, out U_s Sigma (unsorted columns)
   float* V[2];  // l x l column-major: out the accumulated rotations V_s
   int n;
+  int info0;    // sweep counts go to status[1 + info0 + problem]
 };
 struct FinalProb {
   const float* M;

@@ -355,7 +355,7 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
     if (!any) break;
   }
   if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
-  if (tid == 0 && rank == 0 && status) status[1 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;  // diagnostics
+  if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;  // diagnostics
   int bt_, bb_, bf_;
   jc_bufs(rank, e, bt_, bb_, bf_);
   for (int half = 0; half < 2; ++half) {
@@ -714,7 +714,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
     if (!any) break;
   }
   if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
-  if (tid == 0 && rank == 0 && status) status[1 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
+  if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
   // no CTA leaves while a bulk copy it issued may still be writing a peer
   if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   cluster.sync();
