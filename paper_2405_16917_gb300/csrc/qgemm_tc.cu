@@ -115,7 +115,6 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   __shared__ float sR_sh[256];
-  __shared__ float tr_sh[4][32 * 33];
   volatile int* abort_flag = &abort_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,8 +252,9 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
     } else {
       // Each 32 x 32 block (rows = this warp's TMEM lanes) is transposed
       // through shared memory so that a store instruction writes 32
-      // consecutive columns of one row (128 bytes).
-      float* T = tr_sh[q];
+      // consecutive columns of one row (128 bytes); the 32 x 33 blocks live
+      // in the operand ring, free once the accumulator is complete.
+      float* T = reinterpret_cast<float*>(sA) + q * (32 * 33);
       for (int c0 = 0; c0 < p.bn; c0 += 32) {
         float v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
@@ -336,11 +336,9 @@ QtcShape qtc_shape(int kind, int64_t M, int64_t N, int64_t K) {
   sh.kblocks = static_cast<int>(ceil_div(K, stage_k));
   sh.bn = static_cast<int>(N >= 256 ? 256 : round_up(N, 16));
   // short K and a wide output (E3: m x n, K = r; the rank-l updates of the
-  // range-finder backward): 128-column tiles with a short ring, so that two
-  // or three CTAs share an SM and one CTA's epilogue (the HBM-bound part)
-  // overlaps another's loads and MMAs
+  // range-finder backward): a 2-stage ring so that two CTAs share an SM and
+  // one CTA's epilogue (the HBM-bound part) overlaps the other's loads and MMAs
   const bool wide = N >= 1024 && K * kind_elem_bytes(kind) <= 2048;
-  if (wide) sh.bn = 128;
   sh.mtiles = ceil_div(M, kQM);
   sh.ntiles = ceil_div(N, sh.bn);
   const int64_t tiles = sh.mtiles * sh.ntiles;
@@ -360,8 +358,7 @@ QtcShape qtc_shape(int kind, int64_t M, int64_t N, int64_t K) {
   if (st > kQMaxStages) st = kQMaxStages;
   if (st > sh.kb_per_chunk) st = sh.kb_per_chunk;
   if (st < 2) st = 2;
-  // a 2-stage ring (32 KB per stage at BN = 128) leaves room for two CTAs
-  // per SM next to the epilogue's 17 KB of static shared memory
+  // a 2-stage ring (48 KB per stage at BN = 256) leaves room for two CTAs per SM
   if (wide || (sh.kb_per_chunk <= 8 && sh.bn <= 128)) st = 2;
   sh.stages = st;
   return sh;
