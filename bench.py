@@ -297,6 +297,7 @@ def run_lramm(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    n_launch0 = L.launch_count()
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
@@ -306,6 +307,7 @@ def run_lramm(args):
             a = kinds.setdefault(kname, [0.0, 0])
             a[0] += ms
             a[1] += cnt
+    n_launch = L.launch_count() - n_launch0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -448,7 +450,7 @@ def run_lramm(args):
                "sample": "one oracle LRAMM step at m=%d n=%d k=%d r=%d p=%d q=%d, %.1f s"
                          % (cs["m"], cs["n"], cs["k"], cs["r"], cs["p"], cs["q"], t_cpu)}
 
-    launches = sum(c for _, c in kinds.values())
+    launches = n_launch
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
@@ -558,11 +560,13 @@ def run_rf(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    n_launch0 = L.launch_count()
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
         _, (dX, dW) = step(True)
         ends[i].record(stream)
+    n_launch = L.launch_count() - n_launch0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -664,7 +668,7 @@ def run_rf(args):
                "cores": cores_used(), "kind": "oracle",
                "sample": "one oracle range-finder forward + backward at m=%d n=%d k=%d r=%d p=%d q=%d, %.1f s"
                          % (cs["m"], cs["n"], cs["k"], cs["r"], cs["p"], cs["q"], t_cpu)}
-    launches = sum(c for _, c in kinds.values())
+    launches = n_launch
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,

@@ -338,6 +338,10 @@ LRAMM_API lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t
                                             float* out, int32_t sketch, void* ws, size_t ws_bytes,
                                             void* stream);
 
+/* Number of CUDA kernels the library has launched in this process so far
+ * (all plans and threads): the difference around a region counts its launches. */
+LRAMM_API uint64_t lramm_launch_count(void);
+
 /* MXFP4 quantiser (lramm_prec LRAMM_P_MXFP4) of the rows of X (rows x cols,
  * stride ldx, FP32): per row and per 32 consecutive elements, e = ceil(log2(
  * fp32(a_max / 6))) clamped to [-127, 127] (-127 for a zero block), element

@@ -64,6 +64,7 @@ _SIGS = {
     "lramm_qgemm_tc_ws_bytes": (ctypes.c_size_t, [_I32, _I64, _I64, _I64]),
     "lramm_tgemm_tc": (_I32, [_I64, _I64, _I64, _F, _VP, _I64, _VP, _I64, _F, _VP, _I64, _VP, ctypes.c_size_t, _VP]),
     "lramm_tgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
+    "lramm_launch_count": (ctypes.c_uint64, []),
     "lramm_quantize_mx": (_I32, [_VP, _I64, _I64, _I64, _VP, _I64, _VP, _VP]),
     "lramm_qgemm_mx": (_I32, [_VP, _VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _F, _F, _VP, _I64, _VP, _I64, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
@@ -289,6 +290,11 @@ def info_read(ws, n=3, stream=None):
     buf = (ctypes.c_int32 * n)()
     _check(load().lramm_info_read(_ptr(ws), buf, n, _stream(stream)), "lramm_info_read")
     return list(buf)
+
+
+def launch_count():
+    """Kernels the library has launched in this process so far."""
+    return load().lramm_launch_count()
 
 
 def status_read(ws, stream=None):

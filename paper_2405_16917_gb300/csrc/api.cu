@@ -1,3 +1,4 @@
+#include <atomic>
 // C ABI of the LRAMM library: plan, workspace layout and the pipeline
 //   RSVD(A), RSVD(B)  (Sec. 2.2 range finder + Algorithm 1)
 //   E1, E2, E3 chain  (Algorithm 3, QM of Algorithm 2)
@@ -18,6 +19,9 @@ using namespace lramm;
 
 namespace lramm {
 static thread_local char g_cuda_err[256];
+static std::atomic<unsigned long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
 void note_cuda_error(cudaError_t e, const char* where) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
 }
@@ -701,6 +705,8 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
 extern "C" {
 
 const char* lramm_last_cuda_error(void) { return g_cuda_err; }
+
+uint64_t lramm_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 const char* lramm_status_str(lramm_status st) {
   switch (st) {

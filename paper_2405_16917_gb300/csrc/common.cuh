@@ -61,7 +61,12 @@ void note_cuda_error(cudaError_t e, const char* where);
     if (_s != LRAMM_OK) return _s;                            \
   } while (0)
 
+// Every kernel launch of the library is followed by exactly one check;
+// the check also counts the launch (lramm_launch_count).
+void count_launch();
+
 inline lramm_status last_launch_at(const char* where) {
+  count_launch();
   const cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) return LRAMM_OK;
   note_cuda_error(e, where);

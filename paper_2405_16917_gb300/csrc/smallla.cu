@@ -389,9 +389,14 @@ __device__ __forceinline__ void group_bar(int id) {
   asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory");
 }
 
+// Stopping rule of the cluster Jacobi: a sweep whose largest relative inner
+// product stays below kJacobiQuad * tol is the last one.
+constexpr float kJacobiQuad = 20.0f;
+
 template <int RP, int GW>
 __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], float (&ym)[RP], float (&yv)[RP],
-                                           float tol, int grp, int wig, int lane, float (*s_part)[2][4]) {
+                                           float tol, int grp, int wig, int lane, float (*s_part)[2][4],
+                                           float& rmax) {
   float al = 0.f, be = 0.f, ga = 0.f;
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
@@ -435,6 +440,9 @@ __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], flo
   // rotation stays orthogonal to working precision because s and c come
   // from the same t and the tau form below depends on c only through s^2.
   const float nab = al * rsqrtf(al) * (be * rsqrtf(be));   // sqrt(al) sqrt(be); NaN for a zero column: no rotation
+  // largest relative inner product of the sweep (for the stopping rule)
+  const float rel = __fdividef(fabsf(ga), nab);
+  if (rel > rmax) rmax = rel;
   if (!(fabsf(ga) > tol * nab)) return false;
   const float zeta = __fdividef(be - al, 2.0f * ga);
   const float az = fabsf(zeta);
@@ -564,7 +572,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   __shared__ float s_part[16][2][4];
   __shared__ int s_flags[16];
   __shared__ int s_ids[32];
-  __shared__ int s_rot;
+  __shared__ int s_rmax;   // bits of the sweep's largest relative inner product (non-negative)
   __shared__ __align__(8) uint64_t rx_bar[2];   // incoming blocks of even / odd moves
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = warp / GW, wig = warp % GW, p = tid & (32 * GW - 1);
@@ -600,7 +608,8 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   int e = 0;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) s_rmax = 0;
+    float rmax = 0.f;
     __syncthreads();
     for (int br = 0; br < 2 * C - 1; ++br) {
       int bt_, bb_, bfl, bfr;
@@ -634,10 +643,9 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
             float* cy = base + (int64_t)y * cs;
             jc2_load<RP, GW>(cx, ls, p, xm, xv);
             jc2_load<RP, GW>(cy, ls, p, ym, yv);
-            if (jc2_rotate<RP, GW>(xm, xv, ym, yv, tol, grp, wig, lane, s_part)) {
+            if (jc2_rotate<RP, GW>(xm, xv, ym, yv, tol, grp, wig, lane, s_part, rmax)) {
               jc2_store<RP, GW>(cx, ls, p, xm, xv);
               jc2_store<RP, GW>(cy, ls, p, ym, yv);
-              if (p == 0) s_rot = 1;
             }
           }
           __syncthreads();
@@ -654,16 +662,13 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
           float* bcol = botb + (int64_t)k * cs;
           float bm[RP], bv[RP];
           jc2_load<RP, GW>(bcol, ls, p, bm, bv);
-          if (jc2_rotate<RP, GW>(tm, tv, bm, bv, tol, grp, wig, lane, s_part)) {
+          if (jc2_rotate<RP, GW>(tm, tv, bm, bv, tol, grp, wig, lane, s_part, rmax)) {
             jc2_store<RP, GW>(bcol, ls, p, bm, bv);
             trot = true;
           }
           __syncthreads();
         }
-        if (trot) {
-          jc2_store<RP, GW>(tcol, ls, p, tm, tv);
-          if (p == 0) s_rot = 1;
-        }
+        if (trot) jc2_store<RP, GW>(tcol, ls, p, tm, tv);
       }
       if (C > 1) {
         // Move: push the outgoing blocks into the neighbours' landing buffers
@@ -705,13 +710,18 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
       }
       __syncthreads();
     }
-    // convergence: every CTA's rotation flag for the sweep, one cluster barrier
+    // Convergence: the largest relative inner product |a.b| / (|a| |b|) met in
+    // the sweep, over the cluster (one cluster barrier).  Below tol nothing
+    // was rotated; below kJacobiQuad tol the rotations of this sweep leave
+    // inner products of the order of its square (quadratic convergence), so
+    // a further sweep would rotate nothing: stop after this one.
+    if (lane == 0) atomicMax(&s_rmax, __float_as_int(rmax));
     __syncthreads();
-    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rot;
+    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rmax;
     cluster.sync();
-    int any = 0;
-    for (int c = 0; c < C; ++c) any |= s_flags[c];
-    if (!any) break;
+    int mx = 0;
+    for (int c = 0; c < C; ++c) mx = max(mx, s_flags[c]);
+    if (!(__int_as_float(mx) > kJacobiQuad * tol)) break;
   }
   if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
   if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
