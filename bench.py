@@ -134,11 +134,12 @@ def kernel_work(kind, cfg, l, variant):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu captures summarised under profiles/ (lramm_4096, the kernels as
-# they are in this tree); None where no capture of the current kernel exists.
+# the ncu captures summarised under profiles/ (lramm_4096, one operand per
+# launch, the kernels as they are in this tree); None where no capture of the
+# current kernel exists.
 MEASURED_TRAFFIC = {
-    "lramm_4096": {"svd": 642304, "chol": 702464, "trsm": 9308672, "gram": 8941312 + 7308288,
-                   "sketch": 71634688 + 2668544},
+    "lramm_4096": {"svd": 347648, "chol": 406784, "trsm": 4667904, "gram": 4484608 + 3663616,
+                   "sketch": 71603456 + 2272512, "e3": 4272384 + 8035072},
 }
 
 
@@ -147,11 +148,13 @@ def measured_traffic(workload, kind):
 
 
 def jacobi_work(l, sweeps):
-    """Algorithmic FP32 flops of one launch of the one-sided Jacobi SVD (both
-    operands): per sweep every one of the l(l-1)/2 column pairs forms three
-    inner products of length l (6 l flops) and rotates its two columns of M
-    and of V (4 vectors x 3 l flops) -- 18 l flops per pair."""
-    return sum(s * l * (l - 1) / 2 * 18.0 * l for s in sweeps)
+    """Algorithmic FP32 flops of one launch of the one-sided Jacobi SVD (one
+    operand per launch: the two operands' SVDs run on two streams; `sweeps`
+    lists both, the result is their mean): per sweep every one of the
+    l(l-1)/2 column pairs forms three inner products of length l (6 l flops)
+    and rotates its two columns of M and of V (4 vectors x 3 l flops) -- 18 l
+    flops per pair."""
+    return sum(s * l * (l - 1) / 2 * 18.0 * l for s in sweeps) / max(len(sweeps), 1)
 
 
 def fp32_alu_peak_tflops(sm_mhz):
@@ -419,7 +422,8 @@ def run_lramm(args):
                 "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz",
                 "traffic": measured_traffic(args.workload, "svd"),
                 "algorithmic_flops_per_launch": jf,
-                "note": "one-sided Jacobi, sequential rounds of column-pair rotations on 2 x 16-CTA clusters"}
+                "note": "one-sided Jacobi, sequential rounds of column-pair rotations on a 16-CTA cluster "
+                        "(one launch per operand, the two on concurrent streams)"}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
