@@ -360,6 +360,16 @@ def run_lramm(args):
     Cb = torch.empty((m, n), dtype=torch.bfloat16, device=dev)
     t_bf16 = timed(lambda: torch.matmul(A16, B16, out=Cb))
     err_bf16 = rel_err(Cb)
+    # the paper's direct quantised comparators DQ8 / DQ4 (Algorithm 2 on the full operands)
+    Af, Bf = A.float(), B.float()
+    Dq = torch.empty((m, n), dtype=torch.float32, device=dev)
+    dq = {}
+    for name, pq in (("dq8", 1), ("dq4", 2)):
+        wsq = torch.empty(L.load().lramm_dq_ws_bytes(pq, m, n, k), dtype=torch.uint8, device=dev)
+        t_dq = timed(lambda: L.dq_matmul(Af, Bf, prec=pq, out=Dq, ws=wsq))
+        dq[name] = {"tflops": flops / (t_dq * 1e-3) / 1e12, "ms": t_dq, "rel_fro_err_vs_fp64_exact": rel_err(Dq)}
+        del wsq
+    del Af, Bf, Dq
     plain = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=(0, 0, 0), a_type=a_type, b_type=a_type)
     Dp = torch.empty_like(D)
     t_plain = timed(lambda: L.matmul(plan=plain, A=A, B=B, out=Dp, ws=ws), reps=2)
@@ -472,6 +482,7 @@ def run_lramm(args):
                                            "rel_fro_err_vs_fp64_exact": err_bf16},
                        "plain_lramm_fp32": {"tflops": flops / (t_plain * 1e-3) / 1e12, "ms": t_plain,
                                             "rel_fro_err_vs_fp64_exact": err_plain},
+                       "direct_quantised": dq,
                        "device_status": st},
             "breakdown_ms_per_step": {kn: round(v[0] / args.steps, 4) for kn, v in
                                       sorted(kinds.items(), key=lambda kv: -kv[1][0])},

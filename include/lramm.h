@@ -338,6 +338,20 @@ LRAMM_API lramm_status lramm_sketch_product(const void* X, int64_t rows, int64_t
                                             float* out, int32_t sketch, void* ws, size_t ws_bytes,
                                             void* stream);
 
+/* Direct quantised product D = alpha QM(A B, prec) + beta C (Algorithm 2 on
+ * the full operands: the paper's DQ8 / DQ4 comparators of Sec. 4.2).  A: m x k
+ * (stride lda), B: k x n (stride ldb), FP32 row-major; A is quantised per
+ * row and B per column (LRAMM_S_ROWCOL) or each per tensor (LRAMM_S_TENSOR),
+ * with the decisions and dequantisation of lramm_quantize / lramm_qgemm;
+ * prec INT8, INT4 or E4M3 (exact integer sums for INT8 / INT4).  ws:
+ * lramm_dq_ws_bytes(prec, m, n, k) bytes, 256-byte aligned (status word,
+ * codes, scales, split-K partials).  Asynchronous on `stream`. */
+LRAMM_API lramm_status lramm_dq_matmul(int32_t prec, int32_t scale, int64_t m, int64_t n, int64_t k, float alpha,
+                                       const float* A, int64_t lda, const float* B, int64_t ldb, float beta,
+                                       const float* C, int64_t ldc, float* D, int64_t ldd, void* ws, size_t ws_bytes,
+                                       void* stream);
+LRAMM_API size_t lramm_dq_ws_bytes(int32_t prec, int64_t m, int64_t n, int64_t k);
+
 /* Number of CUDA kernels the library has launched in this process so far
  * (all plans and threads): the difference around a region counts its launches. */
 LRAMM_API uint64_t lramm_launch_count(void);

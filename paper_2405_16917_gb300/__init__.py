@@ -65,6 +65,9 @@ _SIGS = {
     "lramm_tgemm_tc": (_I32, [_I64, _I64, _I64, _F, _VP, _I64, _VP, _I64, _F, _VP, _I64, _VP, ctypes.c_size_t, _VP]),
     "lramm_tgemm_tc_ws_bytes": (ctypes.c_size_t, [_I64, _I64, _I64]),
     "lramm_launch_count": (ctypes.c_uint64, []),
+    "lramm_dq_matmul": (_I32, [_I32, _I32, _I64, _I64, _I64, _F, _VP, _I64, _VP, _I64, _F, _VP, _I64, _VP, _I64, _VP,
+                               ctypes.c_size_t, _VP]),
+    "lramm_dq_ws_bytes": (ctypes.c_size_t, [_I32, _I64, _I64, _I64]),
     "lramm_quantize_mx": (_I32, [_VP, _I64, _I64, _I64, _VP, _I64, _VP, _VP]),
     "lramm_qgemm_mx": (_I32, [_VP, _VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _F, _F, _VP, _I64, _VP, _I64, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
@@ -290,6 +293,23 @@ def info_read(ws, n=3, stream=None):
     buf = (ctypes.c_int32 * n)()
     _check(load().lramm_info_read(_ptr(ws), buf, n, _stream(stream)), "lramm_info_read")
     return list(buf)
+
+
+def dq_matmul(A, B, prec=P_INT8, per_row=True, alpha=1.0, beta=0.0, C=None, out=None, ws=None, stream=None):
+    """Direct quantised product alpha QM(A B, prec) + beta C (the DQ8 / DQ4 comparators)."""
+    torch = _torch()
+    _need_cuda(A, B, C)
+    m, k = A.shape
+    n = B.shape[1]
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float32, device=A.device)
+    need = load().lramm_dq_ws_bytes(prec, m, n, k)
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=A.device)
+    _check(load().lramm_dq_matmul(prec, S_ROWCOL if per_row else S_TENSOR, m, n, k, alpha, _ptr(A), A.stride(0), _ptr(B),
+                                  B.stride(0), beta, _ptr(C), C.stride(0) if C is not None else 0, _ptr(out),
+                                  out.stride(0), _ptr(ws), ws.numel(), _stream(stream)), "lramm_dq_matmul")
+    return out
 
 
 def launch_count():

@@ -1116,4 +1116,51 @@ lramm_status lramm_qgemm_mx(const int8_t* L, const int8_t* Le, const int8_t* Rt,
   return qgemm_mx(L, Le, Rt, Re, M, N, K, ldl, ldr, alpha, beta, C, ldc, D, ldd, static_cast<cudaStream_t>(stream));
 }
 
+// Direct QM(A B) of Algorithm 2 (the paper's DQ8 / DQ4 comparators).
+size_t lramm_dq_ws_bytes(int32_t prec, int64_t m, int64_t n, int64_t k) {
+  if (m <= 0 || n <= 0 || k <= 0 || (prec != LRAMM_P_INT8 && prec != LRAMM_P_INT4 && prec != LRAMM_P_E4M3))
+    return kAlign;
+  const int64_t kp = round_up(k, 32);
+  Bump b;
+  b.take(kAlign);                                  // status word
+  b.take(kAlign);                                  // tensor a_max
+  b.take(2 * m * kp);                              // codes of A (widest container)
+  b.take(2 * n * kp);                              // codes of B^T
+  b.take(sizeof(float) * (m + n));                 // scales
+  b.take(sizeof(float) * std::max<size_t>(qgemm_tc_part_floats(prec, m, n, kp), 4));
+  return b.off;
+}
+
+lramm_status lramm_dq_matmul(int32_t prec, int32_t scale, int64_t m, int64_t n, int64_t k, float alpha,
+                             const float* A, int64_t lda, const float* B, int64_t ldb, float beta, const float* C,
+                             int64_t ldc, float* D, int64_t ldd, void* ws, size_t ws_bytes, void* stream) {
+  if (prec != LRAMM_P_INT8 && prec != LRAMM_P_INT4 && prec != LRAMM_P_E4M3) return LRAMM_ERR_INVALID_ARG;
+  if (scale != LRAMM_S_ROWCOL && scale != LRAMM_S_TENSOR) return LRAMM_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 1 || lda < k || ldb < n || ldd < n) return LRAMM_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return LRAMM_OK;
+  if (!A || !B || !D || (beta != 0.f && (!C || ldc < n))) return LRAMM_ERR_INVALID_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) % kAlign) || ws_bytes < lramm_dq_ws_bytes(prec, m, n, k))
+    return LRAMM_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t kp = round_up(k, 32);
+  const int per = scale == LRAMM_S_ROWCOL;
+  Bump b;
+  const size_t o_st = b.take(kAlign), o_am = b.take(kAlign), o_ca = b.take(2 * m * kp), o_cb = b.take(2 * n * kp);
+  const size_t o_s = b.take(sizeof(float) * (m + n));
+  const size_t pf = std::max<size_t>(qgemm_tc_part_floats(prec, m, n, kp), 4);
+  const size_t o_p = b.take(sizeof(float) * pf);
+  int* st = at<int>(ws, o_st);
+  LRAMM_CUDA_TRY(cudaMemsetAsync(st, 0, sizeof(int) * 4, s));
+  void* cA = at<void>(ws, o_ca);
+  void* cB = at<void>(ws, o_cb);
+  float* sA = at<float>(ws, o_s);
+  float* sB = sA + m;
+  LRAMM_TRY(quantize_rows(A, m, k, lda, prec, per, cA, kp, sA, at<unsigned int>(ws, o_am), s));
+  LRAMM_TRY(quantize_cols(B, k, n, ldb, prec, per, cB, kp, sB, at<unsigned int>(ws, o_am), s));
+  if (qgemm_tc_supported(prec, cA, cB, kp, kp, m, n, kp))
+    return qgemm_tc(prec, cA, cB, m, n, kp, kp, kp, per, sA, sB, alpha, beta, C, ldc, D, ldd, at<float>(ws, o_p), pf,
+                    st, s);
+  return qgemm(cA, cB, m, n, kp, kp, kp, prec, per, sA, sB, alpha, beta, C, ldc, D, ldd, 0, s);
+}
+
 }  // extern "C"

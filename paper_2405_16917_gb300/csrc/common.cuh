@@ -222,6 +222,9 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
 lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
                            int per_row, void* codes, int64_t ldcodes, float* scales,
                            unsigned int* amax_ws, cudaStream_t s);
+// Columns of X quantised as the rows of a K-major code matrix (cols x ldcodes).
+lramm_status quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, int per_col,
+                           void* codesT, int64_t ldcodes, float* scales, unsigned int* amax_ws, cudaStream_t s);
 lramm_status quantize_rows_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
                                    int per_row, void* codes, int64_t ldcodes, float* scales,
                                    cudaStream_t s);

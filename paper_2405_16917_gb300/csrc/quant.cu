@@ -111,6 +111,94 @@ lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t l
   return last_launch();
 }
 
+// Column quantiser: the columns of X (rows x cols, row-major) become the
+// rows of a K-major code matrix codesT (cols x ldcodes, ldcodes >= rows,
+// zero beyond rows) with one scale per column (or the tensor a_max) --
+// the right operand of a direct QM(A B).  One CTA per 32 columns: pass 1
+// finds each column's a_max (8 warps over the rows, coalesced rows of 32),
+// pass 2 quantises 32 x 32 tiles and writes them transposed through shared
+// memory.  Same FP32 decisions as quant_rows_kernel.
+template <int PREC>
+__global__ void __launch_bounds__(256) quant_cols_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                         int64_t ldx, void* __restrict__ codesT, int64_t ldcodes,
+                                                         float* __restrict__ scales,
+                                                         const unsigned int* __restrict__ tensor_amax) {
+  __shared__ float s_am[8][32];
+  __shared__ float s_lam[32];
+  __shared__ float tile[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int64_t col = c0 + lane;
+  const float D = PREC == LRAMM_P_INT8 ? 127.0f : (PREC == LRAMM_P_INT4 ? 7.0f : 448.0f);
+  if (tensor_amax) {
+    if (warp == 0) s_am[0][lane] = __uint_as_float(*tensor_amax);
+  } else {
+    float am = 0.f;
+    if (col < cols)
+      for (int64_t r = warp; r < rows; r += 8) am = fmaxf(am, fabsf(X[r * ldx + col]));
+    s_am[warp][lane] = am;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    float am = s_am[0][lane];
+    if (!tensor_amax)
+      for (int w = 1; w < 8; ++w) am = fmaxf(am, s_am[w][lane]);
+    s_lam[lane] = am > 0.f ? __fdiv_rn(D, am) : 0.f;
+    if (col < cols && (tensor_amax == nullptr || col == 0)) scales[tensor_amax ? 0 : col] = __fdiv_rn(am, D);
+  }
+  __syncthreads();
+  for (int64_t r0 = 0; r0 < ldcodes; r0 += 32) {
+    // load 32 rows x 32 columns (row r0 + warp + 8 i, column lane)
+    for (int i = warp; i < 32; i += 8) {
+      const int64_t r = r0 + i;
+      tile[i][lane] = (r < rows && col < cols) ? X[r * ldx + col] : 0.f;
+    }
+    __syncthreads();
+    // write column c0 + j (a row of codesT): lane = row offset within the tile
+    for (int j = warp; j < 32; j += 8) {
+      const int64_t c = c0 + j;
+      const int64_t r = r0 + lane;
+      if (c < cols && r < ldcodes) {
+        const float y = r < rows ? __fmul_rn(tile[lane][j], s_lam[j]) : 0.f;
+        store_code<PREC>(codesT, c * ldcodes + r, y, D);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+lramm_status quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, int per_col,
+                           void* codesT, int64_t ldcodes, float* scales, unsigned int* amax_ws, cudaStream_t s) {
+  if (cols <= 0) return LRAMM_OK;
+  if (ldcodes < rows) return LRAMM_ERR_INVALID_ARG;
+  const unsigned int* tam = nullptr;
+  if (!per_col) {
+    if (!amax_ws) return LRAMM_ERR_INVALID_ARG;
+    LRAMM_CUDA_TRY(cudaMemsetAsync(amax_ws, 0, sizeof(unsigned int), s));
+    int64_t g = ceil_div(rows * cols, 256);
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) g = 1;
+    tensor_amax_kernel<<<(unsigned)g, 256, 0, s>>>(X, rows, cols, ldx, amax_ws);
+    LRAMM_TRY(last_launch());
+    tam = amax_ws;
+  }
+  const unsigned g = static_cast<unsigned>(ceil_div(cols, 32));
+  switch (prec) {
+    case LRAMM_P_INT8:
+      quant_cols_kernel<LRAMM_P_INT8><<<g, 256, 0, s>>>(X, rows, cols, ldx, codesT, ldcodes, scales, tam);
+      break;
+    case LRAMM_P_INT4:
+      quant_cols_kernel<LRAMM_P_INT4><<<g, 256, 0, s>>>(X, rows, cols, ldx, codesT, ldcodes, scales, tam);
+      break;
+    case LRAMM_P_E4M3:
+      quant_cols_kernel<LRAMM_P_E4M3><<<g, 256, 0, s>>>(X, rows, cols, ldx, codesT, ldcodes, scales, tam);
+      break;
+    default:
+      return LRAMM_ERR_INVALID_ARG;
+  }
+  return last_launch();
+}
+
 // ---------------------------------------------------------------------------
 // QM product, SIMT: acc(i,j) = sum_t L(i,t) Rt(j,t) with both operands
 // K-major code matrices.  Integer codes accumulate exactly: FP32 partial
