@@ -16,6 +16,8 @@ Workload table (sizes, spectra, rank parameters):
                  sigma_i = exp(-i/128) + 1e-3; r=384, p=16, q=1
   lramm_32768    m=32768, k=4096, n=32768, FP32, sigma_i = (1+i)^-1.5;
                  r=128, p=16, q=2
+Entry-distribution matrices (`entry_matrix`): the paper's precision tests
+draw i.i.d. U(0,1), Exp(1), N(0,1) and Bernoulli(1/2) entries.
 Seeds: A 1001, B 1002, X 1003, sketch 7.
 """
 import numpy as np
@@ -82,6 +84,24 @@ def exact_rank(rows, cols, rank, seed, decay=0.5):
 def gaussian(rows, cols, seed):
     """i.i.d. N(0,1) entries (FP64)."""
     return np.random.default_rng(seed).standard_normal((rows, cols))
+
+
+ENTRY_DISTS = ("uniform", "exponential", "normal", "binary")
+
+
+def entry_matrix(dist, rows, cols, seed):
+    """i.i.d. entries of the paper's precision tests (Sec. 4.2-4.3, Fig. 3):
+    U(0,1), Exp(1), N(0,1) or Bernoulli(1/2) on {0, 1} (FP64)."""
+    rng = np.random.default_rng(seed)
+    if dist == "uniform":
+        return rng.uniform(0.0, 1.0, (rows, cols))
+    if dist == "exponential":
+        return rng.exponential(1.0, (rows, cols))
+    if dist == "normal":
+        return rng.standard_normal((rows, cols))
+    if dist == "binary":
+        return rng.integers(0, 2, (rows, cols)).astype(np.float64)
+    raise ValueError("unknown entry distribution %r" % dist)
 
 
 def operands(name, scale=None):
