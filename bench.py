@@ -272,8 +272,12 @@ def run_lramm(args):
     sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
     sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
     lead = LEADS.get(args.variant, (0, 1, 0))
+    # the timed steps run an uninstrumented plan; a second, instrumented plan
+    # (CUDA events around every kernel) gives the per-kind breakdown
     plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
-                  sketch=sketch, timing=True, lead=lead[0], lead_prec=lead[1], lead_split=lead[2])
+                  sketch=sketch, lead=lead[0], lead_prec=lead[1], lead_split=lead[2])
+    tplan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
+                   sketch=sketch, timing=True, lead=lead[0], lead_prec=lead[1], lead_split=lead[2])
     ws = plan.workspace(dev)
     D = torch.empty((m, n), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -306,10 +310,6 @@ def run_lramm(args):
         starts[i].record(stream)
         L.matmul(plan, A, B, out=D, ws=ws)
         ends[i].record(stream)
-        for kname, (ms, cnt) in plan.timing().items():
-            a = kinds.setdefault(kname, [0.0, 0])
-            a[0] += ms
-            a[1] += cnt
     n_launch = L.launch_count() - n_launch0
     torch.cuda.synchronize()
     if dist:
@@ -326,6 +326,16 @@ def run_lramm(args):
     flops = 2.0 * m * n * k
     value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
     st = L.status_read(ws)
+
+    # per-kind device time (instrumented plan, outside the timed region)
+    nbd = min(args.steps, 5)
+    for i in range(nbd):
+        flush.zero_()
+        L.matmul(tplan, A, B, out=D, ws=ws)
+        for kname, (ms, cnt) in tplan.timing().items():
+            a = kinds.setdefault(kname, [0.0, 0])
+            a[0] += ms
+            a[1] += cnt
 
     # accuracy of this variant and of the comparators (outside the timed region);
     # outputs above 2^28 entries are compared on a seeded sample of 2048 rows
@@ -411,14 +421,14 @@ def run_lramm(args):
     if dname == "sketch" and sketch_name == "tf32":
         # tcgen05 products streaming X once: bound by HBM bandwidth
         roof = {"bound": "hbm", "achieved": nbytes / avg_s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+                "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
                 "peak_source": peak_src + " hbm_gbs", "traffic": None, "algorithmic_bytes_per_launch": nbytes}
         roof["frac"] = roof["achieved"] / roof["peak"]
     elif dname in ("sketch", "e3", "gram", "trsm", "e1", "e2") and nflops is not None:
         # these kernels are FP32 SIMT in this version: bound by FP32 FMA issue
         roof = {"bound": "alu", "achieved": nflops / avg_s / 1e12,
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
-                "kernel": dname, "launches_per_step": dcnt / args.steps,
+                "kernel": dname, "launches_per_step": dcnt / nbd,
                 "avg_launch_ms": avg_s * 1e3, "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz"}
         roof["frac"] = roof["achieved"] / roof["peak"]
         roof["traffic"] = None
@@ -428,7 +438,7 @@ def run_lramm(args):
         jf = jacobi_work(l, [int(x) for x in info[1:3] if int(x) > 0])
         roof = {"bound": "alu", "achieved": jf / avg_s / 1e12,
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
-                "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+                "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
                 "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz",
                 "traffic": measured_traffic(args.workload, "svd"),
                 "algorithmic_flops_per_launch": jf,
@@ -437,7 +447,7 @@ def run_lramm(args):
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
-                "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+                "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
                 "note": "latency-bound small factorisation; no algorithmic roof"}
     # the bandwidth-bound kernels, each against its own roof (same definitions)
     kroofs = {}
@@ -451,7 +461,7 @@ def run_lramm(args):
             continue
         kroofs[kn] = {"bound": "hbm", "achieved": kb / ks / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                       "frac": kb / ks / 1e9 / pk["hbm_gbs"], "avg_launch_ms": ks * 1e3,
-                      "launches_per_step": kc / args.steps, "algorithmic_bytes_per_launch": kb,
+                      "launches_per_step": kc / nbd, "algorithmic_bytes_per_launch": kb,
                       "traffic": measured_traffic(args.workload, kn)}
 
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
@@ -484,8 +494,10 @@ def run_lramm(args):
                                             "rel_fro_err_vs_fp64_exact": err_plain},
                        "direct_quantised": dq,
                        "device_status": st},
-            "breakdown_ms_per_step": {kn: round(v[0] / args.steps, 4) for kn, v in
+            "breakdown_ms_per_step": {kn: round(v[0] / nbd, 4) for kn, v in
                                       sorted(kinds.items(), key=lambda kv: -kv[1][0])},
+            "breakdown_note": "CUDA events around every kernel of %d separate steps; both operands' streams "
+                              "summed" % nbd,
             "roofline": roof,
             "kernel_rooflines": kroofs,
             "cpu_baseline": cpu,
@@ -535,7 +547,9 @@ def run_rf(args):
     sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
     sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
     plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=(0, 0, prec), a_type=L.BF16, b_type=L.F32,
-                  sketch=sketch, timing=True)
+                  sketch=sketch)
+    tplan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=(0, 0, prec), a_type=L.BF16, b_type=L.F32,
+                   sketch=sketch, timing=True)
     ws = plan.workspace(dev)
     C = torch.empty((m, n), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
@@ -543,16 +557,17 @@ def run_rf(args):
     kinds = {}
 
     def collect():
-        for kname, (ms, cnt) in plan.timing().items():
+        for kname, (ms, cnt) in tplan.timing().items():
             a = kinds.setdefault(kname, [0.0, 0])
             a[0] += ms
             a[1] += cnt
 
     def step(record):
-        out = L.rf_forward(plan, X, W, C=C, ws=ws)
+        pl = tplan if record else plan
+        out = L.rf_forward(pl, X, W, C=C, ws=ws)
         if record:
             collect()
-        grads = L.rf_backward(plan, X, W, G, ws=ws)
+        grads = L.rf_backward(pl, X, W, G, ws=ws)
         if record:
             collect()
         return out, grads
@@ -579,7 +594,7 @@ def run_rf(args):
     for i in range(args.steps):
         flush.zero_()
         starts[i].record(stream)
-        _, (dX, dW) = step(True)
+        _, (dX, dW) = step(False)
         ends[i].record(stream)
     n_launch = L.launch_count() - n_launch0
     torch.cuda.synchronize()
@@ -596,6 +611,10 @@ def run_rf(args):
     flops = 6.0 * m * n * k
     value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
     st = L.status_read(ws)
+    nbd = min(args.steps, 3)   # instrumented steps for the per-kind breakdown (outside the timed region)
+    for _ in range(nbd):
+        flush.zero_()
+        step(True)
 
     # accuracy (outside the timed region): forward against X W, gradients
     # against the dense layer's G W^T and X^T G, all in FP64 on the device
@@ -672,7 +691,7 @@ def run_rf(args):
     dname, (dms, dcnt) = max(kinds.items(), key=lambda kv: kv[1][0])
     avg_s = dms / dcnt * 1e-3
     roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
-            "kernel": dname, "launches_per_step": dcnt / args.steps, "avg_launch_ms": avg_s * 1e3,
+            "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
             "note": "no per-launch algorithmic figure for this kind in the range-finder form"}
 
     cpu = None
@@ -699,8 +718,9 @@ def run_rf(args):
                        "rel_fro_err_dx_vs_fp64_dense": err_dx, "rel_fro_err_dw_vs_fp64_dense": err_dw,
                        "dense_bf16_fwd_bwd": {"tflops": flops / (t_bf16 * 1e-3) / 1e12, "ms": t_bf16},
                        "device_status": st},
-            "breakdown_ms_per_step": {kn: round(v[0] / args.steps, 4) for kn, v in
+            "breakdown_ms_per_step": {kn: round(v[0] / nbd, 4) for kn, v in
                                       sorted(kinds.items(), key=lambda kv: -kv[1][0])},
+            "breakdown_note": "CUDA events around every kernel of %d separate steps" % nbd,
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
@@ -722,8 +742,8 @@ def run_rf(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lramm", "reference"], default="lramm")
     ap.add_argument("--workload", default="lramm_4096", choices=sorted(workloads.CONFIGS))
     ap.add_argument("--variant", default="int8", choices=sorted(VARIANTS))

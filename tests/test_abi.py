@@ -97,3 +97,41 @@ def test_calls_reject_bad_arguments_without_gpu_work(L):
     assert lib.lramm_quantize(fake, 4, 8, 8, 0, 1, fake, 8, fake, nul, nul) == 1      # F32 is not a code
     assert lib.lramm_philox_words(1, 0, 4, ctypes.c_void_p(4), nul) == 1               # misaligned
     assert lib.lramm_status_str(5).decode().startswith("non-positive")
+
+
+def test_plan_validates_lead_tail_fields(L):
+    ok = _plan(L, prec=(1, 1, 4), lead=16, lead_prec=1, lead_split=2)
+    ok.close()
+    for bad in (dict(lead=65), dict(lead=-1), dict(lead=8, lead_prec=0), dict(lead=8, lead_prec=4),
+                dict(lead=8, lead_split=3)):
+        with pytest.raises(L.LrammError) as e:
+            _plan(L, **bad)
+        assert e.value.code == 1, bad
+    with pytest.raises(L.LrammError) as e:
+        _plan(L, prec=(1, 1, 5))
+    assert e.value.code == 1
+
+
+def test_plan_l_limits(L):
+    # l = 576 is the orthonormalisation's limit (two-level Cholesky), 580 is past it
+    p = _plan(L, m=2048, n=2048, k=2048, r=560, p=16)
+    p.close()
+    with pytest.raises(L.LrammError) as e:
+        _plan(L, m=2048, n=2048, k=2048, r=564, p=16)
+    assert e.value.code == 2
+    # l = 342 (not a multiple of 4, past the column-panel Cholesky's shared memory) is refused
+    with pytest.raises(L.LrammError) as e:
+        _plan(L, m=2048, n=2048, k=2048, r=326, p=16)
+    assert e.value.code == 2
+
+
+def test_dq_and_mx_argument_checks(L):
+    lib = L.load()
+    fake, nul = ctypes.c_void_p(256), ctypes.c_void_p(0)
+    assert lib.lramm_dq_matmul(0, 0, 4, 4, 4, 1.0, fake, 4, fake, 4, 0.0, nul, 0, fake, 4, fake, 1 << 20, nul) == 1
+    assert lib.lramm_dq_matmul(1, 2, 4, 4, 4, 1.0, fake, 4, fake, 4, 0.0, nul, 0, fake, 4, fake, 1 << 20, nul) == 1
+    assert lib.lramm_dq_matmul(1, 0, 4, 4, 4, 1.0, fake, 4, fake, 4, 0.0, nul, 0, fake, 4, nul, 0, nul) == 3
+    assert lib.lramm_dq_ws_bytes(1, 4096, 4096, 4096) > lib.lramm_dq_ws_bytes(1, 64, 64, 64)
+    assert lib.lramm_quantize_mx(fake, 4, 40, 40, fake, 40, fake, nul) == 1       # ldcodes not a multiple of 32
+    assert lib.lramm_qgemm_mx(fake, fake, fake, fake, 4, 4, 48, 48, 48, 1.0, 0.0, nul, 0, fake, 4, nul) == 1
+    assert lib.lramm_launch_count() >= 0
