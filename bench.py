@@ -275,13 +275,17 @@ def run_lramm(args):
     # the timed steps run an uninstrumented plan; a second, instrumented plan
     # (CUDA events around every kernel) gives the per-kind breakdown
     plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
-                  sketch=sketch, lead=lead[0], lead_prec=lead[1], lead_split=lead[2])
+                  sketch=sketch, lead=lead[0], lead_prec=lead[1], lead_split=lead[2], graph=True)
     tplan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
                    sketch=sketch, timing=True, lead=lead[0], lead_prec=lead[1], lead_split=lead[2])
     ws = plan.workspace(dev)
     D = torch.empty((m, n), dtype=torch.float32, device=dev)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    # a non-default stream: the plan captures its call into a CUDA graph there
+    # (the first warm-up step) and replays it afterwards
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
 
     for _ in range(max(args.warmup, 0)):
         L.matmul(plan, A, B, out=D, ws=ws)
@@ -483,7 +487,7 @@ def run_lramm(args):
             "config": {"workload": args.workload, "m": m, "n": n, "k": k, "r": r, "p": p, "q": q,
                        "variant": args.variant, "operands": cfg["dtype"], "spectrum": cfg["spectrum"],
                        "lead": {"directions": lead[0], "prec": lead[1], "residual_terms": lead[2]} if lead[0] else None,
-                       "sketch": sketch_name, "scale": "rowcol",
+                       "sketch": sketch_name, "scale": "rowcol", "cuda_graph": True,
                        "jacobi_sweeps": info[1:3], "l2": "flushed: 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "rel_fro_err_vs_fp64_exact": err,

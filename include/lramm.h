@@ -115,6 +115,13 @@ typedef struct lramm_desc {
  * the call's stream, so lramm_timing_read can attribute device time per
  * kernel kind (the per-operator time split of Sec. 4.1, Fig. 2). */
 #define LRAMM_FLAG_TIMING 1
+/* flags: lramm_matmul records its ~110 launches once into a CUDA graph (stream
+ * capture on the call's stream) and replays the graph on later calls with the
+ * same A, B, C, D, workspace, stream and device; any other arguments capture
+ * a new graph.  Ignored with LRAMM_FLAG_TIMING or on the legacy default
+ * stream (0), which cannot be captured.  The caller keeps the captured
+ * buffers alive while the plan may replay them. */
+#define LRAMM_FLAG_GRAPH 2
 
 /* Kernel kinds reported by lramm_timing_read. */
 typedef enum {

@@ -81,6 +81,7 @@ _SIGS = {
 }
 
 FLAG_TIMING = 1
+FLAG_GRAPH = 2
 K_COUNT = 16
 
 
@@ -143,7 +144,7 @@ class Plan:
 
     def __init__(self, m, n, k, r, p, q, seed=7, prec=(P_INT8, P_INT8, P_INT8), scale=S_ROWCOL,
                  sketch=SKETCH_F32, alpha=1.0, beta=0.0, a_type=F32, b_type=F32, lda=None, ldb=None,
-                 ldc=None, max_sweeps=0, timing=False, lead=0, lead_prec=P_INT8, lead_split=0):
+                 ldc=None, max_sweeps=0, timing=False, lead=0, lead_prec=P_INT8, lead_split=0, graph=False):
         lib = load()
         d = Desc()
         d.m, d.n, d.k = m, n, k
@@ -156,7 +157,7 @@ class Plan:
         d.prec[0], d.prec[1], d.prec[2] = prec
         d.scale, d.sketch = scale, sketch
         d.alpha, d.beta = alpha, beta
-        d.max_sweeps, d.flags = max_sweeps, (FLAG_TIMING if timing else 0)
+        d.max_sweeps, d.flags = max_sweeps, (FLAG_TIMING if timing else 0) | (FLAG_GRAPH if graph else 0)
         d.lead, d.lead_prec, d.lead_split = lead, lead_prec, lead_split
         self.desc = d
         h = ctypes.c_void_p()

@@ -70,6 +70,11 @@ struct lramm_plan_s {
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int dev = -1;
+  // LRAMM_FLAG_GRAPH: the captured call and the arguments it was captured with
+  cudaGraphExec_t gexec = nullptr;
+  const void* gkey[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int gdev = -1;
+  size_t glaunches = 0;   // kernels in the captured graph
   // MXFP4 block exponents of the chain operands; the lead / tail E3 buffers
   size_t xV, xW, xZ, xE1, xU, xE2;
   int64_t lq;
@@ -113,7 +118,7 @@ lramm_status validate(const lramm_desc* d) {
     if (!valid_prec(d->prec[i])) return LRAMM_ERR_INVALID_ARG;
   if (d->scale != LRAMM_S_ROWCOL && d->scale != LRAMM_S_TENSOR) return LRAMM_ERR_INVALID_ARG;
   if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_BF16) return LRAMM_ERR_INVALID_ARG;
-  if (d->max_sweeps < 0 || (d->flags & ~LRAMM_FLAG_TIMING) != 0) return LRAMM_ERR_INVALID_ARG;
+  if (d->max_sweeps < 0 || (d->flags & ~(LRAMM_FLAG_TIMING | LRAMM_FLAG_GRAPH)) != 0) return LRAMM_ERR_INVALID_ARG;
   if (d->lead < 0 || d->lead > d->r || d->lead_split < 0 || d->lead_split > 2) return LRAMM_ERR_INVALID_ARG;
   if (d->lead > 0 && d->lead_prec != LRAMM_P_INT8 && d->lead_prec != LRAMM_P_INT4 && d->lead_prec != LRAMM_P_E4M3)
     return LRAMM_ERR_INVALID_ARG;
@@ -742,6 +747,7 @@ lramm_status lramm_plan_destroy(lramm_plan_t plan) {
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
     }
+    if (plan->gexec) cudaGraphExecDestroy(plan->gexec);
     if (plan->s2) {
       cudaStreamSynchronize(plan->s2);
       cudaStreamDestroy(plan->s2);
@@ -815,6 +821,9 @@ lramm_status lramm_chain(lramm_plan_t plan, const float* Ut, const float* Vt, co
   return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
 }
 
+lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const float* C, float* D, void* ws,
+                         cudaStream_t s);
+
 lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const float* C, float* D,
                           void* ws, size_t ws_bytes, void* stream) {
   if (!plan || !A || !B || !D) return LRAMM_ERR_INVALID_ARG;
@@ -822,6 +831,45 @@ lramm_status lramm_matmul(lramm_plan_t plan, const void* A, const void* B, const
   if (plan->l > svd_max_l()) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!(plan->d.flags & LRAMM_FLAG_GRAPH) || plan->timing || s == nullptr) return matmul_body(plan, A, B, C, D, ws, s);
+  // CUDA graph: replay the captured call when the arguments match, else capture anew
+  int dev = 0;
+  LRAMM_CUDA_TRY(cudaGetDevice(&dev));
+  const void* key[6] = {A, B, C, D, ws, stream};
+  bool same = plan->gexec && plan->gdev == dev;
+  for (int i = 0; i < 6 && same; ++i) same = plan->gkey[i] == key[i];
+  if (!same) {
+    if (plan->gexec) {
+      cudaGraphExecDestroy(plan->gexec);
+      plan->gexec = nullptr;
+    }
+    LRAMM_TRY(ensure_streams(plan));   // made outside the capture
+    LRAMM_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    const unsigned long long n0 = g_launches.load(std::memory_order_relaxed);
+    const lramm_status st = matmul_body(plan, A, B, C, D, ws, s);
+    plan->glaunches = g_launches.load(std::memory_order_relaxed) - n0;
+    g_launches.fetch_sub(plan->glaunches, std::memory_order_relaxed);   // captured, not launched
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st != LRAMM_OK || ce != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (st != LRAMM_OK) return st;
+      LRAMM_CUDA_TRY(ce);
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&plan->gexec, g, 0);
+    cudaGraphDestroy(g);
+    LRAMM_CUDA_TRY(ie);
+    for (int i = 0; i < 6; ++i) plan->gkey[i] = key[i];
+    plan->gdev = dev;
+  }
+  // the library's launches inside the graph count as launched on every replay
+  for (size_t i = 0; i < plan->glaunches; ++i) count_launch();
+  LRAMM_CUDA_TRY(cudaGraphLaunch(plan->gexec, s));
+  return LRAMM_OK;
+}
+
+lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const float* C, float* D, void* ws,
+                         cudaStream_t s) {
   const lramm_desc& d = plan->d;
   const int l = plan->l, r = d.r;
   plan->used = 0;

@@ -323,3 +323,31 @@ def test_matmul_alpha_beta_c(L):
     plan0 = L.Plan(m, n, k, 24, 8, 1, seed=7, prec=(0, 0, 0), alpha=0.5, beta=2.0)
     D0 = np_(L.matmul(plan0, dev(A32), dev(B32), C=dev(C))).astype(np.float64)
     assert oracle.lramm.rel_fro(D0, ref_f) <= 1e-5
+
+
+def test_matmul_graph_replay_bit_identical(L):
+    """LRAMM_FLAG_GRAPH: the first call on a (non-default) stream captures the
+    call into a CUDA graph, later calls with the same buffers replay it; the
+    output is bit-identical to the uncaptured call, a new output buffer is
+    captured anew, and the launch counter counts the replayed kernels."""
+    m = n = k = 512
+    A, B = workloads.operands("lramm_512", scale=(m, n, k))
+    A32, B32 = dev(A.astype(np.float32)), dev(B.astype(np.float32))
+    ref_plan = L.Plan(m, n, k, 64, 10, 1, seed=7, prec=(1, 1, 1), sketch=L.SKETCH_TF32)
+    ref = np_(L.matmul(ref_plan, A32, B32))
+    plan = L.Plan(m, n, k, 64, 10, 1, seed=7, prec=(1, 1, 1), sketch=L.SKETCH_TF32, graph=True)
+    ws = plan.workspace()
+    s = torch.cuda.Stream()
+    D1 = torch.empty((m, n), dtype=torch.float32, device="cuda")
+    D2 = torch.empty_like(D1)
+    with torch.cuda.stream(s):
+        L.matmul(plan, A32, B32, out=D1, ws=ws)           # capture + launch
+        c0 = L.launch_count()
+        D1.zero_()
+        L.matmul(plan, A32, B32, out=D1, ws=ws)           # replay
+        per_call = L.launch_count() - c0
+        L.matmul(plan, A32, B32, out=D2, ws=ws)           # other output: capture again
+    s.synchronize()
+    assert L.status_read(ws, stream=s) == 0
+    assert np.array_equal(np_(D1), ref) and np.array_equal(np_(D2), ref)
+    assert per_call > 50
