@@ -110,6 +110,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it); ms unchanged without a process group."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(world, flops_per_step, steps, max_ms):
+    """Whole-job throughput: every rank's work over the slowest rank's time (weak scaling)."""
+    return world * flops_per_step * steps / (max_ms * 1e-3) / 1e12
+
+
 # ------------------------------------------------------------------ roofline
 def kernel_work(kind, cfg, l, variant):
     """Algorithmic (bytes, flops) of ONE launch of a kernel kind on this workload.
@@ -322,13 +338,10 @@ def run_lramm(args):
     clk = clocks.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     flops = 2.0 * m * n * k
-    value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
+    value = whole_job_tflops(world, flops, args.steps, total_ms)
     st = L.status_read(ws)
 
     # per-kind device time (instrumented plan, outside the timed region)
@@ -607,13 +620,10 @@ def run_rf(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     flops = 6.0 * m * n * k
-    value = world * flops * args.steps / (total_ms * 1e-3) / 1e12
+    value = whole_job_tflops(world, flops, args.steps, total_ms)
     st = L.status_read(ws)
     nbd = min(args.steps, 3)   # instrumented steps for the per-kind breakdown (outside the timed region)
     for _ in range(nbd):

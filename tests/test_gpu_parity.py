@@ -351,3 +351,24 @@ def test_matmul_graph_replay_bit_identical(L):
     assert L.status_read(ws, stream=s) == 0
     assert np.array_equal(np_(D1), ref) and np.array_equal(np_(D2), ref)
     assert per_call > 50
+
+
+@pytest.mark.parametrize("which", ["A", "B", "both"])
+def test_matmul_zero_operand(L, which):
+    """Degenerate input: a zero operand. Its sketch, Gram and R factor are
+    zero (the Cholesky meets zero pivots: status 0 or LRAMM_ERR_NUMERIC), the
+    singular values vanish and D is exactly zero -- no NaN or Inf anywhere."""
+    m, n, k = 200, 180, 160
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((m, k)).astype(np.float32)
+    B = rng.standard_normal((k, n)).astype(np.float32)
+    if which in ("A", "both"):
+        A[:] = 0
+    if which in ("B", "both"):
+        B[:] = 0
+    for prec in ((0, 0, 0), (1, 1, 1)):
+        plan = L.Plan(m, n, k, 16, 4, 1, seed=7, prec=prec)
+        ws = plan.workspace()
+        D = np_(L.matmul(plan, dev(A), dev(B), ws=ws))
+        assert L.status_read(ws) in (0, 5)
+        assert np.all(D == 0), prec

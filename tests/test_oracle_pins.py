@@ -123,3 +123,13 @@ def test_hilo_residual():
 
 def test_lead_tail_e3():
     pins.pin_lead_tail(oracle.mixed, oracle.quant)
+
+
+def test_lramm_zero_operand_gives_zero():
+    """Degenerate input: LRAMM of a zero operand is exactly zero in every precision."""
+    rng = np.random.default_rng(5)
+    A = np.zeros((40, 30), dtype=np.float32)
+    B = rng.standard_normal((30, 36)).astype(np.float32)
+    for prec in ((0, 0, 0), (1, 1, 1), (2, 2, 2), (3, 3, 3)):
+        assert np.all(oracle.lramm.lramm(A, B, 6, 2, 1, 7, prec) == 0)
+        assert np.all(oracle.lramm.lramm(B.T.copy(), A.T.copy(), 6, 2, 1, 7, prec) == 0)
