@@ -14,5 +14,6 @@ Modules:
   rf      -- the range-finder form C ~ (X Q)(Q^T W) and its gradients
   mixed   -- MXFP4 (e2m1, 32-element block scales), split-precision
              residuals and the lead / tail E3 of the mixed 4/8-bit chain
+  qsvd    -- the quantised SVD approximation of one matrix (Algorithm 4)
 """
-from . import philox, quant, lramm, rf, mixed  # noqa: F401
+from . import philox, quant, lramm, rf, mixed, qsvd  # noqa: F401

@@ -580,3 +580,138 @@ def pin_lead_tail(mixed, quant, seed=46):
     bound = (np.abs(du) @ np.abs(E2) + np.abs(Ut) @ np.abs(de) + np.abs(lolo) + np.abs(du) @ np.abs(de))
     full = mixed.e3_lead_tail(Ut, E2, quant.PREC_INT4, r, quant.PREC_INT8, 2)
     assert np.all(np.abs(full - exact) <= bound * (1 + 1e-4) + 1e-6 * np.abs(exact).max())
+
+
+# --------------------------------------------------------------------------
+# Algorithm 4: quantised SVD of one matrix, Theorem 4.4
+# --------------------------------------------------------------------------
+def pin_qsvd_unquantised(qs, lr, wl, quant):
+    """Without quantisation Algorithm 4's approximation is U~_k V_k^T, the
+    rank-k RSVD: a matrix of exact rank k is reproduced (to the FP32 storage
+    of the factors), the columns of U~_k = U_k Sigma_k have norms sigma_i,
+    V_k has orthonormal columns, and with a full sketch (l = min(m, n)) the
+    approximation is the truncated SVD of Eckart-Young (numpy's LAPACK)."""
+    F = quant.PREC_F32
+    for (m, n, k, p) in ((60, 45, 6, 4), (40, 70, 5, 3)):
+        A = wl.exact_rank(m, n, k, 91)
+        sv = np.linalg.svd(A, compute_uv=False)
+        for q in (0, 1):
+            _, _, Ap, s = qs.qsvd(A, k, p, q, 5, 0, F, F)
+            assert Ap.shape == A.shape
+            assert lr.rel_fro(Ap, A) < 1e-6
+            Ut, V, _ = qs.factors(A, k, p, q, 5, 0)
+            assert np.allclose(np.linalg.norm(Ut.astype(np.float64), axis=0), sv[:k], rtol=1e-6)
+            assert np.abs(V.astype(np.float64).T @ V - np.eye(k)).max() < 1e-6
+    rng = np.random.default_rng(92)
+    A = rng.standard_normal((36, 28))
+    k = 9
+    _, _, Ap, _ = qs.qsvd(A, k, 28 - k, 0, 3, 0, F, F)
+    Uf, sf, Vft = np.linalg.svd(A, full_matrices=False)
+    Ak = (Uf[:, :k] * sf[:k]) @ Vft[:k]
+    assert np.abs(Ap - Ak).max() < 1e-5 * np.abs(A).max()
+
+
+def _rne(y):
+    """Round half to even on a Python float (Python's round is half-even)."""
+    return float(round(y))
+
+
+def pin_qsvd_codes_bruteforce(qs, quant, seed=93):
+    """The quantised factors carry Eq. (Quantization) codes of the rows of
+    U~_k and V_k (scalar loops: a_max per row or per factor, lambda =
+    fp32(D / a_max), code = round-half-even(fp32(x lambda)) clamped to D,
+    scale fp32(a_max / D)), a row's largest code is D, and A' is the plain
+    product of the dequantised factors (Quant~(Quant(.), T_F) then U~' V'^T)."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((23, 17)) * np.linspace(0.5, 3.0, 17)[None, :]
+    I8, I4 = quant.PREC_INT8, quant.PREC_INT4
+    k, p, q = 5, 3, 1
+    Ut, V, _ = qs.factors(A, k, p, q, 4, 0)
+    for scale in (quant.SCALE_ROWCOL, quant.SCALE_TENSOR):
+        for d1, d2 in ((I8, I4), (I4, I8)):
+            (cu, su), (cv, sv), Ap, _ = qs.qsvd(A, k, p, q, 4, 0, d1, d2, scale)
+            deq = []
+            for M, codes, scales, prec in ((Ut, cu, su, d1), (V, cv, sv, d2)):
+                D = np.float32(127.0 if prec == I8 else 7.0)
+                rows = M.shape[0]
+                if scale == quant.SCALE_TENSOR:
+                    amaxes = [max(abs(float(x)) for x in M.ravel())] * rows
+                else:
+                    amaxes = [max(abs(float(x)) for x in M[i]) for i in range(rows)]
+                out = np.zeros(M.shape)
+                for i in range(rows):
+                    am = np.float32(amaxes[i])
+                    lam = np.float32(D / am)
+                    s_i = np.float32(am / D)
+                    assert np.float32(scales[0 if scale == quant.SCALE_TENSOR else i]) == s_i
+                    for t in range(k):
+                        y = float(np.float32(np.float32(M[i, t]) * lam))
+                        c = min(max(_rne(y), -float(D)), float(D))
+                        assert codes[i, t] == c, (i, t, codes[i, t], c)
+                        out[i, t] = float(np.float32(np.float32(c) * s_i))
+                    if scale == quant.SCALE_ROWCOL:
+                        assert max(abs(codes[i])) == float(D)
+                if scale == quant.SCALE_TENSOR:
+                    assert np.abs(codes).max() == float(D)
+                deq.append(out)
+            ref = np.array([[sum(deq[0][i, t] * deq[1][j, t] for t in range(k))
+                             for j in range(V.shape[0])] for i in range(Ut.shape[0])])
+            assert np.allclose(Ap, ref, rtol=1e-12, atol=1e-14)
+
+
+def _thm44_rhs(sig, m, n, k, D1, D2):
+    """Theorem 4.4's right-hand side, n the larger dimension, r read as k."""
+    nn = max(m, n)
+    s1 = sig[0] ** 2
+    tail = sig[k] ** 2 * (nn - k) if k < len(sig) else 0.0
+    return (tail + m * k * s1 / D1 ** 2 + n * k * s1 / D2 ** 2
+            + m * n * k * s1 / (D1 ** 2 * D2 ** 2))
+
+
+def pin_qsvd_error_bounds(qs, wl, quant):
+    """Theorem 4.2 per factor and Theorem 4.4 for the approximation.
+
+    |U~_k' - U~_k|_F <= sqrt(m k) / lambda_1 with lambda_1 >= D1 / sigma_1
+    (entries of U~ are at most sigma_1), and half of it for round-to-nearest;
+    |V_k' - V_k|_F <= sqrt(n k) / (2 D2) (entries of V at most 1); the
+    approximation error obeys the triangle inequality over the three error
+    terms of the proof and Theorem 4.4's bound.  An exactly rank-k matrix
+    (sigma_{k+1} = 0) keeps only the quantisation terms and its error is not
+    zero."""
+    I8, I4 = quant.PREC_INT8, quant.PREC_INT4
+    rng = np.random.default_rng(94)
+    cases = [("normal", rng.standard_normal((72, 90)), 12),
+             ("uniform", rng.uniform(0.0, 1.0, (90, 64)), 10),
+             ("decay", wl.lowrank(80, 80, 0.85 ** np.arange(80), 95), 14),
+             ("rank6", wl.exact_rank(64, 50, 6, 96), 6)]
+    for name, A, k in cases:
+        m, n = A.shape
+        sig = np.linalg.svd(A, compute_uv=False)
+        Ut, V, _ = qs.factors(A, k, 6, 2, 8, 0)
+        Ak = Ut.astype(np.float64) @ V.astype(np.float64).T
+        for d1, d2 in ((I8, I8), (I8, I4), (I4, I8), (I4, I4)):
+            D1 = 127.0 if d1 == I8 else 7.0
+            D2 = 127.0 if d2 == I8 else 7.0
+            _, du = qs.quantise(Ut, d1, quant.SCALE_ROWCOL)
+            _, dv = qs.quantise(V, d2, quant.SCALE_ROWCOL)
+            _, _, Ap, _ = qs.qsvd(A, k, 6, 2, 8, 0, d1, d2)
+            RU = du - Ut.astype(np.float64)
+            RV = dv - V.astype(np.float64)
+            nu, nv = np.linalg.norm(RU), np.linalg.norm(RV)
+            assert nu <= np.sqrt(m * k) * sig[0] / D1 * (0.5 + 1e-6), (name, d1, nu)
+            assert nv <= np.sqrt(n * k) / D2 * (0.5 + 1e-6), (name, d2, nv)
+            err = np.linalg.norm(Ap - A)
+            tri = (np.linalg.norm(A - Ak) + nu + np.linalg.norm(Ut.astype(np.float64), 2) * nv + nu * nv)
+            assert err <= tri * (1 + 1e-9), (name, d1, d2, err, tri)
+            assert err ** 2 <= _thm44_rhs(sig, m, n, k, D1, D2), (name, d1, d2, err ** 2)
+            if name == "rank6":
+                assert err > 1e-4 * np.linalg.norm(A)
+                assert np.linalg.norm(A - Ak) < 1e-6 * np.linalg.norm(A)
+            if name == "normal":
+                # round-to-nearest leaves errors uniform on half a step:
+                # E |r|^2 = step^2 / 12 per entry, step = a_max(row) / D
+                for M, Dq, prec in ((Ut, D1, d1), (V, D2, d2)):
+                    (c, s), dq = qs.quantise(M, prec, quant.SCALE_ROWCOL)
+                    model = np.sum(np.asarray(s, np.float64) ** 2) * k / 12.0
+                    ratio = np.sum((dq - M.astype(np.float64)) ** 2) / model
+                    assert 0.7 < ratio < 1.3, (name, prec, ratio)

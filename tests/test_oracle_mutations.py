@@ -306,3 +306,58 @@ def test_lead_tail_missing_residual_term_caught(monkeypatch):
     monkeypatch.setattr(Mx, "_qm_codes", bad)
     with pytest.raises(AssertionError):
         pins.pin_lead_tail(Mx, Qn)
+
+
+# Algorithm 4
+def test_qsvd_missing_sigma_caught(monkeypatch):
+    from oracle import qsvd as Qs
+
+    def bad(X, k, p, q, seed, stream):
+        U, s, V = Lr.rsvd(X, k, p, q, seed, stream)
+        return U.astype(np.float32), V.astype(np.float32), s     # U_k instead of U_k Sigma_k
+    monkeypatch.setattr(Qs, "factors", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_qsvd_unquantised(Qs, Lr, workloads, Qn)
+
+
+def test_qsvd_v_scaled_by_columns_caught(monkeypatch):
+    from oracle import qsvd as Qs
+    orig = Qs.quantise
+
+    def bad(M, prec, scale):
+        if prec in (Qn.PREC_INT8, Qn.PREC_INT4) and scale == Qn.SCALE_ROWCOL and M.shape[0] == 17:
+            c, _, s = Qn.quantize(M, prec, 0)                     # one scale per rank index
+            return (c, s), Qn.dequantize(c, s, 0).astype(np.float64)
+        return orig(M, prec, scale)
+    monkeypatch.setattr(Qs, "quantise", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_qsvd_codes_bruteforce(Qs, Qn)
+
+
+def test_qsvd_bit_widths_swapped_caught(monkeypatch):
+    from oracle import qsvd as Qs
+    orig = Qs.qsvd
+
+    def bad(X, k, p, q, seed, stream, prec_u, prec_v, scale=Qn.SCALE_ROWCOL):
+        return orig(X, k, p, q, seed, stream, prec_v, prec_u, scale)
+    monkeypatch.setattr(Qs, "qsvd", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_qsvd_codes_bruteforce(Qs, Qn)
+
+
+def test_qsvd_floor_rounding_caught(monkeypatch):
+    from oracle import qsvd as Qs
+
+    def bad(M, prec, scale):
+        if prec == Qn.PREC_F32:
+            return None, np.asarray(M, np.float64)
+        M = np.asarray(M, np.float32)
+        D = np.float32(Qn.qmax(prec))
+        amax = np.max(np.abs(M), axis=1).astype(np.float32)
+        lam = (D / amax).astype(np.float32)
+        c = np.clip(np.floor((M * lam[:, None]).astype(np.float64)), -D, D)   # truncation, not nearest
+        s = (amax / D).astype(np.float32)
+        return (c, s), (c * s[:, None]).astype(np.float32).astype(np.float64)
+    monkeypatch.setattr(Qs, "quantise", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_qsvd_error_bounds(Qs, workloads, Qn)

@@ -133,3 +133,16 @@ def test_lramm_zero_operand_gives_zero():
     for prec in ((0, 0, 0), (1, 1, 1), (2, 2, 2), (3, 3, 3)):
         assert np.all(oracle.lramm.lramm(A, B, 6, 2, 1, 7, prec) == 0)
         assert np.all(oracle.lramm.lramm(B.T.copy(), A.T.copy(), 6, 2, 1, 7, prec) == 0)
+
+
+# Algorithm 4 / Theorem 4.4
+def test_qsvd_unquantised():
+    pins.pin_qsvd_unquantised(oracle.qsvd, oracle.lramm, workloads, oracle.quant)
+
+
+def test_qsvd_codes_bruteforce():
+    pins.pin_qsvd_codes_bruteforce(oracle.qsvd, oracle.quant)
+
+
+def test_qsvd_error_bounds():
+    pins.pin_qsvd_error_bounds(oracle.qsvd, workloads, oracle.quant)
