@@ -14,6 +14,10 @@ step; rf_linear runs the range-finder form as a linear layer, one step =
 forward C ~ X W plus the hand-written backward (dX, dW), effective
 TFLOP/s = 6mnk / t (the dense layer's forward and backward GEMMs).
 
+qsvd_4096 runs Algorithm 4 (quantised SVD of one matrix): a step is one
+lramm_qsvd call producing the codes and scales of U~_k (d1) and V_k (d2);
+the metric is input entries compressed per second.
+
 Multi-GPU (torchrun): every rank runs an independent replica of the
 workload; value = all ranks' work / max rank time (weak scaling).
 """
@@ -42,6 +46,9 @@ DTYPES = {"int8": "f32+int8", "fp32": "f32", "e4m3": "f32+e4m3", "884": "f32+int
 # E3 lead / tail split (lead rank directions, lead precision, residual terms)
 LEADS = {"lead64_mxfp4": (64, 1, 2), "lead64_int4": (64, 1, 2)}
 FLUSH_BYTES = 256 << 20
+QSVD_METRIC = "quantised-SVD compression throughput (Algorithm 4): input entries per second"
+# Algorithm 4's bit widths (d1 for U~_k, d2 for V_k) per variant
+QSVD_BITS = {"int8": (1, 1), "884": (1, 2), "e4m3": (3, 3), "lead64_int4": (1, 2)}
 
 
 def peaks():
@@ -236,6 +243,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     prec = VARIANTS[args.variant]
+    if args.workload == "qsvd_4096":
+        return run_reference_qsvd(args)
     if args.workload == "rf_linear":
         X, W, G, c = cpu_rf_sample()
         flops = 6.0 * c["m"] * c["n"] * c["k"]
@@ -259,6 +268,45 @@ def run_reference(args):
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": cores_used(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def qsvd_cpu_sample(full=False):
+    """The quantised-SVD workload for the CPU oracle: the full 4096 x 4096
+    matrix (full=True), else a bounded stand-in with the same spectrum rule
+    at 2048 x 2048, r = 128, p = 8 (the reference arm's per-step sample)."""
+    c = dict(workloads.CONFIGS["qsvd_4096"])
+    if not full:
+        c["m"] = c["n"] = c["k"] = 2048
+        c["r"], c["p"] = 128, 8
+    A, _ = workloads.operands("qsvd_4096", scale=(c["m"], c["n"], c["k"]))
+    return A.astype(np.float32), c
+
+
+def cpu_qsvd_step(A, c, bits):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.qsvd.qsvd(A, c["r"], c["p"], c["q"], workloads.SEED_SKETCH, 0, bits[0], bits[1])
+    return time.perf_counter() - t0
+
+
+def run_reference_qsvd(args):
+    bits = QSVD_BITS[args.variant]
+    A, c = qsvd_cpu_sample()
+    for _ in range(args.warmup):
+        cpu_qsvd_step(A, c, bits)
+    ts = [cpu_qsvd_step(A, c, bits) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    v = c["m"] * c["k"] / t / 1e9
+    sample = "oracle Algorithm 4 at %d x %d, r=%d p=%d q=%d per step" % (c["m"], c["k"], c["r"], c["p"], c["q"])
+    line = {"impl": "reference", "metric": QSVD_METRIC, "value": v, "unit": "Gentries/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "variant": args.variant, "sample": sample},
+            "cpu_baseline": {"value": v, "unit": "Gentries/s", "cores": cores_used(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "Gentries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
@@ -753,6 +801,217 @@ def run_rf(args):
     return 0
 
 
+# ------------------------------------------------------------------ Algorithm 4
+def run_qsvd(args):
+    """Quantised SVD of one matrix: one lramm_qsvd call per step (codes and
+    scales of U~_k and V_k); the approximation deq(U~') deq(V')^T timed beside it."""
+    import torch
+
+    import paper_2405_16917_gb300 as L
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lib = L.load()
+    cfg = workloads.CONFIGS["qsvd_4096"]
+    m, k, r, p, q = cfg["m"], cfg["k"], cfg["r"], cfg["p"], cfg["q"]
+    l = r + p
+    if args.variant not in QSVD_BITS:
+        raise SystemExit("qsvd_4096: variant must be one of %s" % sorted(QSVD_BITS))
+    pu, pv = QSVD_BITS[args.variant]
+    A, _ = workloads.device_operands("qsvd_4096", dev)
+    sketch_name = args.sketch or "tf32"
+    sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
+    plan = L.Plan(m, k, k, r, p, q, seed=workloads.SEED_SKETCH, sketch=sketch)
+    tplan = L.Plan(m, k, k, r, p, q, seed=workloads.SEED_SKETCH, sketch=sketch, timing=True)
+    ws = torch.empty(lib.lramm_qsvd_ws_bytes(plan.handle, 0, pu, pv), dtype=torch.uint8, device=dev)
+    ldq = -(-r // 32) * 32
+    Uc = torch.empty((m, ldq), dtype=L.code_dtype(pu), device=dev)
+    Vc = torch.empty((k, ldq), dtype=L.code_dtype(pv), device=dev)
+    Us = torch.empty((m,), dtype=torch.float32, device=dev)
+    Vs = torch.empty((k,), dtype=torch.float32, device=dev)
+    Xr = torch.empty((m, k), dtype=torch.float32, device=dev)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    nul = None
+
+    def call(pl, X, recon):
+        L._check(lib.lramm_qsvd(pl.handle, 0, L._ptr(X), pu, pv, L._ptr(Uc), L._ptr(Us), L._ptr(Vc), L._ptr(Vs),
+                                ldq, L._ptr(nul), L._ptr(nul), L._ptr(Xr if recon else None), k, L._ptr(ws),
+                                ws.numel(), L._stream()), "lramm_qsvd")
+
+    for _ in range(max(args.warmup, 0)):
+        call(plan, A, False)
+    info = L.info_read(ws, 3)
+    st = L.status_read(ws)
+    if st != 0:
+        raise RuntimeError("device status %d after warm-up" % st)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_id = local
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(gpu_id)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    n_launch0 = L.launch_count()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        call(plan, A, False)
+        ends[i].record(stream)
+    n_launch = L.launch_count() - n_launch0
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), dist, dev)
+    ms_step = total_ms / args.steps
+    value = world * m * k * args.steps / (total_ms * 1e-3) / 1e9
+    st = L.status_read(ws)
+
+    # per-kind breakdown with the approximation (instrumented plan, outside the timed region)
+    kinds = {}
+    nbd = min(args.steps, 5)
+    for _ in range(nbd):
+        flush.zero_()
+        call(tplan, A, True)
+        for kname, (ms, cnt) in tplan.timing().items():
+            a = kinds.setdefault(kname, [0.0, 0])
+            a[0] += ms
+            a[1] += cnt
+
+    def timed(fn, reps=5):
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    t_recon = timed(lambda: call(plan, A, True))
+    err = ((Xr.double() - A.double()).norm() / A.double().norm()).item()
+    sig = workloads.spectrum(cfg["spectrum"], min(m, k))
+    tail = float(np.sqrt(np.sum(sig[r:] ** 2) / np.sum(sig ** 2)))
+    # the approximation's product alone: HBM-bound (m k FP32 written, codes read)
+    rk = kinds.get("reconstruct")
+    pk, peak_src = peaks()
+    recon_roof = None
+    if rk:
+        # the product kernel is the last "reconstruct" launch; its time is the kind's
+        # time less the code conversion (a copy of k x ldq codes, timed together)
+        rb = m * k * 4 + (m + k) * ldq * 2
+        rs = rk[0] / nbd * 1e-3
+        recon_roof = {"bound": "hbm", "achieved": rb / rs / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                      "frac": rb / rs / 1e9 / pk["hbm_gbs"], "avg_ms_per_step": rs * 1e3,
+                      "algorithmic_bytes": rb, "launches_per_step": rk[1] / nbd,
+                      "note": "conversion + product launches of one call together"}
+    dname, (dms, dcnt) = max(kinds.items(), key=lambda kv: kv[1][0])
+    avg_s = dms / dcnt * 1e-3
+    if dname == "svd":
+        jf = jacobi_work(l, [int(x) for x in info[1:2] if int(x) > 0])
+        roof = {"bound": "alu", "achieved": jf / avg_s / 1e12,
+                "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
+                "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz",
+                "traffic": measured_traffic("lramm_4096", "svd"), "algorithmic_flops_per_launch": jf}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        roof = {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
+                "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3}
+
+    # end to end: the matrix in from pinned host memory, codes and scales out
+    Ah = A.cpu().pin_memory()
+    Ad = torch.empty_like(A)
+    outs = [(Uc, torch.empty(Uc.shape, dtype=Uc.dtype).pin_memory()),
+            (Vc, torch.empty(Vc.shape, dtype=Vc.dtype).pin_memory()),
+            (Us, torch.empty(Us.shape, dtype=Us.dtype).pin_memory()),
+            (Vs, torch.empty(Vs.shape, dtype=Vs.dtype).pin_memory())]
+
+    def e2e_step():
+        Ad.copy_(Ah, non_blocking=True)
+        call(plan, Ad, False)
+        for d_, h_ in outs:
+            h_.copy_(d_, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(2, min(args.steps, 5))
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    eb.record(stream)
+    eb.synchronize()
+    e2e_ms = ea.elapsed_time(eb) / e2e_steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on the full 4096 x 4096 matrix: one step is a few seconds of host work
+        Ac, cs = qsvd_cpu_sample(full=True)
+        ts_cpu = []
+        while sum(ts_cpu) < 10.0 and len(ts_cpu) < 20:    # about 10 s of host work
+            ts_cpu.append(cpu_qsvd_step(Ac, cs, (pu, pv)))
+        t_cpu = sum(ts_cpu) / len(ts_cpu)
+        cpu = {"value": cs["m"] * cs["k"] / t_cpu / 1e9, "unit": "Gentries/s", "cores": cores_used(),
+               "kind": "oracle", "sample": "%d oracle Algorithm 4 steps on the full %d x %d matrix, r=%d p=%d q=%d, "
+                                             "%.2f s each" % (len(ts_cpu), cs["m"], cs["k"], cs["r"], cs["p"],
+                                                              cs["q"], t_cpu)}
+    if rank == 0:
+        bits = {1: "int8", 2: "int4", 3: "e4m3"}
+        line = {
+            "metric": QSVD_METRIC, "value": value, "unit": "Gentries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+%s+%s" % (bits[pu], bits[pv]), "data": "synthetic",
+            "config": {"workload": "qsvd_4096", "m": m, "n": k, "r": r, "p": p, "q": q,
+                       "d1": bits[pu], "d2": bits[pv], "scale": "per row", "spectrum": cfg["spectrum"],
+                       "sketch": sketch_name,
+                       "l2": "flushed: 256 MB write before each step", "jacobi_sweeps": info[1:2],
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "with_reconstruction_ms": t_recon,
+                       "rel_fro_err_vs_input": err, "rank_r_truncation_floor": tail,
+                       "compressed_bytes": Uc.numel() * Uc.element_size() + Vc.numel() * Vc.element_size()
+                       + 4 * (m + k), "device_status": st},
+            "breakdown_ms_per_step": {kn: round(v[0] / nbd, 4) for kn, v in
+                                      sorted(kinds.items(), key=lambda kv: -kv[1][0])},
+            "breakdown_note": "CUDA events around every kernel of %d separate steps with the approximation" % nbd,
+            "roofline": roof,
+            "kernel_rooflines": {"reconstruct": recon_roof} if recon_roof else {},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * m * k / (e2e_ms * 1e-3) / 1e9, "unit": "Gentries/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": A.numel() * A.element_size(),
+                    "d2h_bytes_per_step": sum(d_.numel() * d_.element_size() for d_, _ in outs)},
+            "gpu_launches": n_launch,
+            "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
+                       "reasons": clk.get("reasons"), "samples": clk.get("samples")},
+            "peaks": peak_src,
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -769,6 +1028,8 @@ def main():
         return run_reference(args)
     if args.workload == "rf_linear":
         return run_rf(args)
+    if args.workload == "qsvd_4096":
+        return run_qsvd(args)
     return run_lramm(args)
 
 

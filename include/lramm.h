@@ -141,7 +141,8 @@ typedef enum {
   LRAMM_K_OTHER = 13,
   LRAMM_K_BWD = 14,       /* range-finder backward: products with G, X, W, Q  */
   LRAMM_K_ADJOINT = 15,   /* range-finder backward: thin-QR adjoints          */
-  LRAMM_K_COUNT = 16
+  LRAMM_K_RECON = 16,     /* Algorithm 4: code conversion + product U~' V'^T  */
+  LRAMM_K_COUNT = 17
 } lramm_kernel_kind;
 
 typedef struct lramm_plan_s* lramm_plan_t;
@@ -382,6 +383,44 @@ LRAMM_API lramm_status lramm_quantize_mx(const float* X, int64_t rows, int64_t c
 LRAMM_API lramm_status lramm_qgemm_mx(const int8_t* L, const int8_t* Le, const int8_t* Rt, const int8_t* Re,
                                       int64_t M, int64_t N, int64_t K, int64_t ldl, int64_t ldr, float alpha,
                                       float beta, const float* C, int64_t ldc, float* D, int64_t ldd, void* stream);
+
+/* Quantised SVD approximation of one operand, Algorithm 4 (its error is
+ * bounded by Theorem 4.4): the randomized SVD of lramm_rsvd truncated to
+ * rank r, U~ = U_r Sigma_r (rows x r) and V_r (cols x r), each quantised by
+ * rows along the rank index with Eqs. (get_lambda) and (Quantization): U~
+ * with d1 = prec_u, V_r with d2 = prec_v; one scale per row (plan scale
+ * LRAMM_S_ROWCOL) or one per factor (LRAMM_S_TENSOR).
+ *   which   0: X is the plan's A (rows m, cols k, stride lda, type a_type),
+ *           1: its B (rows k, cols n); the sketch as lramm_rsvd draws it.
+ *   prec_u, prec_v   LRAMM_P_INT8, LRAMM_P_INT4 or LRAMM_P_E4M3
+ *           (LRAMM_P_MXFP4: LRAMM_ERR_UNSUPPORTED).
+ *   Uc, Us  codes of U~, rows x ldq, in the format lramm_quantize writes for
+ *           prec_u (INT8 as bfloat16 values, INT4 / E4M3 as e4m3 bytes),
+ *           columns r .. ldq-1 zero; FP32 scales a_max / D, rows entries or
+ *           one.  Vc, Vs: the same for V_r (cols x ldq, prec_v).
+ *   ldq     a multiple of 32, >= r; Uc and Vc 16-byte aligned.
+ *   Uf, Vf  optional (NULL to skip): the FP32 factors that were quantised,
+ *           U~ rows x r and V_r cols x r, row-major, dense.
+ *   Xr      optional (NULL to skip): the approximation deq(U~') deq(V')^T,
+ *           rows x cols FP32 with stride ldxr >= cols:
+ *             Xr(i,j) = fp32(acc) * fp32(su_i * sv_j),
+ *             acc = sum_t cu(i,t) cv(j,t)
+ *           exact for INT8 / INT4 codes, FP32-accumulated when E4M3 codes
+ *           take part.  The pair INT8 / E4M3 has no common code product:
+ *           with it Xr must be NULL (else LRAMM_ERR_UNSUPPORTED).
+ *   ws      device workspace of lramm_qsvd_ws_bytes(plan, which, prec_u,
+ *           prec_v) bytes, 256-byte aligned; its first word is the status
+ *           word of lramm_status_read.
+ * All outputs are caller-owned device memory; the call is asynchronous on
+ * `stream`.  Arguments are checked before anything is launched. */
+LRAMM_API lramm_status lramm_qsvd(lramm_plan_t plan, int32_t which, const void* X, int32_t prec_u,
+                                  int32_t prec_v, void* Uc, float* Us, void* Vc, float* Vs, int64_t ldq,
+                                  float* Uf, float* Vf, float* Xr, int64_t ldxr, void* ws, size_t ws_bytes,
+                                  void* stream);
+
+/* Workspace bytes of lramm_qsvd (the plan's workspace plus the code
+ * conversion and split-K buffers of the product); 0 for invalid arguments. */
+LRAMM_API size_t lramm_qsvd_ws_bytes(lramm_plan_t plan, int32_t which, int32_t prec_u, int32_t prec_v);
 
 /* Bytes of workspace lramm_sketch_product needs for an l-column product of a
  * rows x cols operand. */

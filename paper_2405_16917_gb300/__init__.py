@@ -68,6 +68,9 @@ _SIGS = {
     "lramm_dq_matmul": (_I32, [_I32, _I32, _I64, _I64, _I64, _F, _VP, _I64, _VP, _I64, _F, _VP, _I64, _VP, _I64, _VP,
                                ctypes.c_size_t, _VP]),
     "lramm_dq_ws_bytes": (ctypes.c_size_t, [_I32, _I64, _I64, _I64]),
+    "lramm_qsvd": (_I32, [_VP, _I32, _VP, _I32, _I32, _VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _I64, _VP,
+                          ctypes.c_size_t, _VP]),
+    "lramm_qsvd_ws_bytes": (ctypes.c_size_t, [_VP, _I32, _I32, _I32]),
     "lramm_quantize_mx": (_I32, [_VP, _I64, _I64, _I64, _VP, _I64, _VP, _VP]),
     "lramm_qgemm_mx": (_I32, [_VP, _VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _F, _F, _VP, _I64, _VP, _I64, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
@@ -82,7 +85,7 @@ _SIGS = {
 
 FLAG_TIMING = 1
 FLAG_GRAPH = 2
-K_COUNT = 16
+K_COUNT = 17
 
 
 def load(path=LIB_PATH):
@@ -270,6 +273,42 @@ def rsvd(plan, which, X, ws=None, stream=None):
     _check(load().lramm_rsvd(plan.handle, which, _ptr(X), _ptr(U), _ptr(S), _ptr(V), _ptr(ws),
                              ws.numel(), _stream(stream)), "lramm_rsvd")
     return U, S, V
+
+
+def qsvd(plan, which, X, prec_u=P_INT8, prec_v=P_INT8, ldq=None, factors=False, reconstruct=True,
+         ws=None, stream=None):
+    """Algorithm 4 on A (which=0) or B (which=1): the rank-r RSVD, U~ = U_r Sigma_r
+    quantised with prec_u and V_r with prec_v (rows along the rank index).
+
+    Returns a dict: Uc, Us, Vc, Vs (codes and scales as `quantize` lays them
+    out, ldq columns), Uf, Vf (the FP32 factors, when factors=True) and Xr
+    (the approximation deq(U~') deq(V')^T, when reconstruct=True)."""
+    torch = _torch()
+    _need_cuda(X)
+    d = plan.desc
+    rows, cols = (d.m, d.k) if which == 0 else (d.k, d.n)
+    ldq = ldq or -(-d.r // 32) * 32
+    dev = X.device
+    per_row = d.scale == S_ROWCOL
+    out = dict(Uc=torch.empty((rows, ldq), dtype=code_dtype(prec_u), device=dev),
+               Us=torch.empty((rows if per_row else 1,), dtype=torch.float32, device=dev),
+               Vc=torch.empty((cols, ldq), dtype=code_dtype(prec_v), device=dev),
+               Vs=torch.empty((cols if per_row else 1,), dtype=torch.float32, device=dev))
+    if factors:
+        out["Uf"] = torch.empty((rows, d.r), dtype=torch.float32, device=dev)
+        out["Vf"] = torch.empty((cols, d.r), dtype=torch.float32, device=dev)
+    if reconstruct:
+        out["Xr"] = torch.empty((rows, cols), dtype=torch.float32, device=dev)
+    lib = load()
+    need = lib.lramm_qsvd_ws_bytes(plan.handle, which, prec_u, prec_v)
+    if need == 0:
+        raise LrammError(1, "lramm_qsvd_ws_bytes")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=dev)
+    _check(lib.lramm_qsvd(plan.handle, which, _ptr(X), prec_u, prec_v, _ptr(out["Uc"]), _ptr(out["Us"]),
+                          _ptr(out["Vc"]), _ptr(out["Vs"]), ldq, _ptr(out.get("Uf")), _ptr(out.get("Vf")),
+                          _ptr(out.get("Xr")), cols, _ptr(ws), ws.numel(), _stream(stream)), "lramm_qsvd")
+    return out
 
 
 def chain(plan, Ut, Vt, Wt, Zt, C=None, out=None, ws=None, stream=None):

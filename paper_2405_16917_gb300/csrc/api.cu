@@ -779,7 +779,7 @@ lramm_status lramm_timing_read(lramm_plan_t plan, float* ms, int32_t* launches) 
 const char* lramm_kernel_kind_name(int32_t kind) {
   static const char* names[LRAMM_K_COUNT] = {"omega", "sketch", "gram", "chol", "trsm", "rfactor", "svd",
                                              "svdsort", "assemble", "quant", "e1", "e2", "e3", "other",
-                                             "backward", "qr_adjoint"};
+                                             "backward", "qr_adjoint", "reconstruct"};
   return (kind >= 0 && kind < LRAMM_K_COUNT) ? names[kind] : "unknown";
 }
 
@@ -807,6 +807,112 @@ lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* 
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
         sgemm(0, 0, Sd.cols, r, l, 1.f, at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, 0.f, V, r, s));
   LRAMM_CUDA_TRY(cudaMemcpyAsync(S, at<float>(ws, Sd.sig), sizeof(float) * r, cudaMemcpyDeviceToDevice, s));
+  return LRAMM_OK;
+}
+
+// ---- Algorithm 4: quantised SVD of one operand ---------------------------
+
+namespace {
+
+bool qsvd_prec_ok(int p) { return p == LRAMM_P_INT8 || p == LRAMM_P_INT4 || p == LRAMM_P_E4M3; }
+
+// Workspace beyond the plan's: the BF16 copy of INT4 codes that meet INT8
+// codes in one product, and the split-K partials of that product.
+struct QsvdLayout {
+  int pp;         // precision of the code product; -1: the pair has none (INT8 / E4M3)
+  int conv_side;  // 0: U codes, 1: V codes are rewritten as BF16; -1: none
+  int64_t kq;     // K of the product: r rounded up to 32 (the codes are zero beyond r)
+  size_t conv, part, part_floats, total;
+};
+
+QsvdLayout qsvd_layout(const lramm_plan_s* P, int which, int pu, int pv) {
+  QsvdLayout L{};
+  const SideLayout& S = P->side[which];
+  L.kq = round_up(P->d.r, 32);
+  L.conv_side = -1;
+  if (pu == pv) {
+    L.pp = pu;
+  } else if (pu != LRAMM_P_INT8 && pv != LRAMM_P_INT8) {
+    L.pp = LRAMM_P_E4M3;   // INT4 and E4M3 codes are both e4m3 bytes
+  } else if (pu == LRAMM_P_INT4 || pv == LRAMM_P_INT4) {
+    L.pp = LRAMM_P_INT8;   // INT4 codes as BF16 values beside INT8 codes: exact sums
+    L.conv_side = pu == LRAMM_P_INT4 ? 0 : 1;
+  } else {
+    L.pp = -1;
+  }
+  size_t off = static_cast<size_t>(round_up(static_cast<int64_t>(P->total), kAlign));
+  L.conv = off;
+  if (L.conv_side >= 0)
+    off += static_cast<size_t>(round_up(2 * (L.conv_side == 0 ? S.rows : S.cols) * L.kq, kAlign));
+  L.part = off;
+  L.part_floats = L.pp >= 0 ? qgemm_tc_part_floats(L.pp, S.rows, S.cols, L.kq) : 0;
+  off += static_cast<size_t>(round_up(static_cast<int64_t>(sizeof(float) * std::max<size_t>(L.part_floats, 4)), kAlign));
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+size_t lramm_qsvd_ws_bytes(lramm_plan_t plan, int32_t which, int32_t prec_u, int32_t prec_v) {
+  if (!plan || (which != 0 && which != 1) || !qsvd_prec_ok(prec_u) || !qsvd_prec_ok(prec_v)) return 0;
+  return qsvd_layout(plan, which, prec_u, prec_v).total;
+}
+
+lramm_status lramm_qsvd(lramm_plan_t plan, int32_t which, const void* X, int32_t prec_u, int32_t prec_v, void* Uc,
+                        float* Us, void* Vc, float* Vs, int64_t ldq, float* Uf, float* Vf, float* Xr, int64_t ldxr,
+                        void* ws, size_t ws_bytes, void* stream) {
+  if (!plan || (which != 0 && which != 1) || !X || !Uc || !Us || !Vc || !Vs) return LRAMM_ERR_INVALID_ARG;
+  if (prec_u == LRAMM_P_MXFP4 || prec_v == LRAMM_P_MXFP4) return LRAMM_ERR_UNSUPPORTED;
+  if (!qsvd_prec_ok(prec_u) || !qsvd_prec_ok(prec_v)) return LRAMM_ERR_INVALID_ARG;
+  const lramm_desc& d = plan->d;
+  const SideLayout& Sd = plan->side[which];
+  const int l = plan->l, r = d.r;
+  if (ldq < r || ldq % 32 != 0) return LRAMM_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(Uc) % 16 || reinterpret_cast<uintptr_t>(Vc) % 16) return LRAMM_ERR_INVALID_ARG;
+  if (Xr && ldxr < Sd.cols) return LRAMM_ERR_INVALID_ARG;
+  if (plan->l > svd_max_l()) return LRAMM_ERR_UNSUPPORTED;
+  const QsvdLayout Q = qsvd_layout(plan, which, prec_u, prec_v);
+  if (Xr && Q.pp < 0) return LRAMM_ERR_UNSUPPORTED;
+  if (!ws || ws_bytes < Q.total || reinterpret_cast<uintptr_t>(ws) % kAlign) return LRAMM_ERR_WORKSPACE;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int per_row = d.scale == LRAMM_S_ROWCOL;
+  plan->used = 0;
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  // SVD(A, k) and U~ = U_k Sigma_k: the small SVD's left vectors carry sigma
+  const SideRun sd = side_run(plan, which, X);
+  const int one[1] = {1}, zero[1] = {0};
+  LRAMM_TRY(rsvd_sides(plan, &sd, &which, 1, ws, one, zero, s));
+  // the factors: caller's buffers when given, else the plan's factor buffers
+  // (A side: U~ m x r in U~'s, V k x r in V^T's; B side: U~ k x r in W^T's,
+  // V n x r in Z~^T's -- each at least as large)
+  float* Ut = Uf ? Uf : at<float>(ws, which == 0 ? plan->Ut : plan->Wt);
+  float* V = Vf ? Vf : at<float>(ws, which == 0 ? plan->Vt : plan->Zt);
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(0, 0, Sd.rows, r, l, 1.f, at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, 0.f, Ut, r, s));
+  TIMED(plan, LRAMM_K_ASSEMBLE, s,
+        sgemm(0, 0, Sd.cols, r, l, 1.f, at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, 0.f, V, r, s));
+  unsigned int* amax = at<unsigned int>(ws, plan->amax);
+  TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(Ut, Sd.rows, r, r, prec_u, per_row, Uc, ldq, Us, amax, s));
+  TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(V, Sd.cols, r, r, prec_v, per_row, Vc, ldq, Vs, amax, s));
+  if (!Xr) return LRAMM_OK;
+  const void* L = Uc;
+  const void* R = Vc;
+  int64_t ldl = ldq, ldr = ldq;
+  if (Q.conv_side >= 0) {
+    void* cv = at<void>(ws, Q.conv);
+    const int64_t rows = Q.conv_side == 0 ? Sd.rows : Sd.cols;
+    TIMED(plan, LRAMM_K_RECON, s, fp8_codes_to_bf16(Q.conv_side == 0 ? Uc : Vc, rows, Q.kq, ldq, cv, Q.kq, s));
+    if (Q.conv_side == 0) {
+      L = cv;
+      ldl = Q.kq;
+    } else {
+      R = cv;
+      ldr = Q.kq;
+    }
+  }
+  TIMED(plan, LRAMM_K_RECON, s,
+        qgemm_tc(Q.pp, L, R, Sd.rows, Sd.cols, Q.kq, ldl, ldr, per_row, Us, Vs, 1.f, 0.f, nullptr, 0, Xr, ldxr,
+                 at<float>(ws, Q.part), Q.part_floats, at<int>(ws, 0), s));
   return LRAMM_OK;
 }
 

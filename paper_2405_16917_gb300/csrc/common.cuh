@@ -223,6 +223,8 @@ lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t l
                            int per_row, void* codes, int64_t ldcodes, float* scales,
                            unsigned int* amax_ws, cudaStream_t s);
 // Columns of X quantised as the rows of a K-major code matrix (cols x ldcodes).
+lramm_status fp8_codes_to_bf16(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                               cudaStream_t s);
 lramm_status quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, int per_col,
                            void* codesT, int64_t ldcodes, float* scales, unsigned int* amax_ws, cudaStream_t s);
 lramm_status quantize_rows_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,

@@ -111,6 +111,31 @@ lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t l
   return last_launch();
 }
 
+// e4m3 code bytes (INT4 codes, integers |c| <= 7) rewritten as bfloat16
+// values, so that they meet INT8 codes in one BF16 product; every e4m3 value
+// is exact in bfloat16.  Columns cols .. ldd-1 of dst are not written.
+__global__ void fp8_to_bf16_kernel(const uint8_t* __restrict__ src, int64_t rows, int64_t cols, int64_t lds,
+                                   __nv_bfloat16* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, j = e - i * cols;
+    __nv_fp8_e4m3 v;
+    v.__x = src[i * lds + j];
+    dst[i * ldd + j] = __float2bfloat16_rn(static_cast<float>(v));
+  }
+}
+
+lramm_status fp8_codes_to_bf16(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
+                               cudaStream_t s) {
+  if (rows <= 0 || cols <= 0) return LRAMM_OK;
+  int64_t g = ceil_div(rows * cols, 256);
+  if (g > 152 * 8) g = 152 * 8;
+  fp8_to_bf16_kernel<<<(unsigned)g, 256, 0, s>>>(static_cast<const uint8_t*>(src), rows, cols, lds,
+                                                 static_cast<__nv_bfloat16*>(dst), ldd);
+  return last_launch();
+}
+
 // Column quantiser: the columns of X (rows x cols, row-major) become the
 // rows of a K-major code matrix codesT (cols x ldcodes, ldcodes >= rows,
 // zero beyond rows) with one scale per column (or the tensor a_max) --

@@ -135,3 +135,28 @@ def test_dq_and_mx_argument_checks(L):
     assert lib.lramm_quantize_mx(fake, 4, 40, 40, fake, 40, fake, nul) == 1       # ldcodes not a multiple of 32
     assert lib.lramm_qgemm_mx(fake, fake, fake, fake, 4, 4, 48, 48, 48, 1.0, 0.0, nul, 0, fake, 4, nul) == 1
     assert lib.lramm_launch_count() >= 0
+
+
+def test_qsvd_argument_checks(L):
+    lib = L.load()
+    p = _plan(L)
+    fake, nul, bad = ctypes.c_void_p(256), ctypes.c_void_p(0), ctypes.c_void_p(264)
+    I8, I4, E4, MX = L.P_INT8, L.P_INT4, L.P_E4M3, L.P_MXFP4
+
+    def call(which=0, pu=I8, pv=I8, Uc=fake, ldq=64, Xr=fake, ws=fake, wsb=None):
+        return lib.lramm_qsvd(p.handle, which, fake, pu, pv, Uc, fake, fake, fake, ldq, nul, nul, Xr,
+                              4096, ws, p.ws_bytes if wsb is None else wsb, nul)
+    assert call(which=2) == 1
+    assert call(pu=MX) == 2                       # MXFP4 factors: not offered
+    assert call(pv=0) == 1                        # F32 is not a code format
+    assert call(ldq=80) == 1                      # ldq a multiple of 32
+    assert call(ldq=32) == 1                      # ldq >= r
+    assert call(Uc=bad) == 1                      # codes 16-byte aligned
+    assert call(pu=I8, pv=E4) == 2                # no common code product for INT8 / E4M3 ...
+    assert call(pu=I8, pv=E4, Xr=nul, wsb=16) == 3   # ... but the codes alone are fine
+    assert call(wsb=16) == 3                      # workspace too small
+    assert lib.lramm_qsvd_ws_bytes(p.handle, 0, I8, I8) >= p.ws_bytes
+    assert lib.lramm_qsvd_ws_bytes(p.handle, 0, I8, I4) > lib.lramm_qsvd_ws_bytes(p.handle, 0, I8, I8)
+    assert lib.lramm_qsvd_ws_bytes(p.handle, 1, MX, I8) == 0
+    assert lib.lramm_kernel_kind_name(16).decode() == "reconstruct"
+    assert lib.lramm_kernel_kind_name(17).decode() == "unknown"

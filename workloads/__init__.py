@@ -16,6 +16,8 @@ Workload table (sizes, spectra, rank parameters):
                  sigma_i = exp(-i/128) + 1e-3; r=384, p=16, q=1
   lramm_32768    m=32768, k=4096, n=32768, FP32, sigma_i = (1+i)^-1.5;
                  r=128, p=16, q=2
+  qsvd_4096      Algorithm 4 on one 4096 x 4096 FP32 matrix (the A of
+                 lramm_4096: sigma_i = (1+i)^-1); r=256, p=16, q=2
 Entry-distribution matrices (`entry_matrix`): the paper's precision tests
 draw i.i.d. U(0,1), Exp(1), N(0,1) and Bernoulli(1/2) entries.
 Seeds: A 1001, B 1002, X 1003, sketch 7.
@@ -35,6 +37,8 @@ CONFIGS = {
                       noise=0.0, r=384, p=16, q=1),
     "lramm_32768": dict(m=32768, n=32768, k=4096, dtype="f32", spectrum="poly1.5",
                         noise=0.0, r=128, p=16, q=2),
+    "qsvd_4096": dict(m=4096, n=4096, k=4096, dtype="f32", spectrum="poly1",
+                      noise=0.0, r=256, p=16, q=2),
 }
 
 
