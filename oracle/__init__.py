@@ -15,5 +15,6 @@ Modules:
   mixed   -- MXFP4 (e2m1, 32-element block scales), split-precision
              residuals and the lead / tail E3 of the mixed 4/8-bit chain
   qsvd    -- the quantised SVD approximation of one matrix (Algorithm 4)
+  sketch8 -- the range finder with its products on e4m3 codes
 """
-from . import philox, quant, lramm, rf, mixed, qsvd  # noqa: F401
+from . import philox, quant, lramm, rf, mixed, qsvd, sketch8  # noqa: F401

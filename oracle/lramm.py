@@ -55,27 +55,29 @@ def range_finder(X, l, q, seed, stream):
     return Q
 
 
-def rsvd(X, r, p, q, seed, stream):
+def rsvd(X, r, p, q, seed, stream, rf=None):
     """Algorithm 1 on the range-finder basis, truncated to rank r.
 
     Returns U (rows x r), s (r), V (cols x r) in FP64 with X ~ U diag(s) V^T.
+    rf: the range finder (default `range_finder`; oracle.sketch8 supplies
+    the e4m3 one).
     """
     X = np.asarray(X, dtype=F64)
     l = r + p
     if not (1 <= r and l <= min(X.shape)):
         raise ValueError("rsvd: need 1 <= r and r + p <= min(rows, cols)")
-    Q = range_finder(X, l, q, seed, stream)
+    Q = (rf or range_finder)(X, l, q, seed, stream)
     B = Q.T @ X                                    # Algorithm 1: B = Q^* A
     Ub, s, Vbt = np.linalg.svd(B, full_matrices=False)   # SVD(B) = U' S V^*
     U = Q @ Ub[:, :r]                              # U = Q U'
     return U, s[:r], Vbt[:r, :].T
 
 
-def factors(A, B, r, p, q, seed):
+def factors(A, B, r, p, q, seed, rf=None):
     """The four Alg. 3 factors in FP32 storage: U~ (m x r), V (k x r), W (k x r),
     Z~ (r x n), with A ~ U~ V^T and B ~ W Z~."""
-    U, s, V = rsvd(A, r, p, q, seed, 0)
-    W, g, Z = rsvd(B, r, p, q, seed, 1)
+    U, s, V = rsvd(A, r, p, q, seed, 0, rf)
+    W, g, Z = rsvd(B, r, p, q, seed, 1, rf)
     Ut = (U * s[None, :]).astype(np.float32)        # U~ = U_r Sigma_r
     Zt = (Z * g[None, :]).T.astype(np.float32)       # Z~ = Gamma_r Z_r^T
     return Ut, V.astype(np.float32), W.astype(np.float32), Zt
@@ -95,9 +97,9 @@ def chain(Ut, V, W, Zt, prec, scale=quant.SCALE_ROWCOL, alpha=1.0, beta=0.0, C=N
     return D
 
 
-def lramm(A, B, r, p, q, seed, prec, scale=quant.SCALE_ROWCOL, alpha=1.0, beta=0.0, C=None):
+def lramm(A, B, r, p, q, seed, prec, scale=quant.SCALE_ROWCOL, alpha=1.0, beta=0.0, C=None, rf=None):
     """LRAMM (Algorithm 3): D = alpha * E3 + beta * C, D ~ alpha * A B + beta * C."""
-    Ut, V, W, Zt = factors(A, B, r, p, q, seed)
+    Ut, V, W, Zt = factors(A, B, r, p, q, seed, rf)
     return chain(Ut, V, W, Zt, prec, scale, alpha, beta, C)
 
 

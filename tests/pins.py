@@ -715,3 +715,59 @@ def pin_qsvd_error_bounds(qs, wl, quant):
                     model = np.sum(np.asarray(s, np.float64) ** 2) * k / 12.0
                     ratio = np.sum((dq - M.astype(np.float64)) ** 2) / model
                     assert 0.7 < ratio < 1.3, (name, prec, ratio)
+
+
+# --------------------------------------------------------------------------
+# E4M3 range finder (products of the range finder on e4m3 codes)
+# --------------------------------------------------------------------------
+def pin_rf_e4m3_structure(s8, lr, wl):
+    """With the exact product in place of the quantised one, the e4m3 range
+    finder is the range finder of Sec. 2.2 (same steps in the same order):
+    identical bases."""
+    A = wl.lowrank(60, 45, 0.8 ** np.arange(45), 71)
+    for q in (0, 1, 2):
+        Q1 = s8.range_finder_e4m3(A, 12, q, 5, 0, product=np.matmul)
+        Q2 = lr.range_finder(A, 12, q, 5, 0)
+        assert np.array_equal(Q1, Q2)
+
+
+def pin_rf_e4m3_product(s8, quant, seed=72):
+    """One quantised product by scalar loops: e4m3 codes of the rows of L and
+    the columns of R (lambda = fp32(448 / a_max), code = e4m3(fp32(x lambda))),
+    the exact code sum, then fp32(fp32(acc) * fp32(sL * sR))."""
+    rng = np.random.default_rng(seed)
+    L = rng.standard_normal((5, 7)) * np.exp(rng.uniform(-3, 3, (5, 1)))
+    R = rng.standard_normal((7, 4)) * np.exp(rng.uniform(-3, 3, (1, 4)))
+    got = s8.qproduct_e4m3(L, R)
+    D = np.float32(448.0)
+
+    def codes(v):
+        v = [np.float32(x) for x in v]
+        am = np.float32(max(abs(x) for x in v))
+        lam = np.float32(D / am)
+        return [float(quant.round_e4m3(np.float32(x * lam))) for x in v], np.float32(am / D)
+    for i in range(5):
+        cl, sl = codes(L[i])
+        for j in range(4):
+            cr, sr = codes(R[:, j])
+            acc = sum(a * b for a, b in zip(cl, cr))
+            want = float(np.float32(np.float32(acc) * np.float32(sl * sr)))
+            assert got[i, j] == want, (i, j, got[i, j], want)
+
+
+def pin_rf_e4m3_accuracy(s8, lr, wl):
+    """The e4m3 range finder keeps the randomized SVD close to the FP64 one:
+    Q orthonormal, and the rank-r error between the Eckart-Young floor and
+    1.01 times the FP64 range finder's (decaying spectra, q = 1, 2)."""
+    for (m, n, spec, r, p) in ((400, 300, (1.0 + np.arange(300)) ** -1.0, 32, 8),
+                               (300, 360, np.exp(-np.arange(300) / 24.0), 24, 8)):
+        A = wl.lowrank(m, n, spec, 73)
+        floor = np.sqrt(np.sum(spec[r:] ** 2))
+        for q in (1, 2):
+            Q = s8.range_finder_e4m3(A, r + p, q, 9, 0)
+            assert np.abs(Q.T @ Q - np.eye(r + p)).max() < 1e-12
+            U, s, V = s8.rsvd_e4m3(A, r, p, q, 9, 0)
+            U0, s0, V0 = lr.rsvd(A, r, p, q, 9, 0)
+            e8 = np.linalg.norm(A - (U * s) @ V.T)
+            e0 = np.linalg.norm(A - (U0 * s0) @ V0.T)
+            assert floor * (1 - 1e-9) <= e8 <= 1.01 * e0, (m, q, e8, e0, floor)

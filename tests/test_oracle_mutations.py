@@ -361,3 +361,34 @@ def test_qsvd_floor_rounding_caught(monkeypatch):
     monkeypatch.setattr(Qs, "quantise", bad)
     with pytest.raises(AssertionError):
         pins.pin_qsvd_error_bounds(Qs, workloads, Qn)
+
+
+# E4M3 range finder
+def test_rf_e4m3_left_per_column_caught(monkeypatch):
+    from oracle import sketch8 as S8
+
+    def bad(L, R):
+        Lq = np.asarray(L, np.float32)
+        c, _, s = Qn.quantize(Lq, Qn.PREC_E4M3, 0)                 # left operand per column
+        cr, _, sr = Qn.quantize(np.asarray(R, np.float32), Qn.PREC_E4M3, 0)
+        deq = Qn.dequantize(c, s, 0).astype(np.float64)
+        return (deq @ Qn.dequantize(cr, sr, 0).astype(np.float64)).astype(np.float32).astype(np.float64)
+    monkeypatch.setattr(S8, "qproduct_e4m3", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_rf_e4m3_product(S8, Qn)
+
+
+def test_rf_e4m3_power_step_on_x_caught(monkeypatch):
+    from oracle import sketch8 as S8
+    from oracle import philox as Ph
+
+    def bad(X, l, q, seed, stream, product=S8.qproduct_e4m3):
+        X = np.asarray(X, dtype=np.float64)
+        Om = Ph.gaussian_matrix(seed, stream, X.shape[1], l).astype(np.float64)
+        Q = Lr.orth(product(X, Om))
+        for _ in range(q):
+            Q = Lr.orth(product(X, Om))          # the power step re-sketches instead of using X^T Q
+        return Q
+    monkeypatch.setattr(S8, "range_finder_e4m3", bad)
+    with pytest.raises(AssertionError):
+        pins.pin_rf_e4m3_structure(S8, Lr, workloads)

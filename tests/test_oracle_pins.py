@@ -146,3 +146,16 @@ def test_qsvd_codes_bruteforce():
 
 def test_qsvd_error_bounds():
     pins.pin_qsvd_error_bounds(oracle.qsvd, workloads, oracle.quant)
+
+
+# E4M3 range finder
+def test_rf_e4m3_structure():
+    pins.pin_rf_e4m3_structure(oracle.sketch8, oracle.lramm, workloads)
+
+
+def test_rf_e4m3_product():
+    pins.pin_rf_e4m3_product(oracle.sketch8, oracle.quant)
+
+
+def test_rf_e4m3_accuracy():
+    pins.pin_rf_e4m3_accuracy(oracle.sketch8, oracle.lramm, workloads)
