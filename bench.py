@@ -334,7 +334,7 @@ def run_lramm(args):
     A, B = workloads.device_operands(args.workload, dev)
     a_type = L.BF16 if A.dtype == torch.bfloat16 else L.F32
     sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
-    sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
+    sketch = {"tf32": L.SKETCH_TF32, "fp32": L.SKETCH_F32, "e4m3": L.SKETCH_E4M3}[sketch_name]
     lead = LEADS.get(args.variant, (0, 1, 0))
     # the timed steps run an uninstrumented plan; a second, instrumented plan
     # (CUDA events around every kernel) gives the per-kind breakdown
@@ -489,7 +489,7 @@ def run_lramm(args):
                 "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
                 "peak_source": peak_src + " hbm_gbs", "traffic": None, "algorithmic_bytes_per_launch": nbytes}
         roof["frac"] = roof["achieved"] / roof["peak"]
-    elif dname in ("sketch", "e3", "gram", "trsm", "e1", "e2") and nflops is not None:
+    elif dname in ("sketch", "e3", "gram", "trsm", "e1", "e2") and nflops is not None and sketch_name != "e4m3":
         # these kernels are FP32 SIMT in this version: bound by FP32 FMA issue
         roof = {"bound": "alu", "achieved": nflops / avg_s / 1e12,
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
@@ -522,7 +522,7 @@ def run_lramm(args):
         kms, kc = kinds[kn]
         ks = kms / kc * 1e-3
         kb, kf = kernel_work(kn, cfg, l, args.variant)
-        if kn == "sketch" and sketch_name != "tf32":
+        if kn == "sketch" and sketch_name not in ("tf32",):
             continue
         kroofs[kn] = {"bound": "hbm", "achieved": kb / ks / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
                       "frac": kb / ks / 1e9 / pk["hbm_gbs"], "avg_launch_ms": ks * 1e3,
@@ -610,7 +610,7 @@ def run_rf(args):
     g.manual_seed(17)
     G = torch.randn((m, n), generator=g, device=dev, dtype=torch.float32)
     sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
-    sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
+    sketch = {"tf32": L.SKETCH_TF32, "fp32": L.SKETCH_F32, "e4m3": L.SKETCH_E4M3}[sketch_name]
     plan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=(0, 0, prec), a_type=L.BF16, b_type=L.F32,
                   sketch=sketch)
     tplan = L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=(0, 0, prec), a_type=L.BF16, b_type=L.F32,
@@ -827,7 +827,7 @@ def run_qsvd(args):
     pu, pv = QSVD_BITS[args.variant]
     A, _ = workloads.device_operands("qsvd_4096", dev)
     sketch_name = args.sketch or "tf32"
-    sketch = L.SKETCH_TF32 if sketch_name == "tf32" else L.SKETCH_F32
+    sketch = {"tf32": L.SKETCH_TF32, "fp32": L.SKETCH_F32, "e4m3": L.SKETCH_E4M3}[sketch_name]
     plan = L.Plan(m, k, k, r, p, q, seed=workloads.SEED_SKETCH, sketch=sketch)
     tplan = L.Plan(m, k, k, r, p, q, seed=workloads.SEED_SKETCH, sketch=sketch, timing=True)
     ws = torch.empty(lib.lramm_qsvd_ws_bytes(plan.handle, 0, pu, pv), dtype=torch.uint8, device=dev)
@@ -1020,8 +1020,9 @@ def main():
     ap.add_argument("--impl", choices=["lramm", "reference"], default="lramm")
     ap.add_argument("--workload", default="lramm_4096", choices=sorted(workloads.CONFIGS))
     ap.add_argument("--variant", default="int8", choices=sorted(VARIANTS))
-    ap.add_argument("--sketch", choices=["tf32", "fp32"], default=None,
-                    help="products with A and B: tf32 tensor cores (default for quantised variants) or fp32")
+    ap.add_argument("--sketch", choices=["tf32", "fp32", "e4m3"], default=None,
+                    help="products with A and B: tf32 tensor cores (default for quantised variants), fp32, or "
+                         "e4m3 (the range-finder passes on FP8 codes, the projection in tf32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

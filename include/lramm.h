@@ -79,8 +79,20 @@ typedef enum { LRAMM_S_ROWCOL = 0, LRAMM_S_TENSOR = 1 } lramm_scale;
  * projection); the orthonormalisations and small SVD are FP32.
  *   F32  : FP32-accurate products
  *   TF32 : one TF32 pass (10-bit mantissa operands), FP32 accumulate
- *   BF16 : BF16 operands, FP32 accumulate                               */
-typedef enum { LRAMM_SKETCH_F32 = 0, LRAMM_SKETCH_TF32 = 1, LRAMM_SKETCH_BF16 = 2 } lramm_sketch;
+ *   BF16 : BF16 operands, FP32 accumulate
+ *   E4M3 : the range finder of the SVD form (the sketch X Omega and the
+ *          power iterations) on FP8 e4m3 codes, FP32 accumulate: X is
+ *          quantised once per call per row (for X B) and per column (for
+ *          X^T B), each l-column matrix B per column, products dequantised
+ *          as in Algorithm 2; the projection B^T = X^T Q stays TF32.  FP32
+ *          operands only (else LRAMM_ERR_UNSUPPORTED at plan creation);
+ *          the range-finder form rejects it (LRAMM_ERR_UNSUPPORTED).     */
+typedef enum {
+  LRAMM_SKETCH_F32 = 0,
+  LRAMM_SKETCH_TF32 = 1,
+  LRAMM_SKETCH_BF16 = 2,
+  LRAMM_SKETCH_E4M3 = 3
+} lramm_sketch;
 
 typedef struct lramm_desc {
   int64_t m, n, k;        /* A is m x k, B is k x n, C and D are m x n           */
@@ -240,6 +252,15 @@ LRAMM_API lramm_status lramm_gaussian(uint64_t seed, uint32_t stream_id, int64_t
 LRAMM_API lramm_status lramm_quantize(const float* X, int64_t rows, int64_t cols, int64_t ldx,
                             int32_t prec, int32_t per_row, void* codes, int64_t ldcodes,
                             float* scales, void* ws, void* stream);
+
+/* Per-column symmetric quantiser (Eqs. get_lambda, Quantization, one scale
+ * per column of X): the columns of X (rows x cols, stride ldx, FP32) become
+ * the rows of a K-major code matrix codesT (cols x ldcodes, ldcodes >= rows,
+ * zero beyond rows), codes as lramm_quantize writes them for prec;
+ * scales[cols] = a_max / D.  The same decisions as lramm_quantize applied to
+ * X^T.  ws: device scratch of cols 32-bit words.  Asynchronous on `stream`. */
+LRAMM_API lramm_status lramm_quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t ldx, int32_t prec,
+                                           void* codesT, int64_t ldcodes, float* scales, void* ws, void* stream);
 
 /* QM product of Algorithm 2 on quantised codes, both K-major:
  *   L  M x K (stride ldl), Rt N x K (stride ldr); codes as lramm_quantize

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "liblramm.so")
 F32, BF16 = 0, 1
 P_F32, P_INT8, P_INT4, P_E4M3, P_MXFP4 = 0, 1, 2, 3, 4
 S_ROWCOL, S_TENSOR = 0, 1
-SKETCH_F32, SKETCH_TF32, SKETCH_BF16 = 0, 1, 2
+SKETCH_F32, SKETCH_TF32, SKETCH_BF16, SKETCH_E4M3 = 0, 1, 2, 3
 
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace", 4: "cuda error",
           5: "numeric (Cholesky breakdown)", 6: "timeout", 7: "Jacobi not converged"}
@@ -71,6 +71,7 @@ _SIGS = {
     "lramm_qsvd": (_I32, [_VP, _I32, _VP, _I32, _I32, _VP, _VP, _VP, _VP, _I64, _VP, _VP, _VP, _I64, _VP,
                           ctypes.c_size_t, _VP]),
     "lramm_qsvd_ws_bytes": (ctypes.c_size_t, [_VP, _I32, _I32, _I32]),
+    "lramm_quantize_cols": (_I32, [_VP, _I64, _I64, _I64, _I32, _VP, _I64, _VP, _VP, _VP]),
     "lramm_quantize_mx": (_I32, [_VP, _I64, _I64, _I64, _VP, _I64, _VP, _VP]),
     "lramm_qgemm_mx": (_I32, [_VP, _VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _F, _F, _VP, _I64, _VP, _I64, _VP]),
     "lramm_quant_ws_bytes": (ctypes.c_size_t, []),
@@ -410,6 +411,20 @@ def quantize(X, prec, per_row=True, ldcodes=None):
     ws = torch.empty(lib.lramm_quant_ws_bytes(), dtype=torch.uint8, device=X.device)
     _check(lib.lramm_quantize(_ptr(X), rows, cols, X.stride(0), prec, int(per_row), _ptr(codes), ldc,
                               _ptr(scales), _ptr(ws), _stream()), "lramm_quantize")
+    return codes, scales
+
+
+def quantize_cols(X, prec, ldcodes=None):
+    """Per-column codes of X as the rows of a K-major matrix (cols x ldcodes) and FP32 scales."""
+    torch = _torch()
+    _need_cuda(X)
+    rows, cols = X.shape
+    ldc = ldcodes or rows
+    codes = torch.empty((cols, ldc), dtype=code_dtype(prec), device=X.device)
+    scales = torch.empty((cols,), dtype=torch.float32, device=X.device)
+    ws = torch.empty(4 * cols, dtype=torch.uint8, device=X.device)
+    _check(load().lramm_quantize_cols(_ptr(X), rows, cols, X.stride(0), prec, _ptr(codes), ldc, _ptr(scales),
+                                      _ptr(ws), _stream()), "lramm_quantize_cols")
     return codes, scales
 
 

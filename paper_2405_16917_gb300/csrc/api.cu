@@ -43,6 +43,10 @@ struct SideLayout {
   int64_t rows, cols;
   size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, CS, GS;
   size_t part, gpart, gtpart, bsplit;   // this operand's split-K partials and BF16 parts (own stream)
+  // E4M3 range finder: codes of X per row (rows x cols_p) and per column
+  // (cols x rows_p), of the l-column operand (l x max(rows_p, cols_p)), their
+  // scales, column a_max scratch and the products' split-K partials
+  size_t xc, xs, xtc, xts, bc, bs, cam, qp, qp_floats;
 };
 
 }  // namespace
@@ -117,7 +121,9 @@ lramm_status validate(const lramm_desc* d) {
   for (int i = 0; i < 3; ++i)
     if (!valid_prec(d->prec[i])) return LRAMM_ERR_INVALID_ARG;
   if (d->scale != LRAMM_S_ROWCOL && d->scale != LRAMM_S_TENSOR) return LRAMM_ERR_INVALID_ARG;
-  if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_BF16) return LRAMM_ERR_INVALID_ARG;
+  if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_E4M3) return LRAMM_ERR_INVALID_ARG;
+  if (d->sketch == LRAMM_SKETCH_E4M3 && (d->a_type != LRAMM_F32 || d->b_type != LRAMM_F32))
+    return LRAMM_ERR_UNSUPPORTED;
   if (d->max_sweeps < 0 || (d->flags & ~(LRAMM_FLAG_TIMING | LRAMM_FLAG_GRAPH)) != 0) return LRAMM_ERR_INVALID_ARG;
   if (d->lead < 0 || d->lead > d->r || d->lead_split < 0 || d->lead_split > 2) return LRAMM_ERR_INVALID_ARG;
   if (d->lead > 0 && d->lead_prec != LRAMM_P_INT8 && d->lead_prec != LRAMM_P_INT4 && d->lead_prec != LRAMM_P_E4M3)
@@ -209,6 +215,19 @@ void layout(lramm_plan_s* P) {
                    ? b.take(sizeof(float) * gram_tc_part_floats((int)l))
                    : 0;
     S.bsplit = P->bsplit_bytes ? b.take(P->bsplit_bytes) : 0;
+    if (d.sketch == LRAMM_SKETCH_E4M3) {
+      const int64_t rp = round_up(S.rows, 32), cp = round_up(S.cols, 32);
+      S.xc = b.take(S.rows * cp);
+      S.xs = b.take(sizeof(float) * S.rows);
+      S.xtc = b.take(S.cols * rp);
+      S.xts = b.take(sizeof(float) * S.cols);
+      S.bc = b.take(l * std::max(rp, cp));
+      S.bs = b.take(sizeof(float) * l);
+      S.cam = b.take(sizeof(unsigned int) * std::max<int64_t>(S.cols, l));
+      S.qp_floats = std::max(qgemm_tc_part_floats(LRAMM_P_E4M3, S.rows, l, cp),
+                             qgemm_tc_part_floats(LRAMM_P_E4M3, S.cols, l, rp));
+      S.qp = b.take(sizeof(float) * std::max<size_t>(S.qp_floats, 4));
+    }
   }
   {  // split-K partials of the tensor-core code products (E1 with long K)
     auto qp = [](int prec, int64_t M, int64_t N, int64_t K) -> size_t {
@@ -293,11 +312,30 @@ lramm_status check_ws(const lramm_plan_s* P, void* ws, size_t ws_bytes) {
 // X B (a_mn = 0) or X^T B (a_mn = 1) for the range finder: on the tensor
 // cores in TF32 when the plan asks for a TF32 sketch and the shapes allow
 // (TMA needs l and the row stride of X divisible by 4, 16-byte aligned
-// bases), else the FP32 SIMT product.
+// bases), else the FP32 SIMT product.  fp8: a range-finder pass of an E4M3
+// plan -- the product of X's e4m3 codes (made by x_codes) with the
+// per-column e4m3 codes of B on the tensor cores (kind::f8f6f4), dequantised
+// per row of X (or column, for X^T) and per column of B.
 lramm_status x_product(lramm_plan_s* P, void* ws, const SideLayout& S, int a_mn, const void* X, int64_t rows,
-                       int64_t cols, int64_t ldx, int xbf, const float* B, float* out, cudaStream_t s) {
+                       int64_t cols, int64_t ldx, int xbf, const float* B, float* out, cudaStream_t s,
+                       bool fp8 = false) {
   const int l = P->l;
   const int sk = P->d.sketch;
+  if (fp8 && sk == LRAMM_SKETCH_E4M3) {
+    const int64_t rp = round_up(rows, 32), cp = round_up(cols, 32);
+    void* bc = at<void>(ws, S.bc);
+    float* bs = at<float>(ws, S.bs);
+    unsigned int* cam = at<unsigned int>(ws, S.cam);
+    if (!a_mn) {   // X B, B cols x l: codes of B's columns as rows (l x cols_p)
+      LRAMM_TRY(quantize_cols2d(B, cols, l, l, LRAMM_P_E4M3, bc, cp, bs, cam, s));
+      return qgemm_tc(LRAMM_P_E4M3, at<void>(ws, S.xc), bc, rows, l, cp, cp, cp, 1, at<float>(ws, S.xs), bs, 1.f,
+                      0.f, nullptr, 0, out, l, at<float>(ws, S.qp), S.qp_floats, at<int>(ws, 0), s);
+    }
+    // X^T B, B rows x l: codes of B's columns (l x rows_p) against X's column codes
+    LRAMM_TRY(quantize_cols2d(B, rows, l, l, LRAMM_P_E4M3, bc, rp, bs, cam, s));
+    return qgemm_tc(LRAMM_P_E4M3, at<void>(ws, S.xtc), bc, cols, l, rp, rp, rp, 1, at<float>(ws, S.xts), bs, 1.f, 0.f,
+                    nullptr, 0, out, l, at<float>(ws, S.qp), S.qp_floats, at<int>(ws, 0), s);
+  }
   if (xbf && sk != LRAMM_SKETCH_F32 && P->bsplit_bytes && sketch_bf_supported(ldx, l, X, B))
     return sketch_bf(a_mn, X, rows, cols, ldx, B, l, sk == LRAMM_SKETCH_TF32 ? 2 : 1, out, at<float>(ws, S.part),
                      sketch_tc_part_floats(l), at<void>(ws, S.bsplit), P->bsplit_bytes, at<int>(ws, 0), s);
@@ -306,6 +344,17 @@ lramm_status x_product(lramm_plan_s* P, void* ws, const SideLayout& S, int a_mn,
                      sketch_tc_part_floats(l), at<int>(ws, 0), s);
   if (a_mn) return sgemm(1, 0, cols, l, rows, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
   return sgemm(0, 0, rows, l, cols, 1.f, X, ldx, xbf, B, l, 0.f, out, l, s);
+}
+
+// The e4m3 codes of an operand for an E4M3 range finder, once per call:
+// per row (rows x cols_p, for X B) and per column (cols x rows_p, for X^T B).
+lramm_status x_codes(lramm_plan_s* P, void* ws, const SideLayout& S, const void* X, int64_t ldx, cudaStream_t s) {
+  const float* Xf = static_cast<const float*>(X);
+  const int64_t rp = round_up(S.rows, 32), cp = round_up(S.cols, 32);
+  LRAMM_TRY(quantize_rows(Xf, S.rows, S.cols, ldx, LRAMM_P_E4M3, 1, at<void>(ws, S.xc), cp, at<float>(ws, S.xs),
+                          nullptr, s));
+  return quantize_cols2d(Xf, S.rows, S.cols, ldx, LRAMM_P_E4M3, at<void>(ws, S.xtc), rp, at<float>(ws, S.xts),
+                         at<unsigned int>(ws, S.cam), s);
 }
 
 // One operand's share of a randomized SVD run.
@@ -408,6 +457,7 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
                         const int* s1_sigma, const int* s2_sigma, cudaStream_t s) {
   const lramm_desc& d = P->d;
   const int l = P->l;
+  const bool fp8 = d.sketch == LRAMM_SKETCH_E4M3;   // range-finder passes on e4m3 codes
   int* st = at<int>(ws, 0);
   float *R0[2], *R1[2], *C0[2], *C1[2];
   int64_t rows[2], cols[2];
@@ -421,15 +471,19 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
     cols[i] = S.cols;
     float* Om = at<float>(ws, S.omega);
     TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, (uint32_t)which[i], S.cols, l, Om, l, s));
-    TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s));
+    if (fp8) TIMED(P, LRAMM_K_SKETCH, s, x_codes(P, ws, S, sd[i].X, sd[i].ldx, s));
+    TIMED(P, LRAMM_K_SKETCH, s,
+          x_product(P, ws, *sd[i].S, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s, fp8));
   }
   LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, d.q > 0 ? 1 : 2, false, st, s));  // Q
   for (int it = 0; it < d.q; ++it) {
     for (int i = 0; i < ns; ++i)
-      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));
+      TIMED(P, LRAMM_K_SKETCH, s,
+            x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s, fp8));
     LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 1, false, st, s));  // Z^ (span only)
     for (int i = 0; i < ns; ++i)
-      TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 0, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, C0[i], R0[i], s));
+      TIMED(P, LRAMM_K_SKETCH, s,
+            x_product(P, ws, *sd[i].S, 0, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, C0[i], R0[i], s, fp8));
     LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, it == d.q - 1 ? 2 : 1, false, st, s));
   }
   for (int i = 0; i < ns; ++i)
@@ -1110,6 +1164,14 @@ lramm_status lramm_quantize_noalloc(const float* X, int64_t rows, int64_t cols, 
 
 size_t lramm_noalloc_scratch_bytes(void) { return noalloc_scratch_bytes(); }
 
+lramm_status lramm_quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t ldx, int32_t prec, void* codesT,
+                                 int64_t ldcodes, float* scales, void* ws, void* stream) {
+  if (!X || !codesT || !scales || !ws || rows < 1 || cols < 1 || ldx < cols || ldcodes < rows) return LRAMM_ERR_INVALID_ARG;
+  if (prec != LRAMM_P_INT8 && prec != LRAMM_P_INT4 && prec != LRAMM_P_E4M3) return LRAMM_ERR_INVALID_ARG;
+  return quantize_cols2d(X, rows, cols, ldx, prec, codesT, ldcodes, scales, static_cast<unsigned int*>(ws),
+                         static_cast<cudaStream_t>(stream));
+}
+
 lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, int64_t K, int64_t ldl,
                          int64_t ldr, int32_t prec, int32_t per_row, const float* sL, const float* sR,
                          float alpha, float beta, const float* C, int64_t ldc, void* D, int64_t ldd,
@@ -1126,6 +1188,7 @@ lramm_status lramm_qgemm(const void* L, const void* Rt, int64_t M, int64_t N, in
 lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, float* C, void* ws, size_t ws_bytes,
                               void* stream) {
   if (!plan || !X || !W || !C) return LRAMM_ERR_INVALID_ARG;
+  if (plan->d.sketch == LRAMM_SKETCH_E4M3) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const lramm_desc& d = plan->d;
@@ -1156,7 +1219,7 @@ lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, 
                                float* dW, void* ws, size_t ws_bytes, void* stream) {
   if (!plan || !X || !W || !G || !dX || !dW) return LRAMM_ERR_INVALID_ARG;
   const lramm_desc& d = plan->d;
-  if (d.b_type != LRAMM_F32) return LRAMM_ERR_UNSUPPORTED;
+  if (d.b_type != LRAMM_F32 || d.sketch == LRAMM_SKETCH_E4M3) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int l = plan->l;

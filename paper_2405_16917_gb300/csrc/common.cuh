@@ -222,11 +222,16 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
 lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
                            int per_row, void* codes, int64_t ldcodes, float* scales,
                            unsigned int* amax_ws, cudaStream_t s);
-// Columns of X quantised as the rows of a K-major code matrix (cols x ldcodes).
 lramm_status fp8_codes_to_bf16(const void* src, int64_t rows, int64_t cols, int64_t lds, void* dst, int64_t ldd,
                                cudaStream_t s);
+// Columns of X quantised as the rows of a K-major code matrix (cols x ldcodes).
 lramm_status quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, int per_col,
                            void* codesT, int64_t ldcodes, float* scales, unsigned int* amax_ws, cudaStream_t s);
+// The same per-column quantisation (identical codes and scales) on a 2-D
+// grid of column blocks x row chunks, for tall matrices with few columns:
+// amax_cols (cols words of scratch) receives the column a_max first.
+lramm_status quantize_cols2d(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, void* codesT,
+                             int64_t ldcodes, float* scales, unsigned int* amax_cols, cudaStream_t s);
 lramm_status quantize_rows_noalloc(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
                                    int per_row, void* codes, int64_t ldcodes, float* scales,
                                    cudaStream_t s);

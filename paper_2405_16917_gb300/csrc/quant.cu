@@ -224,6 +224,98 @@ lramm_status quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t l
   return last_launch();
 }
 
+// Column a_max over a chunk of rows, merged across CTAs by atomicMax on the
+// float bits (non-negative floats order like their bit patterns).
+__global__ void __launch_bounds__(256) col_amax_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                       int64_t ldx, int64_t rchunk, unsigned int* __restrict__ amax) {
+  __shared__ float s_am[8][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t col = static_cast<int64_t>(blockIdx.x) * 32 + lane;
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rchunk;
+  const int64_t r1 = r0 + rchunk < rows ? r0 + rchunk : rows;
+  float am = 0.f;
+  if (col < cols)
+    for (int64_t r = r0 + warp; r < r1; r += 8) am = fmaxf(am, fabsf(X[r * ldx + col]));
+  s_am[warp][lane] = am;
+  __syncthreads();
+  if (warp == 0) {
+    for (int w = 1; w < 8; ++w) am = fmaxf(am, s_am[w][lane]);
+    if (col < cols) atomicMax(amax + col, __float_as_uint(am));
+  }
+}
+
+// Codes of rows r0 .. r0 + rchunk - 1 (up to ldcodes, zero beyond rows) of
+// 32 columns, written transposed; the column's lambda and scale as in
+// quant_cols_kernel.
+template <int PREC>
+__global__ void __launch_bounds__(256) quant_cols2d_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                           int64_t ldx, int64_t rchunk,
+                                                           const unsigned int* __restrict__ amax,
+                                                           void* __restrict__ codesT, int64_t ldcodes,
+                                                           float* __restrict__ scales) {
+  __shared__ float s_lam[32];
+  __shared__ float tile[32][33];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * 32;
+  const int64_t col = c0 + lane;
+  const float D = PREC == LRAMM_P_INT8 ? 127.0f : (PREC == LRAMM_P_INT4 ? 7.0f : 448.0f);
+  if (warp == 0) {
+    const float am = col < cols ? __uint_as_float(amax[col]) : 0.f;
+    s_lam[lane] = am > 0.f ? __fdiv_rn(D, am) : 0.f;
+    if (blockIdx.y == 0 && col < cols) scales[col] = __fdiv_rn(am, D);
+  }
+  __syncthreads();
+  const int64_t r0 = static_cast<int64_t>(blockIdx.y) * rchunk;
+  const int64_t r1 = r0 + rchunk < ldcodes ? r0 + rchunk : ldcodes;
+  for (int64_t rb = r0; rb < r1; rb += 32) {
+    for (int i = warp; i < 32; i += 8) {
+      const int64_t r = rb + i;
+      tile[i][lane] = (r < rows && col < cols) ? X[r * ldx + col] : 0.f;
+    }
+    __syncthreads();
+    for (int j = warp; j < 32; j += 8) {
+      const int64_t c = c0 + j;
+      const int64_t r = rb + lane;
+      if (c < cols && r < r1) {
+        const float y = r < rows ? __fmul_rn(tile[lane][j], s_lam[j]) : 0.f;
+        store_code<PREC>(codesT, c * ldcodes + r, y, D);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+lramm_status quantize_cols2d(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec, void* codesT,
+                             int64_t ldcodes, float* scales, unsigned int* amax_cols, cudaStream_t s) {
+  if (cols <= 0) return LRAMM_OK;
+  if (ldcodes < rows || !amax_cols) return LRAMM_ERR_INVALID_ARG;
+  const int64_t cblocks = ceil_div(cols, 32);
+  // row chunks (multiples of 32) so that the grid has about two CTAs per SM
+  int64_t nchunks = ceil_div(2 * 152, cblocks);
+  int64_t rchunk = round_up(ceil_div(ldcodes, nchunks), 32);
+  if (rchunk < 32) rchunk = 32;
+  nchunks = ceil_div(ldcodes, rchunk);
+  LRAMM_CUDA_TRY(cudaMemsetAsync(amax_cols, 0, sizeof(unsigned int) * cols, s));
+  col_amax_kernel<<<dim3((unsigned)cblocks, (unsigned)ceil_div(rows, rchunk)), 256, 0, s>>>(X, rows, cols, ldx, rchunk,
+                                                                                            amax_cols);
+  LRAMM_TRY(last_launch());
+  const dim3 g((unsigned)cblocks, (unsigned)nchunks);
+  switch (prec) {
+    case LRAMM_P_INT8:
+      quant_cols2d_kernel<LRAMM_P_INT8><<<g, 256, 0, s>>>(X, rows, cols, ldx, rchunk, amax_cols, codesT, ldcodes, scales);
+      break;
+    case LRAMM_P_INT4:
+      quant_cols2d_kernel<LRAMM_P_INT4><<<g, 256, 0, s>>>(X, rows, cols, ldx, rchunk, amax_cols, codesT, ldcodes, scales);
+      break;
+    case LRAMM_P_E4M3:
+      quant_cols2d_kernel<LRAMM_P_E4M3><<<g, 256, 0, s>>>(X, rows, cols, ldx, rchunk, amax_cols, codesT, ldcodes, scales);
+      break;
+    default:
+      return LRAMM_ERR_INVALID_ARG;
+  }
+  return last_launch();
+}
+
 // ---------------------------------------------------------------------------
 // QM product, SIMT: acc(i,j) = sum_t L(i,t) Rt(j,t) with both operands
 // K-major code matrices.  Integer codes accumulate exactly: FP32 partial
