@@ -41,7 +41,7 @@ constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of eve
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, CS, GS;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, S1T, S2T, CS, GS;
   size_t part, gpart, gtpart, bsplit;   // this operand's split-K partials and BF16 parts (own stream)
   // E4M3 range finder: codes of X per row (rows x cols_p) and per column
   // (cols x rows_p), of the l-column operand (l x max(rows_p, cols_p)), their
@@ -163,6 +163,8 @@ void layout(lramm_plan_s* P) {
     S.sig = b.take(sizeof(float) * l);
     S.S1 = b.take(sizeof(float) * l * r);
     S.S2 = b.take(sizeof(float) * l * r);
+    S.S1T = b.take(sizeof(float) * l * r);
+    S.S2T = b.take(sizeof(float) * l * r);
   }
   P->kp = round_up(d.k, 32);   // code rows padded to whole 32-blocks (MXFP4) and 16-K MMA steps
   P->rp = round_up(r, 32);
@@ -449,6 +451,26 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
   return LRAMM_OK;
 }
 
+// One product of the factor assembly: out (M x N, stride ldo) = A B^T with
+// A (M x l) and B (N x l) K-major.  For the factors that feed a quantised
+// chain inside lramm_matmul (tc: a tensor-core sketch mode, quantised E3,
+// no lead / tail split) a TF32 tensor-core product with this operand's
+// split-K buffer -- its rounding (2^-11 relative) sits far below the
+// quantisation step; otherwise (and for the factors lramm_rsvd and
+// lramm_qsvd return, orthonormal to working precision) the FP32 SIMT
+// product, which takes its operands as given by (ta, Am, lda_s, tb, Bm, ldb_s).
+lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M, int64_t N, const float* A,
+                      const float* B, float* out, int64_t ldo, int ta, const float* Am, int64_t lda_s, int tb,
+                      const float* Bm, int64_t ldb_s, cudaStream_t s, bool tc = false) {
+  const int l = P->l;
+  const lramm_desc& d = P->d;
+  if (tc && d.sketch != LRAMM_SKETCH_F32 && d.lead == 0 && d.prec[2] != LRAMM_P_F32 &&
+      tgemm_tc_supported(A, B, l, l, M, N, l) && tgemm_tc_part_floats(M, N, l) <= sketch_tc_part_floats(l))
+    return tgemm_tc(M, N, l, 1.f, A, l, B, l, 0.f, out, ldo, at<float>(ws, S.part), sketch_tc_part_floats(l),
+                    at<int>(ws, 0), s);
+  return sgemm(ta, tb, M, N, l, 1.f, Am, lda_s, 0, Bm, ldb_s, 0.f, out, ldo, s);
+}
+
 // Range finder, projection and small SVD of one or two operands in lockstep
 // (X rows x cols each).  On exit (workspace, per side): R0 = Q (rows x l),
 // C0 = P (cols x l), sig[:r], S1 = U_s[:, :r] (x sigma if s1_sigma[i]),
@@ -498,8 +520,9 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
     const SideLayout& S = *sd[i].S;
     jb.M[i] = at<float>(ws, S.R);
     jb.V[i] = at<float>(ws, S.Vj);
-    fb.p[i] = FinalProb{at<float>(ws, S.R), at<float>(ws, S.Vj), at<float>(ws, S.sig), at<float>(ws, S.S1),
-                        at<float>(ws, S.S2), s1_sigma[i], s2_sigma[i]};
+    fb.p[i] = FinalProb{at<float>(ws, S.R),   at<float>(ws, S.Vj),  at<float>(ws, S.sig),
+                        at<float>(ws, S.S1),  at<float>(ws, S.S2),  s1_sigma[i],
+                        s2_sigma[i],          at<float>(ws, S.S1T), at<float>(ws, S.S2T)};
   }
   TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s));
   TIMED(P, LRAMM_K_SVDSORT, s, launch_svd_finalize(fb, l, d.r, s));
@@ -857,9 +880,11 @@ lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* 
   const int zero[1] = {0};
   LRAMM_TRY(rsvd_sides(plan, &sd, &which, 1, ws, zero, zero, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(0, 0, Sd.rows, r, l, 1.f, at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, 0.f, U, r, s));
+        assemble(plan, ws, Sd, Sd.rows, r, at<float>(ws, Sd.R0), at<float>(ws, Sd.S1T), U, r, 0,
+                 at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(0, 0, Sd.cols, r, l, 1.f, at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, 0.f, V, r, s));
+        assemble(plan, ws, Sd, Sd.cols, r, at<float>(ws, Sd.C0), at<float>(ws, Sd.S2T), V, r, 0,
+                 at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, s));
   LRAMM_CUDA_TRY(cudaMemcpyAsync(S, at<float>(ws, Sd.sig), sizeof(float) * r, cudaMemcpyDeviceToDevice, s));
   return LRAMM_OK;
 }
@@ -942,9 +967,11 @@ lramm_status lramm_qsvd(lramm_plan_t plan, int32_t which, const void* X, int32_t
   float* Ut = Uf ? Uf : at<float>(ws, which == 0 ? plan->Ut : plan->Wt);
   float* V = Vf ? Vf : at<float>(ws, which == 0 ? plan->Vt : plan->Zt);
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(0, 0, Sd.rows, r, l, 1.f, at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, 0.f, Ut, r, s));
+        assemble(plan, ws, Sd, Sd.rows, r, at<float>(ws, Sd.R0), at<float>(ws, Sd.S1T), Ut, r, 0,
+                 at<float>(ws, Sd.R0), l, 0, at<float>(ws, Sd.S1), r, s));
   TIMED(plan, LRAMM_K_ASSEMBLE, s,
-        sgemm(0, 0, Sd.cols, r, l, 1.f, at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, 0.f, V, r, s));
+        assemble(plan, ws, Sd, Sd.cols, r, at<float>(ws, Sd.C0), at<float>(ws, Sd.S2T), V, r, 0,
+                 at<float>(ws, Sd.C0), l, 0, at<float>(ws, Sd.S2), r, s));
   unsigned int* amax = at<unsigned int>(ws, plan->amax);
   TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(Ut, Sd.rows, r, r, prec_u, per_row, Uc, ldq, Us, amax, s));
   TIMED(plan, LRAMM_K_QUANT, s, quantize_rows(V, Sd.cols, r, r, prec_v, per_row, Vc, ldq, Vs, amax, s));
@@ -1053,18 +1080,22 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   auto side_a = [&]() -> lramm_status {
     LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s));
     TIMED(plan, LRAMM_K_ASSEMBLE, s,
-          sgemm(0, 0, d.m, r, l, 1.f, at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, 0.f, Ut, r, s));
+          assemble(plan, ws, SA, d.m, r, at<float>(ws, SA.R0), at<float>(ws, SA.S1T), Ut, r, 0,
+                   at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, s, true));
     TIMED(plan, LRAMM_K_ASSEMBLE, s,
-          sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SA.S2), r, 0, at<float>(ws, SA.C0), l, 0.f, Vt, d.k, s));
+          assemble(plan, ws, SA, r, d.k, at<float>(ws, SA.S2T), at<float>(ws, SA.C0), Vt, d.k, 1,
+                   at<float>(ws, SA.S2), r, 1, at<float>(ws, SA.C0), l, s, true));
     return LRAMM_OK;
   };
   // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)
   auto side_b = [&]() -> lramm_status {
     LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2));
     TIMED(plan, LRAMM_K_ASSEMBLE, s2,
-          sgemm(1, 1, r, d.k, l, 1.f, at<float>(ws, SB.S1), r, 0, at<float>(ws, SB.R0), l, 0.f, Wt, d.k, s2));
+          assemble(plan, ws, SB, r, d.k, at<float>(ws, SB.S1T), at<float>(ws, SB.R0), Wt, d.k, 1,
+                   at<float>(ws, SB.S1), r, 1, at<float>(ws, SB.R0), l, s2, true));
     TIMED(plan, LRAMM_K_ASSEMBLE, s2,
-          sgemm(0, 0, d.n, r, l, 1.f, at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, 0.f, Zt, r, s2));
+          assemble(plan, ws, SB, d.n, r, at<float>(ws, SB.C0), at<float>(ws, SB.S2T), Zt, r, 0,
+                   at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, s2, true));
     return LRAMM_OK;
   };
   const lramm_status st_a = side_a();

@@ -115,6 +115,8 @@ struct FinalProb {
   float* S1;    // l x r row-major: U_s[:, :r] (x sigma if s1_sigma)
   float* S2;    // l x r row-major: V_s[:, :r] (x sigma if s2_sigma)
   int s1_sigma, s2_sigma;
+  float* S1T;   // r x l row-major: S1^T (K-major operand of the tensor-core assembly)
+  float* S2T;   // r x l row-major: S2^T
 };
 struct FinalBatch {
   FinalProb p[2];

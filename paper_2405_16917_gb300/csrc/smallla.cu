@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(1024) trsm_rows_kernel(SmallBatch bt, int l) {
 // row-major S1 / S2 rows can be written coalesced (consecutive threads,
 // consecutive output columns p).  Ties are broken by column index.
 constexpr int kFinRows = 32;
+constexpr int kFinMaxL = 576;   // largest l of the SVD form (multiple of 32)
 
 __global__ void __launch_bounds__(256) svd_finalize_kernel(FinalBatch fb, int l, int r) {
   const FinalProb& fp = fb.p[blockIdx.y];
@@ -137,11 +138,30 @@ __global__ void __launch_bounds__(256) svd_finalize_kernel(FinalBatch fb, int l,
   int* pos = reinterpret_cast<int*>(sm + l);        // l
   int* inv = pos + l;                               // r: column holding rank p
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j < l; j += nw) {
-    float s = 0.f;
-    for (int i = lane; i < l; i += 32) s = fmaf(M[(int64_t)j * l + i], M[(int64_t)j * l + i], s);
-    s = warp_sum(s);
-    if (lane == 0) nrm[j] = sqrtf(s);
+  // column norms, four columns per warp at a time with every load of the
+  // four issued before the sums (l <= kFinMaxL): the same per-column
+  // summation order as one column at a time
+  for (int j0 = warp; j0 < l; j0 += 4 * nw) {
+    float v[4][kFinMaxL / 32];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + c * nw;
+#pragma unroll
+      for (int u = 0; u < kFinMaxL / 32; ++u) {
+        const int i = lane + 32 * u;
+        v[c][u] = (j < l && i < l) ? M[(int64_t)j * l + i] : 0.f;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + c * nw;
+      float s = 0.f;
+#pragma unroll
+      for (int u = 0; u < kFinMaxL / 32; ++u)
+        if (lane + 32 * u < l) s = fmaf(v[c][u], v[c][u], s);
+      s = warp_sum(s);
+      if (lane == 0 && j < l) nrm[j] = sqrtf(s);
+    }
   }
   __syncthreads();
   for (int j = tid; j < l; j += blockDim.x) {
@@ -158,14 +178,32 @@ __global__ void __launch_bounds__(256) svd_finalize_kernel(FinalBatch fb, int l,
   if (blockIdx.x == 0)
     for (int p = tid; p < r; p += blockDim.x) fp.sig[p] = nrm[inv[p]];
   const int i0 = blockIdx.x * kFinRows, i1 = min(l, i0 + kFinRows);
-  for (int e = tid; e < (i1 - i0) * r; e += blockDim.x) {
-    const int i = i0 + e / r, p = e - (e / r) * r;
-    const int j = inv[p];
-    const float sj = nrm[j];
-    const float u_scale = fp.s1_sigma ? 1.0f : (sj > 0.f ? 1.0f / sj : 0.f);
-    const float v_scale = fp.s2_sigma ? sj : 1.0f;
-    fp.S1[(int64_t)i * r + p] = M[(int64_t)j * l + i] * u_scale;
-    fp.S2[(int64_t)i * r + p] = V[(int64_t)j * l + i] * v_scale;
+  const int ne = (i1 - i0) * r;
+  // four outputs per thread per step, their loads issued together
+  for (int e0 = tid; e0 < ne; e0 += 4 * blockDim.x) {
+    float mv[4], vv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int i = i0 + e / r, p = e - (e / r) * r;
+      const int j = e < ne ? inv[p] : 0;
+      mv[u] = e < ne ? M[(int64_t)j * l + i] : 0.f;
+      vv[u] = e < ne ? V[(int64_t)j * l + i] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= ne) break;
+      const int i = i0 + e / r, p = e - (e / r) * r;
+      const float sj = nrm[inv[p]];
+      const float u_scale = fp.s1_sigma ? 1.0f : (sj > 0.f ? 1.0f / sj : 0.f);
+      const float v_scale = fp.s2_sigma ? sj : 1.0f;
+      const float o1 = mv[u] * u_scale, o2 = vv[u] * v_scale;
+      fp.S1[(int64_t)i * r + p] = o1;
+      fp.S2[(int64_t)i * r + p] = o2;
+      fp.S1T[(int64_t)p * l + i] = o1;
+      fp.S2T[(int64_t)p * l + i] = o2;
+    }
   }
 }
 
