@@ -8,6 +8,7 @@
 #include <float.h>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace lramm {
 namespace {
@@ -456,6 +457,11 @@ __host__ __device__ inline int chol_split_h_dev(int l) {
   return h < 288 ? h : 288;
 }
 
+// TC: the trailing update runs on the tensor cores (kind::tf32, split into
+// TF32 high and low parts: hi hi + lo hi + hi lo, FP32 accumulation in TMEM)
+// from two 128-byte-swizzled K-major copies of the panel below the diagonal
+// block (256 rows x 32 columns each); otherwise in FP32 SIMT register tiles.
+template <bool TC>
 __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, float shift_rel, int* status) {
   const CholProb& cp = cb.p[blockIdx.x];
   const float* __restrict__ G = cp.G;
@@ -465,11 +471,39 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   float* P = reinterpret_cast<float*>(c3_smem4);
   const int np = l * (l + 1) / 2;
   const int lp = static_cast<int>(round_up(l, 4)) + 4;   // row stride of the transposed panel
-  float* PnT = P + round_up(np, 4);                       // kCB x lp
-  float* LC = PnT + kCB * lp;                             // kCB x kLC: LC[t][c] = L_JJ[c][t], c > t
+  // Row j of the trailing block sits at position ((j & 4) ? H : 0) + 4 (j >> 3) + (j & 3)
+  // of a panel row: the halves of each 8-row group in two regions, so that
+  // both the 4-row and the 8-row tiles of the update read them as float4
+  // runs at a 16-byte stride across threads (no bank conflict).
+  const int H = 4 * ((l + 7) / 8);
+  float* PnT = P + round_up(np, 4);                       // kCB x lp (SIMT update)
+  float* LC = TC ? PnT : PnT + kCB * lp;                  // kCB x kLC: LC[t][c] = L_JJ[c][t], c > t
   __shared__ float s_red[32];
   __shared__ float s_rinv[kCB];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  // TC: panel copies at the first 1024-byte boundary after LC (hi: 32 KB, lo: 32 KB)
+  uint8_t* T_hi = nullptr;
+  uint8_t* T_lo = nullptr;
+  uint32_t mphase = 0;
+  if (TC) {
+    uint8_t* after = reinterpret_cast<uint8_t*>(LC + kCB * kLC);
+    T_hi = after + ((1024u - (tc::smem_u32(after) & 1023u)) & 1023u);
+    T_lo = T_hi + 256 * 128;
+    if (tid == 0) {
+      tc::mbar_init(&s_mbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc::smem_u32(&s_tmem))
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+  }
   float md = 0.f;
   for (int i = tid; i < l; i += blockDim.x) md = fmaxf(md, G[static_cast<int64_t>(i) * l + i]);
   md = warp_max_o(md);
@@ -504,7 +538,8 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
       }
     }
   }
-  for (int e = tid; e < kCB * lp; e += blockDim.x) PnT[e] = 0.f;
+  if (!TC)
+    for (int e = tid; e < kCB * lp; e += blockDim.x) PnT[e] = 0.f;
   __syncthreads();
 
   for (int j0 = 0; j0 < l; j0 += kCB) {
@@ -514,13 +549,16 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
 #pragma unroll
       for (int c = 0; c < kCB; ++c)
         a[c] = lane < w ? (c <= lane ? P[opidx(j0 + lane, j0 + c)] : 0.f) : (c == lane ? 1.f : 0.f);
+      // A non-positive pivot is replaced without a branch and latched once
+      // after the block, so that the unrolled pivots form one straight-line
+      // block: the next pivot's chain (it needs only column k+1, updated
+      // first) overlaps the remaining updates of this one.
+      bool bad = false;
 #pragma unroll
       for (int k = 0; k < kCB; ++k) {
         float piv = __shfl_sync(0xffffffffu, a[k], k);
-        if (!(piv > 0.f)) {
-          if (lane == 0) set_status(status, LRAMM_ERR_NUMERIC);
-          piv = FLT_MIN * 1024.f;
-        }
+        bad |= !(piv > 0.f);
+        piv = piv > 0.f ? piv : FLT_MIN * 1024.f;
         const float inv = rsqrtf(piv);
         const float lk = lane == k ? piv * inv : a[k] * inv;
         a[k] = lk;
@@ -528,6 +566,7 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
 #pragma unroll
         for (int c = k + 1; c < kCB; ++c) a[c] = fmaf(-lk, __shfl_sync(0xffffffffu, lk, c), a[c]);
       }
+      if (bad && lane == 0) set_status(status, LRAMM_ERR_NUMERIC);
 #pragma unroll
       for (int c = 0; c < kCB; ++c) {
         if (lane < w && c <= lane) P[opidx(j0 + lane, j0 + c)] = a[c];
@@ -558,14 +597,124 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
         }
       }
 #pragma unroll
-      for (int t = 0; t < kCB; ++t) {
-        P[opidx(row, j0 + t)] = a[t];
-        PnT[t * lp + tid] = a[t];
+      for (int t = 0; t < kCB; ++t) P[opidx(row, j0 + t)] = a[t];
+      if (TC) {  // row tid of the swizzled copies: 16-byte chunk c at position c ^ (tid mod 8)
+        uint8_t* hr = T_hi + tid * 128;
+        uint8_t* lr = T_lo + tid * 128;
+#pragma unroll
+        for (int c = 0; c < kCB / 4; ++c) {
+          float h[4], o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            h[e] = __uint_as_float(__float_as_uint(a[4 * c + e]) & 0xFFFFE000u);
+            o[e] = a[4 * c + e] - h[e];
+          }
+          const int off = (c ^ (tid & 7)) * 16;
+          *reinterpret_cast<float4*>(hr + off) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(lr + off) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+      } else {
+        const int pos = ((tid & 4) ? H : 0) + 4 * (tid >> 3) + (tid & 3);
+#pragma unroll
+        for (int t = 0; t < kCB; ++t) PnT[t * lp + pos] = a[t];
       }
     }
     __syncthreads();
-    // (c) trailing update, rows/cols r0 .. l-1, lower triangle, 4 x 4 tiles
-    {
+    // (c) trailing update, rows/cols r0 .. l-1, lower triangle
+    if (TC) {
+      // D_t = rows 128 t .. 128 t + 127 of the panel copy times the first N_t
+      // rows (only columns c <= i are needed); TMEM columns 256 t ..
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      const int N = static_cast<int>(round_up(n2, 32));
+      const int tiles = (n2 + 127) / 128;
+      const uint32_t tm = s_tmem;
+      if (tid == 0) {
+        tc::tc_fence_after();
+        for (int t = 0; t < tiles; ++t) {
+          const int Nt = t == 0 ? min(N, 128) : N;
+          const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(Nt >> 3) << 17) |
+                                 (static_cast<uint32_t>(128 >> 4) << 24);
+          const uint32_t ah = tc::smem_u32(T_hi + t * 16384), al = tc::smem_u32(T_lo + t * 16384);
+          const uint32_t bh = tc::smem_u32(T_hi), bl = tc::smem_u32(T_lo);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {   // 8 TF32 (32 bytes) of K per instruction
+            const uint64_t dah = tc::kmajor_sw128_desc(ah + kk * 32), dal = tc::kmajor_sw128_desc(al + kk * 32);
+            const uint64_t dbh = tc::kmajor_sw128_desc(bh + kk * 32), dbl = tc::kmajor_sw128_desc(bl + kk * 32);
+            const uint32_t d = tm + static_cast<uint32_t>(t * 256);
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(dah), "l"(dbh), "r"(idesc), "r"(kk > 0 ? 1u : 0u)
+                : "memory");
+            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dal), "l"(dbh),
+                         "r"(idesc)
+                         : "memory");
+            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dah), "l"(dbl),
+                         "r"(idesc)
+                         : "memory");
+          }
+        }
+        tc::mma_commit(&s_mbar);
+      }
+      volatile int never = 0;
+      if (!tc::mbar_wait(&s_mbar, mphase, &never) && tid == 0) set_status(status, LRAMM_ERR_TIMEOUT);
+      mphase ^= 1u;
+      tc::tc_fence_after();
+      const int q = warp & 3, part = warp >> 2;   // TMEM lanes 32 q .. 32 q + 31; column chunks part, part + 4
+      for (int t = 0; t < tiles; ++t) {
+        const int Nt = t == 0 ? min(N, 128) : N;
+        for (int ch = part; ch < Nt / 32; ch += 4) {
+          float v[32];
+          tc::tmem_ld32(tm + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * 256 + ch * 32), v);
+          const int j = t * 128 + q * 32 + lane;
+          const int i = r0 + j;
+          if (j < n2) {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj) {
+              const int c = r0 + ch * 32 + jj;
+              if (c <= i) P[opidx(i, c)] -= v[jj];
+            }
+          }
+        }
+      }
+      tc::tc_fence_before();
+    } else if (n2 >= 96) {  // 8 x 8 tiles
+      const int nb8 = (n2 + 7) / 8;
+      const int ntile = nb8 * (nb8 + 1) / 2;
+      for (int t = tid; t < ntile; t += blockDim.x) {
+        int bi = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+        while (bi * (bi + 1) / 2 > t) --bi;
+        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+        const int bc = t - bi * (bi + 1) / 2;
+        float acc[8][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < kCB; ++k) {
+          const float* row = PnT + k * lp;
+          const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * bi);
+          const float4 a1 = *reinterpret_cast<const float4*>(row + H + 4 * bi);
+          const float4 b0 = *reinterpret_cast<const float4*>(row + 4 * bc);
+          const float4 b1 = *reinterpret_cast<const float4*>(row + H + 4 * bc);
+          const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+          const float b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a8[u], b8[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+          for (int v = 0; v < 8; ++v) {
+            const int i = r0 + 8 * bi + u, c = r0 + 8 * bc + v;
+            if (i < l && c <= i) P[opidx(i, c)] -= acc[u][v];
+          }
+      }
+    } else {  // 4 x 4 tiles
       const int nb4 = (n2 + 3) / 4;
       const int ntile = nb4 * (nb4 + 1) / 2;
       for (int t = tid; t < ntile; t += blockDim.x) {
@@ -580,8 +729,8 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
           for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
 #pragma unroll 8
         for (int k = 0; k < kCB; ++k) {
-          const float4 av = *reinterpret_cast<const float4*>(PnT + k * lp + 4 * bi);
-          const float4 bv = *reinterpret_cast<const float4*>(PnT + k * lp + 4 * bc);
+          const float4 av = *reinterpret_cast<const float4*>(PnT + k * lp + ((bi & 1) ? H : 0) + 4 * (bi >> 1));
+          const float4 bv = *reinterpret_cast<const float4*>(PnT + k * lp + ((bc & 1) ? H : 0) + 4 * (bc >> 1));
           const float a4[4] = {av.x, av.y, av.z, av.w};
           const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
 #pragma unroll
@@ -601,6 +750,10 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
     __syncthreads();
   }
   __syncthreads();
+  if (TC && warp == 1) {
+    tc::tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(s_tmem) : "memory");
+  }
   {
     const int nq = l * l / 4, lq4 = l / 4;
     float4* L4 = reinterpret_cast<float4*>(Lo);
@@ -846,13 +999,28 @@ size_t chol3_smem(int l) {
   return sizeof(float) * (round_up(np, 4) + kCB * lp + kCB * kLC);
 }
 
+// The tensor-core variant: no transposed panel, two 32 KB swizzled panel
+// copies at a 1024-byte boundary.
+size_t chol3_tc_smem(int l) {
+  const size_t np = static_cast<size_t>(l) * (l + 1) / 2;
+  return sizeof(float) * (round_up(np, 4) + kCB * kLC) + 1024 + 2 * 256 * 128;
+}
+
 bool chol3_supported(int l) { return l >= 4 && l % 4 == 0 && l - kCB <= 256 && chol3_smem(l) <= static_cast<size_t>(kSmemMaxO); }
 
 lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s) {
   if (!chol3_supported(l)) return LRAMM_ERR_UNSUPPORTED;
+  if (chol3_tc_smem(l) <= static_cast<size_t>(kSmemMaxO)) {
+    const size_t smem = chol3_tc_smem(l);
+    LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(smem)));
+    chol3_kernel<true><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, status);
+    return last_launch();
+  }
   const size_t smem = chol3_smem(l);
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  chol3_kernel<<<cb.n, 512, smem, s>>>(cb, l, shift_rel, status);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(smem)));
+  chol3_kernel<false><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, status);
   return last_launch();
 }
 
