@@ -549,22 +549,27 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
 #pragma unroll
       for (int c = 0; c < kCB; ++c)
         a[c] = lane < w ? (c <= lane ? P[opidx(j0 + lane, j0 + c)] : 0.f) : (c == lane ? 1.f : 0.f);
-      // A non-positive pivot is replaced without a branch and latched once
-      // after the block, so that the unrolled pivots form one straight-line
-      // block: the next pivot's chain (it needs only column k+1, updated
-      // first) overlaps the remaining updates of this one.
+      // The pivot chain is software-pipelined: lane k+1 forms its own next
+      // diagonal entry from its own multiplier (the value the shuffled update
+      // below gives it, bit for bit), and that entry is broadcast before the
+      // remaining updates of this pivot issue.  A non-positive pivot is
+      // replaced without a branch and latched once after the block, so the
+      // unrolled pivots form straight-line code.
       bool bad = false;
+      float piv = __shfl_sync(0xffffffffu, a[0], 0);
 #pragma unroll
       for (int k = 0; k < kCB; ++k) {
-        float piv = __shfl_sync(0xffffffffu, a[k], k);
         bad |= !(piv > 0.f);
         piv = piv > 0.f ? piv : FLT_MIN * 1024.f;
         const float inv = rsqrtf(piv);
         const float lk = lane == k ? piv * inv : a[k] * inv;
         a[k] = lk;
         if (lane == k) s_rinv[k] = inv;
+        float piv_next = 0.f;
+        if (k + 1 < kCB) piv_next = __shfl_sync(0xffffffffu, fmaf(-lk, lk, a[k + 1]), k + 1);
 #pragma unroll
         for (int c = k + 1; c < kCB; ++c) a[c] = fmaf(-lk, __shfl_sync(0xffffffffu, lk, c), a[c]);
+        piv = piv_next;
       }
       if (bad && lane == 0) set_status(status, LRAMM_ERR_NUMERIC);
 #pragma unroll
