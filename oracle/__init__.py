@@ -16,5 +16,6 @@ Modules:
              residuals and the lead / tail E3 of the mixed 4/8-bit chain
   qsvd    -- the quantised SVD approximation of one matrix (Algorithm 4)
   sketch8 -- the range finder with its products on e4m3 codes
+  tune    -- the probe error estimate and the selection rule of parameter tuning
 """
-from . import philox, quant, lramm, rf, mixed, qsvd, sketch8  # noqa: F401
+from . import philox, quant, lramm, rf, mixed, qsvd, sketch8, tune  # noqa: F401

@@ -771,3 +771,35 @@ def pin_rf_e4m3_accuracy(s8, lr, wl):
             e8 = np.linalg.norm(A - (U * s) @ V.T)
             e0 = np.linalg.norm(A - (U0 * s0) @ V0.T)
             assert floor * (1 - 1e-9) <= e8 <= 1.01 * e0, (m, q, e8, e0, floor)
+
+
+# --------------------------------------------------------------------------
+# Parameter tuning (Sec. 3.5): probe error estimate and selection
+# --------------------------------------------------------------------------
+def pin_probe_error(tn, seed=81):
+    """E ||X G||_F^2 = s ||X||_F^2: with many probe columns the estimate
+    converges to the exact relative Frobenius error (within 3%), with one
+    probe it is a single draw of it; D = A B gives 0 (to rounding)."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((60, 40))
+    B = rng.standard_normal((40, 50))
+    D = A @ B + 0.05 * rng.standard_normal((60, 50)) * np.abs(A @ B).mean()
+    exact = np.linalg.norm(A @ B - D) / np.linalg.norm(A @ B)
+    G = rng.standard_normal((50, 4000))
+    est = tn.probe_error(A, B, D, G)
+    assert abs(est - exact) <= 0.03 * exact, (est, exact)
+    assert tn.probe_error(A, B, A @ B, G[:, :8]) < 1e-14
+    # the estimate is invariant to the scale of the probes
+    assert np.isclose(tn.probe_error(A, B, D, 3.0 * G[:, :16]), tn.probe_error(A, B, D, G[:, :16]), rtol=1e-12)
+
+
+def pin_select(tn):
+    """The selection rule on hand-made tables."""
+    c = [dict(name="a", err=0.05, ms=2.5), dict(name="b", err=0.02, ms=4.0), dict(name="c", err=0.2, ms=1.0),
+         dict(name="d", err=0.02, ms=3.0)]
+    assert tn.select(c, 0.1)["name"] == "a"          # fastest within the target
+    assert tn.select(c, 0.03)["name"] == "d"         # b and d qualify: the faster
+    assert tn.select(c, 0.5)["name"] == "c"
+    assert tn.select(c, 0.001)["name"] == "b"        # none qualifies: the most accurate (first of the ties)
+    c2 = [dict(name="x", err=0.01, ms=2.0), dict(name="y", err=0.005, ms=2.0)]
+    assert tn.select(c2, 0.02)["name"] == "y"        # equal times: the more accurate

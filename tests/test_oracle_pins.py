@@ -159,3 +159,12 @@ def test_rf_e4m3_product():
 
 def test_rf_e4m3_accuracy():
     pins.pin_rf_e4m3_accuracy(oracle.sketch8, oracle.lramm, workloads)
+
+
+# Parameter tuning
+def test_probe_error():
+    pins.pin_probe_error(oracle.tune)
+
+
+def test_select():
+    pins.pin_select(oracle.tune)
