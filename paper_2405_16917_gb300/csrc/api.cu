@@ -38,10 +38,11 @@ int svd_max_l() {
   return v;
 }
 constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of every CholeskyQR pass
+constexpr int64_t kGramTcRows = 2048;          // sketches from this many rows take the tensor-core Gram
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, S1T, S2T, CS, GS;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, S1T, S2T, CS;
   size_t part, gpart, gtpart, bsplit;   // this operand's split-K partials and BF16 parts (own stream)
   // E4M3 range finder: codes of X per row (rows x cols_p) and per column
   // (cols x rows_p), of the l-column operand (l x max(rows_p, cols_p)), their
@@ -155,9 +156,6 @@ void layout(lramm_plan_s* P) {
     S.L2 = b.take(sizeof(float) * l * l);
     S.Xd = b.take(sizeof(float) * ceil_div(l, 32) * 32 * 32);
     S.CS = chol_split_supported((int)l) ? b.take(sizeof(float) * chol_split_scratch_floats((int)l)) : 0;
-    S.GS = (d.sketch != LRAMM_SKETCH_F32 && gram_tc_supported((int)l))
-               ? b.take(sizeof(float) * gram_tc_scratch_floats(std::max(S.rows, S.cols), (int)l))
-               : 0;
     S.R = b.take(sizeof(float) * l * l);
     S.Vj = b.take(sizeof(float) * l * l);
     S.sig = b.take(sizeof(float) * l);
@@ -397,22 +395,22 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
       cb3.p[i] = CholProb{G, Lf, Xd};
       tb3.p[i] = TrsmProb{in[i], out[i], Lf, Xd, rows[i]};
     }
-    // Grams of tall sketches (>= 16384 rows) in split TF32 on the tensor cores
-    // when the products already run in TF32; the rest on the SIMT kernel
+    // Grams of tall sketches (>= kGramTcRows rows) in split TF32 on the
+    // tensor cores when the products already run on them; the rest on the
+    // SIMT kernel
     bool tc[2] = {false, false};
     GramBatch gs{};
     for (int i = 0; i < ns; ++i) {
-      tc[i] = sd[i].S->gtpart && rows[i] >= 16384;
+      tc[i] = sd[i].S->gtpart && rows[i] >= kGramTcRows;
       if (!tc[i]) gs.p[gs.n++] = gb.p[i];
     }
     for (int i = 0; i < ns; ++i)
       if (tc[i]) {
         const float* Yi[1] = {in[i]};
         float* Gi[1] = {at<float>(ws, sd[i].S->G)};
-        float* scr[1] = {at<float>(ws, sd[i].S->GS)};
         lramm_status gst = LRAMM_OK;
         TIMED(P, LRAMM_K_GRAM, s,
-              (gst = gram_tc(1, Yi, &rows[i], Gi, l, scr, at<float>(ws, sd[i].S->gtpart), gram_tc_part_floats(l), st,
+              (gst = gram_tc(1, Yi, &rows[i], Gi, l, at<float>(ws, sd[i].S->gtpart), gram_tc_part_floats(l), st,
                              s)) ==
                       LRAMM_ERR_UNSUPPORTED
                   ? [&] {

@@ -208,12 +208,11 @@ size_t sketch_tc_part_floats(int l);
 bool sketch_bf_supported(int64_t ldx, int l, const void* X, const void* B);
 size_t sketch_bf_split_bytes(int64_t K, int l);
 // Gram G = Y^T Y on the tensor cores in split TF32 (~2^-21 relative), one
-// or two problems; scratch: gram_tc_scratch_floats(rows, l) per problem.
+// or two problems (Y rows x l, stride l, l % 4 == 0).
 bool gram_tc_supported(int l);
-size_t gram_tc_scratch_floats(int64_t rows, int l);
 size_t gram_tc_part_floats(int l);
-lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* const* scratch,
-                     float* part, size_t part_floats, int* status, cudaStream_t s);
+lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* part,
+                     size_t part_floats, int* status, cudaStream_t s);
 lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, const float* B, int l,
                        int nb, float* out, float* part, size_t part_floats, void* split, size_t split_bytes,
                        int* status, cudaStream_t s);

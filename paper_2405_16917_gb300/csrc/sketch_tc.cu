@@ -416,6 +416,9 @@ __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l,
 // and the TF32 rounding of Y_lo are ~2^-21 relative).  Both operands are
 // MN-major views of the same staged K x W tiles (W = l rounded up to 128):
 // the A operand of output row block mt is the tile's columns 128 mt ...
+// TMA brings the FP32 tile of Y; warps 2..5 split it in shared memory into
+// the high part (in place) and the low part (a second buffer of the same
+// layout) before the MMAs of that stage, so Y is read once from memory.
 // One CTA per (row block of G, K range), one launch per problem; split-K
 // partials are added by split_reduce_kernel.
 struct GramTcParams {
@@ -430,10 +433,10 @@ struct GramTcParams {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmL, GramTcParams p) {
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __shared__ __align__(8) uint64_t full_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   volatile int* abort_flag = &abort_sh;
@@ -449,6 +452,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(&full_bar[s], 1);
+      mbar_init(&split_bar[s], 128);
       mbar_init(&empty_bar[s], 1);
     }
     mbar_init(&tmem_bar, 1);
@@ -475,13 +479,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ 
         ok = false;
         break;
       }
-      mbar_expect_tx(&full_bar[s], stage_bytes);
+      mbar_expect_tx(&full_bar[s], p.part_bytes);
       const int k0 = static_cast<int>((kb0 + i) * kBK);
       uint8_t* dst = smem + static_cast<size_t>(s) * stage_bytes;
-      for (int j = 0; j < natoms; ++j) {
-        tma_load_2d(dst + j * (kAtom * kBK * 4), &tmH, &full_bar[s], j * kAtom, k0);
-        tma_load_2d(dst + p.part_bytes + j * (kAtom * kBK * 4), &tmL, &full_bar[s], j * kAtom, k0);
-      }
+      for (int j = 0; j < natoms; ++j) tma_load_2d(dst + j * (kAtom * kBK * 4), &tmY, &full_bar[s], j * kAtom, k0);
       ++issued;
     }
     if (!ok) {
@@ -500,7 +501,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ 
     const uint32_t aoff = static_cast<uint32_t>(mt * (kBM / kAtom)) * (kAtom * kBK * 4);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
-      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+      if (!mbar_wait(&split_bar[s], (i / p.stages) & 1, abort_flag)) {
         set_status(p.status, LRAMM_ERR_TIMEOUT);
         abort_sh = 1;
         break;
@@ -526,6 +527,31 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ 
     }
     mma_commit(&tmem_bar);
   } else if (warp >= 2) {
+    // split each landed stage: high part in place, low part beside it
+    const int st = threadIdx.x - 64;   // 0 .. 127
+    const int nq = static_cast<int>(p.part_bytes / 16);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      float4* h4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes);
+      float4* l4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes + p.part_bytes);
+      for (int e = st; e < nq; e += 128) {
+        const float4 y = h4[e];
+        float4 h;
+        h.x = __uint_as_float(__float_as_uint(y.x) & 0xFFFFE000u);
+        h.y = __uint_as_float(__float_as_uint(y.y) & 0xFFFFE000u);
+        h.z = __uint_as_float(__float_as_uint(y.z) & 0xFFFFE000u);
+        h.w = __uint_as_float(__float_as_uint(y.w) & 0xFFFFE000u);
+        h4[e] = h;
+        l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split_bar[s])) : "memory");
+    }
     const int q = warp & 3;
     volatile int zero = 0;
     const bool ok = mbar_wait(&tmem_bar, 0, &zero);
@@ -550,23 +576,6 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ 
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
-  }
-}
-
-// Y (rows x l) -> Y_hi, Y_lo (rows x W, zero beyond l; W = l rounded up to
-// 32): Y_hi keeps the top
-// 19 bits of each FP32 word (sign, exponent, 10 mantissa bits), Y_lo = Y - Y_hi.
-__global__ void split_tf32_kernel(const float* __restrict__ Y, int64_t rows, int l, int W, float* __restrict__ hi,
-                                  float* __restrict__ lo) {
-  const int64_t n = rows * W;
-  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
-       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t r = e / W;
-    const int j = static_cast<int>(e - r * W);
-    const float y = j < l ? Y[r * l + j] : 0.f;
-    const float h = __uint_as_float(__float_as_uint(y) & 0xFFFFE000u);
-    hi[e] = h;
-    lo[e] = y - h;
   }
 }
 
@@ -752,16 +761,12 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
 
 // Gram on the tensor cores (split TF32) for one or two problems.
 static int gram_tc_width(int l) { return static_cast<int>(round_up(l, kBM)); }   // staged tile width
-static int gram_tc_ld(int l) { return static_cast<int>(round_up(l, kAtom)); }     // Y_hi / Y_lo row length
-
-size_t gram_tc_scratch_floats(int64_t rows, int l) { return 2 * static_cast<size_t>(rows) * gram_tc_ld(l) + 64; }
-
 size_t gram_tc_part_floats(int l) { return static_cast<size_t>(152) * l * l; }
 
 bool gram_tc_supported(int l) { return l >= 4 && l % 4 == 0 && l <= 512; }
 
-lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* const* scratch,
-                     float* part, size_t part_floats, int* status, cudaStream_t s) {
+lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* part,
+                     size_t part_floats, int* status, cudaStream_t s) {
   if (!gram_tc_supported(l) || n < 1 || n > 2) return LRAMM_ERR_UNSUPPORTED;
   GramTcParams p{};
   p.l = l;
@@ -784,30 +789,21 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     p.rows = rows[i];
     p.kblocks = ceil_div(rows[i], kBK);
     int64_t splits = 152 / mtiles;
-    if (splits > p.kblocks / 8) splits = p.kblocks / 8;
+    if (splits > p.kblocks / 2) splits = p.kblocks / 2;   // at least two K blocks per CTA
     if (splits < 1) splits = 1;
     while (splits > 1 && static_cast<size_t>(splits) * l * l > part_floats) --splits;
     p.kb_per_split = static_cast<int>(ceil_div(p.kblocks, splits));
     splits = ceil_div(p.kblocks, p.kb_per_split);   // every CTA has at least one K block
     p.splits = static_cast<int>(splits);
     p.out = splits > 1 ? part : G[i];
-    // Y_hi / Y_lo rows of ld = l rounded to 32; the tile atoms beyond ld are
-    // loaded out of range (x a multiple of 32) and arrive as zeros
-    const int ld = gram_tc_ld(l);
-    float* hi = scratch[i];
-    float* lo = hi + static_cast<size_t>(rows[i]) * ld;
-    int64_t g = ceil_div(rows[i] * ld, 256);
-    if (g > 152 * 8) g = 152 * 8;
-    split_tf32_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(Y[i], rows[i], l, ld, hi, lo);
-    LRAMM_TRY(last_launch());
-    CUtensorMap mh, ml;
-    if (!make_map_f32(&mh, hi, ld, rows[i], static_cast<uint64_t>(ld) * 4, kAtom, kBK,
-                      CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B) ||
-        !make_map_f32(&ml, lo, ld, rows[i], static_cast<uint64_t>(ld) * 4, kAtom, kBK,
+    // the FP32 rows of Y (l % 4 == 0: 16-byte row pitch); tile atoms beyond
+    // l and rows beyond the end are loaded out of range (x a multiple of 32)
+    // and arrive as zeros
+    CUtensorMap my;
+    if (!make_map_f32(&my, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, kAtom, kBK,
                       CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
       return LRAMM_ERR_CUDA;
-    gram_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(mh, ml,
-                                                                                                              p);
+    gram_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, p);
     LRAMM_TRY(last_launch());
     if (splits > 1) {
       const int64_t n4 = static_cast<int64_t>(l) * l / 4;
