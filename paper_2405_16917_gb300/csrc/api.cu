@@ -38,6 +38,16 @@ int svd_max_l() {
   return v;
 }
 constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of every CholeskyQR pass
+// Jacobi stopping multipliers (of tol = 4 sqrt(l) u): a sweep whose largest
+// relative inner product rho is below the multiplier times tol is the last.
+// 20: the converged SVD the rank-r factors of lramm_rsvd / lramm_qsvd and the
+// FP32 chains use (the next sweep would rotate nothing).  1000 (rho below
+// 3.9e-3 at l = 272): the factors of a quantised E3 inside lramm_matmul --
+// the inner products left after such a sweep are about 10 rho^2 <= 1.5e-4,
+// which moves the rank-r product U~ V^T by about 1e-7 relative, far below
+// the quantisation noise of the chain.
+constexpr float kJacobiQuad = 20.0f;
+constexpr float kJacobiQuadQuantised = 1000.0f;
 constexpr int64_t kGramTcRows = 2048;          // sketches from this many rows take the tensor-core Gram
 
 struct SideLayout {
@@ -474,7 +484,7 @@ lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M,
 // C0 = P (cols x l), sig[:r], S1 = U_s[:, :r] (x sigma if s1_sigma[i]),
 // S2 = V_s[:, :r] (x sigma if s2_sigma[i]), with X ~ Q U_s diag(sig) V_s^T P^T.
 lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, int ns, void* ws,
-                        const int* s1_sigma, const int* s2_sigma, cudaStream_t s) {
+                        const int* s1_sigma, const int* s2_sigma, cudaStream_t s, float stopq = kJacobiQuad) {
   const lramm_desc& d = P->d;
   const int l = P->l;
   const bool fp8 = d.sketch == LRAMM_SKETCH_E4M3;   // range-finder passes on e4m3 codes
@@ -514,6 +524,7 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
   FinalBatch fb{};
   jb.n = fb.n = ns;
   jb.info0 = ns == 1 ? which[0] : 0;
+  jb.stopq = stopq;
   for (int i = 0; i < ns; ++i) {
     const SideLayout& S = *sd[i].S;
     jb.M[i] = at<float>(ws, S.R);
@@ -1068,6 +1079,7 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   const SideLayout& SB = plan->side[1];
   const SideRun sd[2] = {side_run(plan, 0, A), side_run(plan, 1, B)};
   const int which[2] = {0, 1}, s1s[2] = {1, 0}, s2s[2] = {0, 1};
+  const float stopq = (d.prec[2] != LRAMM_P_F32 && d.lead == 0) ? kJacobiQuadQuantised : kJacobiQuad;
   // The two operands' RSVDs are independent: A on the caller's stream, B on
   // the plan's second stream, so that one operand's latency-bound small
   // algebra (a few CTAs) runs beside the other's HBM-bound products.
@@ -1076,7 +1088,7 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   LRAMM_CUDA_TRY(cudaEventRecord(plan->ev_fork, s));
   LRAMM_CUDA_TRY(cudaStreamWaitEvent(s2, plan->ev_fork, 0));
   auto side_a = [&]() -> lramm_status {
-    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s));
+    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s, stopq));
     TIMED(plan, LRAMM_K_ASSEMBLE, s,
           assemble(plan, ws, SA, d.m, r, at<float>(ws, SA.R0), at<float>(ws, SA.S1T), Ut, r, 0,
                    at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, s, true));
@@ -1087,7 +1099,7 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   };
   // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)
   auto side_b = [&]() -> lramm_status {
-    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2));
+    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2, stopq));
     TIMED(plan, LRAMM_K_ASSEMBLE, s2,
           assemble(plan, ws, SB, r, d.k, at<float>(ws, SB.S1T), at<float>(ws, SB.R0), Wt, d.k, 1,
                    at<float>(ws, SB.S1), r, 1, at<float>(ws, SB.R0), l, s2, true));

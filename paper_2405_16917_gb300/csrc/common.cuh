@@ -107,6 +107,7 @@ struct JacobiBatch {
   float* V[2];  // l x l column-major: out the accumulated rotations V_s
   int n;
   int info0;    // sweep counts go to status[1 + info0 + problem]
+  float stopq;  // the cluster Jacobi stops after a sweep whose largest relative inner product is <= stopq * tol
 };
 struct FinalProb {
   const float* M;

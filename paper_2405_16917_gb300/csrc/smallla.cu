@@ -428,8 +428,8 @@ __device__ __forceinline__ void group_bar(int id) {
 }
 
 // Stopping rule of the cluster Jacobi: a sweep whose largest relative inner
-// product stays below kJacobiQuad * tol is the last one.
-constexpr float kJacobiQuad = 20.0f;
+// product stays below jb.stopq * tol is the last one (callers pass
+// kJacobiQuad = 20 for a converged SVD).
 
 template <int RP, int GW>
 __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], float (&ym)[RP], float (&yv)[RP],
@@ -750,7 +750,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
     }
     // Convergence: the largest relative inner product |a.b| / (|a| |b|) met in
     // the sweep, over the cluster (one cluster barrier).  Below tol nothing
-    // was rotated; below kJacobiQuad tol the rotations of this sweep leave
+    // was rotated; below stopq tol the rotations of this sweep leave
     // inner products of the order of its square (quadratic convergence), so
     // a further sweep would rotate nothing: stop after this one.
     if (lane == 0) atomicMax(&s_rmax, __float_as_int(rmax));
@@ -759,7 +759,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
     cluster.sync();
     int mx = 0;
     for (int c = 0; c < C; ++c) mx = max(mx, s_flags[c]);
-    if (!(__int_as_float(mx) > kJacobiQuad * tol)) break;
+    if (!(__int_as_float(mx) > jb.stopq * tol)) break;
   }
   if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
   if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
