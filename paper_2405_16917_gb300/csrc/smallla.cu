@@ -239,9 +239,10 @@ __device__ __forceinline__ void jc_bufs(int rank, int e, int& t, int& bo, int& f
 }
 
 // Rotate columns (a, b) (M part at the pointer, V part ls floats further)
-// so that their inner product vanishes; one warp.  Returns whether it did.
+// so that their inner product vanishes; one warp.  Returns whether it did;
+// rmax takes the largest relative inner product |a.b| / (|a| |b|) met.
 __device__ __forceinline__ bool jc_rotate(float* __restrict__ a, float* __restrict__ b, int l, int ls,
-                                          float tol, int lane) {
+                                          float tol, int lane, float& rmax) {
   float al = 0.f, be = 0.f, ga = 0.f;
   for (int i = lane; i < l; i += 32) {
     const float x = a[i], y = b[i];
@@ -252,7 +253,9 @@ __device__ __forceinline__ bool jc_rotate(float* __restrict__ a, float* __restri
   al = warp_sum(al);
   be = warp_sum(be);
   ga = warp_sum(ga);
-  if (!(fabsf(ga) > tol * sqrtf(al) * sqrtf(be))) return false;
+  const float nab = sqrtf(al) * sqrtf(be);
+  if (nab > 0.f && fabsf(ga) / nab > rmax) rmax = fabsf(ga) / nab;
+  if (!(fabsf(ga) > tol * nab)) return false;
   const float zeta = (be - al) / (2.0f * ga);
   const float tt = fabsf(zeta) > 1e18f ? 0.5f / zeta
                                        : copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
@@ -291,6 +294,7 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
   __shared__ int s_flags[16];
   __shared__ int s_ids[32];
   __shared__ int s_rot;
+  __shared__ int s_rmax;   // bits of the sweep's largest relative inner product (non-negative)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const int nslots = 2 * C;
 
@@ -313,7 +317,11 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
   int e = 0;  // block moves so far
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
+    if (tid == 0) {
+      s_rot = 0;
+      s_rmax = 0;
+    }
+    float rmax = 0.f;
     __syncthreads();
     for (int br = 0; br < 2 * C - 1; ++br) {
       int bt_, bb_, bf_;
@@ -335,7 +343,8 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
               y = 1 + (t - k + (be - 1)) % (be - 1);
             }
             if (x >= b || y >= b) continue;
-            if (jc_rotate(base + (int64_t)x * 2 * ls, base + (int64_t)y * 2 * ls, l, ls, tol, lane) && lane == 0)
+            if (jc_rotate(base + (int64_t)x * 2 * ls, base + (int64_t)y * 2 * ls, l, ls, tol, lane, rmax) &&
+                lane == 0)
               s_rot = 1;
           }
           __syncthreads();
@@ -344,7 +353,8 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
       for (int j = 0; j < b; ++j) {  // top column i against bottom column (i + j) mod b
         for (int i = warp; i < b; i += nw) {
           const int k = (i + j) % b;
-          if (jc_rotate(topb + (int64_t)i * 2 * ls, botb + (int64_t)k * 2 * ls, l, ls, tol, lane) && lane == 0)
+          if (jc_rotate(topb + (int64_t)i * 2 * ls, botb + (int64_t)k * 2 * ls, l, ls, tol, lane, rmax) &&
+              lane == 0)
             s_rot = 1;
         }
         __syncthreads();
@@ -383,14 +393,21 @@ jacobi_cluster_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, floa
         ++e;
       }
     }
-    // did any CTA of the cluster rotate in this sweep?
+    // did any CTA of the cluster rotate in this sweep, and how far from
+    // orthogonal was the worst pair?  Stop after a sweep without rotations
+    // or one whose largest relative inner product is below stopq tol (the
+    // next sweep would leave inner products of the order of its square).
+    if (lane == 0) atomicMax(&s_rmax, __float_as_int(rmax));
     __syncthreads();
-    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rot;
+    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rot ? s_rmax : -1;
     cluster.sync();
-    int any = 0;
-    for (int c = 0; c < C; ++c) any |= s_flags[c];
+    int any = 0, mx = 0;
+    for (int c = 0; c < C; ++c) {
+      any |= s_flags[c] >= 0;
+      mx = max(mx, s_flags[c]);
+    }
     cluster.sync();
-    if (!any) break;
+    if (!any || !(__int_as_float(mx) > jb.stopq * tol)) break;
   }
   if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
   if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;  // diagnostics
