@@ -252,6 +252,18 @@ def run_reference(args):
         what = "oracle range-finder forward + backward"
     else:
         A, B, c = cpu_sample(args.workload)
+        # one untimed probe step sizes the sample: the whole run (warm-up +
+        # timed steps) is kept to about two minutes of host work by halving
+        # every size of the stand-in while a step would take longer
+        budget = 120.0 / max(1, args.steps + args.warmup)
+        t_probe = cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))
+        while t_probe > budget and min(c["m"], c["n"], c["k"]) > 512:
+            sc = tuple(max(256, x // 2) for x in (c["m"], c["n"], c["k"]))
+            c["r"], c["p"] = max(16, c["r"] // 2), max(4, c["p"] // 2)
+            A, B = workloads.operands(args.workload, scale=sc)
+            A, B = A.astype(np.float32), B.astype(np.float32)
+            c["m"], c["n"], c["k"] = sc
+            t_probe = cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))
         flops = 2.0 * c["m"] * c["n"] * c["k"]
         step = lambda: cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))  # noqa: E731
         what = "oracle LRAMM"
