@@ -533,8 +533,11 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
                         at<float>(ws, S.S1),  at<float>(ws, S.S2),  s1_sigma[i],
                         s2_sigma[i],          at<float>(ws, S.S1T), at<float>(ws, S.S2T)};
   }
-  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s));
-  TIMED(P, LRAMM_K_SVDSORT, s, launch_svd_finalize(fb, l, d.r, s));
+  jb.r = d.r;
+  for (int i = 0; i < ns; ++i) jb.fin[i] = fb.p[i];
+  bool finalized = false;
+  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s, &finalized));
+  if (!finalized) TIMED(P, LRAMM_K_SVDSORT, s, launch_svd_finalize(fb, l, d.r, s));
   return LRAMM_OK;
 }
 

@@ -102,13 +102,6 @@ struct SmallBatch {
   SmallProb p[2];
   int n;
 };
-struct JacobiBatch {
-  float* M[2];  // l x l column-major: in R^T, out U_s Sigma (unsorted columns)
-  float* V[2];  // l x l column-major: out the accumulated rotations V_s
-  int n;
-  int info0;    // sweep counts go to status[1 + info0 + problem]
-  float stopq;  // the cluster Jacobi stops after a sweep whose largest relative inner product is <= stopq * tol
-};
 struct FinalProb {
   const float* M;
   const float* V;
@@ -119,6 +112,17 @@ struct FinalProb {
   float* S1T;   // r x l row-major: S1^T (K-major operand of the tensor-core assembly)
   float* S2T;   // r x l row-major: S2^T
 };
+struct JacobiBatch {
+  float* M[2];  // l x l column-major: in R^T, out U_s Sigma (unsorted columns)
+  float* V[2];  // l x l column-major: out the accumulated rotations V_s
+  int n;
+  int info0;    // sweep counts go to status[1 + info0 + problem]
+  float stopq;  // the cluster Jacobi stops after a sweep whose largest relative inner product is <= stopq * tol
+  // r > 0: the sorted rank-r outputs of fin[] (as svd_finalize writes them)
+  // are produced by the Jacobi kernel itself where it can (l <= 320)
+  int r;
+  FinalProb fin[2];
+};
 struct FinalBatch {
   FinalProb p[2];
   int n;
@@ -128,7 +132,8 @@ lramm_status launch_chol(SmallBatch bt, int l, float shift_rel, int* status, cud
 // Q = Y L^-T.
 lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s);
 // One-sided Jacobi SVD of each M (thread-block cluster per problem).
-lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s);
+// *finalized: whether the launch also wrote the sorted rank-r outputs (jb.r > 0).
+lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool* finalized);
 // Sort by descending sigma and write the rank-r pieces.
 lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s);
 // orth.cu -- CholeskyQR building blocks, batched over up to two problems.

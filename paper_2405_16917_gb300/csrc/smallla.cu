@@ -537,6 +537,8 @@ __device__ __forceinline__ void jc2_store(float* __restrict__ col, int ls, int p
   }
 }
 
+constexpr int kJ2MaxL = 320;   // largest l of the pair kernel (16 CTAs x 2 blocks x 10 columns)
+
 // Physical buffers of cluster rank `rank` after e moves, four per CTA:
 // top T, bottom B and the landing buffers FL / FR that blocks pushed by the
 // left / right neighbour arrive in (-1: none).  A landing buffer is always
@@ -629,6 +631,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   __shared__ int s_ids[32];
   __shared__ int s_rmax;   // bits of the sweep's largest relative inner product (non-negative)
   __shared__ __align__(8) uint64_t rx_bar[2];   // incoming blocks of even / odd moves
+  __shared__ float s_nrm[kJ2MaxL];               // column norms of the whole problem (rank-r outputs)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = warp / GW, wig = warp % GW, p = tid & (32 * GW - 1);
   const int nslots = 2 * C;
@@ -785,6 +788,57 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   cluster.sync();
   int bt_, bb_, bfl, bfr;
   jc5_bufs(rank, C, e, bt_, bb_, bfl, bfr);
+  if (jb.r > 0) {
+    // The sorted rank-r outputs straight from shared memory, as
+    // svd_finalize_kernel forms them: column norms (same summation order),
+    // shared with every CTA of the cluster, rank by descending norm (ties by
+    // column index), the first r columns scaled and written.
+    const FinalProb& fp = jb.fin[prob];
+    const int r = jb.r;
+    for (int hf = 0; hf < 2; ++hf) {
+      const float* buf = sm + (hf == 0 ? bt_ : bb_) * bufsz;
+      const int blk = s_ids[2 * rank + hf];
+      for (int j = warp; j < b; j += (int)(blockDim.x >> 5)) {
+        const int g = blk * b + j;
+        const float* col = buf + (int64_t)j * cs;
+        float sacc = 0.f;
+        for (int i = lane; i < l; i += 32) sacc = fmaf(col[i], col[i], sacc);
+        sacc = warp_sum(sacc);
+        if (g < l && lane < C) *cluster.map_shared_rank(&s_nrm[g], lane) = sqrtf(sacc);
+      }
+    }
+    cluster.sync();
+    for (int hf = 0; hf < 2; ++hf) {
+      const float* buf = sm + (hf == 0 ? bt_ : bb_) * bufsz;
+      const int blk = s_ids[2 * rank + hf];
+      for (int j = warp; j < b; j += (int)(blockDim.x >> 5)) {
+        const int g = blk * b + j;
+        if (g >= l) continue;
+        const float v = s_nrm[g];
+        int cnt = 0;
+        for (int i = lane; i < l; i += 32) {
+          const float u = s_nrm[i];
+          cnt += (u > v) || (u == v && i < g);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        const int p = cnt;
+        if (p >= r) continue;
+        if (lane == 0) fp.sig[p] = v;
+        const float u_scale = fp.s1_sigma ? 1.0f : (v > 0.f ? 1.0f / v : 0.f);
+        const float v_scale = fp.s2_sigma ? v : 1.0f;
+        const float* col = buf + (int64_t)j * cs;
+        for (int i = lane; i < l; i += 32) {
+          const float o1 = col[i] * u_scale, o2 = col[ls + i] * v_scale;
+          fp.S1[(int64_t)i * r + p] = o1;
+          fp.S2[(int64_t)i * r + p] = o2;
+          fp.S1T[(int64_t)p * l + i] = o1;
+          fp.S2T[(int64_t)p * l + i] = o2;
+        }
+      }
+    }
+    return;
+  }
   for (int hf = 0; hf < 2; ++hf) {
     const float* buf = sm + (hf == 0 ? bt_ : bb_) * bufsz;
     const int blk = s_ids[2 * rank + hf];
@@ -917,12 +971,17 @@ lramm_status launch_jacobi_gw(JacobiBatch jb, int l, int gw, int max_sweeps, int
 #undef JC_CASE
 }
 
-lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s) {
+lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool* finalized) {
+  *finalized = false;
   {
     bool done = false;
     LRAMM_TRY(launch_jacobi_gw(jb, l, kJacobiWarpsPerPair, max_sweeps, status, s, done));
-    if (done) return LRAMM_OK;
+    if (done) {
+      *finalized = jb.r > 0;
+      return LRAMM_OK;
+    }
   }
+  jb.r = 0;   // the three-buffer kernel leaves M and V for svd_finalize
   int C, b, ls;
   size_t smem;
   if (!jacobi_shape(l, C, b, ls, smem)) return LRAMM_ERR_UNSUPPORTED;
