@@ -854,6 +854,182 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
 }
 
 // ---------------------------------------------------------------------------
+// The pair kernel's rounds with the three-buffer moves, for 320 < l <= 544:
+// one warp per column pair (b <= 17 warps), the top column held in
+// registers for the b rounds of a block round, the three inner products in
+// one shuffle tree and the fast rotation of jc2_rotate; the blocks circulate
+// as in jacobi_cluster_kernel (three b-column buffers, pulls behind cluster
+// barriers), since four buffers of b = 17 columns of M and V do not fit in
+// shared memory.  Same schedule, threshold and stopping rule as the pair
+// kernel.
+// ---------------------------------------------------------------------------
+template <int RP>
+__global__ void __launch_bounds__(576)
+jacobi_pair3_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float tol, int* status) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int prob = blockIdx.x / C;
+  float* __restrict__ Mg = jb.M[prob];
+  float* __restrict__ Vg = jb.V[prob];
+  extern __shared__ float4 jp3_smem4[];
+  float* sm = reinterpret_cast<float*>(jp3_smem4);
+  const int cs = 2 * ls;
+  const int64_t bufsz = (int64_t)b * cs;
+  __shared__ float s_part[16][2][4];
+  __shared__ int s_flags[16];
+  __shared__ int s_ids[32];
+  __shared__ int s_rmax;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int grp = warp, p = lane;
+  const int nslots = 2 * C;
+
+  if (tid < nslots) s_ids[tid] = tid;
+  for (int half = 0; half < 2; ++half) {
+    float* buf = sm + half * bufsz;
+    const int blk = 2 * rank + half;
+    for (int64_t e = tid; e < bufsz; e += blockDim.x) {
+      const int j = (int)(e / cs), i = (int)(e - (int64_t)j * cs);
+      const int g = blk * b + j;
+      float v = 0.f;
+      if (g < l) {
+        if (i < l) v = Mg[(int64_t)g * l + i];
+        else if (i >= ls && i - ls < l) v = (i - ls == g) ? 1.f : 0.f;
+      }
+      buf[e] = v;
+    }
+  }
+  cluster.sync();
+
+  const int be = b + (b & 1), half = be / 2, nreal = b / 2;
+  int e = 0;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) s_rmax = 0;
+    float rmax = 0.f;
+    __syncthreads();
+    for (int br = 0; br < 2 * C - 1; ++br) {
+      int bt_, bb_, bf_;
+      jc_bufs(rank, e, bt_, bb_, bf_);
+      float* topb = sm + bt_ * bufsz;
+      float* botb = sm + bb_ * bufsz;
+      if (br == 0) {  // pairs inside each block, circle method on b (+1 dummy) columns
+        for (int t = 0; t < be - 1; ++t) {
+          if (grp < 2 * nreal) {
+            float* base = grp < nreal ? topb : botb;
+            int q = grp < nreal ? grp : grp - nreal;
+            int x = 0, y = 0;
+            for (int k = 0; k < half; ++k) {
+              int xx, yy;
+              if (k == 0) {
+                xx = 0;
+                yy = 1 + t % (be - 1);
+              } else {
+                xx = 1 + (t + k) % (be - 1);
+                yy = 1 + (t - k + (be - 1)) % (be - 1);
+              }
+              if (xx >= b || yy >= b) continue;
+              if (q == 0) {
+                x = xx;
+                y = yy;
+              }
+              --q;
+            }
+            float xm[RP], xv[RP], ym[RP], yv[RP];
+            float* cx = base + (int64_t)x * cs;
+            float* cy = base + (int64_t)y * cs;
+            jc2_load<RP, 1>(cx, ls, p, xm, xv);
+            jc2_load<RP, 1>(cy, ls, p, ym, yv);
+            if (jc2_rotate<RP, 1>(xm, xv, ym, yv, tol, grp, 0, lane, s_part, rmax)) {
+              jc2_store<RP, 1>(cx, ls, p, xm, xv);
+              jc2_store<RP, 1>(cy, ls, p, ym, yv);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      {  // top column grp against bottom column (grp + j) mod b, top held in registers
+        float tm[RP], tv[RP];
+        float* tcol = topb + (int64_t)grp * cs;
+        jc2_load<RP, 1>(tcol, ls, p, tm, tv);
+        bool trot = false;
+        for (int j = 0; j < b; ++j) {
+          int k = grp + j;
+          if (k >= b) k -= b;
+          float* bcol = botb + (int64_t)k * cs;
+          float bm[RP], bv[RP];
+          jc2_load<RP, 1>(bcol, ls, p, bm, bv);
+          if (jc2_rotate<RP, 1>(tm, tv, bm, bv, tol, grp, 0, lane, s_part, rmax)) {
+            jc2_store<RP, 1>(bcol, ls, p, bm, bv);
+            trot = true;
+          }
+          __syncthreads();
+        }
+        if (trot) jc2_store<RP, 1>(tcol, ls, p, tm, tv);
+      }
+      if (C > 1) {
+        cluster.sync();  // every CTA has finished rotating the blocks it is about to hand on
+        // move 1: every CTA but 0 pulls its new top into its free buffer
+        if (rank >= 1) {
+          int st, sb, sf;
+          jc_bufs(rank - 1, e, st, sb, sf);
+          const float4* src =
+              cluster.map_shared_rank(reinterpret_cast<float4*>(sm + (rank == 1 ? sb : st) * bufsz), rank - 1);
+          float4* dst = reinterpret_cast<float4*>(sm + bf_ * bufsz);
+          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        cluster.sync();
+        // move 2: every CTA but the last pulls its new bottom from the next CTA
+        if (rank <= C - 2) {
+          int st, sb, sf;
+          jc_bufs(rank + 1, e, st, sb, sf);
+          const float4* src = cluster.map_shared_rank(reinterpret_cast<float4*>(sm + sb * bufsz), rank + 1);
+          float4* dst = reinterpret_cast<float4*>(sm + (rank == 0 ? bb_ : bt_) * bufsz);
+          for (int64_t q = tid; q < bufsz / 4; q += blockDim.x) dst[q] = src[q];
+        }
+        if (tid == 0) {
+          int nid[32];
+          nid[0] = s_ids[0];
+          nid[2] = s_ids[1];
+          for (int c = 2; c < C; ++c) nid[2 * c] = s_ids[2 * c - 2];
+          nid[2 * C - 1] = s_ids[2 * C - 2];
+          for (int c = 0; c <= C - 2; ++c) nid[2 * c + 1] = s_ids[2 * c + 3];
+          for (int q = 0; q < nslots; ++q) s_ids[q] = nid[q];
+        }
+        cluster.sync();
+        ++e;
+      } else {
+        __syncthreads();
+      }
+    }
+    if (lane == 0) atomicMax(&s_rmax, __float_as_int(rmax));
+    __syncthreads();
+    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rmax;
+    cluster.sync();
+    int mx = 0;
+    for (int c = 0; c < C; ++c) mx = max(mx, s_flags[c]);
+    cluster.sync();
+    if (!(__int_as_float(mx) > jb.stopq * tol)) break;
+  }
+  if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
+  if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
+  int bt_, bb_, bf_;
+  jc_bufs(rank, e, bt_, bb_, bf_);
+  for (int hf = 0; hf < 2; ++hf) {
+    const float* buf = sm + (hf == 0 ? bt_ : bb_) * bufsz;
+    const int blk = s_ids[2 * rank + hf];
+    for (int64_t q = tid; q < (int64_t)b * l; q += blockDim.x) {
+      const int j = (int)(q / l), i = (int)(q - (int64_t)j * l);
+      const int g = blk * b + j;
+      if (g >= l) continue;
+      const float* col = buf + (int64_t)j * cs;
+      Mg[(int64_t)g * l + i] = col[i];
+      Vg[(int64_t)g * l + i] = col[ls + i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Opt-in shared memory per block on sm_100-class GPUs (227 KB), minus the
 // static shared memory the kernels declare themselves.
 static const int kSmemMax = 232448 - 1024;
@@ -971,6 +1147,55 @@ lramm_status launch_jacobi_gw(JacobiBatch jb, int l, int gw, int max_sweeps, int
 #undef JC_CASE
 }
 
+// The pair-style three-buffer kernel: 16 CTAs, blocks of b = ceil(l / 32)
+// columns (one warp each), RP = ceil(l / 32) rows per lane; `done` is false
+// when the shape does not apply (l <= 320 or beyond 544) or does not fit.
+template <int RP>
+static lramm_status launch_pair3_rp(JacobiBatch jb, int l, int b, int max_sweeps, int* status, cudaStream_t s,
+                                    bool& done) {
+  const int C = 16, ls = 32 * RP;
+  const size_t smem = sizeof(float) * 3 * (size_t)b * 2 * ls;
+  if (smem > (size_t)kSmemMax || 32 * b > 576) return LRAMM_OK;
+  auto kern = jacobi_pair3_kernel<RP>;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
+  cfg.blockDim = dim3((unsigned)(32 * b), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  LRAMM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg));
+  if (nclusters < 1) return LRAMM_OK;
+  const float tol = 4.0f * sqrtf((float)l) * 0x1p-24f;
+  LRAMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jb, l, ls, b, max_sweeps, tol, status));
+  done = true;
+  return last_launch();
+}
+
+lramm_status launch_jacobi_pair3(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool& done) {
+  done = false;
+  if (l <= kJ2MaxL || l > 544) return LRAMM_OK;
+  const int b = (int)ceil_div(l, 32), rp = b;
+  switch (rp) {
+    case 11: return launch_pair3_rp<11>(jb, l, b, max_sweeps, status, s, done);
+    case 12: return launch_pair3_rp<12>(jb, l, b, max_sweeps, status, s, done);
+    case 13: return launch_pair3_rp<13>(jb, l, b, max_sweeps, status, s, done);
+    case 14: return launch_pair3_rp<14>(jb, l, b, max_sweeps, status, s, done);
+    case 15: return launch_pair3_rp<15>(jb, l, b, max_sweeps, status, s, done);
+    case 16: return launch_pair3_rp<16>(jb, l, b, max_sweeps, status, s, done);
+    case 17: return launch_pair3_rp<17>(jb, l, b, max_sweeps, status, s, done);
+    default: return LRAMM_OK;
+  }
+}
+
 lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool* finalized) {
   *finalized = false;
   {
@@ -981,7 +1206,12 @@ lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, c
       return LRAMM_OK;
     }
   }
-  jb.r = 0;   // the three-buffer kernel leaves M and V for svd_finalize
+  jb.r = 0;   // the three-buffer kernels leave M and V for svd_finalize
+  {
+    bool done = false;
+    LRAMM_TRY(launch_jacobi_pair3(jb, l, max_sweeps, status, s, done));
+    if (done) return LRAMM_OK;
+  }
   int C, b, ls;
   size_t smem;
   if (!jacobi_shape(l, C, b, ls, smem)) return LRAMM_ERR_UNSUPPORTED;
