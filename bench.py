@@ -161,7 +161,7 @@ def kernel_work(kind, cfg, l, variant):
 # launch, the kernels as they are in this tree); None where no capture of the
 # current kernel exists.
 MEASURED_TRAFFIC = {
-    "lramm_4096": {"svd": 347648, "trsm": 4667904,
+    "lramm_4096": {"trsm": 4667904,
                    "sketch": 71603456 + 2272512, "e3": 4272384 + 8035072},
 }
 
