@@ -382,9 +382,12 @@ struct SideRun {
 // bases of the power iterations); two give orthonormality to working
 // precision.  dst may equal src.  With want_R (two passes): R = L2^T L1^T,
 // so that src = dst R.
+// skip_last_solve: the last pass forms its Gram and Cholesky factor (and R)
+// but not its orthonormal output, so dst keeps what it held (with passes = 2
+// and dst = src: the input X, with X = P1 R1 and P1 in tmp).
 lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, float* const* src,
                         float* const* tmp, float* const* dst, const int64_t* rows, int passes, bool want_R,
-                        int* st, cudaStream_t s) {
+                        int* st, cudaStream_t s, bool skip_last_solve = false) {
   const int l = P->l;
   const float* in[2] = {src[0], ns > 1 ? src[1] : nullptr};
   for (int pass = 0; pass < passes; ++pass) {
@@ -432,17 +435,18 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
                   : gst);
       }
     if (gs.n) TIMED(P, LRAMM_K_GRAM, s, launch_gram(gs, l, at<float>(ws, sd[0].S->gpart), s));
+    const bool solve = !(skip_last_solve && pass == passes - 1);
     if (chol3_supported(l) && l % 4 == 0) {  // blocked Cholesky + panel solve with inverted diagonal blocks
       TIMED(P, LRAMM_K_CHOL, s, launch_chol3(cb3, l, kCholShift, st, s));
-      TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
+      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
     } else if (chol_split_supported(l)) {  // two-level Cholesky, same panel solve
       SplitScratch sc{};
       for (int i = 0; i < ns; ++i) sc.w[i] = at<float>(ws, sd[i].S->CS);
       TIMED(P, LRAMM_K_CHOL, s, launch_chol_split(cb3, sc, l, kCholShift, st, s));
-      TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
+      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
     } else {
       TIMED(P, LRAMM_K_CHOL, s, launch_chol2(cb, l, kCholShift, st, s));
-      TIMED(P, LRAMM_K_TRSM, s, launch_trsm_panel(tb, l, s));
+      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm_panel(tb, l, s));
     }
     for (int i = 0; i < ns; ++i) in[i] = out[i];
   }
@@ -483,8 +487,20 @@ lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M,
 // (X rows x cols each).  On exit (workspace, per side): R0 = Q (rows x l),
 // C0 = P (cols x l), sig[:r], S1 = U_s[:, :r] (x sigma if s1_sigma[i]),
 // S2 = V_s[:, :r] (x sigma if s2_sigma[i]), with X ~ Q U_s diag(sig) V_s^T P^T.
+//
+// M-only form (m_only_req, one operand, where the M-only Jacobi launches;
+// *m_only_done reports it): P is not formed and V_s is not accumulated.
+// With B^T = P1 R1 (the first CholeskyQR pass, P1 in C1, R1 = L1^T) and
+// R^T = U_s Sigma V_s^T, P V_s = B^T U_s Sigma^-1 = P1 (R1 U_s Sigma^-1).
+// On exit C1 = P1 (cols x l), S2 = U_s[:, :r] Sigma^-1 (x sigma if
+// s2_sigma) and Vj holds Y^T = S2^T L1 (r x l, FP32): the products P1 Y are
+// the right factors P V_s[:, :r] (x sigma).  The small factor Y carries the
+// cancellation between R1 and U_s Sigma^-1 in FP32, so the tall product
+// with the well-conditioned P1 is as accurate in TF32 as P V_s.  One
+// triangular solve fewer, and the Jacobi moves and rotates half the data.
 lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, int ns, void* ws,
-                        const int* s1_sigma, const int* s2_sigma, cudaStream_t s, float stopq = kJacobiQuad) {
+                        const int* s1_sigma, const int* s2_sigma, cudaStream_t s, float stopq = kJacobiQuad,
+                        bool m_only_req = false, bool* m_only_done = nullptr) {
   const lramm_desc& d = P->d;
   const int l = P->l;
   const bool fp8 = d.sketch == LRAMM_SKETCH_E4M3;   // range-finder passes on e4m3 codes
@@ -518,7 +534,6 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
   }
   for (int i = 0; i < ns; ++i)
     TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));  // B^T
-  LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 2, true, st, s));  // B^T = P R
   // R row-major is R^T column-major: one-sided Jacobi on R^T = U_s S V_s^T.
   JacobiBatch jb{};
   FinalBatch fb{};
@@ -535,8 +550,23 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
   }
   jb.r = d.r;
   for (int i = 0; i < ns; ++i) jb.fin[i] = fb.p[i];
+  const int max_sweeps = d.max_sweeps > 0 ? d.max_sweeps : 40;
+  bool m_only = false;
+  if (m_only_req && ns == 1) LRAMM_TRY(launch_jacobi_uonly(jb, l, max_sweeps, st, s, true, m_only));
+  LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 2, true, st, s, m_only));  // B^T = P R
+  if (m_only) {
+    bool ok = false;
+    TIMED(P, LRAMM_K_SVD, s, launch_jacobi_uonly(jb, l, max_sweeps, st, s, false, ok));
+    if (!ok) return LRAMM_ERR_UNSUPPORTED;
+    const SideLayout& S = *sd[0].S;
+    TIMED(P, LRAMM_K_RFACTOR, s,
+          sgemm(0, 0, d.r, l, l, 1.f, at<float>(ws, S.S2T), l, 0, at<float>(ws, S.L1), l, 0.f, at<float>(ws, S.Vj), l,
+                s));
+    if (m_only_done) *m_only_done = true;
+    return LRAMM_OK;
+  }
   bool finalized = false;
-  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, d.max_sweeps > 0 ? d.max_sweeps : 40, st, s, &finalized));
+  TIMED(P, LRAMM_K_SVD, s, launch_jacobi(jb, l, max_sweeps, st, s, &finalized));
   if (!finalized) TIMED(P, LRAMM_K_SVDSORT, s, launch_svd_finalize(fb, l, d.r, s));
   return LRAMM_OK;
 }
@@ -1077,12 +1107,17 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   float* Vt = at<float>(ws, plan->Vt);
   float* Wt = at<float>(ws, plan->Wt);
   float* Zt = at<float>(ws, plan->Zt);
-  // A: U~ = Q_A (U_s Sigma) (m x r);  V^T = V_s^T P_A^T (r x k)
+  // A: U~ = Q_A (U_s Sigma) (m x r);  V^T = V_s^T P_A^T (r x k)  (M-only
+  // form: V^T = Y^T P1^T)
   const SideLayout& SA = plan->side[0];
   const SideLayout& SB = plan->side[1];
   const SideRun sd[2] = {side_run(plan, 0, A), side_run(plan, 1, B)};
   const int which[2] = {0, 1}, s1s[2] = {1, 0}, s2s[2] = {0, 1};
   const float stopq = (d.prec[2] != LRAMM_P_F32 && d.lead == 0) ? kJacobiQuadQuantised : kJacobiQuad;
+  // Quantised chains take the M-only small SVD (right factors from B^T):
+  // their codes see the factors only through the rank-r products, which
+  // the two forms give alike to working precision.  FP32 chains keep V_s.
+  const bool m_only = d.prec[2] != LRAMM_P_F32 || d.lead > 0;
   // The two operands' RSVDs are independent: A on the caller's stream, B on
   // the plan's second stream, so that one operand's latency-bound small
   // algebra (a few CTAs) runs beside the other's HBM-bound products.
@@ -1091,24 +1126,37 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   LRAMM_CUDA_TRY(cudaEventRecord(plan->ev_fork, s));
   LRAMM_CUDA_TRY(cudaStreamWaitEvent(s2, plan->ev_fork, 0));
   auto side_a = [&]() -> lramm_status {
-    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s, stopq));
+    bool mo = false;
+    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s, stopq, m_only, &mo));
     TIMED(plan, LRAMM_K_ASSEMBLE, s,
           assemble(plan, ws, SA, d.m, r, at<float>(ws, SA.R0), at<float>(ws, SA.S1T), Ut, r, 0,
                    at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, s, true));
-    TIMED(plan, LRAMM_K_ASSEMBLE, s,
-          assemble(plan, ws, SA, r, d.k, at<float>(ws, SA.S2T), at<float>(ws, SA.C0), Vt, d.k, 1,
-                   at<float>(ws, SA.S2), r, 1, at<float>(ws, SA.C0), l, s, true));
+    if (mo)  // V^T = Y^T P1^T
+      TIMED(plan, LRAMM_K_ASSEMBLE, s,
+            assemble(plan, ws, SA, r, d.k, at<float>(ws, SA.Vj), at<float>(ws, SA.C1), Vt, d.k, 0,
+                     at<float>(ws, SA.Vj), l, 1, at<float>(ws, SA.C1), l, s, true));
+    else
+      TIMED(plan, LRAMM_K_ASSEMBLE, s,
+            assemble(plan, ws, SA, r, d.k, at<float>(ws, SA.S2T), at<float>(ws, SA.C0), Vt, d.k, 1,
+                     at<float>(ws, SA.S2), r, 1, at<float>(ws, SA.C0), l, s, true));
     return LRAMM_OK;
   };
-  // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)
+  // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)  (M-only
+  // form: Z~^T = P1 Y)
   auto side_b = [&]() -> lramm_status {
-    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2, stopq));
+    bool mo = false;
+    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2, stopq, m_only, &mo));
     TIMED(plan, LRAMM_K_ASSEMBLE, s2,
           assemble(plan, ws, SB, r, d.k, at<float>(ws, SB.S1T), at<float>(ws, SB.R0), Wt, d.k, 1,
                    at<float>(ws, SB.S1), r, 1, at<float>(ws, SB.R0), l, s2, true));
-    TIMED(plan, LRAMM_K_ASSEMBLE, s2,
-          assemble(plan, ws, SB, d.n, r, at<float>(ws, SB.C0), at<float>(ws, SB.S2T), Zt, r, 0,
-                   at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, s2, true));
+    if (mo)  // Z~^T = P1 Y
+      TIMED(plan, LRAMM_K_ASSEMBLE, s2,
+            assemble(plan, ws, SB, d.n, r, at<float>(ws, SB.C1), at<float>(ws, SB.Vj), Zt, r, 0,
+                     at<float>(ws, SB.C1), l, 1, at<float>(ws, SB.Vj), l, s2, true));
+    else
+      TIMED(plan, LRAMM_K_ASSEMBLE, s2,
+            assemble(plan, ws, SB, d.n, r, at<float>(ws, SB.C0), at<float>(ws, SB.S2T), Zt, r, 0,
+                     at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, s2, true));
     return LRAMM_OK;
   };
   const lramm_status st_a = side_a();

@@ -134,6 +134,12 @@ lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s);
 // One-sided Jacobi SVD of each M (thread-block cluster per problem).
 // *finalized: whether the launch also wrote the sorted rank-r outputs (jb.r > 0).
 lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool* finalized);
+// The M-only pair Jacobi (l <= 544, jb.r > 0): rotates M = R^T alone and
+// writes sig, S1 (as launch_jacobi does) and S2 = U_s Sigma^-1 (x sigma if
+// s2_sigma) from M.  check_only: only reports in `ok` whether this shape
+// launches on this device (nothing is enqueued).
+lramm_status launch_jacobi_uonly(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool check_only,
+                                 bool& ok);
 // Sort by descending sigma and write the rank-r pieces.
 lramm_status launch_svd_finalize(FinalBatch fb, int l, int r, cudaStream_t s);
 // orth.cu -- CholeskyQR building blocks, batched over up to two problems.

@@ -448,7 +448,7 @@ __device__ __forceinline__ void group_bar(int id) {
 // product stays below jb.stopq * tol is the last one (callers pass
 // kJacobiQuad = 20 for a converged SVD).
 
-template <int RP, int GW>
+template <int RP, int GW, bool WV = true>
 __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], float (&ym)[RP], float (&yv)[RP],
                                            float tol, int grp, int wig, int lane, float (*s_part)[2][4],
                                            float& rmax) {
@@ -511,33 +511,36 @@ __device__ __forceinline__ bool jc2_rotate(float (&xm)[RP], float (&xv)[RP], flo
     const float x = xm[u], y = ym[u];
     xm[u] = x - s * fmaf(tau, x, y);
     ym[u] = y + s * fmaf(-tau, y, x);
-    const float vx = xv[u], vy = yv[u];
-    xv[u] = vx - s * fmaf(tau, vx, vy);
-    yv[u] = vy + s * fmaf(-tau, vy, vx);
+    if (WV) {
+      const float vx = xv[u], vy = yv[u];
+      xv[u] = vx - s * fmaf(tau, vx, vy);
+      yv[u] = vy + s * fmaf(-tau, vy, vx);
+    }
   }
   return true;
 }
 
-template <int RP, int GW>
+template <int RP, int GW, bool WV = true>
 __device__ __forceinline__ void jc2_load(const float* __restrict__ col, int ls, int p, float (&m)[RP], float (&v)[RP]) {
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
     m[u] = col[p + 32 * GW * u];
-    v[u] = col[ls + p + 32 * GW * u];
+    if (WV) v[u] = col[ls + p + 32 * GW * u];
   }
 }
 
-template <int RP, int GW>
+template <int RP, int GW, bool WV = true>
 __device__ __forceinline__ void jc2_store(float* __restrict__ col, int ls, int p, const float (&m)[RP],
                                           const float (&v)[RP]) {
 #pragma unroll
   for (int u = 0; u < RP; ++u) {
     col[p + 32 * GW * u] = m[u];
-    col[ls + p + 32 * GW * u] = v[u];
+    if (WV) col[ls + p + 32 * GW * u] = v[u];
   }
 }
 
 constexpr int kJ2MaxL = 320;   // largest l of the pair kernel (16 CTAs x 2 blocks x 10 columns)
+constexpr int kJUMaxL = 544;   // largest l of its M-only form (16 CTAs x 2 blocks x 17 columns)
 
 // Physical buffers of cluster rank `rank` after e moves, four per CTA:
 // top T, bottom B and the landing buffers FL / FR that blocks pushed by the
@@ -613,8 +616,12 @@ __device__ __forceinline__ void jc_push(const float* src, float* dst_local_view,
       : "memory");
 }
 
-template <int RP, int GW>
-__global__ void __launch_bounds__(640)
+// WV = false is the M-only form: the rotations are applied to M alone (no
+// V_s is accumulated, a column is ls floats instead of 2 ls) and the
+// epilogue writes the S2 outputs from M, for callers that form the right
+// factor from B^T U_s Sigma^-1 (requires jb.r > 0).
+template <int RP, int GW, bool WV = true>
+__global__ void __launch_bounds__(640, 1)
 jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float tol, int* status) {
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
@@ -624,14 +631,14 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
   float* __restrict__ Vg = jb.V[prob];
   extern __shared__ float4 jc2_smem4[];
   float* sm = reinterpret_cast<float*>(jc2_smem4);
-  const int cs = 2 * ls;                      // floats per column: M part, then V part
+  const int cs = WV ? 2 * ls : ls;            // floats per column: M part, then V part
   const int64_t bufsz = (int64_t)b * cs;      // floats per b-column buffer
   __shared__ float s_part[16][2][4];
   __shared__ int s_flags[16];
   __shared__ int s_ids[32];
   __shared__ int s_rmax;   // bits of the sweep's largest relative inner product (non-negative)
   __shared__ __align__(8) uint64_t rx_bar[2];   // incoming blocks of even / odd moves
-  __shared__ float s_nrm[kJ2MaxL];               // column norms of the whole problem (rank-r outputs)
+  __shared__ float s_nrm[WV ? kJ2MaxL : kJUMaxL];  // column norms of the whole problem (rank-r outputs)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int grp = warp / GW, wig = warp % GW, p = tid & (32 * GW - 1);
   const int nslots = 2 * C;
@@ -655,7 +662,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
       float v = 0.f;
       if (g < l) {
         if (i < l) v = Mg[(int64_t)g * l + i];
-        else if (i >= ls && i - ls < l) v = (i - ls == g) ? 1.f : 0.f;
+        else if (WV && i >= ls && i - ls < l) v = (i - ls == g) ? 1.f : 0.f;
       }
       buf[e] = v;
     }
@@ -699,11 +706,11 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
             float xm[RP], xv[RP], ym[RP], yv[RP];
             float* cx = base + (int64_t)x * cs;
             float* cy = base + (int64_t)y * cs;
-            jc2_load<RP, GW>(cx, ls, p, xm, xv);
-            jc2_load<RP, GW>(cy, ls, p, ym, yv);
-            if (jc2_rotate<RP, GW>(xm, xv, ym, yv, tol, grp, wig, lane, s_part, rmax)) {
-              jc2_store<RP, GW>(cx, ls, p, xm, xv);
-              jc2_store<RP, GW>(cy, ls, p, ym, yv);
+            jc2_load<RP, GW, WV>(cx, ls, p, xm, xv);
+            jc2_load<RP, GW, WV>(cy, ls, p, ym, yv);
+            if (jc2_rotate<RP, GW, WV>(xm, xv, ym, yv, tol, grp, wig, lane, s_part, rmax)) {
+              jc2_store<RP, GW, WV>(cx, ls, p, xm, xv);
+              jc2_store<RP, GW, WV>(cy, ls, p, ym, yv);
             }
           }
           __syncthreads();
@@ -712,21 +719,21 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
       {  // top column grp against bottom column (grp + j) mod b, top held in registers
         float tm[RP], tv[RP];
         float* tcol = topb + (int64_t)grp * cs;
-        jc2_load<RP, GW>(tcol, ls, p, tm, tv);
+        jc2_load<RP, GW, WV>(tcol, ls, p, tm, tv);
         bool trot = false;
         for (int j = 0; j < b; ++j) {
           int k = grp + j;
           if (k >= b) k -= b;
           float* bcol = botb + (int64_t)k * cs;
           float bm[RP], bv[RP];
-          jc2_load<RP, GW>(bcol, ls, p, bm, bv);
-          if (jc2_rotate<RP, GW>(tm, tv, bm, bv, tol, grp, wig, lane, s_part, rmax)) {
-            jc2_store<RP, GW>(bcol, ls, p, bm, bv);
+          jc2_load<RP, GW, WV>(bcol, ls, p, bm, bv);
+          if (jc2_rotate<RP, GW, WV>(tm, tv, bm, bv, tol, grp, wig, lane, s_part, rmax)) {
+            jc2_store<RP, GW, WV>(bcol, ls, p, bm, bv);
             trot = true;
           }
           __syncthreads();
         }
-        if (trot) jc2_store<RP, GW>(tcol, ls, p, tm, tv);
+        if (trot) jc2_store<RP, GW, WV>(tcol, ls, p, tm, tv);
       }
       if (C > 1) {
         // Move: push the outgoing blocks into the neighbours' landing buffers
@@ -825,11 +832,14 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
         const int p = cnt;
         if (p >= r) continue;
         if (lane == 0) fp.sig[p] = v;
-        const float u_scale = fp.s1_sigma ? 1.0f : (v > 0.f ? 1.0f / v : 0.f);
-        const float v_scale = fp.s2_sigma ? v : 1.0f;
+        const float inv = v > 0.f ? 1.0f / v : 0.f;
+        const float u_scale = fp.s1_sigma ? 1.0f : inv;
+        // M-only form: S2 = U_s Sigma^-1 (x sigma if s2_sigma) from M = U_s Sigma
+        const float v_scale = WV ? (fp.s2_sigma ? v : 1.0f) : (fp.s2_sigma ? inv : inv * inv);
         const float* col = buf + (int64_t)j * cs;
+        const int voff = WV ? ls : 0;
         for (int i = lane; i < l; i += 32) {
-          const float o1 = col[i] * u_scale, o2 = col[ls + i] * v_scale;
+          const float o1 = col[i] * u_scale, o2 = col[voff + i] * v_scale;
           fp.S1[(int64_t)i * r + p] = o1;
           fp.S2[(int64_t)i * r + p] = o2;
           fp.S1T[(int64_t)p * l + i] = o1;
@@ -848,7 +858,7 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
       if (g >= l) continue;
       const float* col = buf + (int64_t)j * cs;
       Mg[(int64_t)g * l + i] = col[i];
-      Vg[(int64_t)g * l + i] = col[ls + i];
+      if (WV) Vg[(int64_t)g * l + i] = col[ls + i];
     }
   }
 }
@@ -1194,6 +1204,58 @@ lramm_status launch_jacobi_pair3(JacobiBatch jb, int l, int max_sweeps, int* sta
     case 17: return launch_pair3_rp<17>(jb, l, b, max_sweeps, status, s, done);
     default: return LRAMM_OK;
   }
+}
+
+// The M-only pair kernel: C = min(16, ceil(l / 16)) CTAs, blocks of
+// b = ceil(l / 2C) <= 17 columns (one warp each), RP = ceil(l / 32) <= 17
+// rows per lane, four b-column buffers of ls floats per column.
+template <int RP>
+static lramm_status launch_uonly_rp(JacobiBatch jb, int l, int C, int b, size_t smem, int max_sweeps, int* status,
+                                    cudaStream_t s, bool check_only, bool& ok) {
+  ok = false;
+  const int ls = 32 * RP;
+  auto kern = jacobi_pair2_kernel<RP, 1, false>;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (C > 8) LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
+  cfg.blockDim = dim3((unsigned)(32 * b), 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  LRAMM_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg));
+  if (nclusters < 1) return LRAMM_OK;
+  ok = true;
+  if (check_only) return LRAMM_OK;
+  const float tol = 4.0f * sqrtf((float)l) * 0x1p-24f;
+  LRAMM_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, jb, l, ls, b, max_sweeps, tol, status));
+  return last_launch();
+}
+
+lramm_status launch_jacobi_uonly(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool check_only,
+                                 bool& ok) {
+  ok = false;
+  if (l < 2 || l > kJUMaxL || jb.r <= 0 || jb.n < 1) return LRAMM_OK;
+  int C = (int)ceil_div(l, 16);
+  if (C > 16) C = 16;
+  const int b = (int)ceil_div(l, 2 * C), rp = (int)ceil_div(l, 32);
+  const size_t smem = sizeof(float) * 4 * (size_t)b * 32 * rp;
+  if (b > 17 || rp > 17 || smem > (size_t)kSmemMax) return LRAMM_OK;
+#define JU_CASE(R) \
+  case R: return launch_uonly_rp<R>(jb, l, C, b, smem, max_sweeps, status, s, check_only, ok);
+  switch (rp) {
+    JU_CASE(1) JU_CASE(2) JU_CASE(3) JU_CASE(4) JU_CASE(5) JU_CASE(6) JU_CASE(7) JU_CASE(8) JU_CASE(9)
+    JU_CASE(10) JU_CASE(11) JU_CASE(12) JU_CASE(13) JU_CASE(14) JU_CASE(15) JU_CASE(16) JU_CASE(17)
+    default: return LRAMM_OK;
+  }
+#undef JU_CASE
 }
 
 lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, cudaStream_t s, bool* finalized) {
