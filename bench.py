@@ -170,14 +170,21 @@ def measured_traffic(workload, kind):
     return MEASURED_TRAFFIC.get(workload, {}).get(kind)
 
 
-def jacobi_work(l, sweeps):
+def jacobi_work(l, sweeps, with_v=True):
     """Algorithmic FP32 flops of one launch of the one-sided Jacobi SVD (one
     operand per launch: the two operands' SVDs run on two streams; `sweeps`
     lists both, the result is their mean): per sweep every one of the
     l(l-1)/2 column pairs forms three inner products of length l (6 l flops)
     and rotates its two columns of M and of V (4 vectors x 3 l flops) -- 18 l
-    flops per pair."""
-    return sum(s * l * (l - 1) / 2 * 18.0 * l for s in sweeps) / max(len(sweeps), 1)
+    flops per pair; 12 l in the M-only form (no V accumulated)."""
+    per_pair = 18.0 if with_v else 12.0
+    return sum(s * l * (l - 1) / 2 * per_pair * l for s in sweeps) / max(len(sweeps), 1)
+
+
+def m_only_svd(variant, l):
+    """Quantised chains (a quantised E3, or a lead / tail split) of l <= 544
+    take the M-only small SVD inside lramm_matmul."""
+    return (VARIANTS[variant][2] != 0 or variant in LEADS) and l <= 544
 
 
 def fp32_alu_peak_tflops(sm_mhz):
@@ -512,7 +519,8 @@ def run_lramm(args):
         roof["algorithmic_bytes_per_launch"] = nbytes
     elif dname == "svd":
         # latency-bound: l sequential rounds per sweep; reported against the FP32 ALU roof
-        jf = jacobi_work(l, [int(x) for x in info[1:3] if int(x) > 0])
+        mo = m_only_svd(args.variant, l)
+        jf = jacobi_work(l, [int(x) for x in info[1:3] if int(x) > 0], with_v=not mo)
         roof = {"bound": "alu", "achieved": jf / avg_s / 1e12,
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
                 "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
@@ -520,7 +528,8 @@ def run_lramm(args):
                 "traffic": measured_traffic(args.workload, "svd"),
                 "algorithmic_flops_per_launch": jf,
                 "note": "one-sided Jacobi, sequential rounds of column-pair rotations on a 16-CTA cluster "
-                        "(one launch per operand, the two on concurrent streams)"}
+                        "(one launch per operand, the two on concurrent streams)"
+                        + ("; M-only form (no V accumulated): 12 l flops per pair" if mo else "")}
         roof["frac"] = roof["achieved"] / roof["peak"]
     else:
         roof = {"bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
