@@ -757,20 +757,21 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
           }
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
-        if (tid == 0) {
-          int nid[32];
-          nid[0] = s_ids[0];
-          nid[2] = s_ids[1];
-          for (int c = 2; c < C; ++c) nid[2 * c] = s_ids[2 * c - 2];
-          nid[2 * C - 1] = s_ids[2 * C - 2];
-          for (int c = 0; c <= C - 2; ++c) nid[2 * c + 1] = s_ids[2 * c + 3];
-          for (int q = 0; q < nslots; ++q) s_ids[q] = nid[q];
+        // block ids of the slots after this move, one slot per thread (read
+        // here, written after the barrier below): slot 0 keeps its block,
+        // slot 2 takes slot 1's, an even slot 2c >= 4 slot 2c - 2's, the
+        // last slot 2C - 1 slot 2C - 2's, any other odd slot 2c + 1 slot 2c + 3's
+        int nid = 0;
+        if (tid < nslots) {
+          const int src = tid == 0 ? 0 : tid == 2 ? 1 : (tid & 1) == 0 ? tid - 2 : tid == nslots - 1 ? nslots - 2 : tid + 2;
+          nid = s_ids[src];
         }
         if (!failed && !jc_mbar_wait(&rx_bar[e & 1], (e >> 1) & 1)) {
           failed = true;
           set_status(status, LRAMM_ERR_TIMEOUT);
         }
         failed = __syncthreads_or(failed);   // one decision for the whole CTA
+        if (tid < nslots) s_ids[tid] = nid;
         ++e;
       }
       __syncthreads();
