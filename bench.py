@@ -162,7 +162,8 @@ def kernel_work(kind, cfg, l, variant):
 # current kernel exists.
 MEASURED_TRAFFIC = {
     "lramm_4096": {"trsm": 4667904,
-                   "sketch": 71603456 + 2272512, "e3": 4272384 + 8035072},
+                   "sketch": 71603456 + 2272512, "e3": 4272384 + 8035072,
+                   "svd": 350208},   # the M-only Jacobi of the INT8 chain
 }
 
 
@@ -525,7 +526,7 @@ def run_lramm(args):
                 "peak": fp32_alu_peak_tflops(pk.get("sm_max_mhz", 2070.0)), "unit": "TFLOP/s",
                 "kernel": dname, "launches_per_step": dcnt / nbd, "avg_launch_ms": avg_s * 1e3,
                 "peak_source": "derived: 152 SM x 128 FP32 FMA x 2 x sm_max_mhz",
-                "traffic": measured_traffic(args.workload, "svd"),
+                "traffic": measured_traffic(args.workload, "svd") if mo else None,
                 "algorithmic_flops_per_launch": jf,
                 "note": "one-sided Jacobi, sequential rounds of column-pair rotations on a 16-CTA cluster "
                         "(one launch per operand, the two on concurrent streams)"
