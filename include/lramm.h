@@ -142,7 +142,8 @@ typedef enum {
   LRAMM_K_GRAM = 2,       /* Gram matrices of CholeskyQR                      */
   LRAMM_K_CHOL = 3,       /* l x l Cholesky                                   */
   LRAMM_K_TRSM = 4,       /* Q = Y L^-T                                       */
-  LRAMM_K_RFACTOR = 5,    /* R = R2 R1                                        */
+  LRAMM_K_RFACTOR = 5,    /* R = R2 R1; in quantised chains also the l x r    */
+                          /* factor R1 U_s Sigma^-1 of the right factors      */
   LRAMM_K_SVD = 6,        /* one-sided Jacobi SVD of R^T                      */
   LRAMM_K_SVDSORT = 7,    /* sort / truncate to rank r                        */
   LRAMM_K_ASSEMBLE = 8,   /* U~, V^T, W^T, Z~^T from the small SVD            */
