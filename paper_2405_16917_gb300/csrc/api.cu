@@ -42,10 +42,12 @@ constexpr float kCholShift = 4.0f * 0x1p-24f;  // relative diagonal shift of eve
 // relative inner product rho is below the multiplier times tol is the last.
 // 20: the converged SVD the rank-r factors of lramm_rsvd / lramm_qsvd and the
 // FP32 chains use (the next sweep would rotate nothing).  1000 (rho below
-// 3.9e-3 at l = 272): the factors of a quantised E3 inside lramm_matmul --
-// the inner products left after such a sweep are about 10 rho^2 <= 1.5e-4,
-// which moves the rank-r product U~ V^T by about 1e-7 relative, far below
-// the quantisation noise of the chain.
+// 3.9e-3 at l = 272): the factors of quantised chains inside lramm_matmul --
+// the relative inner products left after such a sweep are about 5 rho^2
+// (the next sweep's rho), which moves the rank-r product by about ten times
+// that in the M-only form these chains use (first order in the leftover;
+// with V_s accumulated it would be second order), <= 1e-3 relative, below
+// the code noise of an 8-bit chain.
 constexpr float kJacobiQuad = 20.0f;
 constexpr float kJacobiQuadQuantised = 1000.0f;
 constexpr int64_t kGramTcRows = 2048;          // sketches from this many rows take the tensor-core Gram
@@ -465,10 +467,11 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
 
 // One product of the factor assembly: out (M x N, stride ldo) = A B^T with
 // A (M x l) and B (N x l) K-major.  For the factors that feed a quantised
-// chain inside lramm_matmul (tc: a tensor-core sketch mode, quantised E3,
-// no lead / tail split) a TF32 tensor-core product with this operand's
-// split-K buffer -- its rounding (2^-11 relative) sits far below the
-// quantisation step; otherwise (and for the factors lramm_rsvd and
+// chain inside lramm_matmul (tc: a tensor-core sketch mode, quantised E3;
+// with a lead / tail split, E1 and E2 quantised too, so that every term of
+// E3 carries their codes' noise) a TF32 tensor-core product with this
+// operand's split-K buffer -- its rounding (2^-11 relative) sits far below
+// the quantisation step; otherwise (and for the factors lramm_rsvd and
 // lramm_qsvd return, orthonormal to working precision) the FP32 SIMT
 // product, which takes its operands as given by (ta, Am, lda_s, tb, Bm, ldb_s).
 lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M, int64_t N, const float* A,
@@ -476,7 +479,8 @@ lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M,
                       const float* Bm, int64_t ldb_s, cudaStream_t s, bool tc = false) {
   const int l = P->l;
   const lramm_desc& d = P->d;
-  if (tc && d.sketch != LRAMM_SKETCH_F32 && d.lead == 0 && d.prec[2] != LRAMM_P_F32 &&
+  const bool coded = d.lead == 0 || (d.prec[0] != LRAMM_P_F32 && d.prec[1] != LRAMM_P_F32);
+  if (tc && d.sketch != LRAMM_SKETCH_F32 && coded && d.prec[2] != LRAMM_P_F32 &&
       tgemm_tc_supported(A, B, l, l, M, N, l) && tgemm_tc_part_floats(M, N, l) <= sketch_tc_part_floats(l))
     return tgemm_tc(M, N, l, 1.f, A, l, B, l, 0.f, out, ldo, at<float>(ws, S.part), sketch_tc_part_floats(l),
                     at<int>(ws, 0), s);
@@ -1113,10 +1117,16 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   const SideLayout& SB = plan->side[1];
   const SideRun sd[2] = {side_run(plan, 0, A), side_run(plan, 1, B)};
   const int which[2] = {0, 1}, s1s[2] = {1, 0}, s2s[2] = {0, 1};
-  const float stopq = (d.prec[2] != LRAMM_P_F32 && d.lead == 0) ? kJacobiQuadQuantised : kJacobiQuad;
-  // Quantised chains take the M-only small SVD (right factors from B^T):
-  // their codes see the factors only through the rank-r products, which
-  // the two forms give alike to working precision.  FP32 chains keep V_s.
+  // Loose Jacobi stopping rule where every term of E3 carries 8-bit-or-less
+  // codes: a quantised E3 without lead / tail split, or a lead / tail split
+  // whose E1 and E2 are quantised (E2's own code noise then bounds the
+  // lead's precision).
+  const bool coded_lead = d.lead > 0 && d.prec[0] != LRAMM_P_F32 && d.prec[1] != LRAMM_P_F32;
+  const float stopq = ((d.prec[2] != LRAMM_P_F32 && d.lead == 0) || coded_lead) ? kJacobiQuadQuantised : kJacobiQuad;
+  // Quantised chains take the M-only small SVD (right factors P1 (R1 U_s
+  // Sigma^-1)): their codes see the factors only through the rank-r
+  // products, which the two forms give alike up to the Jacobi's leftover,
+  // below the codes' noise.  FP32 chains keep V_s.
   const bool m_only = d.prec[2] != LRAMM_P_F32 || d.lead > 0;
   // The two operands' RSVDs are independent: A on the caller's stream, B on
   // the plan's second stream, so that one operand's latency-bound small
