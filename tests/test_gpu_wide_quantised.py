@@ -4,10 +4,10 @@ Inside lramm_matmul a quantised chain takes the small SVD in its M-only
 form: the Jacobi rotates M = R^T alone and the right factors are formed as
 P1 (R1 U_s Sigma^-1) from the first CholeskyQR pass of the projection.
 Above l = 320 that form runs shapes the V-accumulating pair kernel does not
-(blocks of 11 to 17 columns).  Two chains: the plain INT8 chain (loose
-Jacobi stopping rule) at l = 400, and the lead / tail chain of the 8192
-workload's recipe (INT8 lead with both residual terms, MXFP4 tail,
-converged stopping rule) at l = 544.  Each is compared with the oracle's
+(blocks of 11 to 17 columns).  Two chains, both on the loose Jacobi
+stopping rule of quantised chains: the plain INT8 chain at l = 400, and the
+lead / tail chain of the 8192 workload's recipe (INT8 E1 and E2, INT8 lead
+with both residual terms, MXFP4 tail) at l = 544.  Each is compared with the oracle's
 quantised chain on the oracle's FP64 factors by the noise criterion of the
 other quantised end-to-end tests.
 """
