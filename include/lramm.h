@@ -48,7 +48,7 @@ extern "C" {
 typedef enum {
   LRAMM_OK = 0,
   LRAMM_ERR_INVALID_ARG = 1,   /* bad shape, stride, pointer or option        */
-  LRAMM_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. l > 320)    */
+  LRAMM_ERR_UNSUPPORTED = 2,   /* valid but not implemented (e.g. l > 576)    */
   LRAMM_ERR_WORKSPACE = 3,     /* workspace smaller than lramm_workspace_size */
   LRAMM_ERR_CUDA = 4,          /* a CUDA runtime call failed                  */
   LRAMM_ERR_NUMERIC = 5,       /* Cholesky pivot <= 0 in an orthonormalisation */
@@ -134,6 +134,18 @@ typedef struct lramm_desc {
  * stream (0), which cannot be captured.  The caller keeps the captured
  * buffers alive while the plan may replay them. */
 #define LRAMM_FLAG_GRAPH 2
+/* flags, for tests of the failure path: every bounded device wait of the
+ * small SVD's thread-block cluster (the block moves of the cluster Jacobi)
+ * gives up after about 2^20 SM clock cycles (half a millisecond) instead of
+ * about 2^30 (half a second). */
+#define LRAMM_FLAG_SHORT_WAITS 4
+/* flags, for tests of the failure path: one CTA of the cluster Jacobi (rank
+ * 1, in clusters of two or more CTAs) skips its first block move, so that
+ * its neighbours' bounded waits expire.  The call then latches
+ * LRAMM_ERR_TIMEOUT in the status word, every CTA waits (bounded) for the
+ * copies already issued into it, the launch returns and the context stays
+ * usable; the call's outputs are undefined. */
+#define LRAMM_FLAG_TEST_DROP_MOVE 8
 
 /* Kernel kinds reported by lramm_timing_read. */
 typedef enum {
@@ -162,7 +174,11 @@ typedef struct lramm_plan_s* lramm_plan_t;
 
 /* Validate a problem description and build a plan (host metadata only).
  * Returns LRAMM_ERR_INVALID_ARG for inconsistent sizes or options,
- * LRAMM_ERR_UNSUPPORTED for l = r + p > 320.  *out is set only on success. */
+ * LRAMM_ERR_UNSUPPORTED for l = r + p > 576 (the orthonormalisation's
+ * limit).  The SVD form (lramm_rsvd, lramm_matmul, lramm_qsvd) also needs
+ * the small SVD to fit, l <= 544; those calls return LRAMM_ERR_UNSUPPORTED
+ * beyond it, the range-finder form runs to 576.  *out is set only on
+ * success. */
 LRAMM_API lramm_status lramm_plan_create(const lramm_desc* desc, lramm_plan_t* out);
 
 /* Release a plan.  NULL is accepted. */
@@ -208,7 +224,9 @@ LRAMM_API lramm_status lramm_status_read(const void* ws, void* stream);
 /* Wait for `stream` and copy the first n (1..64) 32-bit words of the
  * workspace's status area into info (host): info[0] = the status word,
  * info[1], info[2] = Jacobi sweeps of the A- and B-side SVDs of the last
- * call.  Nothing is cleared. */
+ * call, info[3] bit 0 = the last lramm_matmul assembled its factors with
+ * TF32 tensor-core products (quantised chains in a tensor-core sketch mode),
+ * else with FP32 products.  Nothing is cleared. */
 LRAMM_API lramm_status lramm_info_read(const void* ws, int32_t* info, int32_t n, void* stream);
 
 /* Static description of a status code. */

@@ -86,6 +86,8 @@ _SIGS = {
 
 FLAG_TIMING = 1
 FLAG_GRAPH = 2
+FLAG_SHORT_WAITS = 4       # failure-path tests: bounded waits of ~2^20 SM cycles
+FLAG_TEST_DROP_MOVE = 8    # failure-path tests: one cluster-Jacobi CTA skips its first block move
 K_COUNT = 17
 
 
@@ -148,7 +150,8 @@ class Plan:
 
     def __init__(self, m, n, k, r, p, q, seed=7, prec=(P_INT8, P_INT8, P_INT8), scale=S_ROWCOL,
                  sketch=SKETCH_F32, alpha=1.0, beta=0.0, a_type=F32, b_type=F32, lda=None, ldb=None,
-                 ldc=None, max_sweeps=0, timing=False, lead=0, lead_prec=P_INT8, lead_split=0, graph=False):
+                 ldc=None, max_sweeps=0, timing=False, lead=0, lead_prec=P_INT8, lead_split=0, graph=False,
+                 test_flags=0):
         lib = load()
         d = Desc()
         d.m, d.n, d.k = m, n, k
@@ -161,7 +164,8 @@ class Plan:
         d.prec[0], d.prec[1], d.prec[2] = prec
         d.scale, d.sketch = scale, sketch
         d.alpha, d.beta = alpha, beta
-        d.max_sweeps, d.flags = max_sweeps, (FLAG_TIMING if timing else 0) | (FLAG_GRAPH if graph else 0)
+        d.max_sweeps = max_sweeps
+        d.flags = (FLAG_TIMING if timing else 0) | (FLAG_GRAPH if graph else 0) | test_flags
         d.lead, d.lead_prec, d.lead_split = lead, lead_prec, lead_split
         self.desc = d
         h = ctypes.c_void_p()
@@ -436,13 +440,27 @@ def quantize_noalloc(X, prec, per_row=False, ldcodes=None, codes=None, scales=No
     may be passed in (codes, scales) so the call itself allocates nothing.
     """
     torch = _torch()
-    _need_cuda(X)
+    _need_cuda(X, codes, scales)
     rows, cols = X.shape
-    ldc = ldcodes or cols
-    if codes is None:
-        codes = torch.empty((rows, ldc), dtype=code_dtype(prec), device=X.device)
-    if scales is None:
-        scales = torch.empty((rows if per_row else 1,), dtype=torch.float32, device=X.device)
+    cdt = code_dtype(prec)
+    if codes is not None:
+        # caller-supplied codes: the library writes rows x ldc codes through it
+        ldc = ldcodes or codes.stride(0)
+        if codes.dtype != cdt or codes.dim() != 2 or codes.shape[0] != rows or codes.stride(1) != 1 \
+                or codes.stride(0) != ldc or ldc < cols or codes.device != X.device:
+            raise ValueError("quantize_noalloc: codes must be a %s tensor of shape (%d, >= %d) with row stride "
+                             "ldcodes on %s" % (cdt, rows, cols, X.device))
+    else:
+        ldc = ldcodes or cols
+        codes = torch.empty((rows, ldc), dtype=cdt, device=X.device)
+    need = rows if per_row else 1
+    if scales is not None:
+        if scales.dtype != torch.float32 or scales.numel() < need or not scales.is_contiguous() \
+                or scales.device != X.device:
+            raise ValueError("quantize_noalloc: scales must be a contiguous float32 tensor of at least %d "
+                             "elements on %s" % (need, X.device))
+    else:
+        scales = torch.empty((need,), dtype=torch.float32, device=X.device)
     _check(load().lramm_quantize_noalloc(_ptr(X), rows, cols, X.stride(0), prec, int(per_row), _ptr(codes),
                                          ldc, _ptr(scales), _stream()), "lramm_quantize_noalloc")
     return codes, scales

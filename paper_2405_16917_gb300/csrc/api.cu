@@ -86,6 +86,7 @@ struct lramm_plan_s {
   // second stream and fork / join events: the two operands' RSVDs overlap
   cudaStream_t s2 = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_stag = nullptr;   // B's first product waits for A's (staggered chains)
   int dev = -1;
   // LRAMM_FLAG_GRAPH: the captured call and the arguments it was captured with
   cudaGraphExec_t gexec = nullptr;
@@ -96,6 +97,7 @@ struct lramm_plan_s {
   size_t xV, xW, xZ, xE1, xU, xE2;
   int64_t lq;
   size_t cUh, cUl, cEh, cEl, sUh, sUl, sEh, sEl, tres;
+  size_t vU, vE;   // MXFP4 E3 operands as exact BF16 values (m x rp, n x rp); 0 when unused
   size_t xT, xP;
   size_t qpart_floats;
   // range-finder form: codes / scales of T and P^T; the range-finder chain
@@ -137,7 +139,9 @@ lramm_status validate(const lramm_desc* d) {
   if (d->sketch < LRAMM_SKETCH_F32 || d->sketch > LRAMM_SKETCH_E4M3) return LRAMM_ERR_INVALID_ARG;
   if (d->sketch == LRAMM_SKETCH_E4M3 && (d->a_type != LRAMM_F32 || d->b_type != LRAMM_F32))
     return LRAMM_ERR_UNSUPPORTED;
-  if (d->max_sweeps < 0 || (d->flags & ~(LRAMM_FLAG_TIMING | LRAMM_FLAG_GRAPH)) != 0) return LRAMM_ERR_INVALID_ARG;
+  if (d->max_sweeps < 0 ||
+      (d->flags & ~(LRAMM_FLAG_TIMING | LRAMM_FLAG_GRAPH | LRAMM_FLAG_SHORT_WAITS | LRAMM_FLAG_TEST_DROP_MOVE)) != 0)
+    return LRAMM_ERR_INVALID_ARG;
   if (d->lead < 0 || d->lead > d->r || d->lead_split < 0 || d->lead_split > 2) return LRAMM_ERR_INVALID_ARG;
   if (d->lead > 0 && d->lead_prec != LRAMM_P_INT8 && d->lead_prec != LRAMM_P_INT4 && d->lead_prec != LRAMM_P_E4M3)
     return LRAMM_ERR_INVALID_ARG;
@@ -216,6 +220,8 @@ void layout(lramm_plan_s* P) {
     P->sEl = b.take(sizeof(float) * d.n);
     P->tres = b.take(sizeof(float) * std::max(d.m, d.n) * d.lead);
   }
+  P->vU = d.prec[2] == LRAMM_P_MXFP4 ? b.take(2 * d.m * P->rp) : 0;
+  P->vE = d.prec[2] == LRAMM_P_MXFP4 ? b.take(2 * d.n * P->rp) : 0;
   P->bsplit_bytes = (d.a_type == LRAMM_BF16 || d.b_type == LRAMM_BF16)
                         ? sketch_bf_split_bytes(std::max(d.m, std::max(d.k, d.n)), (int)l)
                         : 0;
@@ -481,9 +487,12 @@ lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M,
   const lramm_desc& d = P->d;
   const bool coded = d.lead == 0 || (d.prec[0] != LRAMM_P_F32 && d.prec[1] != LRAMM_P_F32);
   if (tc && d.sketch != LRAMM_SKETCH_F32 && coded && d.prec[2] != LRAMM_P_F32 &&
-      tgemm_tc_supported(A, B, l, l, M, N, l) && tgemm_tc_part_floats(M, N, l) <= sketch_tc_part_floats(l))
+      tgemm_tc_supported(A, B, l, l, M, N, l) && tgemm_tc_part_floats(M, N, l) <= sketch_tc_part_floats(l)) {
+    // info word 3, bit 0: this call assembled a factor on the tensor cores
+    LRAMM_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(ws) + 3 * sizeof(int), 1, 1, s));
     return tgemm_tc(M, N, l, 1.f, A, l, B, l, 0.f, out, ldo, at<float>(ws, S.part), sketch_tc_part_floats(l),
                     at<int>(ws, 0), s);
+  }
   return sgemm(ta, tb, M, N, l, 1.f, Am, lda_s, 0, Bm, ldb_s, 0.f, out, ldo, s);
 }
 
@@ -502,9 +511,16 @@ lramm_status assemble(lramm_plan_s* P, void* ws, const SideLayout& S, int64_t M,
 // cancellation between R1 and U_s Sigma^-1 in FP32, so the tall product
 // with the well-conditioned P1 is as accurate in TF32 as P V_s.  One
 // triangular solve fewer, and the Jacobi moves and rotates half the data.
+//
+// Staggering (two operands on two streams): rec_first is recorded on s after
+// this run's first product, and wait_first is waited on before it, so that
+// the second operand's chain runs one product behind the first and each
+// operand's latency-bound orthonormalisation overlaps the other's
+// bandwidth-bound product instead of coinciding with it.
 lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, int ns, void* ws,
                         const int* s1_sigma, const int* s2_sigma, cudaStream_t s, float stopq = kJacobiQuad,
-                        bool m_only_req = false, bool* m_only_done = nullptr) {
+                        bool m_only_req = false, bool* m_only_done = nullptr, cudaEvent_t rec_first = nullptr,
+                        cudaEvent_t wait_first = nullptr) {
   const lramm_desc& d = P->d;
   const int l = P->l;
   const bool fp8 = d.sketch == LRAMM_SKETCH_E4M3;   // range-finder passes on e4m3 codes
@@ -522,8 +538,10 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
     float* Om = at<float>(ws, S.omega);
     TIMED(P, LRAMM_K_OMEGA, s, launch_gaussian(d.seed, (uint32_t)which[i], S.cols, l, Om, l, s));
     if (fp8) TIMED(P, LRAMM_K_SKETCH, s, x_codes(P, ws, S, sd[i].X, sd[i].ldx, s));
+    if (wait_first) LRAMM_CUDA_TRY(cudaStreamWaitEvent(s, wait_first, 0));
     TIMED(P, LRAMM_K_SKETCH, s,
           x_product(P, ws, *sd[i].S, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s, fp8));
+    if (rec_first) LRAMM_CUDA_TRY(cudaEventRecord(rec_first, s));
   }
   LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, d.q > 0 ? 1 : 2, false, st, s));  // Q
   for (int it = 0; it < d.q; ++it) {
@@ -544,6 +562,8 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
   jb.n = fb.n = ns;
   jb.info0 = ns == 1 ? which[0] : 0;
   jb.stopq = stopq;
+  jb.wait_cycles = (d.flags & LRAMM_FLAG_SHORT_WAITS) ? (1ll << 20) : (1ll << 30);
+  jb.drop_rank = (d.flags & LRAMM_FLAG_TEST_DROP_MOVE) ? 1 : -1;
   for (int i = 0; i < ns; ++i) {
     const SideLayout& S = *sd[i].S;
     jb.M[i] = at<float>(ws, S.R);
@@ -585,11 +605,13 @@ lramm_status ensure_streams(lramm_plan_s* P) {
     cudaStreamDestroy(P->s2);
     cudaEventDestroy(P->ev_fork);
     cudaEventDestroy(P->ev_join);
+    cudaEventDestroy(P->ev_stag);
     P->s2 = nullptr;
   }
   LRAMM_CUDA_TRY(cudaStreamCreateWithFlags(&P->s2, cudaStreamNonBlocking));
   LRAMM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
   LRAMM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  LRAMM_CUDA_TRY(cudaEventCreateWithFlags(&P->ev_stag, cudaEventDisableTiming));
   P->dev = dev;
   return LRAMM_OK;
 }
@@ -743,14 +765,82 @@ lramm_status qm_op(lramm_plan_s* P, void* ws, const QOp& L, const QOp& R, int64_
                     ldc, D, ldd, s);
 }
 
+// The MXFP4 operands of an E3 term as exact BF16 values (the same decisions
+// as quantize_mx), for the tensor-core term product.
+lramm_status mx_values(lramm_plan_s* P, void* ws, const float* Ut, const float* E2t, int64_t off, int64_t K,
+                       int64_t ldq, cudaStream_t s) {
+  const lramm_desc& d = P->d;
+  TIMED(P, LRAMM_K_QUANT, s,
+        quantize_mx_values(Ut + off, d.m, K, d.r, at<__nv_bfloat16>(ws, P->vU), ldq, s));
+  TIMED(P, LRAMM_K_QUANT, s,
+        quantize_mx_values(E2t + off, d.n, K, d.r, at<__nv_bfloat16>(ws, P->vE), ldq, s));
+  return LRAMM_OK;
+}
+
 // E3 with the lead / tail split: the first `lead` rank directions in
 // lead_prec with split-precision residuals, the rest in prec[2]; the terms
-// accumulate into D (the first one carries beta C).
+// accumulate into D (the first one carries beta C).  With an INT8 lead and an
+// INT8 or MXFP4 tail every term runs in one tensor-core launch
+// (qterms_tc: one pass over D; the MXFP4 tail as exact BF16 values);
+// otherwise each term is its own product accumulating into D.
 lramm_status e3_lead_tail(lramm_plan_s* P, const float* Ut, const float* E2t, const float* C, float* D, void* ws,
                           cudaStream_t s) {
   const lramm_desc& d = P->d;
   const int64_t r = d.r, lead = d.lead, tail = r - lead, lq = P->lq, tq = round_up(tail > 0 ? tail : 1, 32);
   const int lp = d.lead_prec, per_row = d.scale == LRAMM_S_ROWCOL;
+  const bool fused = lp == LRAMM_P_INT8 && (tail == 0 || d.prec[2] == LRAMM_P_INT8 || d.prec[2] == LRAMM_P_MXFP4);
+  if (fused) {
+    const QOp uh{at<void>(ws, P->cUh), at<float>(ws, P->sUh), nullptr};
+    const QOp ul{at<void>(ws, P->cUl), at<float>(ws, P->sUl), nullptr};
+    const QOp eh{at<void>(ws, P->cEh), at<float>(ws, P->sEh), nullptr};
+    const QOp el{at<void>(ws, P->cEl), at<float>(ws, P->sEl), nullptr};
+    float* tres = at<float>(ws, P->tres);
+    const void* Lt[4];
+    const void* Rt[4];
+    int64_t Kt[4], ldl[4], ldr[4];
+    const float* sLt[4];
+    const float* sRt[4];
+    int nt = 0;
+    auto add = [&](const void* a, const void* b, int64_t K, int64_t ld, const float* sa, const float* sb) {
+      Lt[nt] = a;
+      Rt[nt] = b;
+      Kt[nt] = K;
+      ldl[nt] = ld;
+      ldr[nt] = ld;
+      sLt[nt] = sa;
+      sRt[nt] = sb;
+      ++nt;
+    };
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut, d.m, lead, r, lp, uh, lq, s));
+    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E2t, d.n, lead, r, lp, eh, lq, s));
+    add(uh.c, eh.c, lq, lq, uh.s, eh.s);
+    if (d.lead_split >= 1) {   // + QM(U~_l^lo, E2_l^hi)
+      TIMED(P, LRAMM_K_QUANT, s, residual_rows(Ut, d.m, lead, r, lp, uh.c, lq, uh.s, per_row, tres, lead, s));
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, tres, d.m, lead, lead, lp, ul, lq, s));
+      add(ul.c, eh.c, lq, lq, ul.s, eh.s);
+    }
+    if (d.lead_split >= 2) {   // + QM(U~_l^hi, E2_l^lo)
+      TIMED(P, LRAMM_K_QUANT, s, residual_rows(E2t, d.n, lead, r, lp, eh.c, lq, eh.s, per_row, tres, lead, s));
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, tres, d.n, lead, lead, lp, el, lq, s));
+      add(uh.c, el.c, lq, lq, uh.s, el.s);
+    }
+    if (tail > 0 && d.prec[2] == LRAMM_P_MXFP4) {
+      LRAMM_TRY(mx_values(P, ws, Ut, E2t, lead, tail, tq, s));
+      add(at<void>(ws, P->vU), at<void>(ws, P->vE), tq, tq, nullptr, nullptr);
+    } else if (tail > 0) {
+      const QOp ut{at<void>(ws, P->cU), at<float>(ws, P->sU), nullptr};
+      const QOp et{at<void>(ws, P->cE2), at<float>(ws, P->sE2), nullptr};
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut + lead, d.m, tail, r, d.prec[2], ut, tq, s));
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E2t + lead, d.n, tail, r, d.prec[2], et, tq, s));
+      add(ut.c, et.c, tq, tq, ut.s, et.s);
+    }
+    if (qterms_tc_supported(nt, Lt, Rt, Kt, ldl, ldr, sLt, d.m, d.n)) {
+      TIMED(P, LRAMM_K_E3, s,
+            qterms_tc(nt, Lt, Rt, Kt, ldl, ldr, sLt, sRt, per_row, d.m, d.n, d.alpha, d.beta, C, d.ldc, D, d.ldc,
+                      at<int>(ws, 0), s));
+      return LRAMM_OK;
+    }
+  }
   const QOp uh{at<void>(ws, P->cUh), at<float>(ws, P->sUh), nullptr};
   const QOp ul{at<void>(ws, P->cUl), at<float>(ws, P->sUl), nullptr};
   const QOp eh{at<void>(ws, P->cEh), at<float>(ws, P->sEh), nullptr};
@@ -819,6 +909,19 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
                                        sizeof(float) * d.n, d.m, cudaMemcpyDeviceToDevice, s));
     TIMED(P, LRAMM_K_E3, s, sgemm(0, 1, d.m, d.n, r, d.alpha, Ut, r, 0, E2t, r, beta, D, d.ldc, s));
   } else {
+    if (d.prec[2] == LRAMM_P_MXFP4) {   // exact BF16 values on the tensor cores (one unscaled term)
+      LRAMM_TRY(mx_values(P, ws, Ut, E2t, 0, r, rp, s));
+      const void* Lt[1] = {at<void>(ws, P->vU)};
+      const void* Rt[1] = {at<void>(ws, P->vE)};
+      const int64_t Kt[1] = {rp}, ldq[1] = {rp};
+      const float* sn[1] = {nullptr};
+      if (qterms_tc_supported(1, Lt, Rt, Kt, ldq, ldq, sn, d.m, d.n)) {
+        TIMED(P, LRAMM_K_E3, s,
+              qterms_tc(1, Lt, Rt, Kt, ldq, ldq, sn, sn, 0, d.m, d.n, d.alpha, beta, C, d.ldc, D, d.ldc,
+                        at<int>(ws, 0), s));
+        return LRAMM_OK;
+      }
+    }
     const QOp u{at<void>(ws, P->cU), at<float>(ws, P->sU), at<int8_t>(ws, P->xU)};
     const QOp e2{at<void>(ws, P->cE2), at<float>(ws, P->sE2), at<int8_t>(ws, P->xE2)};
     TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut, d.m, r, r, d.prec[2], u, rp, s));
@@ -876,6 +979,7 @@ lramm_status lramm_plan_destroy(lramm_plan_t plan) {
       cudaStreamDestroy(plan->s2);
       cudaEventDestroy(plan->ev_fork);
       cudaEventDestroy(plan->ev_join);
+      cudaEventDestroy(plan->ev_stag);
     }
   }
   delete plan;
@@ -1137,7 +1241,7 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   LRAMM_CUDA_TRY(cudaStreamWaitEvent(s2, plan->ev_fork, 0));
   auto side_a = [&]() -> lramm_status {
     bool mo = false;
-    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s, stopq, m_only, &mo));
+    LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s, stopq, m_only, &mo, plan->ev_stag));
     TIMED(plan, LRAMM_K_ASSEMBLE, s,
           assemble(plan, ws, SA, d.m, r, at<float>(ws, SA.R0), at<float>(ws, SA.S1T), Ut, r, 0,
                    at<float>(ws, SA.R0), l, 0, at<float>(ws, SA.S1), r, s, true));
@@ -1155,7 +1259,8 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   // form: Z~^T = P1 Y)
   auto side_b = [&]() -> lramm_status {
     bool mo = false;
-    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2, stopq, m_only, &mo));
+    LRAMM_TRY(rsvd_sides(plan, &sd[1], &which[1], 1, ws, &s1s[1], &s2s[1], s2, stopq, m_only, &mo, nullptr,
+                         plan->ev_stag));
     TIMED(plan, LRAMM_K_ASSEMBLE, s2,
           assemble(plan, ws, SB, r, d.k, at<float>(ws, SB.S1T), at<float>(ws, SB.R0), Wt, d.k, 1,
                    at<float>(ws, SB.S1), r, 1, at<float>(ws, SB.R0), l, s2, true));

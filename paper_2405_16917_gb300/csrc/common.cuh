@@ -86,9 +86,13 @@ lramm_status launch_gaussian(uint64_t seed, uint32_t sid, int64_t rows, int64_t 
 // op(A) is M x K: ta = 0 -> A[m*lda + k], ta = 1 -> A[k*lda + m].
 // op(B) is K x N: tb = 0 -> B[k*ldb + n], tb = 1 -> B[n*ldb + k].
 // a_bf16 = 1 reads A as bfloat16 (same layout rules).
+// Predicated launches (cond != nullptr): the kernels of this library that
+// take a `cond` device word do nothing while it is 0 -- the optional extra
+// work of the CholeskyQR fallback is enqueued unconditionally and runs only
+// when a breakdown set the word.
 lramm_status sgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const void* A,
                    int64_t lda, int a_bf16, const float* B, int64_t ldb, float beta, float* C,
-                   int64_t ldc, cudaStream_t s);
+                   int64_t ldc, cudaStream_t s, const int* cond = nullptr);
 
 // smallla.cu -- small dense linear algebra, batched over up to two problems
 // (the A-side and B-side randomized SVDs run in the same launches).
@@ -122,6 +126,10 @@ struct JacobiBatch {
   // are produced by the Jacobi kernel itself where it can (l <= 320)
   int r;
   FinalProb fin[2];
+  // bounded waits of the cluster Jacobi's block moves (SM clock cycles), and
+  // the rank of a CTA that skips its first move (-1: none; failure-path tests)
+  long long wait_cycles = 1ll << 30;
+  int drop_rank = -1;
 };
 struct FinalBatch {
   FinalProb p[2];
@@ -208,6 +216,16 @@ lramm_status qgemm_tc(int prec, const void* L, const void* R, int64_t M, int64_t
                       const float* C, int64_t ldc, float* D, int64_t ldd, float* part, size_t part_floats,
                       int* status, cudaStream_t s);
 bool tgemm_tc_supported(const float* A, const float* B, int64_t lda, int64_t ldb, int64_t M, int64_t N, int64_t K);
+// qterms_tc: D = alpha sum_t fp32(fp32(L_t R_t^T) * fp32(sL_t sR_t)) + beta C
+// over up to 4 terms of BF16 operands (L_t: M x K_t, R_t: N x K_t, K-major)
+// in one pass over D; sL_t = nullptr marks an unscaled term (exact BF16
+// values, FP32 sums); scaled terms hold INT8 codes with K_t <= 1024.
+bool qterms_tc_supported(int nterms, const void* const* L, const void* const* R, const int64_t* K, const int64_t* ldl,
+                         const int64_t* ldr, const float* const* sL, int64_t M, int64_t N);
+lramm_status qterms_tc(int nterms, const void* const* L, const void* const* R, const int64_t* K, const int64_t* ldl,
+                       const int64_t* ldr, const float* const* sL, const float* const* sR, int per_row, int64_t M,
+                       int64_t N, float alpha, float beta, const float* C, int64_t ldc, float* D, int64_t ldd,
+                       int* status, cudaStream_t s);
 size_t tgemm_tc_part_floats(int64_t M, int64_t N, int64_t K);
 lramm_status tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float* A, int64_t lda, const float* B,
                       int64_t ldb, float beta, float* C, int64_t ldc, float* part, size_t part_floats, int* status,
@@ -255,6 +273,9 @@ size_t noalloc_scratch_bytes();
 // residual r = x - c s of a quantised factor.
 lramm_status quantize_mx(const float* X, int64_t rows, int64_t cols, int64_t ldx, int8_t* codes, int64_t ldc,
                          int8_t* exps, cudaStream_t s);
+// The same decisions, each element written as its exact BF16 value q 2^e.
+lramm_status quantize_mx_values(const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* vals,
+                                int64_t ldv, cudaStream_t s);
 lramm_status qgemm_mx(const int8_t* Lc, const int8_t* Le, const int8_t* Rc, const int8_t* Re, int64_t M, int64_t N,
                       int64_t K, int64_t ldl, int64_t ldr, float alpha, float beta, const float* C, int64_t ldc,
                       float* D, int64_t ldd, cudaStream_t s);

@@ -17,7 +17,8 @@ template <int TA, int TB, typename TAe>
 __global__ void __launch_bounds__(256)
 sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict__ A, int64_t lda,
              const float* __restrict__ B, int64_t ldb, float beta, float* __restrict__ C,
-             int64_t ldc) {
+             int64_t ldc, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;   // predicated launch: the flag is unset, nothing to do
   // double-buffered K tiles: the next tile's elements are fetched into
   // registers while the current one is multiplied (one barrier per tile);
   // rows padded to 68 floats (aligned float4 reads, few store conflicts)
@@ -128,29 +129,29 @@ sgemm_kernel(int64_t M, int64_t N, int64_t K, float alpha, const TAe* __restrict
 template <typename TAe>
 static lramm_status sgemm_t(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha,
                             const TAe* A, int64_t lda, const float* B, int64_t ldb, float beta,
-                            float* C, int64_t ldc, cudaStream_t s) {
+                            float* C, int64_t ldc, const int* cond, cudaStream_t s) {
   if (M <= 0 || N <= 0) return LRAMM_OK;
   if (ceil_div(M, 64) > 65535) return LRAMM_ERR_UNSUPPORTED;
   dim3 grid((unsigned)ceil_div(N, 64), (unsigned)ceil_div(M, 64));
   if (ta == 0 && tb == 0)
-    sgemm_kernel<0, 0, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    sgemm_kernel<0, 0, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cond);
   else if (ta == 0 && tb == 1)
-    sgemm_kernel<0, 1, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    sgemm_kernel<0, 1, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cond);
   else if (ta == 1 && tb == 0)
-    sgemm_kernel<1, 0, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    sgemm_kernel<1, 0, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cond);
   else
-    sgemm_kernel<1, 1, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    sgemm_kernel<1, 1, TAe><<<grid, 256, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, cond);
   return last_launch();
 }
 
 lramm_status sgemm(int ta, int tb, int64_t M, int64_t N, int64_t K, float alpha, const void* A,
                    int64_t lda, int a_bf16, const float* B, int64_t ldb, float beta, float* C,
-                   int64_t ldc, cudaStream_t s) {
+                   int64_t ldc, cudaStream_t s, const int* cond) {
   if (a_bf16)
     return sgemm_t<__nv_bfloat16>(ta, tb, M, N, K, alpha, static_cast<const __nv_bfloat16*>(A), lda,
-                                  B, ldb, beta, C, ldc, s);
+                                  B, ldb, beta, C, ldc, cond, s);
   return sgemm_t<float>(ta, tb, M, N, K, alpha, static_cast<const float*>(A), lda, B, ldb, beta, C,
-                        ldc, s);
+                        ldc, cond, s);
 }
 
 }  // namespace lramm

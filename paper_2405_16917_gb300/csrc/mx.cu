@@ -64,6 +64,40 @@ __global__ void __launch_bounds__(256) quant_mx_kernel(const float* __restrict__
   }
 }
 
+// The same quantiser writing each element's value q 2^e as bfloat16 (K
+// columns padded with zeros to ldv): q has at most two significant bits, so
+// the value is exact in BF16 for every block exponent of a finite input
+// (subnormal below 2^-126).  These are the operands of the tensor-core E3
+// product, whose BF16 products are exact.
+__global__ void __launch_bounds__(256) quant_mx_values_kernel(const float* __restrict__ X, int64_t rows, int64_t cols,
+                                                              int64_t ldx, __nv_bfloat16* __restrict__ vals,
+                                                              int64_t ldv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
+  const int64_t nb = ldv / kMxB;
+  for (int64_t row = blockIdx.x * static_cast<int64_t>(blockDim.x >> 5) + (threadIdx.x >> 5); row < rows;
+       row += warps) {
+    const float* x = X + row * ldx;
+    for (int64_t b = 0; b < nb; ++b) {
+      const int64_t j = b * kMxB + lane;
+      const float v = j < cols ? x[j] : 0.f;
+      const int e = mx_exponent(warp_max_mx(fabsf(v)));
+      const float q = round_e2m1(ldexpf(v, -e));
+      vals[row * ldv + j] = __float2bfloat16_rn(ldexpf(q, e));
+    }
+  }
+}
+
+lramm_status quantize_mx_values(const float* X, int64_t rows, int64_t cols, int64_t ldx, __nv_bfloat16* vals,
+                                int64_t ldv, cudaStream_t s) {
+  if (rows <= 0) return LRAMM_OK;
+  if (ldv % kMxB || ldv < cols) return LRAMM_ERR_INVALID_ARG;
+  int64_t g = ceil_div(rows, 8);
+  if (g > 152 * 16) g = 152 * 16;
+  quant_mx_values_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(X, rows, cols, ldx, vals, ldv);
+  return last_launch();
+}
+
 lramm_status quantize_mx(const float* X, int64_t rows, int64_t cols, int64_t ldx, int8_t* codes, int64_t ldc,
                          int8_t* exps, cudaStream_t s) {
   if (rows <= 0) return LRAMM_OK;

@@ -323,6 +323,235 @@ __global__ void qgemm_tc_reduce_kernel(QtcParams p) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// A sum of QM terms in one pass over the output (the lead / tail E3 of
+// Algorithm 3 with split-precision residuals):
+//   D = alpha sum_t fp32(fp32(acc_t) * fp32(sL_t[i] sR_t[j])) + beta C,
+//   acc_t[i][j] = sum_k L_t[i][k] R_t[j][k]    (BF16 operands, K-major)
+// Term t accumulates in its own TMEM region (columns t * BN ..); the K blocks
+// of all terms stream through one ring.  Scaled terms hold INT8 codes (exact
+// sums of at most 1024 products); an unscaled term holds exact BF16 values
+// (the MXFP4 tail: e2m1 code times its block's power of two) whose products
+// the tensor core sums in FP32.  The epilogue adds the terms in order, each
+// rounded as a separate pass would round it:
+//   o = fp32(alpha T_0) (+ beta C), then o = fp32(o + fp32(alpha T_t)).
+constexpr int kMaxTerms = 4;
+constexpr int kTermBN = 64;   // output columns per CTA: 4 regions of 64 TMEM columns, two CTAs per SM
+
+struct QtermsParams {
+  int64_t M, N;
+  int nterms, kb_total;
+  int kb_start[kMaxTerms + 1];   // first ring block of each term; kb_start[nterms] = kb_total
+  const float* sL[kMaxTerms];    // nullptr: unscaled term
+  const float* sR[kMaxTerms];
+  int per_row;
+  int stages;
+  uint32_t a_bytes, b_bytes, tmem_cols;
+  float alpha, beta;
+  const float* C;
+  int64_t ldc;
+  float* D;
+  int64_t ldd;
+  int tma_store;
+  int* status;
+};
+
+__global__ void __launch_bounds__(kQThreads, 2)
+qterms_tc_kernel(const __grid_constant__ CUtensorMap tmL0, const __grid_constant__ CUtensorMap tmL1,
+                 const __grid_constant__ CUtensorMap tmL2, const __grid_constant__ CUtensorMap tmL3,
+                 const __grid_constant__ CUtensorMap tmR0, const __grid_constant__ CUtensorMap tmR1,
+                 const __grid_constant__ CUtensorMap tmR2, const __grid_constant__ CUtensorMap tmR3,
+                 const __grid_constant__ CUtensorMap tmD, QtermsParams p) {
+  constexpr int kStageK = kQKB / 2;   // 64 BF16 per stage
+  extern __shared__ uint8_t qt_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(qt_smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + static_cast<size_t>(p.stages) * p.a_bytes;
+  __shared__ __align__(8) uint64_t full_bar[kQMaxStages], empty_bar[kQMaxStages], tmem_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  __shared__ float sR_sh[kMaxTerms][kTermBN];
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t n0 = static_cast<int64_t>(blockIdx.x) * kTermBN;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.y) * kQM;
+  const int nkb = p.kb_total;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tmem_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+  const uint32_t tx_bytes = p.a_bytes + p.b_bytes;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: the terms' K blocks in order.  Each term's loads
+    // name their own tensor-map parameters directly (no map is picked
+    // through a runtime index).
+    int issued = 0;
+    bool ok = true;
+    auto load_term = [&](const CUtensorMap* ml, const CUtensorMap* mr, int t) {
+      for (int i = p.kb_start[t]; ok && i < p.kb_start[t + 1]; ++i) {
+        const int s = i % p.stages;
+        if (i >= p.stages && !mbar_wait(&empty_bar[s], ((i / p.stages) & 1) ^ 1, abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full_bar[s], tx_bytes);
+        const int k0 = (i - p.kb_start[t]) * kStageK;
+        tma_load_2d(sA + static_cast<size_t>(s) * p.a_bytes, ml, &full_bar[s], k0, static_cast<int>(m0));
+        tma_load_2d(sB + static_cast<size_t>(s) * p.b_bytes, mr, &full_bar[s], k0, static_cast<int>(n0));
+        ++issued;
+      }
+    };
+    load_term(&tmL0, &tmR0, 0);
+    if (p.nterms > 1) load_term(&tmL1, &tmR1, 1);
+    if (p.nterms > 2) load_term(&tmL2, &tmR2, 2);
+    if (p.nterms > 3) load_term(&tmL3, &tmR3, 3);
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      const int first = issued > p.stages ? issued - p.stages : 0;
+      for (int i = first; i < issued; ++i) {
+        volatile int zero = 0;
+        mbar_wait(&full_bar[i % p.stages], (i / p.stages) & 1, &zero);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: term t into TMEM columns t * BN ..
+    const uint32_t idesc = idesc_kind<kKindBF16>(kQM, kTermBN);
+    int t = 0;
+    for (int i = 0; i < nkb; ++i) {
+      while (i >= p.kb_start[t + 1]) ++t;
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t a_base = smem_u32(sA + static_cast<size_t>(s) * p.a_bytes);
+      const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * p.b_bytes);
+      const uint32_t d = tmem + static_cast<uint32_t>(t * kTermBN);
+      const bool first = i == p.kb_start[t];
+#pragma unroll
+      for (int kk = 0; kk < kQKB / 32; ++kk)  // 16 BF16 (32 bytes) of K per instruction
+        mma_kind<kKindBF16>(d, kmajor_sw128_desc(a_base + kk * 32), kmajor_sw128_desc(b_base + kk * 32), idesc,
+                            (!first || kk > 0) ? 1u : 0u);
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&tmem_bar);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lanes 32q .. 32q+31 are rows m0 + 32q + lane
+    const int q = warp & 3;
+    const int et = threadIdx.x - 64;   // 0 .. 127
+    for (int e = et; e < p.nterms * kTermBN; e += 128) {
+      const int t = e / kTermBN, j = e - t * kTermBN;
+      const int64_t col = n0 + j;
+      sR_sh[t][j] = col < p.N ? (p.sR[t] ? (p.per_row ? p.sR[t][col] : p.sR[t][0]) : 1.f) : 0.f;
+    }
+    epi_bar();
+    volatile int zero = 0;  // wait for the MMAs even after an abort: they read shared memory
+    const bool ok = mbar_wait(&tmem_bar, 0, &zero);
+    tc_fence_after();
+    const int64_t rbase = m0 + q * 32;
+    const int64_t row_own = rbase + lane;
+    float sl_own[kMaxTerms];
+#pragma unroll
+    for (int t = 0; t < kMaxTerms; ++t)
+      sl_own[t] = (t < p.nterms && row_own < p.M)
+                      ? (p.sL[t] ? (p.per_row ? p.sL[t][row_own] : p.sL[t][0]) : 1.f)
+                      : 0.f;
+    for (int c0 = 0, nb = 0; c0 < kTermBN; c0 += 32, ++nb) {
+      // this lane's row, columns c0 .. c0+31: the terms combined in order
+      float o[32];
+      for (int t = 0; t < p.nterms; ++t) {
+        float v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * kTermBN + c0), v);
+        const bool scaled = p.sL[t] != nullptr;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const float term = scaled ? __fmul_rn(p.alpha, __fmul_rn(v[j], __fmul_rn(sl_own[t], sR_sh[t][c0 + j])))
+                                    : __fmul_rn(p.alpha, v[j]);
+          o[j] = t == 0 ? term : __fadd_rn(o[j], term);
+        }
+        if (t == 0 && p.beta != 0.f && row_own < p.M) {   // beta C joins the first term
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t col = n0 + c0 + j;
+            if (col < p.N) o[j] = fmaf(p.beta, p.C[row_own * p.ldc + col], o[j]);
+          }
+        }
+      }
+      if (p.tma_store) {
+        // swizzled 32 x 32 staging block in the (now idle) operand ring, stored by TMA
+        float* stg = reinterpret_cast<float*>(sA) + (q * 2 + (nb & 1)) * 1024;
+        if (nb >= 2) {
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          __syncwarp();
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          *reinterpret_cast<float4*>(stg + lane * 32 + ((c ^ (lane & 7)) << 2)) =
+              make_float4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0 && ok && rbase < p.M && n0 + c0 < p.N) {   // TMA clips the block at M and N
+          asm volatile(
+              "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                  reinterpret_cast<uint64_t>(&tmD)),
+              "r"(static_cast<int>(n0 + c0)), "r"(static_cast<int>(rbase)), "r"(smem_u32(stg))
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      } else {
+        // 32 x 32 block transposed through shared memory: each store writes
+        // 32 consecutive columns of one row
+        float* T = reinterpret_cast<float*>(sA) + q * (32 * 33);
+        __syncwarp();
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) T[lane * 33 + jj] = o[jj];
+        __syncwarp();
+        const int64_t col = n0 + c0 + lane;
+        const bool col_ok = ok && col < p.N;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int64_t row = rbase + r;
+          if (!col_ok || row >= p.M) continue;
+          p.D[row * p.ldd + col] = T[r * 33 + lane];
+        }
+        __syncwarp();
+      }
+    }
+    if (p.tma_store) {
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      __syncwarp();
+    }
+    if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
 constexpr int kQSmemBudget = 232448 - 4096;  // opt-in maximum minus alignment slack and static shared memory
 
 struct QtcShape {
@@ -504,6 +733,69 @@ lramm_status tgemm_tc(int64_t M, int64_t N, int64_t K, float alpha, const float*
   p.scaled = 0;
   p.status = status;
   return launch_tc(kKindTF32, A, B, M, N, K, lda, ldb, p, s);
+}
+
+bool qterms_tc_supported(int nterms, const void* const* L, const void* const* R, const int64_t* K, const int64_t* ldl,
+                         const int64_t* ldr, const float* const* sL, int64_t M, int64_t N) {
+  if (nterms < 1 || nterms > kMaxTerms) return false;
+  for (int t = 0; t < nterms; ++t) {
+    if (!tc_operands_ok(kKindBF16, L[t], R[t], ldl[t], ldr[t], M, N, K[t])) return false;
+    if (sL[t] && K[t] > kQChunkBlocks * (kQKB / 2)) return false;   // exact integer sums: at most 1024 products
+  }
+  return M / kQM < 65535;
+}
+
+lramm_status qterms_tc(int nterms, const void* const* L, const void* const* R, const int64_t* K, const int64_t* ldl,
+                       const int64_t* ldr, const float* const* sL, const float* const* sR, int per_row, int64_t M,
+                       int64_t N, float alpha, float beta, const float* C, int64_t ldc, float* D, int64_t ldd,
+                       int* status, cudaStream_t s) {
+  if (!qterms_tc_supported(nterms, L, R, K, ldl, ldr, sL, M, N)) return LRAMM_ERR_UNSUPPORTED;
+  if (beta != 0.f && !C) return LRAMM_ERR_INVALID_ARG;
+  QtermsParams p{};
+  p.M = M;
+  p.N = N;
+  p.nterms = nterms;
+  constexpr int kStageK = kQKB / 2;
+  int kb = 0;
+  for (int t = 0; t < nterms; ++t) {
+    p.kb_start[t] = kb;
+    kb += static_cast<int>(ceil_div(K[t], kStageK));
+    p.sL[t] = sL[t];
+    p.sR[t] = sL[t] ? sR[t] : nullptr;
+  }
+  p.kb_start[nterms] = kb;
+  for (int t = nterms + 1; t <= kMaxTerms; ++t) p.kb_start[t] = kb;
+  p.kb_total = kb;
+  p.per_row = per_row;
+  p.a_bytes = kQM * kQKB;
+  p.b_bytes = kTermBN * kQKB;
+  p.stages = 3;
+  p.tmem_cols = static_cast<uint32_t>(kMaxTerms * kTermBN);   // 256: two CTAs per SM
+  p.alpha = alpha;
+  p.beta = beta;
+  p.C = C;
+  p.ldc = ldc;
+  p.D = D;
+  p.ldd = ldd;
+  p.status = status;
+  CUtensorMap mL[kMaxTerms], mR[kMaxTerms];
+  for (int t = 0; t < kMaxTerms; ++t) {
+    const int u = t < nterms ? t : 0;   // unused slots repeat term 0's maps
+    if (!make_map_2d(&mL[t], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, L[u], K[u], M, ldl[u] * 2, kQKB / 2, kQM,
+                     CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map_2d(&mR[t], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, R[u], K[u], N, ldr[u] * 2, kQKB / 2, kTermBN,
+                     CU_TENSOR_MAP_SWIZZLE_128B))
+      return LRAMM_ERR_CUDA;
+  }
+  CUtensorMap mD;
+  p.tma_store = beta == 0.f && (reinterpret_cast<uintptr_t>(D) % 16) == 0 && (ldd * 4) % 16 == 0 && ldd >= N &&
+                make_map_2d(&mD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, D, N, M, ldd * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (!p.tma_store) mD = mL[0];   // unused
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(qterms_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const dim3 grid(static_cast<unsigned>(ceil_div(N, kTermBN)), static_cast<unsigned>(ceil_div(M, kQM)));
+  qterms_tc_kernel<<<grid, kQThreads, smem, s>>>(mL[0], mL[1], mL[2], mL[3], mR[0], mR[1], mR[2], mR[3], mD, p);
+  return last_launch();
 }
 
 }  // namespace lramm

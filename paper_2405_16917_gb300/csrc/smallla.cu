@@ -588,11 +588,11 @@ __device__ __forceinline__ void jc_mbar_init(uint64_t* bar) {
 __device__ __forceinline__ void jc_mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(jc_smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Bounded wait on a phase parity (about half a second of SM clocks); false
-// when the limit expires.
-__device__ __forceinline__ bool jc_mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait on a phase parity (`limit` SM clock cycles: about half a
+// second by default); false when the limit expires.
+__device__ __forceinline__ bool jc_mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
-  while (clock64() - t0 < (1ll << 30)) {
+  while (clock64() - t0 < limit) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -653,6 +653,8 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
     if (C > 1) jc_mbar_expect(&rx_bar[0], rx_bytes);   // move 0
   }
   bool failed = false;
+  int e_fail = -1;        // the move whose wait expired (this CTA)
+  bool any_fail = false;  // some CTA of the cluster gave up (known to all after a sweep)
   for (int half = 0; half < 2; ++half) {
     float* buf = sm + half * bufsz;
     const int blk = 2 * rank + half;
@@ -743,19 +745,20 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
         __syncthreads();
         if (tid == 0 && !failed) {
           // after a timeout nothing more is armed, pushed or awaited: the
-          // neighbours' waits expire in turn and every CTA runs to the end
+          // neighbours' waits expire in turn, the failure reaches every CTA
+          // at the sweep's end, and each drains the copies issued into it
           jc_mbar_expect(&rx_bar[(e + 1) & 1], rx_bytes);   // next move; its previous phase is complete
-          if (rank >= 1) {  // bottom -> left neighbour's right landing buffer
+          const bool drop = rank == jb.drop_rank && e == 0;   // failure-path tests only
+          if (rank >= 1 && !drop) {  // bottom -> left neighbour's right landing buffer
             int t2, b2, l2, r2;
             jc5_bufs(rank - 1, C, e, t2, b2, l2, r2);
             jc_push(sm + bb_ * bufsz, sm + r2 * bufsz, &rx_bar[e & 1], rank - 1, blk_bytes);
           }
-          if (rank <= C - 2) {  // top (CTA 0: bottom) -> right neighbour's left landing buffer
+          if (rank <= C - 2 && !drop) {  // top (CTA 0: bottom) -> right neighbour's left landing buffer
             int t2, b2, l2, r2;
             jc5_bufs(rank + 1, C, e, t2, b2, l2, r2);
             jc_push(sm + (rank == 0 ? bb_ : bt_) * bufsz, sm + l2 * bufsz, &rx_bar[e & 1], rank + 1, blk_bytes);
           }
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
         // block ids of the slots after this move, one slot per thread (read
         // here, written after the barrier below): slot 0 keeps its block,
@@ -766,11 +769,12 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
           const int src = tid == 0 ? 0 : tid == 2 ? 1 : (tid & 1) == 0 ? tid - 2 : tid == nslots - 1 ? nslots - 2 : tid + 2;
           nid = s_ids[src];
         }
-        if (!failed && !jc_mbar_wait(&rx_bar[e & 1], (e >> 1) & 1)) {
+        if (!failed && !jc_mbar_wait(&rx_bar[e & 1], (e >> 1) & 1, jb.wait_cycles)) {
           failed = true;
           set_status(status, LRAMM_ERR_TIMEOUT);
         }
         failed = __syncthreads_or(failed);   // one decision for the whole CTA
+        if (failed && e_fail < 0) e_fail = e;
         if (tid < nslots) s_ids[tid] = nid;
         ++e;
       }
@@ -783,16 +787,33 @@ jacobi_pair2_kernel(JacobiBatch jb, int l, int ls, int b, int max_sweeps, float 
     // a further sweep would rotate nothing: stop after this one.
     if (lane == 0) atomicMax(&s_rmax, __float_as_int(rmax));
     __syncthreads();
-    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = s_rmax;
+    // a CTA that gave up publishes INT_MAX: every CTA stops after this sweep
+    if (tid < C) *cluster.map_shared_rank(&s_flags[rank], tid) = failed ? INT_MAX : s_rmax;
     cluster.sync();
     int mx = 0;
     for (int c = 0; c < C; ++c) mx = max(mx, s_flags[c]);
+    if (mx == INT_MAX) {
+      any_fail = true;
+      break;
+    }
     if (!(__int_as_float(mx) > jb.stopq * tol)) break;
   }
-  if (sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
+  if (!any_fail && sweep >= max_sweeps && tid == 0 && rank == 0) set_status(status, LRAMM_WARN_NOCONV);
   if (tid == 0 && rank == 0 && status) status[1 + jb.info0 + prob] = sweep < max_sweeps ? sweep + 1 : sweep;
-  // no CTA leaves while a bulk copy it issued may still be writing a peer
-  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  if (any_fail) {
+    // Every push of every CTA was issued before the barrier above, and each
+    // was aimed at a move phase its receiver had armed (a CTA arms a move's
+    // phase one move ahead, and its neighbours stop pushing at most one move
+    // after it stops).  A CTA whose wait expired drains the two phases it
+    // left armed -- the move it gave up on and the next -- with bounded
+    // waits, then the cluster barrier below: no bulk copy is still writing
+    // into any CTA's shared memory when the CTAs go on (and exit).
+    if (e_fail >= 0 && tid == 0)
+      for (int mv = e_fail; mv <= e_fail + 1; ++mv) jc_mbar_wait(&rx_bar[mv & 1], (mv >> 1) & 1, jb.wait_cycles);
+    __syncthreads();
+  }
+  // (a completed push needs no wait of its sender: each landed in a phase its
+  // receiver awaited, which the sweep loop's waits or the drain above cover)
   cluster.sync();
   int bt_, bb_, bfl, bfr;
   jc5_bufs(rank, C, e, bt_, bb_, bfl, bfr);
