@@ -4,7 +4,9 @@ lramm_32768 (m = n = 32768, k = 4096, sigma_i = (1+i)^-1.5, r = 128, p = 16,
 q = 2, INT8 factors): the oracle's randomized SVDs run in full (FP64); the
 m x n output is compared on a seeded sample of 256 rows, which the oracle
 computes exactly (with per-row scales on the left factor and per-column
-scales on E2, a row of D depends only on that row of U~).
+scales on E2, a row of D depends only on that row of U~).  Its "forward and
+backward" runs the same operands through the range-finder form (forward on
+the sampled rows, both gradients in full).
 
 rf_linear (X 16384 x 4096 BF16, W 4096 x 11008 FP32, sigma_i =
 exp(-i/128) + 1e-3, r = 384, p = 16, q = 1): forward in FP32 and with FP8
@@ -125,5 +127,41 @@ def test_rf_linear_backward(L, rf):
     dX, dW = (t.cpu().numpy().astype(np.float64) for t in L.rf_backward(plan, X, W, G, ws=ws))
     assert L.status_read(ws) == 0
     rX, rW = oracle.rf.rf_backward(Xh, Wh, G.cpu().numpy(), c["r"], c["p"], c["q"], workloads.SEED_SKETCH)
+    assert oracle.lramm.rel_fro(dX, rX) <= 1e-4
+    assert oracle.lramm.rel_fro(dW, rW) <= 1e-4
+
+
+def test_lramm_32768_range_finder_forward_backward(L, big):
+    """The 32768 workload's "forward and backward": its operands through the
+    range-finder form C = (A Q)(Q^T B) (the differentiable form; the SVD form
+    has no backward), FP32 path.  Forward on the 256 sampled rows <= 1e-5;
+    the hand-written backward (dX = G P Q^T, dW through the QR adjoints of
+    the q = 2 power chain) for a dense Gaussian G against the oracle's
+    gradients, relative Frobenius <= 1e-4 over the full 32768 x 4096 and
+    4096 x 32768 gradients."""
+    A, B, _, rows, _ = big
+    c = workloads.CONFIGS["lramm_32768"]
+    plan = L.Plan(c["m"], c["n"], c["k"], c["r"], c["p"], c["q"], seed=workloads.SEED_SKETCH, prec=(0, 0, 0),
+                  sketch=L.SKETCH_F32)
+    ws = plan.workspace()
+    C = L.rf_forward(plan, A, B, ws=ws)
+    assert L.status_read(ws) == 0
+    Cs = C[torch.from_numpy(rows).cuda()].cpu().numpy().astype(np.float64)
+    del C
+    torch.cuda.empty_cache()
+    g = torch.Generator(device=A.device)
+    g.manual_seed(23)
+    G = torch.randn((c["m"], c["n"]), generator=g, device=A.device, dtype=torch.float32)
+    dX, dW = L.rf_backward(plan, A, B, G, ws=ws)
+    assert L.status_read(ws) == 0
+    dX, dW = dX.cpu().numpy().astype(np.float64), dW.cpu().numpy().astype(np.float64)
+    Gh = G.cpu().numpy()
+    del G, ws
+    torch.cuda.empty_cache()
+    Ah, Bh = A.cpu().numpy(), B.cpu().numpy()
+    T, P, _ = oracle.rf.rf_factors(Ah, Bh, c["r"], c["p"], c["q"], workloads.SEED_SKETCH)
+    assert oracle.lramm.rel_fro(Cs, T[rows] @ P) <= 1e-5
+    del T, P
+    rX, rW = oracle.rf.rf_backward(Ah, Bh, Gh, c["r"], c["p"], c["q"], workloads.SEED_SKETCH)
     assert oracle.lramm.rel_fro(dX, rX) <= 1e-4
     assert oracle.lramm.rel_fro(dW, rW) <= 1e-4

@@ -6,8 +6,10 @@ the C ABI against the oracle (oracle/mixed.py).
 * Block-scaled product: exact block sums; the sum over blocks is FP32 on the
   GPU, so |D - ref| <= nb 2^-24 sum_b |term_b| (+ one rounding).
 * Lead / tail chain on identical FP32 factors: every QM term is formed
-  exactly as the oracle forms it; the terms are added in FP32 (GPU) vs FP64
-  (oracle): relative Frobenius <= 1e-6.
+  exactly as the oracle forms it (integer E1, E2 and lead terms are
+  bit-identical); the MXFP4 tail sums its blocks and the terms are added in
+  FP32 (GPU) vs FP64 (oracle): element by element within those sums' FP32
+  bounds (tests/elementwise.py).
 * End to end (RSVD in FP32 on the GPU, FP64 in the oracle): the
   quantisation-noise criterion of the other end-to-end tests.
 """
@@ -16,6 +18,7 @@ import pytest
 
 import oracle
 import workloads
+from tests import elementwise as EW
 from tests.test_gpu_parity import _factors, quantised_agreement
 
 pytestmark = pytest.mark.gpu
@@ -88,7 +91,26 @@ def test_chain_lead_tail_matches_oracle(L, lead, split, tail, scale):
     plan = L.Plan(m, n, k, r, 0, 0, prec=prec, scale=scale, lead=lead, lead_prec=1, lead_split=split)
     D = L.chain(plan, dev(Ut), dev(Vt), dev(Wt), dev(Zt)).cpu().numpy().astype(np.float64)
     ref = MX.chain_lead_tail(Ut, Vt.T, Wt.T, Zt.T, prec, lead, 1, split, scale)
-    assert oracle.lramm.rel_fro(D, ref) <= 1e-6
+    bound = EW.lead_tail_bound(Ut, Vt, Wt, Zt, prec, lead, 1, split, scale)
+    bad = np.abs(D - ref) > bound
+    assert not bad.any(), "%d entries outside the bound, worst %.3g x bound" % (
+        int(bad.sum()), float(np.max(np.abs(D - ref) / bound)))
+
+
+@pytest.mark.parametrize("tail", [4, 1])
+def test_chain_lead_tail_alpha_beta(L, tail):
+    """D = alpha E3 + beta C with the lead / tail E3 in one tensor-core pass
+    (INT8 lead with both residuals; MXFP4 or INT8 tail): beta C joins the
+    first term, as when every term is its own pass."""
+    m, n, k, r, lead = 260, 300, 200, 48, 16
+    Ut, Vt, Wt, Zt = _factors(m, n, k, r, 63)
+    C = np.random.default_rng(64).standard_normal((m, n)).astype(np.float32)
+    prec = (1, 1, tail)
+    plan = L.Plan(m, n, k, r, 0, 0, prec=prec, lead=lead, lead_prec=1, lead_split=2, alpha=0.75, beta=-1.5)
+    D = L.chain(plan, dev(Ut), dev(Vt), dev(Wt), dev(Zt), C=dev(C)).cpu().numpy().astype(np.float64)
+    ref = MX.chain_lead_tail(Ut, Vt.T, Wt.T, Zt.T, prec, lead, 1, 2, alpha=0.75, beta=-1.5, C=C)
+    bound = EW.lead_tail_bound(Ut, Vt, Wt, Zt, prec, lead, 1, 2, alpha=0.75, beta=-1.5, C=C)
+    assert np.all(np.abs(D - ref) <= bound), float(np.max(np.abs(D - ref) / bound))
 
 
 def test_chain_mxfp4_everywhere(L):
@@ -100,19 +122,24 @@ def test_chain_mxfp4_everywhere(L):
     assert oracle.lramm.rel_fro(D, ref) <= 1e-5
 
 
-def test_lead_tail_end_to_end_bf16(L):
+@pytest.mark.parametrize("sketch", ["f32", "tf32"])
+def test_lead_tail_end_to_end_bf16(L, sketch):
     """The 8192 workload's recipe at 512: BF16 operands, INT8 lead with both
-    residuals, MXFP4 tail; the lead split cuts the error of the all-4-bit E3."""
+    residuals, MXFP4 tail; the lead split cuts the error of the all-4-bit E3.
+    With tensor-core products (the bench's mode: BF16 operands on kind::f16
+    and the factors assembled in TF32, info word 3) and without."""
     m = n = k = 512
     A, B = workloads.operands("lramm_8192", scale=(m, n, k))
     Ab = torch.from_numpy(A.astype(np.float32)).to(torch.bfloat16)
     Bb = torch.from_numpy(B.astype(np.float32)).to(torch.bfloat16)
     A32, B32 = Ab.float().numpy(), Bb.float().numpy()
     r, p, q, lead = 64, 8, 1, 16
+    sk = L.SKETCH_TF32 if sketch == "tf32" else L.SKETCH_F32
     plan = L.Plan(m, n, k, r, p, q, seed=7, prec=(1, 1, 4), a_type=L.BF16, b_type=L.BF16, lead=lead, lead_prec=1,
-                  lead_split=2)
+                  lead_split=2, sketch=sk)
     ws = plan.workspace()
     D = L.matmul(plan, Ab.cuda(), Bb.cuda(), ws=ws).cpu().numpy().astype(np.float64)
+    assert (int(L.info_read(ws, 4)[3]) & 1) == (1 if sketch == "tf32" else 0)
     assert L.status_read(ws) == 0
     fac = oracle.lramm.factors(A32, B32, r, p, q, 7)
     ref_q = MX.chain_lead_tail(*fac, (1, 1, 4), lead, 1, 2)

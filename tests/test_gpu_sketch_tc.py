@@ -104,12 +104,13 @@ def test_sketch_product_bf16_operand(L, rows, cols, l, transpose, sketch):
 
 
 @pytest.mark.parametrize("m,k,r,p,q", [(16384, 600, 128, 16, 2), (20000, 500, 60, 4, 0), (16400, 700, 256, 16, 1),
-                                       (4096, 1000, 128, 16, 2)])
+                                       (4096, 1000, 128, 16, 2), (3000, 800, 272, 16, 1), (2100, 900, 20, 8, 2)])
 def test_rsvd_tf32_split_gram(L, m, k, r, p, q):
-    """TF32 mode runs the CholeskyQR Grams of tall sketches (>= 16384 rows) in
-    split TF32 on the tensor cores (l = 144, 64, 272; K tails): orthogonality
-    to working precision after the two final passes, and the rank-r product
-    within a few TF32 roundings."""
+    """TF32 mode runs the CholeskyQR Grams of tall sketches (>= 2048 rows) in
+    split TF32 on the tensor cores (l = 144, 64, 272, 288, 28; ragged row
+    counts; l > 256 takes two MMA column groups): orthogonality to working
+    precision after the two final passes, and the rank-r product within a
+    few TF32 roundings."""
     X = workloads.lowrank(m, k, workloads.spectrum("poly1", min(m, k)), 88 + m).astype(np.float32)
     plan = L.Plan(m, m, k, r, p, q, seed=7, sketch=L.SKETCH_TF32)
     ws = plan.workspace()
