@@ -2,15 +2,17 @@
 """LRAMM benchmark: effective TFLOP/s (2mnk / t) of Algorithm 3 on one GB300.
 
 A step is one lramm_matmul call (RSVD of A and B, quantisation, E1/E2/E3
-chain) on the m=n=k=4096 workload (FP32 operands, sigma_i = (1+i)^-1,
-r=256, p=16, q=2) with inputs resident in HBM.  The L2 is flushed (256 MB
-write) before every timed step, outside the step's event pair.
+chain) with inputs resident in HBM.  Default workload: the rectangular
+m = n = 32768, k = 4096 product (FP32 operands, sigma_i = (1+i)^-1.5,
+r = 128, p = 16, q = 2, INT8 factors with per-row / per-column scales).
+The L2 is flushed (256 MB write) before every timed step, outside the
+step's event pair.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--variant int8|fp32|e4m3]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload W] [--variant int8|fp32|e4m3|...]
   python bench.py --impl reference ...   (the CPU oracle, timed on host cores)
 
-Other workloads (--workload): lramm_512, lramm_8192, lramm_32768 run the same
-step; rf_linear runs the range-finder form as a linear layer, one step =
+Other workloads (--workload): lramm_512, lramm_4096, lramm_8192 run the
+same step; rf_linear runs the range-finder form as a linear layer, one step =
 forward C ~ X W plus the hand-written backward (dX, dW), effective
 TFLOP/s = 6mnk / t (the dense layer's forward and backward GEMMs).
 
@@ -194,21 +196,54 @@ def fp32_alu_peak_tflops(sm_mhz):
 
 
 # ------------------------------------------------------------------ CPU oracle
-def cpu_oracle_step(A, B, cfg, prec, lead=None):
+def cpu_oracle_step(A, B, cfg, prec, lead=None, rows=None):
+    """Seconds of one oracle LRAMM step on A, B (FP32 numpy).
+
+    rows: a sorted sample of A's row indices, for outputs too large to form
+    on the host: the randomized SVDs of both operands and E1, E2 run in full,
+    E3 (whose cost is proportional to the rows of U~; per-row scales make
+    each output row independent of the others) on the sampled rows only,
+    its time scaled by m / len(rows)."""
     import oracle
+    r, p, q = cfg["r"], cfg["p"], cfg["q"]
     t0 = time.perf_counter()
+    if rows is None:
+        if lead:
+            fac = oracle.lramm.factors(A, B, r, p, q, workloads.SEED_SKETCH)
+            oracle.mixed.chain_lead_tail(*fac, prec, min(lead[0], r), lead[1], lead[2])
+        else:
+            oracle.lramm.lramm(A, B, r, p, q, workloads.SEED_SKETCH, prec)
+        return time.perf_counter() - t0
+    Ut, V, W, Zt = oracle.lramm.factors(A, B, r, p, q, workloads.SEED_SKETCH)
+    E1 = oracle.mixed.qm_any(np.asarray(V, np.float32).T, W, prec[0], oracle.quant.SCALE_ROWCOL)
+    E2 = oracle.mixed.qm_any(E1, Zt, prec[1], oracle.quant.SCALE_ROWCOL)
+    t1 = time.perf_counter()
+    Us = Ut[rows]
     if lead:
-        fac = oracle.lramm.factors(A, B, cfg["r"], cfg["p"], cfg["q"], workloads.SEED_SKETCH)
-        oracle.mixed.chain_lead_tail(*fac, prec, min(lead[0], cfg["r"]), lead[1], lead[2])
+        oracle.mixed.e3_lead_tail(Us, E2, prec[2], min(lead[0], r), lead[1], lead[2])
     else:
-        oracle.lramm.lramm(A, B, cfg["r"], cfg["p"], cfg["q"], workloads.SEED_SKETCH, prec)
-    return time.perf_counter() - t0
+        oracle.mixed.qm_any(Us, E2, prec[2], oracle.quant.SCALE_ROWCOL)
+    t2 = time.perf_counter()
+    return (t1 - t0) + (t2 - t1) * A.shape[0] / len(rows)
+
+
+# outputs with more entries than this are formed on a seeded row sample
+# (the error against the FP64 product and the oracle's E3)
+SAMPLE_ENTRIES = 1 << 28
+SAMPLE_ROWS = 2048
+
+
+def sample_rows(m, n):
+    """The seeded row sample of an m x n output (None: all rows)."""
+    if m * n <= SAMPLE_ENTRIES:
+        return None
+    return np.sort(np.random.default_rng(5).choice(m, SAMPLE_ROWS, replace=False))
 
 
 def cpu_sample(name):
-    """A bounded sample of the workload for the CPU oracle: the full workload
-    when it is small, else a stand-in with every size halved until one oracle
-    step is expected to take well under ~15 s."""
+    """A bounded stand-in of the workload for the CPU oracle: every size
+    halved (r and p too) until the problem has at most 4096^3 multiply-adds,
+    for when the full-shape oracle step would not fit the run's time."""
     c = dict(workloads.CONFIGS[name])
     sc = (c["m"], c["n"], c["k"])
     while sc[0] * sc[1] * sc[2] > 4096 ** 3:
@@ -259,22 +294,35 @@ def run_reference(args):
         step = lambda: cpu_rf_step(X, W, G, c, prec[2])  # noqa: E731
         what = "oracle range-finder forward + backward"
     else:
-        A, B, c = cpu_sample(args.workload)
-        # one untimed probe step sizes the sample: the whole run (warm-up +
-        # timed steps) is kept to about two minutes of host work by halving
-        # every size of the stand-in while a step would take longer
-        budget = 120.0 / max(1, args.steps + args.warmup)
-        t_probe = cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))
-        while t_probe > budget and min(c["m"], c["n"], c["k"]) > 512:
-            sc = tuple(max(256, x // 2) for x in (c["m"], c["n"], c["k"]))
-            c["r"], c["p"] = max(16, c["r"] // 2), max(4, c["p"] // 2)
-            A, B = workloads.operands(args.workload, scale=sc)
-            A, B = A.astype(np.float32), B.astype(np.float32)
-            c["m"], c["n"], c["k"] = sc
-            t_probe = cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))
+        # the full workload, E3 on a seeded row sample when the output is
+        # too large for the host (see cpu_oracle_step); one untimed probe step
+        # checks that the run (warm-up + timed steps) stays within about two
+        # and a half minutes of host work, else every size of a stand-in is
+        # halved while a step would take longer
+        lead = LEADS.get(args.variant)
+        c = dict(workloads.CONFIGS[args.workload])
+        budget = 150.0 / max(1, args.steps + args.warmup)
+        A, B = workloads.operands(args.workload)
+        A, B = A.astype(np.float32), B.astype(np.float32)
+        rows = sample_rows(c["m"], c["n"])
+        w0 = time.perf_counter()
+        cpu_oracle_step(A, B, c, prec, lead, rows)
+        if time.perf_counter() - w0 > budget:
+            rows = None
+            A, B, c = cpu_sample(args.workload)
+            t_probe = cpu_oracle_step(A, B, c, prec, lead)
+            while t_probe > budget and min(c["m"], c["n"], c["k"]) > 512:
+                sc = tuple(max(256, x // 2) for x in (c["m"], c["n"], c["k"]))
+                c["r"], c["p"] = max(16, c["r"] // 2), max(4, c["p"] // 2)
+                A, B = workloads.operands(args.workload, scale=sc)
+                A, B = A.astype(np.float32), B.astype(np.float32)
+                c["m"], c["n"], c["k"] = sc
+                t_probe = cpu_oracle_step(A, B, c, prec, lead)
         flops = 2.0 * c["m"] * c["n"] * c["k"]
-        step = lambda: cpu_oracle_step(A, B, c, prec, LEADS.get(args.variant))  # noqa: E731
-        what = "oracle LRAMM"
+        step = lambda: cpu_oracle_step(A, B, c, prec, lead, rows)  # noqa: E731
+        what = "oracle LRAMM" + ("" if rows is None else
+                                 " (randomized SVDs, E1, E2 in full; E3 on %d seeded rows, time scaled by m/%d)"
+                                 % (len(rows), len(rows)))
     for _ in range(args.warmup):
         step()
     ts = [step() for _ in range(args.steps)]
@@ -424,9 +472,8 @@ def run_lramm(args):
 
     # accuracy of this variant and of the comparators (outside the timed region);
     # outputs above 2^28 entries are compared on a seeded sample of 2048 rows
-    rows = None
-    if m * n > (1 << 28):
-        rows = torch.from_numpy(np.sort(np.random.default_rng(5).choice(m, 2048, replace=False))).to(dev)
+    rows_np = sample_rows(m, n)
+    rows = None if rows_np is None else torch.from_numpy(rows_np).to(dev)
     Asub = A if rows is None else A[rows]
     exact = Asub.double() @ B.double()
     nrm = exact.norm().item()
@@ -471,30 +518,63 @@ def run_lramm(args):
     err_plain = rel_err(Dp)
     del exact
 
-    # end to end through the public API with host buffers: H2D of A, B from
-    # pinned memory, lramm_matmul, D2H of D, every step
+    # end to end through the public API with host buffers: every step copies
+    # its A and B from pinned host memory to the device, runs lramm_matmul and
+    # reads its D back to pinned host memory.  Two buffer sets (and two plans
+    # sharing one workspace, so that each keeps its captured graph) pipeline
+    # the steps: step i+1's host-to-device copies and step i's device-to-host
+    # copy run on their own streams beside the compute stream.
     Ah, Bh = A.cpu().pin_memory(), B.cpu().pin_memory()
     Dh = torch.empty((m, n), dtype=torch.float32).pin_memory()
-    Ad, Bd = torch.empty_like(A), torch.empty_like(B)
+    del Dp
+    Ad = [torch.empty_like(A) for _ in range(2)]
+    Bd = [torch.empty_like(B) for _ in range(2)]
+    Dd = [D, torch.empty_like(D)]
+    plans = [plan, L.Plan(m, n, k, r, p, q, seed=workloads.SEED_SKETCH, prec=prec, a_type=a_type, b_type=a_type,
+                          sketch=sketch, lead=lead[0], lead_prec=lead[1], lead_split=lead[2], graph=True)]
+    s_h2d, s_d2h = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev_in = [torch.cuda.Event() for _ in range(2)]     # inputs of buffer b on the device
+    ev_done = [torch.cuda.Event() for _ in range(2)]   # step on buffer b computed
+    ev_out = [torch.cuda.Event() for _ in range(2)]    # D of buffer b read back
+    for e in ev_done + ev_out:
+        e.record(stream)
 
-    def e2e_step():
-        Ad.copy_(Ah, non_blocking=True)
-        Bd.copy_(Bh, non_blocking=True)
-        L.matmul(plan, Ad, Bd, out=D, ws=ws)
-        Dh.copy_(D, non_blocking=True)
+    def e2e_step(i):
+        b = i % 2
+        s_h2d.wait_event(ev_done[b])             # buffer b's inputs no longer read
+        with torch.cuda.stream(s_h2d):
+            Ad[b].copy_(Ah, non_blocking=True)
+            Bd[b].copy_(Bh, non_blocking=True)
+        ev_in[b].record(s_h2d)
+        stream.wait_event(ev_in[b])
+        stream.wait_event(ev_out[b])              # buffer b's D read back
+        L.matmul(plans[b], Ad[b], Bd[b], out=Dd[b], ws=ws)
+        ev_done[b].record(stream)
+        s_d2h.wait_event(ev_done[b])
+        with torch.cuda.stream(s_d2h):
+            Dh.copy_(Dd[b], non_blocking=True)
+        ev_out[b].record(s_d2h)
 
-    e2e_steps = max(2, min(args.steps, 5))
-    for _ in range(2):
-        e2e_step()
+    e2e_steps = max(4, min(args.steps, 8))
+    for i in range(2):
+        e2e_step(i)
     torch.cuda.synchronize()
     ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ea.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
+    s_h2d.wait_event(ea)
+    s_d2h.wait_event(ea)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    for st_ in (s_h2d, s_d2h):
+        e_ = torch.cuda.Event()
+        e_.record(st_)
+        stream.wait_event(e_)
     eb.record(stream)
     eb.synchronize()
     e2e_ms = ea.elapsed_time(eb) / e2e_steps
     e2e_val = world * flops / (e2e_ms * 1e-3) / 1e12
+    e2e_ok = L.status_read(ws) == 0 and bool(torch.equal(Dh[:4], Dd[(e2e_steps - 1) % 2][:4].cpu()))
+    del Ad, Bd, Dd
 
     # roofline of the dominant kernel kind (largest device time in the timed steps)
     pk, peak_src = peaks()
@@ -554,12 +634,18 @@ def run_lramm(args):
     # CPU oracle on a bounded sample (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Ac, Bc, cs = cpu_sample(args.workload)
-        t_cpu = cpu_oracle_step(Ac, Bc, cs, prec, LEADS.get(args.variant))
-        cpu = {"value": 2.0 * cs["m"] * cs["n"] * cs["k"] / t_cpu / 1e12, "unit": "TFLOP/s",
-               "cores": cores_used(), "kind": "oracle",
-               "sample": "one oracle LRAMM step at m=%d n=%d k=%d r=%d p=%d q=%d, %.1f s"
-                         % (cs["m"], cs["n"], cs["k"], cs["r"], cs["p"], cs["q"], t_cpu)}
+        # the workload's own operands at full size (FP32 on the host; BF16
+        # operands widen exactly), E3 on the error's row sample when the
+        # output is too large for the host
+        Ac, Bc = A.float().cpu().numpy(), B.float().cpu().numpy()
+        t_cpu = cpu_oracle_step(Ac, Bc, cfg, prec, LEADS.get(args.variant), rows_np)
+        del Ac, Bc
+        cpu = {"value": flops / t_cpu / 1e12, "unit": "TFLOP/s", "cores": cores_used(), "kind": "oracle",
+               "sample": "one oracle LRAMM step at m=%d n=%d k=%d r=%d p=%d q=%d%s, %.1f s"
+                         % (m, n, k, r, p, q,
+                            "" if rows_np is None else
+                            " (randomized SVDs, E1, E2 in full; E3 on the %d sampled rows, its time scaled by "
+                            "m/%d)" % (len(rows_np), len(rows_np)), t_cpu)}
 
     launches = n_launch
     if rank == 0:
@@ -574,7 +660,7 @@ def run_lramm(args):
                        "jacobi_sweeps": info[1:3], "l2": "flushed: 256 MB write before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "rel_fro_err_vs_fp64_exact": err,
-                       "err_rows": "all" if rows is None else "2048 sampled rows (seed 5)",
+                       "err_rows": "all" if rows is None else "%d sampled rows (seed 5)" % SAMPLE_ROWS,
                        "dense_bf16_gemm": {"tflops": flops / (t_bf16 * 1e-3) / 1e12, "ms": t_bf16,
                                            "rel_fro_err_vs_fp64_exact": err_bf16},
                        "plain_lramm_fp32": {"tflops": flops / (t_plain * 1e-3) / 1e12, "ms": t_plain,
@@ -590,7 +676,9 @@ def run_lramm(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "TFLOP/s", "ms_per_step": e2e_ms,
                     "h2d_bytes_per_step": A.numel() * A.element_size() + B.numel() * B.element_size(),
-                    "d2h_bytes_per_step": D.numel() * D.element_size()},
+                    "d2h_bytes_per_step": D.numel() * D.element_size(), "steps": e2e_steps,
+                    "pipelined": "two buffer sets: step i+1's host-to-device copies and step i's device-to-host "
+                                 "copy overlap the compute stream", "result_checked": e2e_ok},
             "gpu_launches": launches,
             "clocks": {"sm_mhz": clk.get("sm_mhz"), "sm_max_mhz": clk.get("sm_max_mhz"),
                        "reasons": clk.get("reasons"), "samples": clk.get("samples")},
@@ -1040,7 +1128,7 @@ def main():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["lramm", "reference"], default="lramm")
-    ap.add_argument("--workload", default="lramm_4096", choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--workload", default="lramm_32768", choices=sorted(workloads.CONFIGS))
     ap.add_argument("--variant", default="int8", choices=sorted(VARIANTS))
     ap.add_argument("--sketch", choices=["tf32", "fp32", "e4m3"], default=None,
                     help="products with A and B: tf32 tensor cores (default for quantised variants), fp32, or "
