@@ -395,11 +395,13 @@ def run_lramm(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     L.load()
-    cfg = workloads.CONFIGS[args.workload]
+    cfg = dict(workloads.CONFIGS[args.workload])
+    if args.mn_div > 1:   # a reduced instance: m and n divided, k, r, p, q kept
+        cfg["m"], cfg["n"] = cfg["m"] // args.mn_div, cfg["n"] // args.mn_div
     m, n, k, r, p, q = cfg["m"], cfg["n"], cfg["k"], cfg["r"], cfg["p"], cfg["q"]
     l = r + p
     prec = VARIANTS[args.variant]
-    A, B = workloads.device_operands(args.workload, dev)
+    A, B = workloads.device_operands(args.workload, dev, sizes=(m, n, k))
     a_type = L.BF16 if A.dtype == torch.bfloat16 else L.F32
     sketch_name = args.sketch or ("fp32" if args.variant == "fp32" else "tf32")
     sketch = {"tf32": L.SKETCH_TF32, "fp32": L.SKETCH_F32, "e4m3": L.SKETCH_E4M3}[sketch_name]
@@ -1134,6 +1136,9 @@ def main():
                     help="products with A and B: tf32 tensor cores (default for quantised variants), fp32, or "
                          "e4m3 (the range-finder passes on FP8 codes, the projection in tf32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mn-div", type=int, default=1,
+                    help="run a reduced instance of an lramm_* workload: m and n divided by this (k, r, p, q "
+                         "kept); the JSON line then names the reduced sizes (profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

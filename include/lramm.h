@@ -226,7 +226,10 @@ LRAMM_API lramm_status lramm_status_read(const void* ws, void* stream);
  * info[1], info[2] = Jacobi sweeps of the A- and B-side SVDs of the last
  * call, info[3] bit 0 = the last lramm_matmul assembled its factors with
  * TF32 tensor-core products (quantised chains in a tensor-core sketch mode),
- * else with FP32 products.  Nothing is cleared. */
+ * else with FP32 products; info[20], info[21] = how many Cholesky
+ * factorisations of the A- and B-side randomized SVDs met a non-positive
+ * pivot and took the shifted CholeskyQR fallback (larger shift, then a third
+ * pass where the orthonormalisation had two).  Nothing is cleared. */
 LRAMM_API lramm_status lramm_info_read(const void* ws, int32_t* info, int32_t n, void* stream);
 
 /* Static description of a status code. */

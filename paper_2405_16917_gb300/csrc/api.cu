@@ -25,11 +25,24 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void note_cuda_error(cudaError_t e, const char* where) {
   snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+int num_sms() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return 152;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 152;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
 }  // namespace lramm
 
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int kStatusWords = 24;   // status-area words cleared at the start of a call
 constexpr int kMaxL = 576;   // the SVD form stops earlier, at jacobi_max_l()
 
 // Largest l of the small SVD (the SVD form); the range-finder form needs none.
@@ -54,7 +67,7 @@ constexpr int64_t kGramTcRows = 2048;          // sketches from this many rows t
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, Xd, R, Vj, sig, S1, S2, S1T, S2T, CS;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, L3, Xd, R, Vj, sig, S1, S2, S1T, S2T, CS;
   size_t part, gpart, gtpart, bsplit;   // this operand's split-K partials and BF16 parts (own stream)
   // E4M3 range finder: codes of X per row (rows x cols_p) and per column
   // (cols x rows_p), of the l-column operand (l x max(rows_p, cols_p)), their
@@ -170,6 +183,7 @@ void layout(lramm_plan_s* P) {
     S.G = b.take(sizeof(float) * l * l);
     S.L1 = b.take(sizeof(float) * l * l);
     S.L2 = b.take(sizeof(float) * l * l);
+    S.L3 = b.take(sizeof(float) * l * l);
     S.Xd = b.take(sizeof(float) * ceil_div(l, 32) * 32 * 32);
     S.CS = chol_split_supported((int)l) ? b.take(sizeof(float) * chol_split_scratch_floats((int)l)) : 0;
     S.R = b.take(sizeof(float) * l * l);
@@ -383,22 +397,65 @@ struct SideRun {
   const SideLayout* S;
 };
 
+// The shifted-CholeskyQR fallback (retry) keeps two words of the status area
+// per side: kBrkWord + 2 side (a Cholesky of the current pass met a
+// non-positive pivot) and kBrkWord + 2 side + 1 (some pass of this
+// orthonormalisation did; the conditional third pass runs).
+constexpr int kBrkWord = 16;
+constexpr int kBrkCountWord = 20;   // + side: factorisations of this call that broke down (diagnostics)
+
+// Relative diagonal shift of the fallback's factorisation: above the rounding
+// error of an l x l Cholesky (~l u) and of the Gram of `rows` rows
+// (~sqrt(rows) u), so that it succeeds for a numerically rank-deficient Y.
+float chol_shift_big(int64_t rows, int l) {
+  return 0x1p-24f * (16.0f * static_cast<float>(l) + 8.0f * sqrtf(static_cast<float>(rows)));
+}
+
 // Orthonormalise, for every side s, the rows_s x l matrix src[s] (stride l)
 // by `passes` CholeskyQR passes (Gram, Cholesky, Q = Y L^-T); every pass
 // shifts the Gram diagonal by 4u max(diag) so a rank-deficient sketch still
-// factors (the shift costs ~4u in orthonormality).  One pass suffices where only the span matters (the intermediate
-// bases of the power iterations); two give orthonormality to working
-// precision.  dst may equal src.  With want_R (two passes): R = L2^T L1^T,
-// so that src = dst R.
+// factors (the shift costs ~4u in orthonormality).  One pass suffices where
+// only the span matters (the intermediate bases of the power iterations);
+// two give orthonormality to working precision.  dst may equal src.  With
+// want_R (two passes): R = L2^T L1^T, so that src = dst R.
 // skip_last_solve: the last pass forms its Gram and Cholesky factor (and R)
 // but not its orthonormal output, so dst keeps what it held (with passes = 2
 // and dst = src: the input X, with X = P1 R1 and P1 in tmp).
+//
+// retry (one side; the blocked and two-level Cholesky paths): the shifted
+// CholeskyQR fallback for sketches too ill-conditioned for the 4u shift.  A
+// Cholesky that meets a non-positive pivot is redone with the shift
+// chol_shift_big (inside the blocked kernel; by a launch predicated on the
+// breakdown word for the two-level one), which always factors; the pass's Q
+// then spans Y with a condition number near 1 / sqrt(that shift).  With FP32
+// products and passes = 2 a third pass, predicated on the same event,
+// restores orthonormality to working precision (shifted CholeskyQR3), R
+// becoming L3^T L2^T L1^T.  With tensor-core products (TF32 / BF16 parts /
+// e4m3) the second pass already leaves an orthogonality error near
+// u / shift < 2^-12, below those products' own rounding, and no third pass
+// is enqueued.  Without a breakdown the predicated launches do nothing and
+// the results are those of the plain passes.
 lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, float* const* src,
                         float* const* tmp, float* const* dst, const int64_t* rows, int passes, bool want_R,
-                        int* st, cudaStream_t s, bool skip_last_solve = false) {
+                        int* st, cudaStream_t s, bool skip_last_solve = false, bool retry = false) {
   const int l = P->l;
+  const bool c3 = chol3_supported(l) && l % 4 == 0;
+  const bool csplit = !c3 && chol_split_supported(l);
+  retry = retry && ns == 1 && (c3 || csplit);
+  const bool third = retry && passes == 2 && P->d.sketch == LRAMM_SKETCH_F32;
+  int* brk = nullptr;
+  int* any = nullptr;
+  if (retry) {
+    brk = at<int>(ws, 0) + kBrkWord + 2 * (sd[0].S == &P->side[1] ? 1 : 0);
+    any = brk + 1;
+    // (a blocked single pass needs neither word: its restart is internal)
+    if (csplit || third) LRAMM_CUDA_TRY(cudaMemsetAsync(brk, 0, 2 * sizeof(int), s));
+  }
+  const int total = passes + (third ? 1 : 0);
   const float* in[2] = {src[0], ns > 1 ? src[1] : nullptr};
-  for (int pass = 0; pass < passes; ++pass) {
+  for (int pass = 0; pass < total; ++pass) {
+    const bool extra = pass == passes;          // the fallback's third pass: runs after a breakdown only
+    const int* cond = extra ? any : nullptr;
     float* out[2];
     SmallBatch cb{}, tb{};
     CholBatch cb3{};
@@ -407,9 +464,9 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
     cb.n = tb.n = gb.n = cb3.n = tb3.n = ns;
     for (int i = 0; i < ns; ++i) {
       float* G = at<float>(ws, sd[i].S->G);
-      float* Lf = at<float>(ws, pass == 0 ? sd[i].S->L1 : sd[i].S->L2);
+      float* Lf = at<float>(ws, pass == 0 ? sd[i].S->L1 : (pass == 1 ? sd[i].S->L2 : sd[i].S->L3));
       float* Xd = at<float>(ws, sd[i].S->Xd);
-      out[i] = pass == passes - 1 ? dst[i] : tmp[i];
+      out[i] = pass >= passes - 1 ? dst[i] : tmp[i];
       gb.p[i] = GramProb{in[i], rows[i], G};
       cb.p[i] = SmallProb{G, Lf, nullptr, 0};
       tb.p[i] = SmallProb{in[i], out[i], Lf, rows[i]};
@@ -432,26 +489,51 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
         lramm_status gst = LRAMM_OK;
         TIMED(P, LRAMM_K_GRAM, s,
               (gst = gram_tc(1, Yi, &rows[i], Gi, l, at<float>(ws, sd[i].S->gtpart), gram_tc_part_floats(l), st,
-                             s)) ==
-                      LRAMM_ERR_UNSUPPORTED
+                             s, cond)) == LRAMM_ERR_UNSUPPORTED
                   ? [&] {
                       GramBatch g1{};
                       g1.n = 1;
                       g1.p[0] = gb.p[i];
-                      return launch_gram(g1, l, at<float>(ws, sd[i].S->gpart), s);
+                      return launch_gram(g1, l, at<float>(ws, sd[i].S->gpart), s, cond);
                     }()
                   : gst);
       }
-    if (gs.n) TIMED(P, LRAMM_K_GRAM, s, launch_gram(gs, l, at<float>(ws, sd[0].S->gpart), s));
-    const bool solve = !(skip_last_solve && pass == passes - 1);
-    if (chol3_supported(l) && l % 4 == 0) {  // blocked Cholesky + panel solve with inverted diagonal blocks
-      TIMED(P, LRAMM_K_CHOL, s, launch_chol3(cb3, l, kCholShift, st, s));
-      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
-    } else if (chol_split_supported(l)) {  // two-level Cholesky, same panel solve
+    if (gs.n) TIMED(P, LRAMM_K_GRAM, s, launch_gram(gs, l, at<float>(ws, sd[0].S->gpart), s, cond));
+    // the solve: skipped in the last pass with skip_last_solve; with the
+    // fallback, the second pass's solve feeds the third and runs with it
+    bool solve = true;
+    const int* scond = cond;
+    if (skip_last_solve) {
+      if (extra) solve = false;
+      else if (pass == passes - 1) {
+        if (third) scond = any;
+        else solve = false;
+      }
+    }
+    const bool guard = retry && !extra;   // breakdowns of this pass are retried
+    if (c3) {  // blocked Cholesky (restarting itself with the larger shift) + panel solve
+      if (guard) {
+      cb3.p[0].brk_any = any;
+      cb3.p[0].brk_count = at<int>(ws, 0) + kBrkCountWord + (sd[0].S == &P->side[1] ? 1 : 0);
+    }
+      TIMED(P, LRAMM_K_CHOL, s,
+            launch_chol3(cb3, l, kCholShift, st, s, cond, guard ? chol_shift_big(rows[0], l) : 0.f));
+      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s, scond));
+    } else if (csplit) {  // two-level Cholesky, same panel solve
       SplitScratch sc{};
       for (int i = 0; i < ns; ++i) sc.w[i] = at<float>(ws, sd[i].S->CS);
-      TIMED(P, LRAMM_K_CHOL, s, launch_chol_split(cb3, sc, l, kCholShift, st, s));
-      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s));
+      CholBatch cg = cb3;
+      if (guard) {
+        cg.p[0].brk = brk;
+        cg.p[0].brk_any = any;
+        cg.p[0].brk_count = at<int>(ws, 0) + kBrkCountWord + (sd[0].S == &P->side[1] ? 1 : 0);
+      }
+      TIMED(P, LRAMM_K_CHOL, s, launch_chol_split(cg, sc, l, kCholShift, st, s, cond));
+      if (guard) {   // redone with the larger shift after a breakdown, then the word cleared
+        TIMED(P, LRAMM_K_CHOL, s, launch_chol_split(cb3, sc, l, chol_shift_big(rows[0], l), st, s, brk));
+        LRAMM_CUDA_TRY(cudaMemsetAsync(brk, 0, sizeof(int), s));
+      }
+      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s, scond));
     } else {
       TIMED(P, LRAMM_K_CHOL, s, launch_chol2(cb, l, kCholShift, st, s));
       if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm_panel(tb, l, s));
@@ -461,12 +543,17 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
   if (want_R)
     for (int i = 0; i < ns; ++i) {
       const SideLayout& S = *sd[i].S;
-      if (passes == 2)
+      if (passes != 2) return LRAMM_ERR_INVALID_ARG;
+      TIMED(P, LRAMM_K_RFACTOR, s,
+            sgemm(1, 1, l, l, l, 1.f, at<float>(ws, S.L2), l, 0, at<float>(ws, S.L1), l, 0.f, at<float>(ws, S.R), l,
+                  s));
+      if (third) {   // after the third pass: R = L3^T (L2^T L1^T), through Vj (free until the small SVD)
         TIMED(P, LRAMM_K_RFACTOR, s,
-              sgemm(1, 1, l, l, l, 1.f, at<float>(ws, S.L2), l, 0, at<float>(ws, S.L1), l, 0.f,
-                    at<float>(ws, S.R), l, s));
-      else
-        return LRAMM_ERR_INVALID_ARG;
+              sgemm(1, 0, l, l, l, 1.f, at<float>(ws, S.L3), l, 0, at<float>(ws, S.R), l, 0.f, at<float>(ws, S.Vj),
+                    l, s, any));
+        TIMED(P, LRAMM_K_RFACTOR, s,
+              launch_copy_cond(at<float>(ws, S.Vj), at<float>(ws, S.R), static_cast<int64_t>(l) * l, any, s));
+      }
     }
   return LRAMM_OK;
 }
@@ -543,16 +630,16 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
           x_product(P, ws, *sd[i].S, 0, sd[i].X, S.rows, S.cols, sd[i].ldx, sd[i].xbf, Om, R0[i], s, fp8));
     if (rec_first) LRAMM_CUDA_TRY(cudaEventRecord(rec_first, s));
   }
-  LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, d.q > 0 ? 1 : 2, false, st, s));  // Q
+  LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, d.q > 0 ? 1 : 2, false, st, s, false, true));  // Q
   for (int it = 0; it < d.q; ++it) {
     for (int i = 0; i < ns; ++i)
       TIMED(P, LRAMM_K_SKETCH, s,
             x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s, fp8));
-    LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 1, false, st, s));  // Z^ (span only)
+    LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 1, false, st, s, false, true));  // Z^ (span only)
     for (int i = 0; i < ns; ++i)
       TIMED(P, LRAMM_K_SKETCH, s,
             x_product(P, ws, *sd[i].S, 0, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, C0[i], R0[i], s, fp8));
-    LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, it == d.q - 1 ? 2 : 1, false, st, s));
+    LRAMM_TRY(orth_sides(P, ws, sd, ns, R0, R1, R0, rows, it == d.q - 1 ? 2 : 1, false, st, s, false, true));
   }
   for (int i = 0; i < ns; ++i)
     TIMED(P, LRAMM_K_SKETCH, s, x_product(P, ws, *sd[i].S, 1, sd[i].X, rows[i], cols[i], sd[i].ldx, sd[i].xbf, R0[i], C0[i], s));  // B^T
@@ -577,7 +664,7 @@ lramm_status rsvd_sides(lramm_plan_s* P, const SideRun* sd, const int* which, in
   const int max_sweeps = d.max_sweeps > 0 ? d.max_sweeps : 40;
   bool m_only = false;
   if (m_only_req && ns == 1) LRAMM_TRY(launch_jacobi_uonly(jb, l, max_sweeps, st, s, true, m_only));
-  LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 2, true, st, s, m_only));  // B^T = P R
+  LRAMM_TRY(orth_sides(P, ws, sd, ns, C0, C1, C0, cols, 2, true, st, s, m_only, true));  // B^T = P R
   if (m_only) {
     bool ok = false;
     TIMED(P, LRAMM_K_SVD, s, launch_jacobi_uonly(jb, l, max_sweeps, st, s, false, ok));
@@ -1025,7 +1112,7 @@ lramm_status lramm_rsvd(lramm_plan_t plan, int32_t which, const void* X, float* 
   const SideLayout& Sd = plan->side[which];
   const int l = plan->l, r = plan->d.r;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusWords * sizeof(int), s));
   const SideRun sd = side_run(plan, which, X);
   const int zero[1] = {0};
   LRAMM_TRY(rsvd_sides(plan, &sd, &which, 1, ws, zero, zero, s));
@@ -1106,7 +1193,7 @@ lramm_status lramm_qsvd(lramm_plan_t plan, int32_t which, const void* X, int32_t
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int per_row = d.scale == LRAMM_S_ROWCOL;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusWords * sizeof(int), s));
   // SVD(A, k) and U~ = U_k Sigma_k: the small SVD's left vectors carry sigma
   const SideRun sd = side_run(plan, which, X);
   const int one[1] = {1}, zero[1] = {0};
@@ -1154,7 +1241,7 @@ lramm_status lramm_chain(lramm_plan_t plan, const float* Ut, const float* Vt, co
   LRAMM_TRY(check_ws(plan, ws, ws_bytes));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusWords * sizeof(int), s));
   return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
 }
 
@@ -1210,7 +1297,7 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   const lramm_desc& d = plan->d;
   const int l = plan->l, r = d.r;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusWords * sizeof(int), s));
   float* Ut = at<float>(ws, plan->Ut);
   float* Vt = at<float>(ws, plan->Vt);
   float* Wt = at<float>(ws, plan->Wt);
@@ -1401,7 +1488,7 @@ lramm_status lramm_rf_forward(lramm_plan_t plan, const void* X, const void* W, f
   const lramm_desc& d = plan->d;
   const int l = plan->l;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusWords * sizeof(int), s));
   const SideRun sx = side_run(plan, 0, X), sw = side_run(plan, 1, W);
   LRAMM_TRY(range_finder_side(plan, sw, ws, false, s));
   const float* Q = at<float>(ws, sw.S->R0);
@@ -1432,7 +1519,7 @@ lramm_status lramm_rf_backward(lramm_plan_t plan, const void* X, const void* W, 
   const int l = plan->l;
   const int64_t m = d.m, n = d.n, k = d.k;
   plan->used = 0;
-  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, 4 * sizeof(int), s));
+  LRAMM_CUDA_TRY(cudaMemsetAsync(ws, 0, kStatusWords * sizeof(int), s));
   const SideRun sx = side_run(plan, 0, X), sw = side_run(plan, 1, W);
   LRAMM_TRY(range_finder_side(plan, sw, ws, true, s));
   auto Qi = [&](int i) { return at<float>(ws, plan->bq) + (int64_t)i * k * l; };

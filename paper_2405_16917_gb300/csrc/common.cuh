@@ -61,6 +61,10 @@ void note_cuda_error(cudaError_t e, const char* where);
     if (_s != LRAMM_OK) return _s;                            \
   } while (0)
 
+// Streaming multiprocessors of the calling thread's current device (queried
+// once per device): grids and split-K counts are sized from it.
+int num_sms();
+
 // Every kernel launch of the library is followed by exactly one check;
 // the check also counts the launch (lramm_launch_count).
 void count_launch();
@@ -164,6 +168,11 @@ struct CholProb {
   const float* G;   // l x l
   float* L;         // l x l, lower, zeros above
   float* Xd;        // ceil(l/32) blocks of 32 x 32: inverses of L's diagonal blocks
+  // breakdown words: with brk set, a non-positive pivot stores 1 in *brk (and
+  // in *brk_any) instead of latching LRAMM_ERR_NUMERIC, for a retry
+  int* brk = nullptr;
+  int* brk_any = nullptr;
+  int* brk_count = nullptr;   // incremented once per factorisation that broke down (diagnostics)
 };
 struct CholBatch {
   CholProb p[2];
@@ -181,8 +190,13 @@ struct TrsmBatch {
   int n;
 };
 bool chol3_supported(int l);
-lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s);
-lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s);
+// shift_big_rel > 0: on a non-positive pivot the kernel refactors with that
+// larger relative shift (and sets *brk_any of the problem when given).
+lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s,
+                          const int* cond = nullptr, float shift_big_rel = 0.f);
+lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s, const int* cond = nullptr);
+// dst = src (n floats) when *cond != 0
+lramm_status launch_copy_cond(const float* src, float* dst, int64_t n, const int* cond, cudaStream_t s);
 // Two-level Cholesky for 288 < l <= 576 (l % 4 == 0) on chol3 / trsm3 /
 // sgemm; scratch: chol_split_scratch_floats(l) floats per problem.
 struct SplitScratch {
@@ -190,9 +204,10 @@ struct SplitScratch {
 };
 bool chol_split_supported(int l);
 size_t chol_split_scratch_floats(int l);
-lramm_status launch_chol_split(CholBatch cb, SplitScratch sc, int l, float shift_rel, int* status, cudaStream_t s);
+lramm_status launch_chol_split(CholBatch cb, SplitScratch sc, int l, float shift_rel, int* status, cudaStream_t s,
+                               const int* cond = nullptr);
 size_t gram_part_floats(int l);
-lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s);
+lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s, const int* cond = nullptr);
 lramm_status launch_chol2(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s);
 lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s);
 // Range-finder backward helpers: out = copyltu(M) (lower triangle mirrored),
@@ -242,7 +257,7 @@ size_t sketch_bf_split_bytes(int64_t K, int l);
 bool gram_tc_supported(int l);
 size_t gram_tc_part_floats(int l);
 lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* part,
-                     size_t part_floats, int* status, cudaStream_t s);
+                     size_t part_floats, int* status, cudaStream_t s, const int* cond = nullptr);
 lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, const float* B, int l,
                        int nb, float* out, float* part, size_t part_floats, void* split, size_t split_bytes,
                        int* status, cudaStream_t s);

@@ -93,7 +93,7 @@ lramm_status quantize_mx_values(const float* X, int64_t rows, int64_t cols, int6
   if (rows <= 0) return LRAMM_OK;
   if (ldv % kMxB || ldv < cols) return LRAMM_ERR_INVALID_ARG;
   int64_t g = ceil_div(rows, 8);
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > num_sms() * 16) g = num_sms() * 16;
   quant_mx_values_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(X, rows, cols, ldx, vals, ldv);
   return last_launch();
 }
@@ -103,7 +103,7 @@ lramm_status quantize_mx(const float* X, int64_t rows, int64_t cols, int64_t ldx
   if (rows <= 0) return LRAMM_OK;
   if (ldc % kMxB || ldc < cols) return LRAMM_ERR_INVALID_ARG;
   int64_t g = ceil_div(rows, 8);
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > num_sms() * 16) g = num_sms() * 16;
   quant_mx_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(X, rows, cols, ldx, codes, ldc, exps);
   return last_launch();
 }
@@ -214,7 +214,7 @@ lramm_status residual_rows(const float* X, int64_t rows, int64_t cols, int64_t l
                            cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return LRAMM_OK;
   int64_t g = ceil_div(rows * cols, 256);
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > num_sms() * 8) g = num_sms() * 8;
   if (code_type_of(prec) == CODE_BF16)
     resid_kernel<CODE_BF16><<<static_cast<unsigned>(g), 256, 0, s>>>(X, rows, cols, ldx, codes, ldcodes, scales,
                                                                       per_row, out, ldo);

@@ -39,7 +39,9 @@ __device__ __forceinline__ void tile_of(int t, int& ti, int& tj) {
 // of Y are 16-byte aligned (l % 4 == 0), one float4 per thread and operand.
 template <bool VEC>
 __global__ void __launch_bounds__(256)
-gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_per_split, float* __restrict__ part) {
+gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_per_split, float* __restrict__ part,
+                    const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   const GramProb& gp = gb.p[blockIdx.z];
   const float* __restrict__ Y = gp.Y;
   const int64_t rows = gp.rows;
@@ -134,7 +136,9 @@ gram_partial_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_pe
 // few hundred rows); the slices are added in FP64 by the reduction.
 // Needs l % 4 == 0 and 16-byte aligned rows.
 __global__ void __launch_bounds__(64)
-gram_partial8_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_per_split, float* __restrict__ part) {
+gram_partial8_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_per_split, float* __restrict__ part,
+                     const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   const GramProb& gp = gb.p[blockIdx.z];
   const float* __restrict__ Y = gp.Y;
   const int64_t rows = gp.rows;
@@ -213,7 +217,9 @@ gram_partial8_kernel(GramBatch gb, int l, int ntiles, int splits, int64_t rows_p
 // tile holds both triangles computed from identical products, so G is
 // exactly symmetric.  Each thread adds four consecutive elements of a tile
 // row (float4 reads of the partials, four slices in flight).
-__global__ void gram_reduce_kernel(GramBatch gb, int l, int ntiles, int splits, const float* __restrict__ part) {
+__global__ void gram_reduce_kernel(GramBatch gb, int l, int ntiles, int splits, const float* __restrict__ part,
+                                   const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   const int64_t per4 = static_cast<int64_t>(ntiles) * kGT * kGT / 4;
   const int64_t tile_stride4 = per4;   // between slices
   const float4* part4 = reinterpret_cast<const float4*>(part);
@@ -462,7 +468,9 @@ __host__ __device__ inline int chol_split_h_dev(int l) {
 // from two 128-byte-swizzled K-major copies of the panel below the diagonal
 // block (256 rows x 32 columns each); otherwise in FP32 SIMT register tiles.
 template <bool TC>
-__global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, float shift_rel, int* status) {
+__global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, float shift_rel, float shift_big_rel,
+                                                       int* status, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;   // predicated launch (the CholeskyQR fallback)
   const CholProb& cp = cb.p[blockIdx.x];
   const float* __restrict__ G = cp.G;
   float* __restrict__ Lo = cp.L;
@@ -480,6 +488,7 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   float* LC = TC ? PnT : PnT + kCB * lp;                  // kCB x kLC: LC[t][c] = L_JJ[c][t], c > t
   __shared__ float s_red[32];
   __shared__ float s_rinv[kCB];
+  __shared__ int s_bad;   // a pivot of this attempt was not positive
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -504,6 +513,7 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
     __syncthreads();
     tc::tc_fence_after();
   }
+  if (tid == 0) s_bad = 0;
   float md = 0.f;
   for (int i = tid; i < l; i += blockDim.x) md = fmaxf(md, G[static_cast<int64_t>(i) * l + i]);
   md = warp_max_o(md);
@@ -515,246 +525,270 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
     if (lane == 0) s_red[0] = v;
   }
   __syncthreads();
-  const float shift = shift_rel * s_red[0];
-  {  // G (row-major, l % 4 == 0) into the packed lower triangle: 8 float4 loads in flight per thread
-    const int nq = l * l / 4, lq4 = l / 4;
-    const float4* G4 = reinterpret_cast<const float4*>(G);
-    for (int q0 = tid; q0 < nq; q0 += 8 * blockDim.x) {
-      float4 v[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + u * blockDim.x;
-        if (q < nq) v[u] = G4[q];
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int q = q0 + u * blockDim.x;
-        if (q >= nq) break;
-        const int i = q / lq4, j = 4 * (q - i * lq4);
-        const float e4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
-#pragma unroll
-        for (int t = 0; t < 4; ++t)
-          if (j + t <= i) P[opidx(i, j + t)] = e4[t] + (i == j + t ? shift : 0.f);
+  // Attempt 0 factors G + shift_rel max(diag) I.  If a pivot is not positive
+  // and shift_big_rel > 0, attempt 1 factors G + shift_big_rel max(diag) I
+  // from scratch (the shifted CholeskyQR fallback: the caller then adds a
+  // pass).  A non-positive pivot of the last attempt is replaced by a tiny
+  // positive value and reported.
+  bool restarted = false;
+  for (int attempt = 0;; ++attempt) {
+    const float shift = (attempt == 0 ? shift_rel : shift_big_rel) * s_red[0];
+    {  // G (row-major, l % 4 == 0) into the packed lower triangle: 8 float4 loads in flight per thread
+      const int nq = l * l / 4, lq4 = l / 4;
+      const float4* G4 = reinterpret_cast<const float4*>(G);
+      for (int q0 = tid; q0 < nq; q0 += 8 * blockDim.x) {
+        float4 v[8];
+  #pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u * blockDim.x;
+          if (q < nq) v[u] = G4[q];
+        }
+  #pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int q = q0 + u * blockDim.x;
+          if (q >= nq) break;
+          const int i = q / lq4, j = 4 * (q - i * lq4);
+          const float e4[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+  #pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (j + t <= i) P[opidx(i, j + t)] = e4[t] + (i == j + t ? shift : 0.f);
+        }
       }
     }
-  }
-  if (!TC)
-    for (int e = tid; e < kCB * lp; e += blockDim.x) PnT[e] = 0.f;
-  __syncthreads();
+    if (!TC)
+      for (int e = tid; e < kCB * lp; e += blockDim.x) PnT[e] = 0.f;
+    __syncthreads();
 
-  for (int j0 = 0; j0 < l; j0 += kCB) {
-    const int w = min(kCB, l - j0);
-    if (warp == 0) {
-      float a[kCB];
-#pragma unroll
-      for (int c = 0; c < kCB; ++c)
-        a[c] = lane < w ? (c <= lane ? P[opidx(j0 + lane, j0 + c)] : 0.f) : (c == lane ? 1.f : 0.f);
-      // The pivot chain is software-pipelined: lane k+1 forms its own next
-      // diagonal entry from its own multiplier (the value the shuffled update
-      // below gives it, bit for bit), and that entry is broadcast before the
-      // remaining updates of this pivot issue.  A non-positive pivot is
-      // replaced without a branch and latched once after the block, so the
-      // unrolled pivots form straight-line code.
-      bool bad = false;
-      float piv = __shfl_sync(0xffffffffu, a[0], 0);
-#pragma unroll
-      for (int k = 0; k < kCB; ++k) {
-        bad |= !(piv > 0.f);
-        piv = piv > 0.f ? piv : FLT_MIN * 1024.f;
-        const float inv = rsqrtf(piv);
-        const float lk = lane == k ? piv * inv : a[k] * inv;
-        a[k] = lk;
-        if (lane == k) s_rinv[k] = inv;
-        float piv_next = 0.f;
-        if (k + 1 < kCB) piv_next = __shfl_sync(0xffffffffu, fmaf(-lk, lk, a[k + 1]), k + 1);
-#pragma unroll
-        for (int c = k + 1; c < kCB; ++c) a[c] = fmaf(-lk, __shfl_sync(0xffffffffu, lk, c), a[c]);
-        piv = piv_next;
-      }
-      if (bad && lane == 0) set_status(status, LRAMM_ERR_NUMERIC);
-#pragma unroll
-      for (int c = 0; c < kCB; ++c) {
-        if (lane < w && c <= lane) P[opidx(j0 + lane, j0 + c)] = a[c];
-        LC[c * kLC + lane] = (lane < w && c < lane) ? a[c] : 0.f;
-      }
-    }
-    __syncthreads();
-    const int r0 = j0 + kCB;   // first row below the diagonal block
-    const int n2 = l - r0;
-    if (n2 <= 0) break;
-    // (b) rows below: x L_JJ^T = a, right-looking in registers
-    if (tid < n2) {
-      const int row = r0 + tid;
-      float a[kCB];
-#pragma unroll
-      for (int t = 0; t < kCB; ++t) a[t] = P[opidx(row, j0 + t)];
-#pragma unroll
-      for (int t = 0; t < kCB; ++t) {
-        const float x = a[t] * s_rinv[t];
-        a[t] = x;
-#pragma unroll
-        for (int c4 = ((t + 1) / 4) * 4; c4 < kCB; c4 += 4) {
-          const float4 lv = *reinterpret_cast<const float4*>(LC + t * kLC + c4);
-          if (c4 + 0 > t) a[c4 + 0] = fmaf(-x, lv.x, a[c4 + 0]);
-          if (c4 + 1 > t) a[c4 + 1] = fmaf(-x, lv.y, a[c4 + 1]);
-          if (c4 + 2 > t) a[c4 + 2] = fmaf(-x, lv.z, a[c4 + 2]);
-          if (c4 + 3 > t) a[c4 + 3] = fmaf(-x, lv.w, a[c4 + 3]);
+    for (int j0 = 0; j0 < l; j0 += kCB) {
+      const int w = min(kCB, l - j0);
+      if (warp == 0) {
+        float a[kCB];
+  #pragma unroll
+        for (int c = 0; c < kCB; ++c)
+          a[c] = lane < w ? (c <= lane ? P[opidx(j0 + lane, j0 + c)] : 0.f) : (c == lane ? 1.f : 0.f);
+        // The pivot chain is software-pipelined: lane k+1 forms its own next
+        // diagonal entry from its own multiplier (the value the shuffled update
+        // below gives it, bit for bit), and that entry is broadcast before the
+        // remaining updates of this pivot issue.  A non-positive pivot is
+        // replaced without a branch and latched once after the block, so the
+        // unrolled pivots form straight-line code.
+        bool bad = false;
+        float piv = __shfl_sync(0xffffffffu, a[0], 0);
+  #pragma unroll
+        for (int k = 0; k < kCB; ++k) {
+          bad |= !(piv > 0.f);
+          piv = piv > 0.f ? piv : FLT_MIN * 1024.f;
+          const float inv = rsqrtf(piv);
+          const float lk = lane == k ? piv * inv : a[k] * inv;
+          a[k] = lk;
+          if (lane == k) s_rinv[k] = inv;
+          float piv_next = 0.f;
+          if (k + 1 < kCB) piv_next = __shfl_sync(0xffffffffu, fmaf(-lk, lk, a[k + 1]), k + 1);
+  #pragma unroll
+          for (int c = k + 1; c < kCB; ++c) a[c] = fmaf(-lk, __shfl_sync(0xffffffffu, lk, c), a[c]);
+          piv = piv_next;
+        }
+        if (bad && lane == 0) s_bad = 1;
+  #pragma unroll
+        for (int c = 0; c < kCB; ++c) {
+          if (lane < w && c <= lane) P[opidx(j0 + lane, j0 + c)] = a[c];
+          LC[c * kLC + lane] = (lane < w && c < lane) ? a[c] : 0.f;
         }
       }
-#pragma unroll
-      for (int t = 0; t < kCB; ++t) P[opidx(row, j0 + t)] = a[t];
-      if (TC) {  // row tid of the swizzled copies: 16-byte chunk c at position c ^ (tid mod 8)
-        uint8_t* hr = T_hi + tid * 128;
-        uint8_t* lr = T_lo + tid * 128;
-#pragma unroll
-        for (int c = 0; c < kCB / 4; ++c) {
-          float h[4], o[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            h[e] = __uint_as_float(__float_as_uint(a[4 * c + e]) & 0xFFFFE000u);
-            o[e] = a[4 * c + e] - h[e];
-          }
-          const int off = (c ^ (tid & 7)) * 16;
-          *reinterpret_cast<float4*>(hr + off) = make_float4(h[0], h[1], h[2], h[3]);
-          *reinterpret_cast<float4*>(lr + off) = make_float4(o[0], o[1], o[2], o[3]);
-        }
-      } else {
-        const int pos = ((tid & 4) ? H : 0) + 4 * (tid >> 3) + (tid & 3);
-#pragma unroll
-        for (int t = 0; t < kCB; ++t) PnT[t * lp + pos] = a[t];
-      }
-    }
-    __syncthreads();
-    // (c) trailing update, rows/cols r0 .. l-1, lower triangle
-    if (TC) {
-      // D_t = rows 128 t .. 128 t + 127 of the panel copy times the first N_t
-      // rows (only columns c <= i are needed); TMEM columns 256 t ..
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
-      const int N = static_cast<int>(round_up(n2, 32));
-      const int tiles = (n2 + 127) / 128;
-      const uint32_t tm = s_tmem;
-      if (tid == 0) {
+      const int r0 = j0 + kCB;   // first row below the diagonal block
+      const int n2 = l - r0;
+      if (n2 <= 0) break;
+      // (b) rows below: x L_JJ^T = a, right-looking in registers
+      if (tid < n2) {
+        const int row = r0 + tid;
+        float a[kCB];
+  #pragma unroll
+        for (int t = 0; t < kCB; ++t) a[t] = P[opidx(row, j0 + t)];
+  #pragma unroll
+        for (int t = 0; t < kCB; ++t) {
+          const float x = a[t] * s_rinv[t];
+          a[t] = x;
+  #pragma unroll
+          for (int c4 = ((t + 1) / 4) * 4; c4 < kCB; c4 += 4) {
+            const float4 lv = *reinterpret_cast<const float4*>(LC + t * kLC + c4);
+            if (c4 + 0 > t) a[c4 + 0] = fmaf(-x, lv.x, a[c4 + 0]);
+            if (c4 + 1 > t) a[c4 + 1] = fmaf(-x, lv.y, a[c4 + 1]);
+            if (c4 + 2 > t) a[c4 + 2] = fmaf(-x, lv.z, a[c4 + 2]);
+            if (c4 + 3 > t) a[c4 + 3] = fmaf(-x, lv.w, a[c4 + 3]);
+          }
+        }
+  #pragma unroll
+        for (int t = 0; t < kCB; ++t) P[opidx(row, j0 + t)] = a[t];
+        if (TC) {  // row tid of the swizzled copies: 16-byte chunk c at position c ^ (tid mod 8)
+          uint8_t* hr = T_hi + tid * 128;
+          uint8_t* lr = T_lo + tid * 128;
+  #pragma unroll
+          for (int c = 0; c < kCB / 4; ++c) {
+            float h[4], o[4];
+  #pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              h[e] = __uint_as_float(__float_as_uint(a[4 * c + e]) & 0xFFFFE000u);
+              o[e] = a[4 * c + e] - h[e];
+            }
+            const int off = (c ^ (tid & 7)) * 16;
+            *reinterpret_cast<float4*>(hr + off) = make_float4(h[0], h[1], h[2], h[3]);
+            *reinterpret_cast<float4*>(lr + off) = make_float4(o[0], o[1], o[2], o[3]);
+          }
+        } else {
+          const int pos = ((tid & 4) ? H : 0) + 4 * (tid >> 3) + (tid & 3);
+  #pragma unroll
+          for (int t = 0; t < kCB; ++t) PnT[t * lp + pos] = a[t];
+        }
+      }
+      __syncthreads();
+      // (c) trailing update, rows/cols r0 .. l-1, lower triangle
+      if (TC) {
+        // D_t = rows 128 t .. 128 t + 127 of the panel copy times the first N_t
+        // rows (only columns c <= i are needed); TMEM columns 256 t ..
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        const int N = static_cast<int>(round_up(n2, 32));
+        const int tiles = (n2 + 127) / 128;
+        const uint32_t tm = s_tmem;
+        if (tid == 0) {
+          tc::tc_fence_after();
+          for (int t = 0; t < tiles; ++t) {
+            const int Nt = t == 0 ? min(N, 128) : N;
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(Nt >> 3) << 17) |
+                                   (static_cast<uint32_t>(128 >> 4) << 24);
+            const uint32_t ah = tc::smem_u32(T_hi + t * 16384), al = tc::smem_u32(T_lo + t * 16384);
+            const uint32_t bh = tc::smem_u32(T_hi), bl = tc::smem_u32(T_lo);
+  #pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {   // 8 TF32 (32 bytes) of K per instruction
+              const uint64_t dah = tc::kmajor_sw128_desc(ah + kk * 32), dal = tc::kmajor_sw128_desc(al + kk * 32);
+              const uint64_t dbh = tc::kmajor_sw128_desc(bh + kk * 32), dbl = tc::kmajor_sw128_desc(bl + kk * 32);
+              const uint32_t d = tm + static_cast<uint32_t>(t * 256);
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                  "l"(dah), "l"(dbh), "r"(idesc), "r"(kk > 0 ? 1u : 0u)
+                  : "memory");
+              asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dal), "l"(dbh),
+                           "r"(idesc)
+                           : "memory");
+              asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dah), "l"(dbl),
+                           "r"(idesc)
+                           : "memory");
+            }
+          }
+          tc::mma_commit(&s_mbar);
+        }
+        volatile int never = 0;
+        if (!tc::mbar_wait(&s_mbar, mphase, &never) && tid == 0) set_status(status, LRAMM_ERR_TIMEOUT);
+        mphase ^= 1u;
         tc::tc_fence_after();
+        const int q = warp & 3, part = warp >> 2;   // TMEM lanes 32 q .. 32 q + 31; column chunks part, part + 4
         for (int t = 0; t < tiles; ++t) {
           const int Nt = t == 0 ? min(N, 128) : N;
-          const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(Nt >> 3) << 17) |
-                                 (static_cast<uint32_t>(128 >> 4) << 24);
-          const uint32_t ah = tc::smem_u32(T_hi + t * 16384), al = tc::smem_u32(T_lo + t * 16384);
-          const uint32_t bh = tc::smem_u32(T_hi), bl = tc::smem_u32(T_lo);
-#pragma unroll
-          for (int kk = 0; kk < 4; ++kk) {   // 8 TF32 (32 bytes) of K per instruction
-            const uint64_t dah = tc::kmajor_sw128_desc(ah + kk * 32), dal = tc::kmajor_sw128_desc(al + kk * 32);
-            const uint64_t dbh = tc::kmajor_sw128_desc(bh + kk * 32), dbl = tc::kmajor_sw128_desc(bl + kk * 32);
-            const uint32_t d = tm + static_cast<uint32_t>(t * 256);
-            asm volatile(
-                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-                "l"(dah), "l"(dbh), "r"(idesc), "r"(kk > 0 ? 1u : 0u)
-                : "memory");
-            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dal), "l"(dbh),
-                         "r"(idesc)
-                         : "memory");
-            asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;" ::"r"(d), "l"(dah), "l"(dbl),
-                         "r"(idesc)
-                         : "memory");
-          }
-        }
-        tc::mma_commit(&s_mbar);
-      }
-      volatile int never = 0;
-      if (!tc::mbar_wait(&s_mbar, mphase, &never) && tid == 0) set_status(status, LRAMM_ERR_TIMEOUT);
-      mphase ^= 1u;
-      tc::tc_fence_after();
-      const int q = warp & 3, part = warp >> 2;   // TMEM lanes 32 q .. 32 q + 31; column chunks part, part + 4
-      for (int t = 0; t < tiles; ++t) {
-        const int Nt = t == 0 ? min(N, 128) : N;
-        for (int ch = part; ch < Nt / 32; ch += 4) {
-          float v[32];
-          tc::tmem_ld32(tm + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * 256 + ch * 32), v);
-          const int j = t * 128 + q * 32 + lane;
-          const int i = r0 + j;
-          if (j < n2) {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj) {
-              const int c = r0 + ch * 32 + jj;
-              if (c <= i) P[opidx(i, c)] -= v[jj];
+          for (int ch = part; ch < Nt / 32; ch += 4) {
+            float v[32];
+            tc::tmem_ld32(tm + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * 256 + ch * 32), v);
+            const int j = t * 128 + q * 32 + lane;
+            const int i = r0 + j;
+            if (j < n2) {
+  #pragma unroll
+              for (int jj = 0; jj < 32; ++jj) {
+                const int c = r0 + ch * 32 + jj;
+                if (c <= i) P[opidx(i, c)] -= v[jj];
+              }
             }
           }
         }
-      }
-      tc::tc_fence_before();
-    } else if (n2 >= 96) {  // 8 x 8 tiles
-      const int nb8 = (n2 + 7) / 8;
-      const int ntile = nb8 * (nb8 + 1) / 2;
-      for (int t = tid; t < ntile; t += blockDim.x) {
-        int bi = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-        while (bi * (bi + 1) / 2 > t) --bi;
-        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-        const int bc = t - bi * (bi + 1) / 2;
-        float acc[8][8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-          for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
-#pragma unroll 1
-        for (int k = 0; k < kCB; ++k) {
-          const float* row = PnT + k * lp;
-          const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * bi);
-          const float4 a1 = *reinterpret_cast<const float4*>(row + H + 4 * bi);
-          const float4 b0 = *reinterpret_cast<const float4*>(row + 4 * bc);
-          const float4 b1 = *reinterpret_cast<const float4*>(row + H + 4 * bc);
-          const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-          const float b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
+        tc::tc_fence_before();
+      } else if (n2 >= 96) {  // 8 x 8 tiles
+        const int nb8 = (n2 + 7) / 8;
+        const int ntile = nb8 * (nb8 + 1) / 2;
+        for (int t = tid; t < ntile; t += blockDim.x) {
+          int bi = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+          while (bi * (bi + 1) / 2 > t) --bi;
+          while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+          const int bc = t - bi * (bi + 1) / 2;
+          float acc[8][8];
+  #pragma unroll
           for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a8[u], b8[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const int i = r0 + 8 * bi + u, c = r0 + 8 * bc + v;
-            if (i < l && c <= i) P[opidx(i, c)] -= acc[u][v];
+  #pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
+  #pragma unroll 1
+          for (int k = 0; k < kCB; ++k) {
+            const float* row = PnT + k * lp;
+            const float4 a0 = *reinterpret_cast<const float4*>(row + 4 * bi);
+            const float4 a1 = *reinterpret_cast<const float4*>(row + H + 4 * bi);
+            const float4 b0 = *reinterpret_cast<const float4*>(row + 4 * bc);
+            const float4 b1 = *reinterpret_cast<const float4*>(row + H + 4 * bc);
+            const float a8[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+  #pragma unroll
+            for (int u = 0; u < 8; ++u)
+  #pragma unroll
+              for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(a8[u], b8[v], acc[u][v]);
           }
-      }
-    } else {  // 4 x 4 tiles
-      const int nb4 = (n2 + 3) / 4;
-      const int ntile = nb4 * (nb4 + 1) / 2;
-      for (int t = tid; t < ntile; t += blockDim.x) {
-        int bi = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-        while (bi * (bi + 1) / 2 > t) --bi;
-        while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-        const int bc = t - bi * (bi + 1) / 2;
-        float acc[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < kCB; ++k) {
-          const float4 av = *reinterpret_cast<const float4*>(PnT + k * lp + ((bi & 1) ? H : 0) + 4 * (bi >> 1));
-          const float4 bv = *reinterpret_cast<const float4*>(PnT + k * lp + ((bc & 1) ? H : 0) + 4 * (bc >> 1));
-          const float a4[4] = {av.x, av.y, av.z, av.w};
-          const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
-#pragma unroll
+  #pragma unroll
+          for (int u = 0; u < 8; ++u)
+  #pragma unroll
+            for (int v = 0; v < 8; ++v) {
+              const int i = r0 + 8 * bi + u, c = r0 + 8 * bc + v;
+              if (i < l && c <= i) P[opidx(i, c)] -= acc[u][v];
+            }
+        }
+      } else {  // 4 x 4 tiles
+        const int nb4 = (n2 + 3) / 4;
+        const int ntile = nb4 * (nb4 + 1) / 2;
+        for (int t = tid; t < ntile; t += blockDim.x) {
+          int bi = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+          while (bi * (bi + 1) / 2 > t) --bi;
+          while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+          const int bc = t - bi * (bi + 1) / 2;
+          float acc[4][4];
+  #pragma unroll
           for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a4[u], b4[v], acc[u][v]);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            const int i = r0 + 4 * bi + u, c = r0 + 4 * bc + v;
-            if (i < l && c <= i) P[opidx(i, c)] -= acc[u][v];
+  #pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+  #pragma unroll 8
+          for (int k = 0; k < kCB; ++k) {
+            const float4 av = *reinterpret_cast<const float4*>(PnT + k * lp + ((bi & 1) ? H : 0) + 4 * (bi >> 1));
+            const float4 bv = *reinterpret_cast<const float4*>(PnT + k * lp + ((bc & 1) ? H : 0) + 4 * (bc >> 1));
+            const float a4[4] = {av.x, av.y, av.z, av.w};
+            const float b4[4] = {bv.x, bv.y, bv.z, bv.w};
+  #pragma unroll
+            for (int u = 0; u < 4; ++u)
+  #pragma unroll
+              for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a4[u], b4[v], acc[u][v]);
           }
+  #pragma unroll
+          for (int u = 0; u < 4; ++u)
+  #pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              const int i = r0 + 4 * bi + u, c = r0 + 4 * bc + v;
+              if (i < l && c <= i) P[opidx(i, c)] -= acc[u][v];
+            }
+        }
       }
+      __syncthreads();
     }
     __syncthreads();
+    if (!s_bad || attempt > 0 || !(shift_big_rel > 0.f)) break;
+    __syncthreads();   // every thread has read s_bad
+    if (tid == 0) s_bad = 0;
+    restarted = true;
   }
-  __syncthreads();
+  if (tid == 0) {
+    if (s_bad) {
+      if (cp.brk) {   // the caller retries with a larger shift
+        *cp.brk = 1;
+        if (cp.brk_any) *cp.brk_any = 1;
+      } else {
+        set_status(status, LRAMM_ERR_NUMERIC);
+      }
+    }
+    if (restarted && cp.brk_any) *cp.brk_any = 1;
+    if ((restarted || s_bad) && cp.brk_count) atomicAdd(cp.brk_count, 1);
+  }
   if (TC && warp == 1) {
     tc::tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(s_tmem) : "memory");
@@ -828,7 +862,9 @@ __device__ __forceinline__ void trsm3_stage_X(const float* __restrict__ Xd, int 
 
 constexpr int kR3 = 64;
 
-__global__ void __launch_bounds__(256) trsm3_kernel(TrsmBatch tb, int l, int lqQ, int lqL) {
+__global__ void __launch_bounds__(256) trsm3_kernel(TrsmBatch tb, int l, int lqQ, int lqL,
+                                                    const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   const TrsmProb& tp = tb.p[blockIdx.y];
   const int64_t r0 = static_cast<int64_t>(blockIdx.x) * kR3;
   if (r0 >= tp.rows) return;
@@ -949,7 +985,7 @@ size_t gram_part_floats(int l) {
   return static_cast<size_t>(2) * 320 * kGT * kGT;
 }
 
-lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s) {
+lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s, const int* cond) {
   const int nt = (l + kGT - 1) / kGT;
   const int ntiles = nt * (nt + 1) / 2;
   int64_t rows = 0;
@@ -957,7 +993,7 @@ lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s) {
   bool vec = l % 4 == 0;
   for (int i = 0; i < gb.n; ++i) vec = vec && (reinterpret_cast<uintptr_t>(gb.p[i].Y) & 15) == 0;
   // 64-thread CTAs (8 x 8 per thread) run several per SM: aim at ~6 per SM
-  const int want = vec ? 6 * 152 : 2 * 152;
+  const int want = vec ? 6 * num_sms() : 2 * num_sms();
   int splits = static_cast<int>((want / gb.n + ntiles - 1) / ntiles);
   if (splits > 320 / ntiles) splits = 320 / ntiles;
   if (splits < 1) splits = 1;
@@ -966,12 +1002,12 @@ lramm_status launch_gram(GramBatch gb, int l, float* part, cudaStream_t s) {
   splits = static_cast<int>(ceil_div(rows, rps));
   if (static_cast<size_t>(gb.n) * splits * ntiles > 2 * 320) return LRAMM_ERR_UNSUPPORTED;
   if (vec)
-    gram_partial8_kernel<<<dim3(ntiles, splits, gb.n), 64, 0, s>>>(gb, l, ntiles, splits, rps, part);
+    gram_partial8_kernel<<<dim3(ntiles, splits, gb.n), 64, 0, s>>>(gb, l, ntiles, splits, rps, part, cond);
   else
-    gram_partial_kernel<false><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part);
+    gram_partial_kernel<false><<<dim3(ntiles, splits, gb.n), 256, 0, s>>>(gb, l, ntiles, splits, rps, part, cond);
   LRAMM_TRY(last_launch());
   const int64_t g = ceil_div(static_cast<int64_t>(ntiles) * kGT * kGT / 4 * gb.n, 64);
-  gram_reduce_kernel<<<static_cast<unsigned>(g), 64, 0, s>>>(gb, l, ntiles, splits, part);
+  gram_reduce_kernel<<<static_cast<unsigned>(g), 64, 0, s>>>(gb, l, ntiles, splits, part, cond);
   return last_launch();
 }
 
@@ -1013,23 +1049,24 @@ size_t chol3_tc_smem(int l) {
 
 bool chol3_supported(int l) { return l >= 4 && l % 4 == 0 && l - kCB <= 256 && chol3_smem(l) <= static_cast<size_t>(kSmemMaxO); }
 
-lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s) {
+lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s, const int* cond,
+                          float shift_big_rel) {
   if (!chol3_supported(l)) return LRAMM_ERR_UNSUPPORTED;
   if (chol3_tc_smem(l) <= static_cast<size_t>(kSmemMaxO)) {
     const size_t smem = chol3_tc_smem(l);
     LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         static_cast<int>(smem)));
-    chol3_kernel<true><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, status);
+    chol3_kernel<true><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, shift_big_rel, status, cond);
     return last_launch();
   }
   const size_t smem = chol3_smem(l);
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       static_cast<int>(smem)));
-  chol3_kernel<false><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, status);
+  chol3_kernel<false><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, shift_big_rel, status, cond);
   return last_launch();
 }
 
-lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s) {
+lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s, const int* cond) {
   // float4 staging: rows of Y, Q and L start on 16-byte boundaries
   if (l % 4 != 0) return LRAMM_ERR_UNSUPPORTED;
   for (int i = 0; i < tb.n; ++i)
@@ -1043,7 +1080,7 @@ lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s) {
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(trsm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
   int64_t rows = 0;
   for (int i = 0; i < tb.n; ++i) rows = tb.p[i].rows > rows ? tb.p[i].rows : rows;
-  trsm3_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kR3)), tb.n), 256, smem, s>>>(tb, l, lqQ, lqL);
+  trsm3_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kR3)), tb.n), 256, smem, s>>>(tb, l, lqQ, lqL, cond);
   return last_launch();
 }
 
@@ -1085,7 +1122,9 @@ __host__ __device__ inline SplitPtrs split_ptrs(float* w, int l) {
   return p;
 }
 
-__global__ void __launch_bounds__(256) chol_split_prep_kernel(CholBatch cb, SplitScratch sc, int l, float shift_rel) {
+__global__ void __launch_bounds__(256) chol_split_prep_kernel(CholBatch cb, SplitScratch sc, int l, float shift_rel,
+                                                              const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   const CholProb& cp = cb.p[blockIdx.y];
   const float* __restrict__ G = cp.G;
   __shared__ float s_red[8];
@@ -1115,7 +1154,9 @@ __global__ void __launch_bounds__(256) chol_split_prep_kernel(CholBatch cb, Spli
   }
 }
 
-__global__ void __launch_bounds__(256) chol_split_assemble_kernel(CholBatch cb, SplitScratch sc, int l) {
+__global__ void __launch_bounds__(256) chol_split_assemble_kernel(CholBatch cb, SplitScratch sc, int l,
+                                                                  const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
   float* __restrict__ Lo = cb.p[blockIdx.y].L;
   const int h = chol_split_h_dev(l), m = l - h;
   const SplitPtrs sp = split_ptrs(sc.w[blockIdx.y], l);
@@ -1130,29 +1171,47 @@ __global__ void __launch_bounds__(256) chol_split_assemble_kernel(CholBatch cb, 
   }
 }
 
-lramm_status launch_chol_split(CholBatch cb, SplitScratch sc, int l, float shift_rel, int* status, cudaStream_t s) {
+lramm_status launch_chol_split(CholBatch cb, SplitScratch sc, int l, float shift_rel, int* status, cudaStream_t s,
+                               const int* cond) {
   if (!chol_split_supported(l)) return LRAMM_ERR_UNSUPPORTED;
   const int h = chol_split_h(l), m = l - h;
   const dim3 grid(static_cast<unsigned>(ceil_div(static_cast<int64_t>(l) * l, 256 * 8)), cb.n);
-  chol_split_prep_kernel<<<grid, 256, 0, s>>>(cb, sc, l, shift_rel);
+  chol_split_prep_kernel<<<grid, 256, 0, s>>>(cb, sc, l, shift_rel, cond);
   LRAMM_TRY(last_launch());
   CholBatch c1{}, c2{};
   TrsmBatch t1{};
   c1.n = c2.n = t1.n = cb.n;
   for (int i = 0; i < cb.n; ++i) {
     const SplitPtrs sp = split_ptrs(sc.w[i], l);
-    c1.p[i] = CholProb{sp.G11, sp.L11, cb.p[i].Xd};
+    c1.p[i] = CholProb{sp.G11, sp.L11, cb.p[i].Xd, cb.p[i].brk, cb.p[i].brk_any, cb.p[i].brk_count};
     t1.p[i] = TrsmProb{sp.G21, sp.L21, sp.L11, cb.p[i].Xd, m};
-    c2.p[i] = CholProb{sp.S, sp.L22, cb.p[i].Xd + static_cast<int64_t>(h / kCB) * kCB * kCB};
+    c2.p[i] = CholProb{sp.S, sp.L22, cb.p[i].Xd + static_cast<int64_t>(h / kCB) * kCB * kCB, cb.p[i].brk,
+                       cb.p[i].brk_any, cb.p[i].brk_count};
   }
-  LRAMM_TRY(launch_chol3(c1, h, 0.f, status, s));
-  LRAMM_TRY(launch_trsm3(t1, h, s));
+  LRAMM_TRY(launch_chol3(c1, h, 0.f, status, s, cond));
+  LRAMM_TRY(launch_trsm3(t1, h, s, cond));
   for (int i = 0; i < cb.n; ++i) {
     const SplitPtrs sp = split_ptrs(sc.w[i], l);
-    LRAMM_TRY(sgemm(0, 1, m, m, h, -1.f, sp.L21, h, 0, sp.L21, h, 1.f, sp.S, m, s));   // S = G22 - L21 L21^T
+    LRAMM_TRY(sgemm(0, 1, m, m, h, -1.f, sp.L21, h, 0, sp.L21, h, 1.f, sp.S, m, s, cond));   // S = G22 - L21 L21^T
   }
-  LRAMM_TRY(launch_chol3(c2, m, 0.f, status, s));
-  chol_split_assemble_kernel<<<grid, 256, 0, s>>>(cb, sc, l);
+  LRAMM_TRY(launch_chol3(c2, m, 0.f, status, s, cond));
+  chol_split_assemble_kernel<<<grid, 256, 0, s>>>(cb, sc, l, cond);
+  return last_launch();
+}
+
+__global__ void copy_cond_kernel(const float* __restrict__ src, float* __restrict__ dst, int64_t n,
+                                 const int* __restrict__ cond) {
+  if (*cond == 0) return;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < n;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    dst[e] = src[e];
+}
+
+lramm_status launch_copy_cond(const float* src, float* dst, int64_t n, const int* cond, cudaStream_t s) {
+  if (n <= 0) return LRAMM_OK;
+  int64_t g = ceil_div(n, 256);
+  if (g > num_sms() * 4) g = num_sms() * 4;
+  copy_cond_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(src, dst, n, cond);
   return last_launch();
 }
 

@@ -79,7 +79,7 @@ __global__ void gaussian_kernel(uint64_t seed, uint32_t sid, int64_t rows, int64
 
 static int grid_for(int64_t work, int threads) {
   int64_t g = ceil_div(work, threads);
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > num_sms() * 32) g = num_sms() * 32;
   if (g < 1) g = 1;
   return (int)g;
 }

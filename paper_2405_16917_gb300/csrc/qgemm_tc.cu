@@ -60,6 +60,7 @@ struct QtcParams {
   float* part;   // chunks > 1: chunks x M x N partial sums
   int scaled;    // codes: dequantise with sL, sR; TF32: no scales
   int tma_store; // one chunk, beta = 0, D a valid TMA target: 32 x 32 blocks stored by TMA
+  int nstg;      // staging blocks per epilogue warp (stores in flight per warp)
   int* status;
 };
 
@@ -213,16 +214,20 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
       // Each lane owns one output row of the block: the dequantised values go
       // to a staging block in the 128-byte swizzled layout (16-byte chunk c
       // of row r at chunk position c ^ (r mod 8)) and one lane stores the
-      // block with a TMA bulk copy; two staging blocks per warp alternate.
-      // The blocks live in the operand ring (at least 2 x 16 KB of A tiles),
-      // free once the accumulator is complete: every copy into the ring was
-      // consumed by an MMA before tmem_bar arrived.
+      // block with a TMA bulk copy; nstg staging blocks per warp rotate, so
+      // that many stores of a warp are in flight (the output write is what
+      // bounds this product).  The blocks live in the operand ring, free once
+      // the accumulator is complete: every copy into the ring was consumed by
+      // an MMA before tmem_bar arrived.
       for (int c0 = 0, nb = 0; c0 < p.bn; c0 += 32, ++nb) {
         float v[32];
         tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
-        float* stg = reinterpret_cast<float*>(sA) + (q * 2 + (nb & 1)) * 1024;
-        if (nb >= 2) {   // this staging block's previous store has finished reading it
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        float* stg = reinterpret_cast<float*>(sA) + (q * p.nstg + nb % p.nstg) * 1024;
+        if (nb >= p.nstg) {   // this staging block's previous store has finished reading it
+          if (lane == 0) {
+            if (p.nstg == 4) asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+            else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          }
           __syncwarp();
         }
 #pragma unroll
@@ -633,7 +638,11 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
   // TMA stores of the output: one K chunk, no beta C term, D 16-byte aligned
   // with a row pitch that is a multiple of 16 bytes
   CUtensorMap mD;
-  p.tma_store = sh.chunks == 1 && p.beta == 0.f && p.stages * p.a_bytes >= 8 * 4096 &&
+  // staging blocks of 4 KB in the operand ring: four per epilogue warp where
+  // the ring holds 16, else two
+  const uint32_t ring = static_cast<uint32_t>(p.stages) * (p.a_bytes + p.b_bytes);
+  p.nstg = ring >= 16 * 4096 ? 4 : 2;
+  p.tma_store = sh.chunks == 1 && p.beta == 0.f && ring >= 8 * 4096 &&
                 (reinterpret_cast<uintptr_t>(p.D) % 16) == 0 &&
                 (p.ldd * 4) % 16 == 0 && p.ldd >= N &&
                 make_map_2d(&mD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.D, N, M, p.ldd * 4, 32, 32,
@@ -661,7 +670,7 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
   LRAMM_TRY(last_launch());
   if (sh.chunks > 1) {
     int64_t g = ceil_div(M * N, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > num_sms() * 8) g = num_sms() * 8;
     if (kind == kKindBF16)
       qgemm_tc_reduce_kernel<true><<<static_cast<unsigned>(g), 256, 0, s>>>(p);
     else

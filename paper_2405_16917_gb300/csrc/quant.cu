@@ -86,7 +86,7 @@ lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t l
     if (!amax_ws) return LRAMM_ERR_INVALID_ARG;
     LRAMM_CUDA_TRY(cudaMemsetAsync(amax_ws, 0, sizeof(unsigned int), s));
     int64_t g = ceil_div(rows * cols, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > num_sms() * 8) g = num_sms() * 8;
     if (g < 1) g = 1;
     tensor_amax_kernel<<<(unsigned)g, 256, 0, s>>>(X, rows, cols, ldx, amax_ws);
     LRAMM_TRY(last_launch());
@@ -94,7 +94,7 @@ lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t l
   }
   const int threads = 256, wpb = threads / 32;
   int64_t g = ceil_div(rows, wpb);
-  if (g > 152 * 16) g = 152 * 16;
+  if (g > num_sms() * 16) g = num_sms() * 16;
   switch (prec) {
     case LRAMM_P_INT8:
       quant_rows_kernel<LRAMM_P_INT8><<<(unsigned)g, threads, 0, s>>>(X, rows, cols, ldx, codes, ldcodes, scales, tam);
@@ -130,7 +130,7 @@ lramm_status fp8_codes_to_bf16(const void* src, int64_t rows, int64_t cols, int6
                                cudaStream_t s) {
   if (rows <= 0 || cols <= 0) return LRAMM_OK;
   int64_t g = ceil_div(rows * cols, 256);
-  if (g > 152 * 8) g = 152 * 8;
+  if (g > num_sms() * 8) g = num_sms() * 8;
   fp8_to_bf16_kernel<<<(unsigned)g, 256, 0, s>>>(static_cast<const uint8_t*>(src), rows, cols, lds,
                                                  static_cast<__nv_bfloat16*>(dst), ldd);
   return last_launch();
@@ -201,7 +201,7 @@ lramm_status quantize_cols(const float* X, int64_t rows, int64_t cols, int64_t l
     if (!amax_ws) return LRAMM_ERR_INVALID_ARG;
     LRAMM_CUDA_TRY(cudaMemsetAsync(amax_ws, 0, sizeof(unsigned int), s));
     int64_t g = ceil_div(rows * cols, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > num_sms() * 8) g = num_sms() * 8;
     if (g < 1) g = 1;
     tensor_amax_kernel<<<(unsigned)g, 256, 0, s>>>(X, rows, cols, ldx, amax_ws);
     LRAMM_TRY(last_launch());
@@ -291,7 +291,7 @@ lramm_status quantize_cols2d(const float* X, int64_t rows, int64_t cols, int64_t
   if (ldcodes < rows || !amax_cols) return LRAMM_ERR_INVALID_ARG;
   const int64_t cblocks = ceil_div(cols, 32);
   // row chunks (multiples of 32) so that the grid has about two CTAs per SM
-  int64_t nchunks = ceil_div(2 * 152, cblocks);
+  int64_t nchunks = ceil_div(2 * num_sms(), cblocks);
   int64_t rchunk = round_up(ceil_div(ldcodes, nchunks), 32);
   if (rchunk < 32) rchunk = 32;
   nchunks = ceil_div(ldcodes, rchunk);

@@ -433,7 +433,8 @@ struct GramTcParams {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p) {
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;   // predicated launch (the CholeskyQR fallback)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
@@ -580,7 +581,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p) {
 }
 
 // out = sum over splits of part[s] (fixed order), n4 float4 per split.
-__global__ void split_reduce_kernel(const float4* __restrict__ part, int splits, int64_t n4, float4* __restrict__ out) {
+__global__ void split_reduce_kernel(const float4* __restrict__ part, int splits, int64_t n4, float4* __restrict__ out,
+                                    const int* __restrict__ cond = nullptr) {
+  if (cond && *cond == 0) return;
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float4 a = part[i];
@@ -611,7 +614,10 @@ bool sketch_tc_supported(int xbf, int64_t ldx, int l, const void* X, const void*
 
 // Split-K partials: one 128-row block per CTA slot (two slots per SM when l
 // is narrow enough for two CTAs per SM).
-size_t sketch_tc_part_floats(int l) { return static_cast<size_t>(l <= 160 ? 2 * 152 : 152) * kBM * l; }
+// (workspace is sized at plan creation, before a device is known: for 152
+// SMs; on a larger part the split count is capped by these buffers)
+constexpr size_t kPartSlots = 152;
+size_t sketch_tc_part_floats(int l) { return (l <= 160 ? 2 * kPartSlots : kPartSlots) * kBM * l; }
 
 bool sketch_bf_supported(int64_t ldx, int l, const void* X, const void* B) {
   return l % 4 == 0 && l >= 4 && ldx % 8 == 0 && (reinterpret_cast<uintptr_t>(X) % 16) == 0 &&
@@ -649,7 +655,7 @@ lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int6
   p.tmem_cols = tc;
   p.status = status;
   const int64_t mtiles = ceil_div(M, kBM);
-  int64_t splits = 152 / (mtiles * nslices);
+  int64_t splits = num_sms() / (mtiles * nslices);
   if (splits > p.kblocks / 8) splits = p.kblocks / 8;
   if (splits < 1) splits = 1;
   while (splits > 1 && static_cast<size_t>(splits) * M * l > part_floats) --splits;
@@ -662,7 +668,7 @@ lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int6
   __nv_bfloat16* lo = nb > 1 ? hi + K * p.npad : nullptr;
   {
     int64_t g = ceil_div(K * p.npad, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > num_sms() * 8) g = num_sms() * 8;
     split_bf16_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(B, K, l, p.npad, hi, lo);
     LRAMM_TRY(last_launch());
   }
@@ -684,7 +690,7 @@ lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int6
   if (splits > 1) {
     const int64_t n4 = M * l / 4;
     int64_t g = ceil_div(n4, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > num_sms() * 8) g = num_sms() * 8;
     split_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
                                                                   static_cast<int>(splits), n4,
                                                                   reinterpret_cast<float4*>(out));
@@ -715,10 +721,11 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
   // (measured 1.4x faster on the 32768 x 4096 products); otherwise one CTA
   // per SM with the deepest ring that fits.
   const uint32_t stage_bytes = p.a_bytes + p.b_bytes;
-  int slots = 152;
+  const int nsm = num_sms();
+  int slots = nsm;
   if (1024 + 3 * stage_bytes <= 112 * 1024) {   // two CTAs within the SM's 228 KB
     p.stages = 3;
-    slots = 2 * 152;
+    slots = 2 * nsm;
   } else {
     p.stages = static_cast<int>((kSmemBudget - 1024) / stage_bytes);
     if (p.stages > kMaxStages) p.stages = kMaxStages;
@@ -750,7 +757,7 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
   if (splits > 1) {
     const int64_t n4 = M * l / 4;
     int64_t g = ceil_div(n4, 256);
-    if (g > 152 * 8) g = 152 * 8;
+    if (g > num_sms() * 8) g = num_sms() * 8;
     split_reduce_kernel<<<static_cast<unsigned>(g), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
                                                                   static_cast<int>(splits), n4,
                                                                   reinterpret_cast<float4*>(out));
@@ -761,12 +768,12 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
 
 // Gram on the tensor cores (split TF32) for one or two problems.
 static int gram_tc_width(int l) { return static_cast<int>(round_up(l, kBM)); }   // staged tile width
-size_t gram_tc_part_floats(int l) { return static_cast<size_t>(152) * l * l; }
+size_t gram_tc_part_floats(int l) { return kPartSlots * l * l; }
 
 bool gram_tc_supported(int l) { return l >= 4 && l % 4 == 0 && l <= 512; }
 
 lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* const* G, int l, float* part,
-                     size_t part_floats, int* status, cudaStream_t s) {
+                     size_t part_floats, int* status, cudaStream_t s, const int* cond) {
   if (!gram_tc_supported(l) || n < 1 || n > 2) return LRAMM_ERR_UNSUPPORTED;
   GramTcParams p{};
   p.l = l;
@@ -788,7 +795,7 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
     p.rows = rows[i];
     p.kblocks = ceil_div(rows[i], kBK);
-    int64_t splits = 152 / mtiles;
+    int64_t splits = num_sms() / mtiles;
     if (splits > p.kblocks / 2) splits = p.kblocks / 2;   // at least two K blocks per CTA
     if (splits < 1) splits = 1;
     while (splits > 1 && static_cast<size_t>(splits) * l * l > part_floats) --splits;
@@ -803,15 +810,16 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     if (!make_map_f32(&my, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, kAtom, kBK,
                       CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
       return LRAMM_ERR_CUDA;
-    gram_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, p);
+    gram_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, p,
+                                                                                                          cond);
     LRAMM_TRY(last_launch());
     if (splits > 1) {
       const int64_t n4 = static_cast<int64_t>(l) * l / 4;
       int64_t g2 = ceil_div(n4, 256);
-      if (g2 > 152 * 8) g2 = 152 * 8;
+      if (g2 > num_sms() * 8) g2 = num_sms() * 8;
       split_reduce_kernel<<<static_cast<unsigned>(g2), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
                                                                      static_cast<int>(splits), n4,
-                                                                     reinterpret_cast<float4*>(G[i]));
+                                                                     reinterpret_cast<float4*>(G[i]), cond);
       LRAMM_TRY(last_launch());
     }
   }

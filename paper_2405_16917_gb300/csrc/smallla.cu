@@ -1084,7 +1084,7 @@ lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s) {
   int64_t rows = 0;
   for (int i = 0; i < bt.n; ++i) rows = bt.p[i].rows > rows ? bt.p[i].rows : rows;
   int64_t grid = ceil_div(rows, nw);
-  const int64_t cap = (152 + bt.n - 1) / bt.n;
+  const int64_t cap = (num_sms() + bt.n - 1) / bt.n;
   if (grid > cap) grid = cap;
   trsm_rows_kernel<<<dim3((unsigned)grid, bt.n), threads, smem, s>>>(bt, l);
   return last_launch();

@@ -39,7 +39,12 @@ def probe_matrix(n, probes, seed):
 
 
 def estimate_error(A, B, D, probes=8, seed=11):
-    """||(A B - D) G||_F / ||A B G||_F with G = n x probes Gaussian (FP32 products)."""
+    """||(A B - D) G||_F / ||A B G||_F with G = n x probes Gaussian (FP32 products).
+
+    The products run in the library; the two Frobenius norms of the m x
+    probes results are taken on the host.  They are the tuner's measurement
+    of a candidate's error (a few thousand numbers), not a step of the
+    product path, which lramm_matmul runs entirely on the device."""
     import paper_2405_16917_gb300 as L
     n = B.shape[1]
     G = probe_matrix(n, probes, seed)

@@ -125,7 +125,7 @@ def operands(name, scale=None):
     return A, B
 
 
-def device_operands(name, device, dtype=None):
+def device_operands(name, device, dtype=None, sizes=None):
     """(A, B) of a full-size workload generated on a torch device (FP32 or BF16).
 
     Uses the same seeded Gaussian draws as `operands` (numpy, host side) but
@@ -137,7 +137,7 @@ def device_operands(name, device, dtype=None):
     import torch
 
     c = CONFIGS[name]
-    m, n, k = c["m"], c["n"], c["k"]
+    m, n, k = sizes if sizes is not None else (c["m"], c["n"], c["k"])
     tdt = dtype or (torch.bfloat16 if c["dtype"] == "bf16" else torch.float32)
 
     def haar_dev(rows, cols, rng):
