@@ -67,7 +67,7 @@ constexpr int64_t kGramTcRows = 2048;          // sketches from this many rows t
 
 struct SideLayout {
   int64_t rows, cols;
-  size_t omega, R0, R1, C0, C1, G, L1, L2, L3, Xd, R, Vj, sig, S1, S2, S1T, S2T, CS;
+  size_t omega, R0, R1, C0, C1, G, L1, L2, L3, Xd, Lh, Ll, R, Vj, sig, S1, S2, S1T, S2T, CS;
   size_t part, gpart, gtpart, bsplit;   // this operand's split-K partials and BF16 parts (own stream)
   // E4M3 range finder: codes of X per row (rows x cols_p) and per column
   // (cols x rows_p), of the l-column operand (l x max(rows_p, cols_p)), their
@@ -185,6 +185,8 @@ void layout(lramm_plan_s* P) {
     S.L2 = b.take(sizeof(float) * l * l);
     S.L3 = b.take(sizeof(float) * l * l);
     S.Xd = b.take(sizeof(float) * ceil_div(l, 32) * 32 * 32);
+    S.Lh = b.take(sizeof(float) * l * l);   // L^-1 in TF32 parts (tensor-core bases)
+    S.Ll = b.take(sizeof(float) * l * l);
     S.CS = chol_split_supported((int)l) ? b.take(sizeof(float) * chol_split_scratch_floats((int)l)) : 0;
     S.R = b.take(sizeof(float) * l * l);
     S.Vj = b.take(sizeof(float) * l * l);
@@ -443,6 +445,10 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
   const bool csplit = !c3 && chol_split_supported(l);
   retry = retry && ns == 1 && (c3 || csplit);
   const bool third = retry && passes == 2 && P->d.sketch == LRAMM_SKETCH_F32;
+  // tensor-core range finders: the bases Q = Y L^-T by the split-TF32
+  // product with L^-1 (accuracy of the split-TF32 Gram); FP32 range finders
+  // keep the FP32 panel solve
+  const bool tcb = P->d.sketch != LRAMM_SKETCH_F32 && basis_tc_supported(l);
   int* brk = nullptr;
   int* any = nullptr;
   if (retry) {
@@ -518,7 +524,17 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
     }
       TIMED(P, LRAMM_K_CHOL, s,
             launch_chol3(cb3, l, kCholShift, st, s, cond, guard ? chol_shift_big(rows[0], l) : 0.f));
-      if (solve) TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s, scond));
+      if (solve && tcb) {   // Q = Y L^-T on the tensor cores from the explicit inverse
+        LinvBatch lb{};
+        lb.n = ns;
+        for (int i = 0; i < ns; ++i)
+          lb.p[i] = LinvProb{cb3.p[i].L, cb3.p[i].Xd, at<float>(ws, sd[i].S->Lh), at<float>(ws, sd[i].S->Ll)};
+        TIMED(P, LRAMM_K_TRSM, s, launch_linv(lb, l, s, scond));
+        for (int i = 0; i < ns; ++i)
+          TIMED(P, LRAMM_K_TRSM, s, basis_tc(in[i], rows[i], lb.p[i].Lh, lb.p[i].Ll, out[i], l, st, s, scond));
+      } else if (solve) {
+        TIMED(P, LRAMM_K_TRSM, s, launch_trsm3(tb3, l, s, scond));
+      }
     } else if (csplit) {  // two-level Cholesky, same panel solve
       SplitScratch sc{};
       for (int i = 0; i < ns; ++i) sc.w[i] = at<float>(ws, sd[i].S->CS);

@@ -195,6 +195,19 @@ bool chol3_supported(int l);
 lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s,
                           const int* cond = nullptr, float shift_big_rel = 0.f);
 lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s, const int* cond = nullptr);
+// L^-1 of chol3_kernel's factor (L dense lower, Xd its inverted diagonal
+// blocks) as TF32 high / low parts Lh, Ll (l x l row-major each).
+struct LinvProb {
+  const float* L;
+  const float* Xd;
+  float* Lh;
+  float* Ll;
+};
+struct LinvBatch {
+  LinvProb p[2];
+  int n;
+};
+lramm_status launch_linv(LinvBatch lb, int l, cudaStream_t s, const int* cond = nullptr);
 // dst = src (n floats) when *cond != 0
 lramm_status launch_copy_cond(const float* src, float* dst, int64_t n, const int* cond, cudaStream_t s);
 // Two-level Cholesky for 288 < l <= 576 (l % 4 == 0) on chol3 / trsm3 /
@@ -263,6 +276,11 @@ lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int6
                        int* status, cudaStream_t s);
 lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int64_t ldx, int xbf, const float* B,
                        int l, float* out, float* part, size_t part_floats, int* status, cudaStream_t s);
+// Q = Y L^-T (Y rows x l, stride l; Q may be Y) in split TF32 from the parts
+// Lh + Ll = L^-1 written by launch_linv; l % 4 == 0, 16 <= l <= 288.
+bool basis_tc_supported(int l);
+lramm_status basis_tc(const float* Y, int64_t rows, const float* Lh, const float* Ll, float* Q, int l, int* status,
+                      cudaStream_t s, const int* cond = nullptr);
 
 // quant.cu
 lramm_status quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,

@@ -450,8 +450,10 @@ __global__ void __launch_bounds__(256) trsm_panel_kernel(SmallBatch bt, int l, i
 //       forward substitution, reading columns of L_JJ as float4 broadcasts;
 //   (c) the trailing update A_22 -= L_2J L_2J^T in 4 x 4 register tiles from
 //       a transposed copy of the panel.
-// At the end every warp inverts some diagonal blocks L_JJ (lane c forms
-// column c of the inverse) for the triangular solve of the tall sketch.
+// While warp 0 factors diagonal block J+1, warps 1..7 write column block J
+// of L to global memory and warps 8..15 invert L_JJ (for the triangular
+// solve, or the explicit inverse, of the tall sketch); the last block
+// follows the panel loop.
 // A non-positive pivot latches LRAMM_ERR_NUMERIC and is replaced by a tiny
 // positive value, as in chol2_kernel.
 // ---------------------------------------------------------------------------
@@ -461,6 +463,52 @@ constexpr int kLC = kCB + 4;   // row stride of the column-major copy of L_JJ
 __host__ __device__ inline int chol_split_h_dev(int l) {
   const int h = ((l + 1) / 2 + kCB - 1) / kCB * kCB;
   return h < 288 ? h : 288;
+}
+
+// Inverse of the diagonal block at j0 (w x w, w <= 32) of the packed
+// factor P into xg (32 x 32 row-major, zero outside w x w), by the eight
+// warps v = 0..7 of the calling group (named barrier 2, 256 threads): column
+// c = 4v + lane / 8 on the eight lanes 8 (lane / 8) .. +7, lane e of them
+// holding rows e, e+8, e+16, e+24.  Forward substitution in column order
+// (b = e_c; for each t: x_t = b_t / L_tt, then b_i -= L_it x_t for i > t;
+// finally x_i = b_i / L_ii): each x_i is the same FP32 chain as the
+// row-order substitution x_i = -(sum_t L_it x_t) / L_ii.  s_rl: 32 floats.
+__device__ __forceinline__ void chol_inv_block(const float* P, int j0, int w, float* xg, float* s_rl, int v,
+                                               int lane) {
+  if (v == 0) s_rl[lane] = 1.0f / (lane < w ? P[opidx(j0 + lane, j0 + lane)] : 1.0f);
+  asm volatile("bar.sync 2, 256;" ::: "memory");
+  const int c = 4 * v + (lane >> 3), e = lane & 7, base = lane & ~7;
+  float b[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) b[u] = e + 8 * u == c ? 1.f : 0.f;
+#pragma unroll 1
+  for (int t = 0; t < w; ++t) {
+    // b_t from its owner lane (slot t / 8, picked with bit masks: a
+    // conditional pick was turned into a local-memory copy of b)
+    const uint32_t su = static_cast<uint32_t>(t >> 3);
+    uint32_t mine = 0u;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) mine |= __float_as_uint(b[u]) & (0u - static_cast<uint32_t>(su == u));
+    const float xt = __uint_as_float(__shfl_sync(0xffffffffu, mine, base | (t & 7))) * s_rl[t];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = e + 8 * u;
+      if (i > t && i < w) b[u] = fmaf(-P[opidx(j0 + i, j0 + t)], xt, b[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int i = e + 8 * u;
+    xg[i * kCB + c] = (i < w && c < w) ? b[u] * s_rl[i] : 0.f;
+  }
+}
+
+// Column block j0 .. j0+31 of L (row-major, zero above the diagonal) from
+// the packed factor, rows v, v + nv, ..; lane = column.
+__device__ __forceinline__ void chol_write_L_block(const float* P, float* Lo, int l, int j0, int v, int nv, int lane) {
+  const int col = j0 + lane;
+  if (col >= l) return;
+  for (int r = v; r < l; r += nv) Lo[static_cast<int64_t>(r) * l + col] = r >= col ? P[opidx(r, col)] : 0.f;
 }
 
 // TC: the trailing update runs on the tensor cores (kind::tf32, split into
@@ -488,6 +536,7 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   float* LC = TC ? PnT : PnT + kCB * lp;                  // kCB x kLC: LC[t][c] = L_JJ[c][t], c > t
   __shared__ float s_red[32];
   __shared__ float s_rinv[kCB];
+  __shared__ float s_rl[kCB];   // 1 / L_tt of the diagonal block being inverted
   __shared__ int s_bad;   // a pivot of this attempt was not positive
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
@@ -594,6 +643,13 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
           if (lane < w && c <= lane) P[opidx(j0 + lane, j0 + c)] = a[c];
           LC[c * kLC + lane] = (lane < w && c < lane) ? a[c] : 0.f;
         }
+      } else if (j0 > 0) {
+        // meanwhile the previous column block is final: warps 1..7 write it
+        // to L, warps 8..15 invert its diagonal block
+        if (warp >= 8)
+          chol_inv_block(P, j0 - kCB, kCB, Xd + static_cast<int64_t>(j0 / kCB - 1) * kCB * kCB, s_rl, warp - 8, lane);
+        else
+          chol_write_L_block(P, Lo, l, j0 - kCB, warp - 1, 7, lane);
       }
       __syncthreads();
       const int r0 = j0 + kCB;   // first row below the diagonal block
@@ -793,35 +849,14 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
     tc::tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(s_tmem) : "memory");
   }
+  // The last column block (the others were written and inverted inside the
+  // panel loop, during the next diagonal block's factorisation).
   {
-    const int nq = l * l / 4, lq4 = l / 4;
-    float4* L4 = reinterpret_cast<float4*>(Lo);
-    for (int q = tid; q < nq; q += blockDim.x) {
-      const int i = q / lq4, j = 4 * (q - i * lq4);
-      float e4[4];
-#pragma unroll
-      for (int t = 0; t < 4; ++t) e4[t] = j + t <= i ? P[opidx(i, j + t)] : 0.f;
-      L4[q] = make_float4(e4[0], e4[1], e4[2], e4[3]);
-    }
-  }
-  // inverses of the diagonal blocks: column `lane` of L_JJ^-1 by forward
-  // substitution, L_JJ read from shared memory (one element for all lanes)
-  const int nb = (l + kCB - 1) / kCB;
-  for (int J = warp; J < nb; J += nw) {
-    const int j0 = J * kCB, w = min(kCB, l - j0);
-    float x[kCB];
-#pragma unroll
-    for (int i = 0; i < kCB; ++i) {
-      const float* Li = P + opidx(j0 + min(i, w - 1), j0);
-      const float rinv = i < w ? 1.0f / Li[i] : 1.0f;
-      float acc = 0.f;
-#pragma unroll
-      for (int t = 0; t < i; ++t) acc = fmaf(i < w ? Li[t] : 0.f, x[t], acc);
-      x[i] = lane < i ? -acc * rinv : (lane == i ? rinv : 0.f);
-    }
-    float* xg = Xd + static_cast<int64_t>(J) * kCB * kCB;
-#pragma unroll
-    for (int i = 0; i < kCB; ++i) xg[i * kCB + lane] = (i < w && lane < w) ? x[i] : 0.f;
+    const int jl = ((l - 1) / kCB) * kCB;
+    if (warp >= 8)
+      chol_inv_block(P, jl, l - jl, Xd + static_cast<int64_t>(jl / kCB) * kCB * kCB, s_rl, warp - 8, lane);
+    else
+      chol_write_L_block(P, Lo, l, jl, warp, 8, lane);
   }
 }
 
@@ -977,6 +1012,101 @@ __global__ void __launch_bounds__(256) trsm3_kernel(TrsmBatch tb, int l, int lqQ
   }
 }
 
+// ---------------------------------------------------------------------------
+// L^-1 from the blocked factor, one CTA per 32-column block J: the block's
+// diagonal part is X_JJ = L_JJ^-1 (from chol3_kernel) and its rows below
+// follow block row by block row,
+//   Li_IJ = -X_II (sum_{K=J}^{I-1} L_IK Li_KJ),   I = J+1, ..,
+// with the column block held in shared memory and each block row's panel of
+// L (rows of block I, columns j0 .. i0-1) and X_II staged there first (one
+// round of coalesced loads per block row).  The result is written as TF32
+// high and low parts (Lh = the top 10 mantissa bits, Ll = Li - Lh, both
+// l x l row-major, zero above the diagonal) for basis_tc_kernel.
+// Thread t owns row t / 8 and columns 4 (t mod 8) .. +3 of a 32 x 32 block.
+// ---------------------------------------------------------------------------
+constexpr int kLiS = kCB + 1;   // row stride of the column block and of S, X in shared memory
+
+__global__ void __launch_bounds__(256) linv_kernel(LinvBatch lb, int l, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
+  const LinvProb& pb = lb.p[blockIdx.y];
+  extern __shared__ float4 li_smem4[];
+  const int J = blockIdx.x, j0 = J * kCB, nb = (l + kCB - 1) / kCB;
+  const int pw = l - j0 + 4;                 // row stride of the staged panel (at most l - j0 columns)
+  float* C = reinterpret_cast<float*>(li_smem4);   // rows j0 .. l-1 of column block J (row r at r - j0)
+  float* S = C + (l - j0) * kLiS;           // 32 x kLiS
+  float* X = S + kCB * kLiS;                // 32 x kLiS: X_II
+  float* Pn = X + kCB * kLiS;               // 32 x pw: L rows i0 .., columns j0 .. i0-1
+  const int tid = threadIdx.x, i = tid >> 3, jq = 4 * (tid & 7);
+  const float* __restrict__ L = pb.L;
+  {  // X_JJ (rows and columns beyond l are zero in Xd)
+    const float* xr = pb.Xd + static_cast<int64_t>(J) * kCB * kCB + i * kCB + jq;
+    if (j0 + i < l)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) C[i * kLiS + jq + u] = xr[u];
+  }
+  for (int I = J + 1; I < nb; ++I) {
+    const int i0 = I * kCB, wI = min(kCB, l - i0), kw = i0 - j0;   // kw: a multiple of 32
+    // stage the panel and X_II
+    for (int e = tid; e < wI * (kw / 4); e += 256) {
+      const int r = e / (kw / 4), c4 = e - r * (kw / 4);
+      const float4 v = *reinterpret_cast<const float4*>(L + static_cast<int64_t>(i0 + r) * l + j0 + 4 * c4);
+      float* d = Pn + r * pw + 4 * c4;
+      d[0] = v.x;
+      d[1] = v.y;
+      d[2] = v.z;
+      d[3] = v.w;
+    }
+    {
+      const float4 v = *reinterpret_cast<const float4*>(pb.Xd + static_cast<int64_t>(I) * kCB * kCB + i * kCB + jq);
+      X[i * kLiS + jq] = v.x;
+      X[i * kLiS + jq + 1] = v.y;
+      X[i * kLiS + jq + 2] = v.z;
+      X[i * kLiS + jq + 3] = v.w;
+    }
+    __syncthreads();
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (i < wI) {
+      const float* pr = Pn + i * pw;
+#pragma unroll 4
+      for (int k = 0; k < kw; ++k) {
+        const float lv = pr[k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = fmaf(lv, C[k * kLiS + jq + u], a[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) S[i * kLiS + jq + u] = a[u];
+    __syncthreads();
+    if (i < wI) {
+      float t[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int m = 0; m < kCB; ++m) {
+        const float x = X[i * kLiS + m];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) t[u] = fmaf(x, S[m * kLiS + jq + u], t[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) C[(kw + i) * kLiS + jq + u] = -t[u];
+    }
+    __syncthreads();
+  }
+  // column block J of Lh, Ll: rows 0 .. l-1, zeros above row j0
+  const int col = j0 + jq;
+  if (col < l) {
+    for (int r = i; r < l; r += 32) {
+      float h[4], o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float v = r >= j0 ? C[(r - j0) * kLiS + jq + u] : 0.f;
+        h[u] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+        o[u] = v - h[u];
+      }
+      *reinterpret_cast<float4*>(pb.Lh + static_cast<int64_t>(r) * l + col) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4*>(pb.Ll + static_cast<int64_t>(r) * l + col) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+  }
+}
+
 }  // namespace
 
 size_t gram_part_floats(int l) {
@@ -1081,6 +1211,20 @@ lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s, const int* cond) 
   int64_t rows = 0;
   for (int i = 0; i < tb.n; ++i) rows = tb.p[i].rows > rows ? tb.p[i].rows : rows;
   trsm3_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kR3)), tb.n), 256, smem, s>>>(tb, l, lqQ, lqL, cond);
+  return last_launch();
+}
+
+lramm_status launch_linv(LinvBatch lb, int l, cudaStream_t s, const int* cond) {
+  if (l % 4 != 0 || l < 4) return LRAMM_ERR_UNSUPPORTED;
+  for (int i = 0; i < lb.n; ++i)
+    if ((reinterpret_cast<uintptr_t>(lb.p[i].L) | reinterpret_cast<uintptr_t>(lb.p[i].Lh) |
+         reinterpret_cast<uintptr_t>(lb.p[i].Ll)) & 15)
+      return LRAMM_ERR_UNSUPPORTED;
+  // column block, S, X_II and the widest panel (block 0's)
+  const size_t smem = sizeof(float) * ((static_cast<size_t>(l) + 2 * kCB) * kLiS + static_cast<size_t>(kCB) * (l + 4));
+  if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  linv_kernel<<<dim3(static_cast<unsigned>(ceil_div(l, kCB)), lb.n), 256, smem, s>>>(lb, l, cond);
   return last_launch();
 }
 

@@ -102,6 +102,7 @@ __device__ __forceinline__ void mma_kind(uint32_t d_tmem, uint64_t adesc, uint64
 }
 
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar8() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 template <int KIND>
 __global__ void __launch_bounds__(kQThreads, 2)
@@ -219,9 +220,15 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
       // bounds this product).  The blocks live in the operand ring, free once
       // the accumulator is complete: every copy into the ring was consumed by
       // an MMA before tmem_bar arrived.
+      // The TMEM load of the next 32 columns is in flight while this block
+      // is scaled, staged and stored.
+      const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+      uint32_t v[32], vn[32];
+      tmem_ld32_issue(trow, v);
+      tmem_ld_wait(v);
       for (int c0 = 0, nb = 0; c0 < p.bn; c0 += 32, ++nb) {
-        float v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
+        const bool more = c0 + 32 < p.bn;
+        if (more) tmem_ld32_issue(trow + static_cast<uint32_t>(c0 + 32), vn);
         float* stg = reinterpret_cast<float*>(sA) + (q * p.nstg + nb % p.nstg) * 1024;
         if (nb >= p.nstg) {   // this staging block's previous store has finished reading it
           if (lane == 0) {
@@ -236,8 +243,8 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
             const float sr = sR_sh[c0 + 4 * c + e];
-            o[e] = p.scaled ? __fmul_rn(p.alpha, __fmul_rn(v[4 * c + e], __fmul_rn(sl_own, sr)))
-                            : __fmul_rn(p.alpha, v[4 * c + e]);
+            const float x = __uint_as_float(v[4 * c + e]);
+            o[e] = p.scaled ? __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl_own, sr))) : __fmul_rn(p.alpha, x);
           }
           *reinterpret_cast<float4*>(stg + lane * 32 + ((c ^ (lane & 7)) << 2)) = make_float4(o[0], o[1], o[2], o[3]);
         }
@@ -251,8 +258,15 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
               : "memory");
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
+        if (more) {
+          tmem_ld_wait(vn);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] = vn[j];
+        }
       }
-      if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+      // the staging blocks must be read out before the CTA exits; the global
+      // writes complete by themselves (visible at kernel completion)
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       __syncwarp();
     } else {
       // Each 32 x 32 block (rows = this warp's TMEM lanes) is transposed
@@ -294,6 +308,213 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
+// Persistent form of qgemm_tc_kernel for one K chunk with the output stored
+// by TMA and no beta C term (the E3 shape: thousands of 128 x 256 tiles of
+// a short-K product, bound by writing its FP32 output).  One CTA per SM
+// walks the tiles t = blockIdx.x, + gridDim.x, ...: the operand ring keeps
+// loading across tiles, and two 256-column TMEM accumulators let the MMAs of
+// the next tile run while the epilogue warps drain the current one, so the
+// output stream does not pause between tiles (with independent CTAs it
+// stopped whenever both CTAs of an SM were loading or multiplying).  The
+// arithmetic and the stores are those of qgemm_tc_kernel's TMA-store
+// epilogue, so the results are bit-identical.
+constexpr int kPStages = 2;       // operand ring (48 KB per stage at BN = 256)
+constexpr int kPStg = 4;          // staging blocks of 4 KB per epilogue warp
+constexpr int kPThreads = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue (two per TMEM lane quadrant)
+
+template <int KIND>
+__global__ void __launch_bounds__(kPThreads, 1)
+qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
+                 const __grid_constant__ CUtensorMap tmD, QtcParams p, int ntn, int64_t ntiles) {
+  constexpr int kStageK = kQKB / kind_elem_bytes(KIND);
+  extern __shared__ uint8_t q_smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(q_smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + static_cast<size_t>(kPStages) * p.a_bytes;
+  float* stg_base = reinterpret_cast<float*>(sB + static_cast<size_t>(kPStages) * p.b_bytes);   // 8 x kPStg x 4 KB
+  float* sR_sh = stg_base + 8 * kPStg * 1024;                                                    // p.bn floats
+  __shared__ __align__(8) uint64_t full_bar[kPStages], empty_bar[kPStages], accf[2], acce[2], done_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nkb = p.kblocks;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPStages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&accf[a], 1);
+      mbar_init(&acce[a], 8);   // one arrival per epilogue warp
+    }
+    mbar_init(&done_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: every K block of every tile of this CTA, in order
+    int64_t it = 0;
+    bool ok = true;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      const int m0 = static_cast<int>(t / ntn) * kQM, n0 = static_cast<int>(t % ntn) * p.bn;
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = static_cast<int>(it % kPStages);
+        if (it >= kPStages && !mbar_wait(&empty_bar[s], static_cast<uint32_t>((it / kPStages) & 1) ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        mbar_expect_tx(&full_bar[s], p.a_bytes + p.b_bytes);
+        tma_load_2d(sA + static_cast<size_t>(s) * p.a_bytes, &tmL, &full_bar[s], kb * kStageK, m0);
+        tma_load_2d(sB + static_cast<size_t>(s) * p.b_bytes, &tmR, &full_bar[s], kb * kStageK, n0);
+      }
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      volatile int zero = 0;   // the copies still in flight land before the CTA exits
+      for (int64_t i = it > kPStages ? it - kPStages : 0; i < it; ++i)
+        mbar_wait(&full_bar[i % kPStages], static_cast<uint32_t>((i / kPStages) & 1), &zero);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer: accumulator j & 1 for the j-th tile of this CTA
+    const uint32_t idesc = idesc_kind<KIND>(kQM, p.bn);
+    int64_t it = 0;
+    bool ok = true;
+    int j = 0;
+    for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++j) {
+      const int a = j & 1;
+      if (j >= 2 && !mbar_wait(&acce[a], static_cast<uint32_t>((j / 2 - 1) & 1), abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + static_cast<uint32_t>(a * 256);
+      for (int kb = 0; kb < nkb; ++kb, ++it) {
+        const int s = static_cast<int>(it % kPStages);
+        if (!mbar_wait(&full_bar[s], static_cast<uint32_t>((it / kPStages) & 1), abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(sA + static_cast<size_t>(s) * p.a_bytes);
+        const uint32_t b_base = smem_u32(sB + static_cast<size_t>(s) * p.b_bytes);
+#pragma unroll
+        for (int kk = 0; kk < kQKB / 32; ++kk)  // 32 bytes of K per instruction
+          mma_kind<KIND>(d, kmajor_sw128_desc(a_base + kk * 32), kmajor_sw128_desc(b_base + kk * 32), idesc,
+                         (kb > 0 || kk > 0) ? 1u : 0u);
+        mma_commit(&empty_bar[s]);
+      }
+      if (ok) mma_commit(&accf[a]);
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+    }
+    // every MMA issued has finished before the CTA frees TMEM and exits
+    mma_commit(&done_bar);
+    volatile int zero = 0;
+    mbar_wait(&done_bar, 0, &zero);
+  } else if (warp >= 2) {
+    // ---- epilogue: TMEM lanes 32q .. 32q+31 are rows m0 + 32q + lane;
+    // warps 2..5 take the tile's first half of the columns, 6..9 the second
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int et = threadIdx.x - 64;   // 0 .. 255
+    float* stg0 = stg_base + (warp - 2) * kPStg * 1024;
+    const int cbeg = half * (p.bn / 2), cend = cbeg + p.bn / 2;
+    int sc = 0;   // staging blocks used by this warp
+    bool ok = true;
+    int j = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
+      const int a = j & 1;
+      const int64_t m0 = (t / ntn) * kQM, n0 = (t % ntn) * p.bn;
+      epi_bar8();   // every epilogue warp is done with the previous tile's column scales
+      for (int c = et; c < p.bn; c += 256) {
+        const int64_t col = n0 + c;
+        sR_sh[c] = col < p.N ? (p.per_row ? p.sR[col] : p.sR[0]) : 0.f;
+      }
+      epi_bar8();
+      const int64_t rbase = m0 + q * 32;
+      const float sl_own = rbase + lane < p.M ? (p.per_row ? p.sL[rbase + lane] : p.sL[0]) : 0.f;
+      // after an abort the warp keeps walking the tiles through the two
+      // named barriers above (so no epilogue warp waits on one that left)
+      // and does nothing else
+      if (ok && !mbar_wait(&accf[a], static_cast<uint32_t>((j / 2) & 1), abort_flag)) ok = false;
+      if (!ok) continue;
+      tc_fence_after();
+      const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(a * 256);
+      uint32_t v[32], vn[32];
+      tmem_ld32_issue(trow + static_cast<uint32_t>(cbeg), v);
+      tmem_ld_wait(v);
+      for (int c0 = cbeg; c0 < cend; c0 += 32, ++sc) {
+        const bool more = c0 + 32 < cend;
+        if (more) tmem_ld32_issue(trow + static_cast<uint32_t>(c0 + 32), vn);
+        float* stg = stg0 + (sc % kPStg) * 1024;
+        if (sc >= kPStg) {   // this staging block's previous store has been read out
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
+          __syncwarp();
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          float o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float sr = sR_sh[c0 + 4 * c + e];
+            const float x = __uint_as_float(v[4 * c + e]);
+            o[e] = __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl_own, sr)));
+          }
+          *reinterpret_cast<float4*>(stg + lane * 32 + ((c ^ (lane & 7)) << 2)) = make_float4(o[0], o[1], o[2], o[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0 && rbase < p.M && n0 + c0 < p.N) {   // TMA clips the block at M and N
+          asm volatile(
+              "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                  reinterpret_cast<uint64_t>(&tmD)),
+              "r"(static_cast<int>(n0 + c0)), "r"(static_cast<int>(rbase)), "r"(smem_u32(stg))
+              : "memory");
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+        if (more) {
+          tmem_ld_wait(vn);
+#pragma unroll
+          for (int e = 0; e < 32; ++e) v[e] = vn[e];
+        }
+      }
+      // accumulator a drained: the MMAs of tile j + 2 may overwrite it
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[a])) : "memory");
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncwarp();
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
 }
 
@@ -482,17 +703,30 @@ qterms_tc_kernel(const __grid_constant__ CUtensorMap tmL0, const __grid_constant
       sl_own[t] = (t < p.nterms && row_own < p.M)
                       ? (p.sL[t] ? (p.per_row ? p.sL[t][row_own] : p.sL[t][0]) : 1.f)
                       : 0.f;
+    // TMEM blocks (column block, term) in order, each load in flight while
+    // the previous block is combined (and, after a column block's last
+    // term, while that block is staged and stored)
+    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    uint32_t vn[32];
+    tmem_ld32_issue(trow, vn);
     for (int c0 = 0, nb = 0; c0 < kTermBN; c0 += 32, ++nb) {
       // this lane's row, columns c0 .. c0+31: the terms combined in order
       float o[32];
       for (int t = 0; t < p.nterms; ++t) {
-        float v[32];
-        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * kTermBN + c0), v);
+        uint32_t v[32];
+        tmem_ld_wait(vn);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = vn[j];
+        if (t + 1 < p.nterms)
+          tmem_ld32_issue(trow + static_cast<uint32_t>((t + 1) * kTermBN + c0), vn);
+        else if (c0 + 32 < kTermBN)
+          tmem_ld32_issue(trow + static_cast<uint32_t>(c0 + 32), vn);
         const bool scaled = p.sL[t] != nullptr;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const float term = scaled ? __fmul_rn(p.alpha, __fmul_rn(v[j], __fmul_rn(sl_own[t], sR_sh[t][c0 + j])))
-                                    : __fmul_rn(p.alpha, v[j]);
+          const float x = __uint_as_float(v[j]);
+          const float term = scaled ? __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl_own[t], sR_sh[t][c0 + j])))
+                                    : __fmul_rn(p.alpha, x);
           o[j] = t == 0 ? term : __fadd_rn(o[j], term);
         }
         if (t == 0 && p.beta != 0.f && row_own < p.M) {   // beta C joins the first term
@@ -543,8 +777,8 @@ qterms_tc_kernel(const __grid_constant__ CUtensorMap tmL0, const __grid_constant
         __syncwarp();
       }
     }
-    if (p.tma_store) {
-      if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (p.tma_store) {   // staging blocks read out before the CTA exits
+      if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       __syncwarp();
     }
     if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
@@ -648,6 +882,24 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
                 make_map_2d(&mD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, p.D, N, M, p.ldd * 4, 32, 32,
                             CU_TENSOR_MAP_SWIZZLE_128B);
   if (!p.tma_store) mD = mL;   // unused
+  // many output tiles of a one-chunk code product stored by TMA: the
+  // persistent kernel, one CTA per SM
+  const int64_t ntl = sh.mtiles * sh.ntiles;
+  if (p.tma_store && p.scaled && sh.chunks == 1 && kind != kKindTF32 && sh.bn == 256 && ntl >= 4 * num_sms()) {
+    const size_t psmem = 1024 + static_cast<size_t>(kPStages) * (p.a_bytes + p.b_bytes) +
+                         static_cast<size_t>(8 * kPStg) * 4096 + sizeof(float) * p.bn;
+    const unsigned gp = static_cast<unsigned>(num_sms());
+    if (kind == kKindBF16) {
+      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tcp_kernel<kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)psmem));
+      qgemm_tcp_kernel<kKindBF16><<<gp, kPThreads, psmem, s>>>(mL, mR, mD, p, static_cast<int>(sh.ntiles), ntl);
+    } else {
+      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tcp_kernel<kKindFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)psmem));
+      qgemm_tcp_kernel<kKindFP8><<<gp, kPThreads, psmem, s>>>(mL, mR, mD, p, static_cast<int>(sh.ntiles), ntl);
+    }
+    return last_launch();
+  }
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
   const dim3 grid(static_cast<unsigned>(sh.ntiles), static_cast<unsigned>(sh.mtiles), static_cast<unsigned>(sh.chunks));
   switch (kind) {

@@ -393,6 +393,198 @@ sketch_bf_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Q = Y L^-T on the tensor cores in split TF32: the CholeskyQR basis of the
+// tensor-core range finders, a dense product with the explicit inverse in
+// place of the panel triangular solve.  Y is rows x l (stride l); L^-1 comes
+// as its TF32 high part Lh and low part Ll (l x l row-major, zero above the
+// diagonal; Lh + Ll = L^-1 exactly in FP32); Q is rows x l and may be Y.
+// Per K step of 8, three MMAs Yh Lh^T + Yl Lh^T + Yh Ll^T (FP32
+// accumulation in TMEM, ~2^-21 relative, as the split-TF32 Gram); Y is
+// split into Yh (in place) and Yl by the epilogue warps as each stage lands.
+// Both operands are K-major with the 128-byte swizzle.  One CTA per 128
+// rows reads all of its rows before its epilogue stores any (so Q = Y is
+// safe); the output leaves as 32 x 32 blocks staged in the drained operand
+// ring and written by TMA.  Waits are bounded as in sketch_tc_kernel.
+// ---------------------------------------------------------------------------
+struct BasisParams {
+  int64_t rows;
+  int l, n1, n2, nrows, nbox;   // MMA widths; rows of the L tiles (n1 + n2) and of one TMA box
+  int kblocks, stages;
+  uint32_t a_bytes, b_bytes, tmem_cols;   // one part of a Y tile (128 x 32) / of an L tile (nrows x 32)
+  int* status;
+};
+
+__device__ __forceinline__ uint32_t idesc_tf32_kk(int M, int N) { return idesc_tf32(M, N, 0, 0); }
+
+__global__ void __launch_bounds__(kThreads, 1)
+basis_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmLh,
+                const __grid_constant__ CUtensorMap tmLl, const __grid_constant__ CUtensorMap tmQ, BasisParams p,
+                const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;   // predicated launch (the CholeskyQR fallback)
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = static_cast<int64_t>(blockIdx.x) * kBM;
+  const int nkb = p.kblocks;
+  const uint32_t stage_bytes = 2 * p.a_bytes + 2 * p.b_bytes;   // Yh | Yl | Lh | Ll
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full_bar[s], 1);
+      mbar_init(&split_bar[s], 128);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&tmem_bar, 1);
+    abort_sh = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                 "r"(p.tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer: a 128 x 32 tile of Y and the nrows x 32 tiles of Lh, Ll per stage
+    int issued = 0;
+    bool ok = true;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (i >= p.stages && !mbar_wait(&empty_bar[s], ((i / p.stages) & 1) ^ 1, abort_flag)) {
+        ok = false;
+        break;
+      }
+      mbar_expect_tx(&full_bar[s], p.a_bytes + 2 * p.b_bytes);
+      const int k0 = i * kBK;
+      uint8_t* st = smem + static_cast<size_t>(s) * stage_bytes;
+      tma_load_2d(st, &tmY, &full_bar[s], k0, static_cast<int>(m0));
+      for (int r0 = 0; r0 < p.nrows; r0 += p.nbox) {
+        tma_load_2d(st + 2 * p.a_bytes + r0 * 128, &tmLh, &full_bar[s], k0, r0);
+        tma_load_2d(st + 2 * p.a_bytes + p.b_bytes + r0 * 128, &tmLl, &full_bar[s], k0, r0);
+      }
+      ++issued;
+    }
+    if (!ok) {
+      set_status(p.status, LRAMM_ERR_TIMEOUT);
+      abort_sh = 1;
+      const int first = issued > p.stages ? issued - p.stages : 0;
+      for (int i = first; i < issued; ++i) {
+        volatile int zero = 0;
+        mbar_wait(&full_bar[i % p.stages], (i / p.stages) & 1, &zero);
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    const uint32_t id1 = idesc_tf32_kk(kBM, p.n1);
+    const uint32_t id2 = p.n2 ? idesc_tf32_kk(kBM, p.n2) : 0u;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&split_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t yh = smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
+      const uint32_t yl = yh + p.a_bytes, lh = yh + 2 * p.a_bytes, ll = lh + p.b_bytes;
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {   // 8 TF32 (32 bytes) of K per instruction
+        const uint32_t ko = kk * 32;
+        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, kmajor_desc(yh + ko), kmajor_desc(lh + ko), id1, acc0);
+        mma_tf32(tmem, kmajor_desc(yl + ko), kmajor_desc(lh + ko), id1, 1u);
+        mma_tf32(tmem, kmajor_desc(yh + ko), kmajor_desc(ll + ko), id1, 1u);
+        if (p.n2) {   // L rows 256 .. : 256 rows of 128 bytes further on
+          mma_tf32(tmem + 256, kmajor_desc(yh + ko), kmajor_desc(lh + 32768 + ko), id2, acc0);
+          mma_tf32(tmem + 256, kmajor_desc(yl + ko), kmajor_desc(lh + 32768 + ko), id2, 1u);
+          mma_tf32(tmem + 256, kmajor_desc(yh + ko), kmajor_desc(ll + 32768 + ko), id2, 1u);
+        }
+      }
+      mma_commit(&empty_bar[s]);
+    }
+    mma_commit(&tmem_bar);
+  } else if (warp >= 2) {
+    // split each landed Y tile: high part in place, low part beside it
+    // (element-wise, so the swizzled layout carries over)
+    const int st = threadIdx.x - 64;   // 0 .. 127
+    const int nq = static_cast<int>(p.a_bytes / 16);
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % p.stages;
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+        set_status(p.status, LRAMM_ERR_TIMEOUT);
+        abort_sh = 1;
+        break;
+      }
+      float4* h4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes);
+      float4* l4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes + p.a_bytes);
+      for (int e = st; e < nq; e += 128) {
+        const float4 y = h4[e];
+        float4 h;
+        h.x = __uint_as_float(__float_as_uint(y.x) & 0xFFFFE000u);
+        h.y = __uint_as_float(__float_as_uint(y.y) & 0xFFFFE000u);
+        h.z = __uint_as_float(__float_as_uint(y.z) & 0xFFFFE000u);
+        h.w = __uint_as_float(__float_as_uint(y.w) & 0xFFFFE000u);
+        h4[e] = h;
+        l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split_bar[s])) : "memory");
+    }
+    // ---- epilogue: TMEM lanes 32q .. 32q+31 are rows m0 + 32q + lane.
+    // Every copy into the ring was consumed by an MMA before tmem_bar
+    // arrived, so the ring holds the staging blocks (two per warp).
+    const int q = warp & 3;
+    volatile int zero = 0;   // wait for the MMAs even after an abort: they read shared memory
+    const bool ok = mbar_wait(&tmem_bar, 0, &zero);
+    tc_fence_after();
+    const int64_t rbase = m0 + q * 32;
+    const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16);
+    for (int c0 = 0, nb = 0; c0 < p.l; c0 += 32, ++nb) {
+      float v[32];
+      tmem_ld32(trow + static_cast<uint32_t>(c0), v);
+      float* stg = reinterpret_cast<float*>(smem) + (q * 2 + (nb & 1)) * 1024;
+      if (nb >= 2) {   // this staging block's previous store has been read out
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        *reinterpret_cast<float4*>(stg + lane * 32 + ((c ^ (lane & 7)) << 2)) =
+            make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0 && ok && rbase < p.rows) {   // TMA clips the block at rows and l
+        asm volatile(
+            "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                reinterpret_cast<uint64_t>(&tmQ)),
+            "r"(c0), "r"(static_cast<int>(rbase)), "r"(smem_u32(stg))
+            : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      }
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncwarp();
+    if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols) : "memory");
+  }
+}
+
 // B (K x l FP32, row-major) -> B_hi, B_lo (K x npad BF16, zero padded).
 __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l, int npad, __nv_bfloat16* __restrict__ hi,
                                   __nv_bfloat16* __restrict__ lo) {
@@ -587,7 +779,20 @@ __global__ void split_reduce_kernel(const float4* __restrict__ part, int splits,
   for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n4;
        i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     float4 a = part[i];
-    for (int s = 1; s < splits; ++s) {
+    int s = 1;
+    for (; s + 8 <= splits; s += 8) {   // eight loads in flight, added in split order
+      float4 b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b[u] = part[static_cast<int64_t>(s + u) * n4 + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a.x += b[u].x;
+        a.y += b[u].y;
+        a.z += b[u].z;
+        a.w += b[u].w;
+      }
+    }
+    for (; s < splits; ++s) {
       const float4 b = part[static_cast<int64_t>(s) * n4 + i];
       a.x += b.x;
       a.y += b.y;
@@ -595,6 +800,58 @@ __global__ void split_reduce_kernel(const float4* __restrict__ part, int splits,
       a.w += b.w;
     }
     out[i] = a;
+  }
+}
+
+// The same sum for many splits and few outputs (the Gram partials): four
+// threads per float4 of out, each adding a quarter of the splits in split
+// order, then the four partial sums added in a fixed order ((q0 + q1) + q2)
+// + q3 (deterministic, four times the loads in flight).  64 outputs per
+// 256-thread CTA.
+__global__ void __launch_bounds__(256) split_reduce4_kernel(const float4* __restrict__ part, int splits, int64_t n4,
+                                                           float4* __restrict__ out, const int* __restrict__ cond) {
+  if (cond && *cond == 0) return;
+  __shared__ float4 red[4][64];
+  const int o = threadIdx.x & 63, g = threadIdx.x >> 6;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(64) + o;
+  const int per = (splits + 3) / 4;
+  const int s0 = g * per, s1 = min(splits, s0 + per);
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i < n4 && s0 < s1) {
+    a = part[static_cast<int64_t>(s0) * n4 + i];
+    int s = s0 + 1;
+    for (; s + 8 <= s1; s += 8) {
+      float4 b[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) b[u] = part[static_cast<int64_t>(s + u) * n4 + i];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        a.x += b[u].x;
+        a.y += b[u].y;
+        a.z += b[u].z;
+        a.w += b[u].w;
+      }
+    }
+    for (; s < s1; ++s) {
+      const float4 b = part[static_cast<int64_t>(s) * n4 + i];
+      a.x += b.x;
+      a.y += b.y;
+      a.z += b.z;
+      a.w += b.w;
+    }
+  }
+  red[g][o] = a;
+  __syncthreads();
+  if (g == 0 && i < n4) {
+    float4 t = red[0][o];
+    for (int q = 1; q < 4; ++q) {
+      if (q * per >= splits) break;   // groups past the last split are empty
+      t.x += red[q][o].x;
+      t.y += red[q][o].y;
+      t.z += red[q][o].z;
+      t.w += red[q][o].w;
+    }
+    out[i] = t;
   }
 }
 
@@ -815,15 +1072,56 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     LRAMM_TRY(last_launch());
     if (splits > 1) {
       const int64_t n4 = static_cast<int64_t>(l) * l / 4;
-      int64_t g2 = ceil_div(n4, 256);
-      if (g2 > num_sms() * 8) g2 = num_sms() * 8;
-      split_reduce_kernel<<<static_cast<unsigned>(g2), 256, 0, s>>>(reinterpret_cast<const float4*>(part),
-                                                                     static_cast<int>(splits), n4,
-                                                                     reinterpret_cast<float4*>(G[i]), cond);
+      split_reduce4_kernel<<<static_cast<unsigned>(ceil_div(n4, 64)), 256, 0, s>>>(
+          reinterpret_cast<const float4*>(part), static_cast<int>(splits), n4, reinterpret_cast<float4*>(G[i]), cond);
       LRAMM_TRY(last_launch());
     }
   }
   return LRAMM_OK;
+}
+
+// Q = Y L^-T in split TF32 from the inverse's parts (see basis_tc_kernel).
+bool basis_tc_supported(int l) { return l >= 16 && l % 4 == 0 && l <= 288; }
+
+lramm_status basis_tc(const float* Y, int64_t rows, const float* Lh, const float* Ll, float* Q, int l, int* status,
+                      cudaStream_t s, const int* cond) {
+  if (!basis_tc_supported(l)) return LRAMM_ERR_UNSUPPORTED;
+  if (rows <= 0) return LRAMM_OK;
+  if (rows > INT32_MAX) return LRAMM_ERR_UNSUPPORTED;
+  if ((reinterpret_cast<uintptr_t>(Y) | reinterpret_cast<uintptr_t>(Lh) | reinterpret_cast<uintptr_t>(Ll) |
+       reinterpret_cast<uintptr_t>(Q)) & 15)
+    return LRAMM_ERR_UNSUPPORTED;
+  BasisParams p{};
+  p.rows = rows;
+  p.l = l;
+  p.n1 = l <= 256 ? static_cast<int>(round_up(l, 16)) : 256;
+  p.n2 = l <= 256 ? 0 : static_cast<int>(round_up(l - 256, 16));
+  p.nrows = p.n1 + p.n2;
+  p.nbox = p.nrows <= 256 ? p.nrows : p.nrows / 2;   // a multiple of 8, at most 256
+  p.kblocks = static_cast<int>(ceil_div(l, kBK));
+  p.a_bytes = kBM * kBK * 4;
+  p.b_bytes = static_cast<uint32_t>(p.nrows) * kBK * 4;
+  const uint32_t stage = 2 * p.a_bytes + 2 * p.b_bytes;
+  int st = static_cast<int>((kSmemBudget - 1024) / stage);
+  if (st > kMaxStages) st = kMaxStages;
+  if (st > p.kblocks) st = p.kblocks;
+  if (st < 1 || (st < 2 && p.kblocks > 1)) return LRAMM_ERR_UNSUPPORTED;
+  p.stages = st;
+  uint32_t tc = 32;
+  while (tc < static_cast<uint32_t>(p.n1 + p.n2 + (p.n2 ? 256 - p.n1 : 0))) tc <<= 1;
+  p.tmem_cols = tc;
+  p.status = status;
+  CUtensorMap mY, mLh, mLl, mQ;
+  const uint64_t pitch = static_cast<uint64_t>(l) * 4;
+  if (!make_map_f32(&mY, Y, l, rows, pitch, kAtom, kBM, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map_f32(&mLh, Lh, l, l, pitch, kAtom, p.nbox, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map_f32(&mLl, Ll, l, l, pitch, kAtom, p.nbox, CU_TENSOR_MAP_SWIZZLE_128B) ||
+      !make_map_f32(&mQ, Q, l, rows, pitch, kAtom, 32, CU_TENSOR_MAP_SWIZZLE_128B))
+    return LRAMM_ERR_CUDA;
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * stage;
+  LRAMM_CUDA_TRY(cudaFuncSetAttribute(basis_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  basis_tc_kernel<<<static_cast<unsigned>(ceil_div(rows, kBM)), kThreads, smem, s>>>(mY, mLh, mLl, mQ, p, cond);
+  return last_launch();
 }
 
 }  // namespace lramm

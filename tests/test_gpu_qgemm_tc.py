@@ -86,6 +86,44 @@ def test_dequantised_matches_oracle(L, per_row, M, K, N):
     assert np.array_equal(D, ref)
 
 
+# Many output tiles (at least four 128 x 256 tiles per SM): the persistent
+# kernel (one CTA per SM, double-buffered TMEM accumulators).  Ragged M, N
+# and K (a multiple of 16, as the entry point requires); its results must be those of the per-tile kernel bit for bit.
+PERSIST_SHAPES = [(5000, 5000, 128), (4999, 4100, 208), (8192, 4864, 64)]
+
+
+@pytest.mark.parametrize("M,N,K", PERSIST_SHAPES)
+def test_integer_sum_exact_persistent(L, M, N, K):
+    rng = np.random.default_rng(M + 5 * N + 9 * K)
+    a = rng.integers(-127, 128, (M, K))
+    b = rng.integers(-127, 128, (N, K))
+    D = np_(L.qgemm_tc(codes(a), codes(b), ones(M), ones(N)))
+    assert np.array_equal(D, oracle.quant.code_product(a, b.T).astype(np.float32))
+
+
+@pytest.mark.parametrize("per_row", [True, False])
+def test_dequantised_matches_oracle_persistent(L, per_row):
+    rng = np.random.default_rng(41 + per_row)
+    M, K, N = 4100, 130, 4864
+    Lm = (rng.standard_normal((M, K)) * np.exp(rng.uniform(-2, 2, (M, 1)))).astype(np.float32)
+    R = (rng.standard_normal((K, N)) * np.exp(rng.uniform(-2, 2, (1, N)))).astype(np.float32)
+    Kp = K + (-K) % 16
+    cL, sL = L.quantize(dev(Lm), 1, per_row, ldcodes=Kp)
+    cR, sR = L.quantize(dev(np.ascontiguousarray(R.T)), 1, per_row, ldcodes=Kp)
+    D = np_(L.qgemm_tc(cL, cR, sL, sR, per_row=per_row, alpha=0.5))
+    ref = (np.float32(0.5) * oracle.quant.qm(Lm, R, 1, 0 if per_row else 1)).astype(np.float32)
+    assert np.array_equal(D, ref)
+
+
+def test_int4_codes_exact_persistent(L):
+    rng = np.random.default_rng(17)
+    M, N, K = 5000, 4100, 256
+    a = rng.integers(-7, 8, (M, K))
+    b = rng.integers(-7, 8, (N, K))
+    D = np_(L.qgemm_tc(e4m3(a), e4m3(b), ones(M), ones(N), prec=L.P_INT4))
+    assert np.array_equal(D, oracle.quant.code_product(a, b.T).astype(np.float32))
+
+
 def test_alpha_beta(L):
     """D = alpha QM + beta C: one FP32 multiply and one FMA after the dequantisation."""
     rng = np.random.default_rng(5)
