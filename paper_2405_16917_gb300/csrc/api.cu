@@ -517,7 +517,9 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
       }
     }
     const bool guard = retry && !extra;   // breakdowns of this pass are retried
-    if (c3) {  // blocked Cholesky (restarting itself with the larger shift) + panel solve
+    if (c3) {  // blocked Cholesky (restarting itself with the larger shift) + panel solve or inverse
+      if (tcb || !solve)   // no panel solve: no inverted diagonal blocks (the inverse forms its own)
+        for (int i = 0; i < ns; ++i) cb3.p[i].Xd = nullptr;
       if (guard) {
       cb3.p[0].brk_any = any;
       cb3.p[0].brk_count = at<int>(ws, 0) + kBrkCountWord + (sd[0].S == &P->side[1] ? 1 : 0);
@@ -528,7 +530,7 @@ lramm_status orth_sides(lramm_plan_s* P, void* ws, const SideRun* sd, int ns, fl
         LinvBatch lb{};
         lb.n = ns;
         for (int i = 0; i < ns; ++i)
-          lb.p[i] = LinvProb{cb3.p[i].L, cb3.p[i].Xd, at<float>(ws, sd[i].S->Lh), at<float>(ws, sd[i].S->Ll)};
+          lb.p[i] = LinvProb{cb3.p[i].L, at<float>(ws, sd[i].S->Lh), at<float>(ws, sd[i].S->Ll)};
         TIMED(P, LRAMM_K_TRSM, s, launch_linv(lb, l, s, scond));
         for (int i = 0; i < ns; ++i)
           TIMED(P, LRAMM_K_TRSM, s, basis_tc(in[i], rows[i], lb.p[i].Lh, lb.p[i].Ll, out[i], l, st, s, scond));

@@ -167,7 +167,7 @@ struct GramBatch {
 struct CholProb {
   const float* G;   // l x l
   float* L;         // l x l, lower, zeros above
-  float* Xd;        // ceil(l/32) blocks of 32 x 32: inverses of L's diagonal blocks
+  float* Xd;        // ceil(l/32) blocks of 32 x 32: inverses of L's diagonal blocks (chol3: null = not wanted)
   // breakdown words: with brk set, a non-positive pivot stores 1 in *brk (and
   // in *brk_any) instead of latching LRAMM_ERR_NUMERIC, for a retry
   int* brk = nullptr;
@@ -195,11 +195,10 @@ bool chol3_supported(int l);
 lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cudaStream_t s,
                           const int* cond = nullptr, float shift_big_rel = 0.f);
 lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s, const int* cond = nullptr);
-// L^-1 of chol3_kernel's factor (L dense lower, Xd its inverted diagonal
-// blocks) as TF32 high / low parts Lh, Ll (l x l row-major each).
+// L^-1 of a Cholesky factor (L dense lower, l x l row-major) as TF32 high /
+// low parts Lh, Ll (l x l row-major each).
 struct LinvProb {
   const float* L;
-  const float* Xd;
   float* Lh;
   float* Ll;
 };

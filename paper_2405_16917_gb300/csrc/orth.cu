@@ -450,10 +450,10 @@ __global__ void __launch_bounds__(256) trsm_panel_kernel(SmallBatch bt, int l, i
 //       forward substitution, reading columns of L_JJ as float4 broadcasts;
 //   (c) the trailing update A_22 -= L_2J L_2J^T in 4 x 4 register tiles from
 //       a transposed copy of the panel.
-// While warp 0 factors diagonal block J+1, warps 1..7 write column block J
-// of L to global memory and warps 8..15 invert L_JJ (for the triangular
-// solve, or the explicit inverse, of the tall sketch); the last block
-// follows the panel loop.
+// While warp 0 factors diagonal block J+1, four warps write column block J
+// of L to global memory and, when the problem asks for them (Xd given: the
+// panel triangular solve), eight warps invert L_JJ, all on the SM
+// sub-partitions other than warp 0's; the last block follows the panel loop.
 // A non-positive pivot latches LRAMM_ERR_NUMERIC and is replaced by a tiny
 // positive value, as in chol2_kernel.
 // ---------------------------------------------------------------------------
@@ -502,6 +502,11 @@ __device__ __forceinline__ void chol_inv_block(const float* P, int j0, int w, fl
     xg[i * kCB + c] = (i < w && c < w) ? b[u] * s_rl[i] : 0.f;
   }
 }
+
+// The eight inverting warps of chol3_kernel: 1, 2, 3, 5, 6, 7, 9, 10 (none
+// on warp 0's SM sub-partition), numbered 0..7.
+__device__ __forceinline__ bool inv_warp(int w) { return (w & 3) != 0 && w <= 10; }
+__device__ __forceinline__ int inv_index(int w) { return w - 1 - (w > 4) - (w > 8); }
 
 // Column block j0 .. j0+31 of L (row-major, zero above the diagonal) from
 // the packed factor, rows v, v + nv, ..; lane = column.
@@ -644,12 +649,14 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
           LC[c * kLC + lane] = (lane < w && c < lane) ? a[c] : 0.f;
         }
       } else if (j0 > 0) {
-        // meanwhile the previous column block is final: warps 1..7 write it
-        // to L, warps 8..15 invert its diagonal block
-        if (warp >= 8)
-          chol_inv_block(P, j0 - kCB, kCB, Xd + static_cast<int64_t>(j0 / kCB - 1) * kCB * kCB, s_rl, warp - 8, lane);
-        else
-          chol_write_L_block(P, Lo, l, j0 - kCB, warp - 1, 7, lane);
+        // meanwhile the previous column block is final: eight warps invert
+        // its diagonal block and four write it to L, all on the three SM
+        // sub-partitions that do not issue warp 0 (warps 4, 8, 12 idle)
+        if (Xd != nullptr && inv_warp(warp))
+          chol_inv_block(P, j0 - kCB, kCB, Xd + static_cast<int64_t>(j0 / kCB - 1) * kCB * kCB, s_rl,
+                         inv_index(warp), lane);
+        else if (warp == 11 || warp >= 13)
+          chol_write_L_block(P, Lo, l, j0 - kCB, warp == 11 ? 0 : warp - 12, 4, lane);
       }
       __syncthreads();
       const int r0 = j0 + kCB;   // first row below the diagonal block
@@ -853,10 +860,12 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   // panel loop, during the next diagonal block's factorisation).
   {
     const int jl = ((l - 1) / kCB) * kCB;
-    if (warp >= 8)
-      chol_inv_block(P, jl, l - jl, Xd + static_cast<int64_t>(jl / kCB) * kCB * kCB, s_rl, warp - 8, lane);
+    if (Xd == nullptr)
+      chol_write_L_block(P, Lo, l, jl, warp, nw, lane);
+    else if (inv_warp(warp))
+      chol_inv_block(P, jl, l - jl, Xd + static_cast<int64_t>(jl / kCB) * kCB * kCB, s_rl, inv_index(warp), lane);
     else
-      chol_write_L_block(P, Lo, l, jl, warp, 8, lane);
+      chol_write_L_block(P, Lo, l, jl, (warp & 3) == 0 ? warp >> 2 : (warp == 11 ? 4 : warp - 8), 8, lane);
   }
 }
 
@@ -1013,91 +1022,97 @@ __global__ void __launch_bounds__(256) trsm3_kernel(TrsmBatch tb, int l, int lqQ
 }
 
 // ---------------------------------------------------------------------------
-// L^-1 from the blocked factor, one CTA per 32-column block J: the block's
-// diagonal part is X_JJ = L_JJ^-1 (from chol3_kernel) and its rows below
-// follow block row by block row,
-//   Li_IJ = -X_II (sum_{K=J}^{I-1} L_IK Li_KJ),   I = J+1, ..,
-// with the column block held in shared memory and each block row's panel of
-// L (rows of block I, columns j0 .. i0-1) and X_II staged there first (one
-// round of coalesced loads per block row).  The result is written as TF32
-// high and low parts (Lh = the top 10 mantissa bits, Ll = Li - Lh, both
-// l x l row-major, zero above the diagonal) for basis_tc_kernel.
-// Thread t owns row t / 8 and columns 4 (t mod 8) .. +3 of a 32 x 32 block.
+// L^-1 from the Cholesky factor, one CTA (1024 threads) per 32-column
+// block J.  Block row by block row (I = J, J+1, ..) the column block solves
+//   L_II Li_IJ = -(sum_{K=J}^{I-1} L_IK Li_KJ)     (Li_JJ: L_JJ Li_JJ = I)
+// by forward substitution in column order: warp c holds column c, lane i
+// row i; for each t: x_t = b_t / L_tt (lane t), shuffled to the warp, then
+// b_i -= L_it x_t for i > t.  The block sum is an FP32 dot product of L's
+// rows with the column block (eight warps, four columns a thread), which is
+// held transposed in shared memory (row c of Ct is column c of the block)
+// so that both operands are read as float4; the diagonal block L_II is copied transposed so that the lanes
+// read its columns without bank conflicts.  The rows of L below block J
+// (columns j0 ..) are staged by cp.async, once when they fit, else block
+// row by block row.  The result is written as TF32 high and low parts
+// (Lh = the top 10 mantissa bits, Ll = Li - Lh, both l x l row-major, zero
+// above the diagonal) for basis_tc_kernel.
 // ---------------------------------------------------------------------------
-constexpr int kLiS = kCB + 1;   // row stride of the column block and of S, X in shared memory
+__device__ __forceinline__ void cp_async16_li(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
 
-__global__ void __launch_bounds__(256) linv_kernel(LinvBatch lb, int l, const int* __restrict__ cond) {
+__global__ void __launch_bounds__(1024) linv_kernel(LinvBatch lb, int l, int whole, const int* __restrict__ cond) {
   if (cond && *cond == 0) return;
   const LinvProb& pb = lb.p[blockIdx.y];
   extern __shared__ float4 li_smem4[];
   const int J = blockIdx.x, j0 = J * kCB, nb = (l + kCB - 1) / kCB;
-  const int pw = l - j0 + 4;                 // row stride of the staged panel (at most l - j0 columns)
-  float* C = reinterpret_cast<float*>(li_smem4);   // rows j0 .. l-1 of column block J (row r at r - j0)
-  float* S = C + (l - j0) * kLiS;           // 32 x kLiS
-  float* X = S + kCB * kLiS;                // 32 x kLiS: X_II
-  float* Pn = X + kCB * kLiS;               // 32 x pw: L rows i0 .., columns j0 .. i0-1
-  const int tid = threadIdx.x, i = tid >> 3, jq = 4 * (tid & 7);
+  const int cs = l - j0 + 4;                 // row stride of Ct and of the staged rows (a multiple of 4)
+  float* Ct = reinterpret_cast<float*>(li_smem4);   // 32 x cs: Ct[c][r - j0] = Li(r, j0 + c)
+  float* Dt = Ct + kCB * cs;                // 32 x 33: L_II transposed
+  float* Ss = Dt + kCB * (kCB + 1);         // 32 x 33: the block sum, Ss[c][i]
+  float* Pn = Ss + kCB * (kCB + 1);         // staged rows of L, columns j0 ..
+  const int tid = threadIdx.x, c = tid >> 5, i = tid & 31;
   const float* __restrict__ L = pb.L;
-  {  // X_JJ (rows and columns beyond l are zero in Xd)
-    const float* xr = pb.Xd + static_cast<int64_t>(J) * kCB * kCB + i * kCB + jq;
-    if (j0 + i < l)
-#pragma unroll
-      for (int u = 0; u < 4; ++u) C[i * kLiS + jq + u] = xr[u];
-  }
-  for (int I = J + 1; I < nb; ++I) {
+  auto stage = [&](int r_first, int nrows, int ncols4) {
+    for (int q = tid; q < nrows * ncols4; q += 1024) {
+      const int r = q / ncols4, c4 = q - r * ncols4;
+      cp_async16_li(Pn + r * cs + 4 * c4, L + static_cast<int64_t>(r_first + r) * l + j0 + 4 * c4);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+  };
+  if (whole) stage(j0, l - j0, (l - j0) / 4);   // rows j0 .. l-1
+  for (int I = J; I < nb; ++I) {
     const int i0 = I * kCB, wI = min(kCB, l - i0), kw = i0 - j0;   // kw: a multiple of 32
-    // stage the panel and X_II
-    for (int e = tid; e < wI * (kw / 4); e += 256) {
-      const int r = e / (kw / 4), c4 = e - r * (kw / 4);
-      const float4 v = *reinterpret_cast<const float4*>(L + static_cast<int64_t>(i0 + r) * l + j0 + 4 * c4);
-      float* d = Pn + r * pw + 4 * c4;
-      d[0] = v.x;
-      d[1] = v.y;
-      d[2] = v.z;
-      d[3] = v.w;
-    }
-    {
-      const float4 v = *reinterpret_cast<const float4*>(pb.Xd + static_cast<int64_t>(I) * kCB * kCB + i * kCB + jq);
-      X[i * kLiS + jq] = v.x;
-      X[i * kLiS + jq + 1] = v.y;
-      X[i * kLiS + jq + 2] = v.z;
-      X[i * kLiS + jq + 3] = v.w;
-    }
+    if (!whole) stage(i0, wI, (kw + wI + 3) / 4);                  // rows of block I, columns j0 .. i0 + wI
     __syncthreads();
-    float a[4] = {0.f, 0.f, 0.f, 0.f};
-    if (i < wI) {
-      const float* pr = Pn + i * pw;
+    const float* prow = Pn + (whole ? kw + i : i) * cs;   // row i0 + i of L (columns j0 ..)
+    // the diagonal block, transposed: Dt[t][i] = L(i0 + i, i0 + t)
+    Dt[c * (kCB + 1) + i] = (i < wI && c < wI) ? prow[kw + c] : 0.f;
+    if (I > J && tid < 256) {
+      // the block sum, by the first eight warps: thread (row ii, columns
+      // 4 cg .. +3), each row of L read once for four columns
+      const int ii = tid & 31, cg = tid >> 5;
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
+      if (ii < wI) {
+        const float* pr = Pn + (whole ? kw + ii : ii) * cs;
+#pragma unroll 2
+        for (int k = 0; k < kw; k += 4) {
+          const float4 lv = *reinterpret_cast<const float4*>(pr + k);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const float4 cv = *reinterpret_cast<const float4*>(Ct + (4 * cg + v) * cs + k);
+            a[v] = fmaf(lv.x, cv.x, a[v]);
+            a[v] = fmaf(lv.y, cv.y, a[v]);
+            a[v] = fmaf(lv.z, cv.z, a[v]);
+            a[v] = fmaf(lv.w, cv.w, a[v]);
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Ss[(4 * cg + v) * (kCB + 1) + ii] = a[v];
+    }
+    const float rv = i < wI ? 1.0f / prow[kw + i] : 1.0f;   // 1 / L_ii
+    __syncthreads();   // Dt and Ss complete
+    float b = I == J ? (i == c ? 1.f : 0.f) : -Ss[c * (kCB + 1) + i];
 #pragma unroll 4
-      for (int k = 0; k < kw; ++k) {
-        const float lv = pr[k];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = fmaf(lv, C[k * kLiS + jq + u], a[u]);
-      }
+    for (int t = 0; t < wI; ++t) {
+      const float xt = __shfl_sync(0xffffffffu, b * rv, t);
+      if (i > t && i < wI) b = fmaf(-Dt[t * (kCB + 1) + i], xt, b);
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) S[i * kLiS + jq + u] = a[u];
-    __syncthreads();
-    if (i < wI) {
-      float t[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-      for (int m = 0; m < kCB; ++m) {
-        const float x = X[i * kLiS + m];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) t[u] = fmaf(x, S[m * kLiS + jq + u], t[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) C[(kw + i) * kLiS + jq + u] = -t[u];
-    }
+    if (i < wI) Ct[c * cs + kw + i] = b * rv;
     __syncthreads();
   }
-  // column block J of Lh, Ll: rows 0 .. l-1, zeros above row j0
-  const int col = j0 + jq;
+  // column block J of Lh, Ll: rows 0 .. l-1, zeros above row j0; thread:
+  // row tid / 8 (+ 128 n), columns 4 (tid mod 8) .. +3
+  const int jq = 4 * (tid & 7), col = j0 + jq;
   if (col < l) {
-    for (int r = i; r < l; r += 32) {
+    for (int r = tid >> 3; r < l; r += 128) {
       float h[4], o[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float v = r >= j0 ? C[(r - j0) * kLiS + jq + u] : 0.f;
+        const float v = r >= j0 ? Ct[(jq + u) * cs + r - j0] : 0.f;
         h[u] = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
         o[u] = v - h[u];
       }
@@ -1220,11 +1235,16 @@ lramm_status launch_linv(LinvBatch lb, int l, cudaStream_t s, const int* cond) {
     if ((reinterpret_cast<uintptr_t>(lb.p[i].L) | reinterpret_cast<uintptr_t>(lb.p[i].Lh) |
          reinterpret_cast<uintptr_t>(lb.p[i].Ll)) & 15)
       return LRAMM_ERR_UNSUPPORTED;
-  // column block, S, X_II and the widest panel (block 0's)
-  const size_t smem = sizeof(float) * ((static_cast<size_t>(l) + 2 * kCB) * kLiS + static_cast<size_t>(kCB) * (l + 4));
+  // the transposed column block and the rows of L below block 0 (the
+  // largest): all at once when they fit, else one block row at a time
+  const size_t nbk = ceil_div(l, kCB);
+  const size_t whole_smem = sizeof(float) * ((static_cast<size_t>(kCB) + l) * (l + 4) + 2 * kCB * (kCB + 1));
+  const size_t step_smem = sizeof(float) * (2 * static_cast<size_t>(kCB) * (l + 4) + 2 * kCB * (kCB + 1));
+  const int whole = whole_smem <= static_cast<size_t>(kSmemMaxO) ? 1 : 0;
+  const size_t smem = whole ? whole_smem : step_smem;
   if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
-  linv_kernel<<<dim3(static_cast<unsigned>(ceil_div(l, kCB)), lb.n), 256, smem, s>>>(lb, l, cond);
+  linv_kernel<<<dim3(static_cast<unsigned>(nbk), lb.n), 1024, smem, s>>>(lb, l, whole, cond);
   return last_launch();
 }
 

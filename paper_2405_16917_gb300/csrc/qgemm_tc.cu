@@ -324,8 +324,9 @@ qgemm_tc_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__
 constexpr int kPStages = 2;       // operand ring (48 KB per stage at BN = 256)
 constexpr int kPStg = 4;          // staging blocks of 4 KB per epilogue warp
 constexpr int kPThreads = 320;    // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue (two per TMEM lane quadrant)
+constexpr int kPBN = 256;         // tile width (the launcher requires BN = 256)
 
-template <int KIND>
+template <int KIND, bool A1>   // A1: alpha == 1 (the multiply by alpha is exact and skipped)
 __global__ void __launch_bounds__(kPThreads, 1)
 qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmR,
                  const __grid_constant__ CUtensorMap tmD, QtcParams p, int ntn, int64_t ntiles) {
@@ -438,7 +439,7 @@ qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant_
     const int half = (warp - 2) >> 2;
     const int et = threadIdx.x - 64;   // 0 .. 255
     float* stg0 = stg_base + (warp - 2) * kPStg * 1024;
-    const int cbeg = half * (p.bn / 2), cend = cbeg + p.bn / 2;
+    const int cbeg = half * (kPBN / 2);
     int sc = 0;   // staging blocks used by this warp
     bool ok = true;
     int j = 0;
@@ -460,12 +461,8 @@ qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant_
       if (!ok) continue;
       tc_fence_after();
       const uint32_t trow = tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(a * 256);
-      uint32_t v[32], vn[32];
-      tmem_ld32_issue(trow + static_cast<uint32_t>(cbeg), v);
-      tmem_ld_wait(v);
-      for (int c0 = cbeg; c0 < cend; c0 += 32, ++sc) {
-        const bool more = c0 + 32 < cend;
-        if (more) tmem_ld32_issue(trow + static_cast<uint32_t>(c0 + 32), vn);
+      // one 32 x 32 block: scale, stage (128-byte swizzle), store by TMA
+      auto emit = [&](const uint32_t(&v)[32], int c0) {
         float* stg = stg0 + (sc % kPStg) * 1024;
         if (sc >= kPStg) {   // this staging block's previous store has been read out
           if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory");
@@ -473,13 +470,14 @@ qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant_
         }
 #pragma unroll
         for (int c = 0; c < 8; ++c) {
-          float o[4];
+          const float4 sr = *reinterpret_cast<const float4*>(sR_sh + c0 + 4 * c);
+          float o[4] = {__fmul_rn(__uint_as_float(v[4 * c]), __fmul_rn(sl_own, sr.x)),
+                        __fmul_rn(__uint_as_float(v[4 * c + 1]), __fmul_rn(sl_own, sr.y)),
+                        __fmul_rn(__uint_as_float(v[4 * c + 2]), __fmul_rn(sl_own, sr.z)),
+                        __fmul_rn(__uint_as_float(v[4 * c + 3]), __fmul_rn(sl_own, sr.w))};
+          if (!A1)
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float sr = sR_sh[c0 + 4 * c + e];
-            const float x = __uint_as_float(v[4 * c + e]);
-            o[e] = __fmul_rn(p.alpha, __fmul_rn(x, __fmul_rn(sl_own, sr)));
-          }
+            for (int e = 0; e < 4; ++e) o[e] = __fmul_rn(p.alpha, o[e]);
           *reinterpret_cast<float4*>(stg + lane * 32 + ((c ^ (lane & 7)) << 2)) = make_float4(o[0], o[1], o[2], o[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -492,12 +490,23 @@ qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant_
               : "memory");
           asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
-        if (more) {
-          tmem_ld_wait(vn);
-#pragma unroll
-          for (int e = 0; e < 32; ++e) v[e] = vn[e];
-        }
-      }
+        ++sc;
+      };
+      // the warp's four blocks, each TMEM load in flight while the previous
+      // block is emitted (two register sets, no copies)
+      uint32_t va[32], vb[32];
+      tmem_ld32_issue(trow + static_cast<uint32_t>(cbeg), va);
+      tmem_ld_wait(va);
+      tmem_ld32_issue(trow + static_cast<uint32_t>(cbeg + 32), vb);
+      emit(va, cbeg);
+      tmem_ld_wait(vb);
+      tmem_ld32_issue(trow + static_cast<uint32_t>(cbeg + 64), va);
+      emit(vb, cbeg + 32);
+      tmem_ld_wait(va);
+      tmem_ld32_issue(trow + static_cast<uint32_t>(cbeg + 96), vb);
+      emit(va, cbeg + 64);
+      tmem_ld_wait(vb);
+      emit(vb, cbeg + 96);
       // accumulator a drained: the MMAs of tile j + 2 may overwrite it
       tc_fence_before();
       __syncwarp();
@@ -889,15 +898,22 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
     const size_t psmem = 1024 + static_cast<size_t>(kPStages) * (p.a_bytes + p.b_bytes) +
                          static_cast<size_t>(8 * kPStg) * 4096 + sizeof(float) * p.bn;
     const unsigned gp = static_cast<unsigned>(num_sms());
+    const int nt = static_cast<int>(sh.ntiles);
+    const bool a1 = p.alpha == 1.f;
+#define LRAMM_TCP(K, A)                                                                                      \
+  do {                                                                                                       \
+    LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tcp_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                        (int)psmem));                                                        \
+    qgemm_tcp_kernel<K, A><<<gp, kPThreads, psmem, s>>>(mL, mR, mD, p, nt, ntl);                              \
+  } while (0)
     if (kind == kKindBF16) {
-      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tcp_kernel<kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)psmem));
-      qgemm_tcp_kernel<kKindBF16><<<gp, kPThreads, psmem, s>>>(mL, mR, mD, p, static_cast<int>(sh.ntiles), ntl);
+      if (a1) LRAMM_TCP(kKindBF16, true);
+      else LRAMM_TCP(kKindBF16, false);
     } else {
-      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tcp_kernel<kKindFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)psmem));
-      qgemm_tcp_kernel<kKindFP8><<<gp, kPThreads, psmem, s>>>(mL, mR, mD, p, static_cast<int>(sh.ntiles), ntl);
+      if (a1) LRAMM_TCP(kKindFP8, true);
+      else LRAMM_TCP(kKindFP8, false);
     }
+#undef LRAMM_TCP
     return last_launch();
   }
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);

@@ -615,6 +615,8 @@ __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l,
 // partials are added by split_reduce_kernel.
 struct GramTcParams {
   int l, W, n1, n2;
+  int mpc;       // M tiles per CTA: 2 when l <= 256 (both from one staged tile), else 1 (grid x = M tile)
+  int nload;     // 32-column atoms loaded and split per stage: ceil(l / 32) (the rest only pad MMA reads)
   int64_t rows, kblocks;
   int kb_per_split;
   int stages;
@@ -639,7 +641,6 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
   const int64_t kb0 = static_cast<int64_t>(split) * p.kb_per_split;
   const int64_t kb1 = min(p.kblocks, kb0 + p.kb_per_split);
   const int nkb = static_cast<int>(kb1 - kb0);   // >= 1: the host sizes the splits to the K range
-  const int natoms = p.W / kAtom;
   const uint32_t stage_bytes = 2 * p.part_bytes;
 
   if (threadIdx.x == 0) {
@@ -672,10 +673,10 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
         ok = false;
         break;
       }
-      mbar_expect_tx(&full_bar[s], p.part_bytes);
+      mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(p.nload) * (kAtom * kBK * 4));
       const int k0 = static_cast<int>((kb0 + i) * kBK);
       uint8_t* dst = smem + static_cast<size_t>(s) * stage_bytes;
-      for (int j = 0; j < natoms; ++j) tma_load_2d(dst + j * (kAtom * kBK * 4), &tmY, &full_bar[s], j * kAtom, k0);
+      for (int j = 0; j < p.nload; ++j) tma_load_2d(dst + j * (kAtom * kBK * 4), &tmY, &full_bar[s], j * kAtom, k0);
       ++issued;
     }
     if (!ok) {
@@ -689,9 +690,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
     }
   } else if (warp == 1 && lane == 0) {
     const uint32_t id1 = idesc_tf32(kBM, p.n1, 1, 1);
+    const uint32_t id1b = idesc_tf32(kBM, p.mpc == 2 ? ((p.l - kBM + 15) / 16) * 16 : 16, 1, 1);
     const uint32_t id2 = p.n2 ? idesc_tf32(kBM, p.n2, 1, 1) : 0u;
     const uint32_t seg2 = static_cast<uint32_t>(256 / kAtom) * (kAtom * kBK * 4);
-    const uint32_t aoff = static_cast<uint32_t>(mt * (kBM / kAtom)) * (kAtom * kBK * 4);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
       if (!mbar_wait(&split_bar[s], (i / p.stages) & 1, abort_flag)) {
@@ -702,18 +703,26 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
       tc_fence_after();
       const uint32_t hi = smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
       const uint32_t lo = hi + p.part_bytes;
+      for (int t = 0; t < p.mpc; ++t) {   // M tile mt + t into TMEM columns 256 t (n2 = 0 when mpc = 2)
+        const uint32_t aoff = static_cast<uint32_t>((mt + t) * (kBM / kAtom)) * (kAtom * kBK * 4);
+        const uint32_t d = tmem + static_cast<uint32_t>(t * 256);
+        // with two tiles per CTA the second needs only columns 128 .. l-1
+        // (its rows' columns 0 .. 127 are the first tile's, transposed)
+        const uint32_t boff = t == 1 ? static_cast<uint32_t>(kBM / kAtom) * (kAtom * kBK * 4) : 0u;
+        const uint32_t idt = t == 1 ? id1b : id1;
 #pragma unroll
-      for (int kk = 0; kk < kBK / 8; ++kk) {
-        const uint32_t ko = kk * 1024;
-        const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-        // (A, B) = (hi, hi), (hi, lo), (lo, hi)
-        mma_tf32(tmem, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + ko), id1, acc0);
-        mma_tf32(tmem, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + ko), id1, 1u);
-        mma_tf32(tmem, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + ko), id1, 1u);
-        if (p.n2) {
-          mma_tf32(tmem + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, acc0);
-          mma_tf32(tmem + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + seg2 + ko), id2, 1u);
-          mma_tf32(tmem + 256, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, 1u);
+        for (int kk = 0; kk < kBK / 8; ++kk) {
+          const uint32_t ko = kk * 1024;
+          const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
+          // (A, B) = (hi, hi), (hi, lo), (lo, hi)
+          mma_tf32(d, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + boff + ko), idt, acc0);
+          mma_tf32(d, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + boff + ko), idt, 1u);
+          mma_tf32(d, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + boff + ko), idt, 1u);
+          if (p.n2) {
+            mma_tf32(d + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, acc0);
+            mma_tf32(d + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + seg2 + ko), id2, 1u);
+            mma_tf32(d + 256, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, 1u);
+          }
         }
       }
       mma_commit(&empty_bar[s]);
@@ -722,7 +731,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
   } else if (warp >= 2) {
     // split each landed stage: high part in place, low part beside it
     const int st = threadIdx.x - 64;   // 0 .. 127
-    const int nq = static_cast<int>(p.part_bytes / 16);
+    const int nq = p.nload * (kAtom * kBK * 4 / 16);   // the loaded atoms (the rest only pad MMA reads)
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
       if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
@@ -749,17 +758,28 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
     volatile int zero = 0;
     const bool ok = mbar_wait(&tmem_bar, 0, &zero);
     tc_fence_after();
-    const int row = mt * kBM + q * 32 + lane;
-    float* dst = p.out + (static_cast<int64_t>(p.splits > 1 ? split : 0) * p.l + row) * p.l;
-    for (int c0 = 0; c0 < p.l; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(c0), v);
-      if (!ok) continue;
-      if (row < p.l) {
-        const int nv = min(32, p.l - c0);
+    float* gbase = p.out + static_cast<int64_t>(p.splits > 1 ? split : 0) * p.l * p.l;
+    for (int t = 0; t < p.mpc; ++t) {
+      const int row = (mt + t) * kBM + q * 32 + lane;
+      if ((mt + t) * kBM + q * 32 >= p.l) continue;   // this warp's TMEM lanes hold no row of G
+      float* dst = gbase + static_cast<int64_t>(row) * p.l;
+      // two tiles per CTA: the second tile's TMEM column j is G column 128 + j
+      const int cfirst = (p.mpc == 2 && t == 1) ? kBM : 0;
+      for (int c0 = cfirst; c0 < p.l; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * 256 + c0 - cfirst), v);
+        if (!ok) continue;
+        if (row < p.l) {
+          const int nv = min(32, p.l - c0);
 #pragma unroll
-        for (int j = 0; j < 32; j += 4)
-          if (j < nv) *reinterpret_cast<float4*>(dst + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          for (int j = 0; j < 32; j += 4)
+            if (j < nv) *reinterpret_cast<float4*>(dst + c0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          if (p.mpc == 2 && t == 0 && c0 >= kBM) {   // G[c][row] = G[row][c], c >= 128: lanes write consecutive rows
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (j < nv) gbase[static_cast<int64_t>(c0 + j) * p.l + row] = v[j];
+          }
+        }
       }
     }
     if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
@@ -1041,18 +1061,23 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   p.stages = static_cast<int>((kSmemBudget - 1024) / (2 * p.part_bytes));
   if (p.stages > kMaxStages) p.stages = kMaxStages;
   if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
+  const int mtiles = static_cast<int>(ceil_div(l, kBM));
+  // l <= 256: one CTA issues both M tiles' MMAs from each staged tile (the
+  // tile is loaded and split once), accumulators at TMEM columns 0 and 256
+  p.mpc = (mtiles == 2 && p.n2 == 0) ? 2 : 1;
+  p.nload = static_cast<int>(ceil_div(l, kAtom));
   uint32_t tc = 32;
   while (tc < static_cast<uint32_t>(p.n1 + p.n2)) tc <<= 1;
-  p.tmem_cols = tc;
+  p.tmem_cols = p.mpc == 2 ? 512u : tc;
   p.status = status;
-  const int mtiles = static_cast<int>(ceil_div(l, kBM));
+  const int gx = mtiles / p.mpc;
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * 2 * p.part_bytes;
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int i = 0; i < n; ++i) {
     if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
     p.rows = rows[i];
     p.kblocks = ceil_div(rows[i], kBK);
-    int64_t splits = num_sms() / mtiles;
+    int64_t splits = num_sms() / (p.mpc == 2 ? 2 : mtiles);
     if (splits > p.kblocks / 2) splits = p.kblocks / 2;   // at least two K blocks per CTA
     if (splits < 1) splits = 1;
     while (splits > 1 && static_cast<size_t>(splits) * l * l > part_floats) --splits;
@@ -1067,8 +1092,7 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     if (!make_map_f32(&my, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, kAtom, kBK,
                       CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
       return LRAMM_ERR_CUDA;
-    gram_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, p,
-                                                                                                          cond);
+    gram_tc_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, p, cond);
     LRAMM_TRY(last_launch());
     if (splits > 1) {
       const int64_t n4 = static_cast<int64_t>(l) * l / 4;
