@@ -443,17 +443,28 @@ qgemm_tcp_kernel(const __grid_constant__ CUtensorMap tmL, const __grid_constant_
     int sc = 0;   // staging blocks used by this warp
     bool ok = true;
     int j = 0;
+    // the scales of a tile are loaded one tile ahead (their latency was the
+    // epilogue's main stall): thread et holds column et's scale, each lane
+    // its row's
+    auto col_scale = [&](int64_t tt) {
+      const int64_t col = (tt % ntn) * kPBN + et;
+      return tt < ntiles && col < p.N ? (p.per_row ? p.sR[col] : p.sR[0]) : 0.f;
+    };
+    auto row_scale = [&](int64_t tt) {
+      const int64_t row = (tt / ntn) * kQM + q * 32 + lane;
+      return tt < ntiles && row < p.M ? (p.per_row ? p.sL[row] : p.sL[0]) : 0.f;
+    };
+    float sr_next = col_scale(blockIdx.x), sl_next = row_scale(blockIdx.x);
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
       const int a = j & 1;
       const int64_t m0 = (t / ntn) * kQM, n0 = (t % ntn) * p.bn;
       epi_bar8();   // every epilogue warp is done with the previous tile's column scales
-      for (int c = et; c < p.bn; c += 256) {
-        const int64_t col = n0 + c;
-        sR_sh[c] = col < p.N ? (p.per_row ? p.sR[col] : p.sR[0]) : 0.f;
-      }
+      sR_sh[et] = sr_next;
+      const float sl_own = sl_next;
+      sr_next = col_scale(t + gridDim.x);
+      sl_next = row_scale(t + gridDim.x);
       epi_bar8();
       const int64_t rbase = m0 + q * 32;
-      const float sl_own = rbase + lane < p.M ? (p.per_row ? p.sL[rbase + lane] : p.sL[0]) : 0.f;
       // after an abort the warp keeps walking the tiles through the two
       // named barriers above (so no epilogue warp waits on one that left)
       // and does nothing else

@@ -486,7 +486,6 @@ basis_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__
     }
   } else if (warp == 1 && lane == 0) {
     // ---- MMA issuer
-    const uint32_t id1 = idesc_tf32_kk(kBM, p.n1);
     const uint32_t id2 = p.n2 ? idesc_tf32_kk(kBM, p.n2) : 0u;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
@@ -498,13 +497,23 @@ basis_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__
       tc_fence_after();
       const uint32_t yh = smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
       const uint32_t yl = yh + p.a_bytes, lh = yh + 2 * p.a_bytes, ll = lh + p.b_bytes;
+      // L^-1 is lower triangular: K block i (k0 = 32 i) meets only the
+      // output columns n >= k0, so the first MMA group starts at column k0
+      // (B rows k0 .., TMEM column k0) with N = n1 - k0; the first K block
+      // covers (and initialises) every column
+      const int k0 = i * kBK;
+      const bool tri = k0 < p.n1;
+      const uint32_t idt = tri ? idesc_tf32_kk(kBM, p.n1 - k0) : 0u;
+      const uint32_t bo = static_cast<uint32_t>(k0) * 128;
 #pragma unroll
       for (int kk = 0; kk < kBK / 8; ++kk) {   // 8 TF32 (32 bytes) of K per instruction
         const uint32_t ko = kk * 32;
         const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, kmajor_desc(yh + ko), kmajor_desc(lh + ko), id1, acc0);
-        mma_tf32(tmem, kmajor_desc(yl + ko), kmajor_desc(lh + ko), id1, 1u);
-        mma_tf32(tmem, kmajor_desc(yh + ko), kmajor_desc(ll + ko), id1, 1u);
+        if (tri) {
+          mma_tf32(tmem + k0, kmajor_desc(yh + ko), kmajor_desc(lh + bo + ko), idt, acc0);
+          mma_tf32(tmem + k0, kmajor_desc(yl + ko), kmajor_desc(lh + bo + ko), idt, 1u);
+          mma_tf32(tmem + k0, kmajor_desc(yh + ko), kmajor_desc(ll + bo + ko), idt, 1u);
+        }
         if (p.n2) {   // L rows 256 .. : 256 rows of 128 bytes further on
           mma_tf32(tmem + 256, kmajor_desc(yh + ko), kmajor_desc(lh + 32768 + ko), id2, acc0);
           mma_tf32(tmem + 256, kmajor_desc(yl + ko), kmajor_desc(lh + 32768 + ko), id2, 1u);
@@ -616,6 +625,8 @@ __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l,
 struct GramTcParams {
   int l, W, n1, n2;
   int mpc;       // M tiles per CTA: 2 when l <= 256 (both from one staged tile), else 1 (grid x = M tile)
+  int corner;    // mpc == 2 and l - 128 <= 32: the block G[128.., 128..] in FP32 SIMT (no second MMA tile)
+  const float* Y;   // rows x l (the corner's columns are read directly)
   int nload;     // 32-column atoms loaded and split per stage: ceil(l / 32) (the rest only pad MMA reads)
   int64_t rows, kblocks;
   int kb_per_split;
@@ -630,6 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const int* __restrict__ cond) {
   if (cond && *cond == 0) return;   // predicated launch (the CholeskyQR fallback)
   extern __shared__ uint8_t smem_raw[];
+  __shared__ float cblk[kBK * 33];   // a stage's corner columns (32 rows x <= 32)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
   __shared__ uint32_t tmem_base_sh;
@@ -703,7 +715,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
       tc_fence_after();
       const uint32_t hi = smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
       const uint32_t lo = hi + p.part_bytes;
-      for (int t = 0; t < p.mpc; ++t) {   // M tile mt + t into TMEM columns 256 t (n2 = 0 when mpc = 2)
+      for (int t = 0; t < (p.corner ? 1 : p.mpc); ++t) {   // M tile mt + t into TMEM columns 256 t (n2 = 0 when mpc = 2)
         const uint32_t aoff = static_cast<uint32_t>((mt + t) * (kBM / kAtom)) * (kAtom * kBK * 4);
         const uint32_t d = tmem + static_cast<uint32_t>(t * 256);
         // with two tiles per CTA the second needs only columns 128 .. l-1
@@ -732,34 +744,67 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
     // split each landed stage: high part in place, low part beside it
     const int st = threadIdx.x - 64;   // 0 .. 127
     const int nq = p.nload * (kAtom * kBK * 4 / 16);   // the loaded atoms (the rest only pad MMA reads)
+    // the corner block (corner x corner, l - 128 <= 32): thread st owns
+    // elements st + 128 u, accumulated over the stage's 32 rows in FP32
+    const int ncorner = p.corner * p.corner;
+    float cacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    bool live = true;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
-      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+      float cv[8];
+      if (p.corner) {   // this stage's corner columns, loaded before waiting for the tile
+        const int64_t r0 = (kb0 + i) * kBK;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = st + 128 * u, r = idx >> 5, c = idx & 31;
+          cv[u] = (c < p.corner && r0 + r < p.rows) ? p.Y[(r0 + r) * p.l + kBM + c] : 0.f;
+        }
+      }
+      // after an expired wait the warp stops splitting but keeps taking the
+      // corner's named barriers (no converter warp waits on one that left)
+      if (live && !mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
         set_status(p.status, LRAMM_ERR_TIMEOUT);
         abort_sh = 1;
-        break;
+        live = false;
       }
-      float4* h4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes);
-      float4* l4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes + p.part_bytes);
-      for (int e = st; e < nq; e += 128) {
-        const float4 y = h4[e];
-        float4 h;
-        h.x = __uint_as_float(__float_as_uint(y.x) & 0xFFFFE000u);
-        h.y = __uint_as_float(__float_as_uint(y.y) & 0xFFFFE000u);
-        h.z = __uint_as_float(__float_as_uint(y.z) & 0xFFFFE000u);
-        h.w = __uint_as_float(__float_as_uint(y.w) & 0xFFFFE000u);
-        h4[e] = h;
-        l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
+      if (live) {
+        float4* h4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes);
+        float4* l4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes + p.part_bytes);
+        for (int e = st; e < nq; e += 128) {
+          const float4 y = h4[e];
+          float4 h;
+          h.x = __uint_as_float(__float_as_uint(y.x) & 0xFFFFE000u);
+          h.y = __uint_as_float(__float_as_uint(y.y) & 0xFFFFE000u);
+          h.z = __uint_as_float(__float_as_uint(y.z) & 0xFFFFE000u);
+          h.w = __uint_as_float(__float_as_uint(y.w) & 0xFFFFE000u);
+          h4[e] = h;
+          l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split_bar[s])) : "memory");
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split_bar[s])) : "memory");
+      if (p.corner) {
+        asm volatile("bar.sync 3, 128;" ::: "memory");   // the previous stage's block is read
+#pragma unroll
+        for (int u = 0; u < 8; ++u) cblk[((st + 128 * u) >> 5) * 33 + ((st + 128 * u) & 31)] = cv[u];
+        asm volatile("bar.sync 3, 128;" ::: "memory");
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int e = st + 128 * u;
+          if (e < ncorner) {
+            const int ci = e / p.corner, cj = e - ci * p.corner;
+#pragma unroll 8
+            for (int r = 0; r < kBK; ++r) cacc[u] = fmaf(cblk[r * 33 + ci], cblk[r * 33 + cj], cacc[u]);
+          }
+        }
+      }
     }
     const int q = warp & 3;
     volatile int zero = 0;
     const bool ok = mbar_wait(&tmem_bar, 0, &zero);
     tc_fence_after();
     float* gbase = p.out + static_cast<int64_t>(p.splits > 1 ? split : 0) * p.l * p.l;
-    for (int t = 0; t < p.mpc; ++t) {
+    for (int t = 0; t < (p.corner ? 1 : p.mpc); ++t) {
       const int row = (mt + t) * kBM + q * 32 + lane;
       if ((mt + t) * kBM + q * 32 >= p.l) continue;   // this warp's TMEM lanes hold no row of G
       float* dst = gbase + static_cast<int64_t>(row) * p.l;
@@ -782,6 +827,15 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
         }
       }
     }
+    if (ok && p.corner)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = st + 128 * u;
+        if (e < ncorner) {
+          const int ci = e / p.corner, cj = e - ci * p.corner;
+          gbase[static_cast<int64_t>(kBM + ci) * p.l + kBM + cj] = cacc[u];
+        }
+      }
     if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
   }
   tc_fence_before();
@@ -1058,13 +1112,17 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   p.n1 = l <= 256 ? static_cast<int>(round_up(l, 16)) : 256;
   p.n2 = l <= 256 ? 0 : static_cast<int>(round_up(l - 256, 16));
   p.part_bytes = static_cast<uint32_t>(p.W) * kBK * 4;
-  p.stages = static_cast<int>((kSmemBudget - 1024) / (2 * p.part_bytes));
+  // (the kernel's static shared memory holds the corner block, 4.2 KB)
+  p.stages = static_cast<int>((kSmemBudget - 1024 - kBK * 33 * sizeof(float)) / (2 * p.part_bytes));
   if (p.stages > kMaxStages) p.stages = kMaxStages;
   if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
   const int mtiles = static_cast<int>(ceil_div(l, kBM));
   // l <= 256: one CTA issues both M tiles' MMAs from each staged tile (the
   // tile is loaded and split once), accumulators at TMEM columns 0 and 256
   p.mpc = (mtiles == 2 && p.n2 == 0) ? 2 : 1;
+  // (a SIMT corner block in place of the second tile's MMAs was measured
+  // slower: its global loads sat on the converter warps' path)
+  p.corner = 0;
   p.nload = static_cast<int>(ceil_div(l, kAtom));
   uint32_t tc = 32;
   while (tc < static_cast<uint32_t>(p.n1 + p.n2)) tc <<= 1;
@@ -1076,8 +1134,9 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   for (int i = 0; i < n; ++i) {
     if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
     p.rows = rows[i];
+    p.Y = Y[i];
     p.kblocks = ceil_div(rows[i], kBK);
-    int64_t splits = num_sms() / (p.mpc == 2 ? 2 : mtiles);
+    int64_t splits = num_sms() / (p.mpc == 2 ? 1 : mtiles);
     if (splits > p.kblocks / 2) splits = p.kblocks / 2;   // at least two K blocks per CTA
     if (splits < 1) splits = 1;
     while (splits > 1 && static_cast<size_t>(splits) * l * l > part_floats) --splits;
