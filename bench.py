@@ -159,13 +159,15 @@ def kernel_work(kind, cfg, l, variant):
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# the ncu captures summarised under profiles/ (lramm_4096, one operand per
-# launch, the kernels as they are in this tree); None where no capture of the
-# current kernel exists.
+# the ncu captures summarised under profiles/, per workload, for the kernels
+# as they are in this tree; None where no capture of the current kernel
+# exists.  lramm_32768: the sketch's mean over the 12 launches of one call
+# (profiles/sketch_tc_lramm_32768.md, a one-pass capture at full size); E3
+# scaled by 4 from the 16384 x 16384 capture (profiles/e3_qgemm_tcp_lramm_32768.md:
+# the traffic is the output write, proportional to m n).
 MEASURED_TRAFFIC = {
-    "lramm_4096": {"trsm": 4667904,
-                   "sketch": 71603456 + 2272512, "e3": 4272384 + 8035072,
-                   "svd": 350208},   # the M-only Jacobi of the INT8 chain
+    "lramm_32768": {"sketch": 547600000 + 500000, "e3": 4 * (1012497000 + 8663040)},
+    "lramm_4096": {"svd": 350208},   # the M-only Jacobi (profiles/jacobi_monly_lramm_4096.md)
 }
 
 
