@@ -550,6 +550,10 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   uint8_t* T_hi = nullptr;
   uint8_t* T_lo = nullptr;
   uint32_t mphase = 0;
+  // TMEM: one 128-column accumulator while the trailing block has at most
+  // 128 rows (l <= 160), else two tiles at columns 0 and 256 (kept small so
+  // that the CTA finds room beside other kernels' accumulators on its SM)
+  const uint32_t tmem_cols = l - kCB <= 128 ? 128u : 512u;
   if (TC) {
     uint8_t* after = reinterpret_cast<uint8_t*>(LC + kCB * kLC);
     T_hi = after + ((1024u - (tc::smem_u32(after) & 1023u)) & 1023u);
@@ -559,7 +563,8 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc::smem_u32(&s_tmem))
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
+                   "r"(tmem_cols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -655,8 +660,10 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
         if (Xd != nullptr && inv_warp(warp))
           chol_inv_block(P, j0 - kCB, kCB, Xd + static_cast<int64_t>(j0 / kCB - 1) * kCB * kCB, s_rl,
                          inv_index(warp), lane);
-        else if (warp == 11 || warp >= 13)
+        else if (nw == 16 && (warp == 11 || warp >= 13))
           chol_write_L_block(P, Lo, l, j0 - kCB, warp == 11 ? 0 : warp - 12, 4, lane);
+        else if (nw < 16 && (warp & 3) != 0)   // fewer threads (no inversion): warps off warp 0's sub-partition
+          chol_write_L_block(P, Lo, l, j0 - kCB, warp - 1 - (warp >> 2), 3 * nw / 4, lane);
       }
       __syncthreads();
       const int r0 = j0 + kCB;   // first row below the diagonal block
@@ -746,10 +753,10 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
         if (!tc::mbar_wait(&s_mbar, mphase, &never) && tid == 0) set_status(status, LRAMM_ERR_TIMEOUT);
         mphase ^= 1u;
         tc::tc_fence_after();
-        const int q = warp & 3, part = warp >> 2;   // TMEM lanes 32 q .. 32 q + 31; column chunks part, part + 4
+        const int q = warp & 3, part = warp >> 2;   // TMEM lanes 32 q .. 32 q + 31; column chunks part, part + nw / 4
         for (int t = 0; t < tiles; ++t) {
           const int Nt = t == 0 ? min(N, 128) : N;
-          for (int ch = part; ch < Nt / 32; ch += 4) {
+          for (int ch = part; ch < Nt / 32; ch += nw >> 2) {
             float v[32];
             tc::tmem_ld32(tm + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(t * 256 + ch * 32), v);
             const int j = t * 128 + q * 32 + lane;
@@ -854,7 +861,7 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   }
   if (TC && warp == 1) {
     tc::tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(s_tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(tmem_cols) : "memory");
   }
   // The last column block (the others were written and inverted inside the
   // panel loop, during the next diagonal block's factorisation).
@@ -1201,7 +1208,14 @@ lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cud
     const size_t smem = chol3_tc_smem(l);
     LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         static_cast<int>(smem)));
-    chol3_kernel<true><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, shift_big_rel, status, cond);
+    // Without the diagonal-block inversions (eight warps of their own) 384
+    // threads do the rest: three quarters of the SM's registers, so that the
+    // CTA finds room beside a concurrent range-finder product's CTA on its SM
+    // instead of waiting for an empty SM.  The panel solve takes one thread
+    // per row below the diagonal block (at most 256: l - 32 <= 256).
+    bool inv = false;
+    for (int i = 0; i < cb.n; ++i) inv = inv || cb.p[i].Xd != nullptr;
+    chol3_kernel<true><<<cb.n, inv ? 512 : 384, smem, s>>>(cb, l, shift_rel, shift_big_rel, status, cond);
     return last_launch();
   }
   const size_t smem = chol3_smem(l);

@@ -621,12 +621,18 @@ __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l,
 // the high part (in place) and the low part (a second buffer of the same
 // layout) before the MMAs of that stage, so Y is read once from memory.
 // One CTA per (row block of G, K range), one launch per problem; split-K
-// partials are added by split_reduce_kernel.
+// partials are added by split_reduce4_kernel.
+//
+// 128 < l <= 144: the rows 128 .. l-1 of G are the first tile's columns
+// (transposed) except the corner block G[128.., 128..] (at most 16 x 16),
+// which the converter warps accumulate in FP32 from a second, unswizzled TMA
+// copy of those columns: one M tile of MMAs instead of two (the MMA issue
+// is the kernel's clock), and a staged tile of ceil(l / 32) atoms.
 struct GramTcParams {
   int l, W, n1, n2;
   int mpc;       // M tiles per CTA: 2 when l <= 256 (both from one staged tile), else 1 (grid x = M tile)
-  int corner;    // mpc == 2 and l - 128 <= 32: the block G[128.., 128..] in FP32 SIMT (no second MMA tile)
-  const float* Y;   // rows x l (the corner's columns are read directly)
+  int corner;    // the corner width l - 128 when it is built in FP32 SIMT (then only tile 0 is MMA'd), else 0
+  uint32_t cstride;   // bytes per stage of the corner copy (32 rows x corner FP32, 128-byte multiple)
   int nload;     // 32-column atoms loaded and split per stage: ceil(l / 32) (the rest only pad MMA reads)
   int64_t rows, kblocks;
   int kb_per_split;
@@ -638,10 +644,10 @@ struct GramTcParams {
 };
 
 __global__ void __launch_bounds__(kThreads, 1)
-gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const int* __restrict__ cond) {
+gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmC, GramTcParams p,
+               const int* __restrict__ cond) {
   if (cond && *cond == 0) return;   // predicated launch (the CholeskyQR fallback)
   extern __shared__ uint8_t smem_raw[];
-  __shared__ float cblk[kBK * 33];   // a stage's corner columns (32 rows x <= 32)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[kMaxStages], split_bar[kMaxStages], empty_bar[kMaxStages], tmem_bar;
   __shared__ uint32_t tmem_base_sh;
@@ -685,10 +691,14 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
         ok = false;
         break;
       }
-      mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(p.nload) * (kAtom * kBK * 4));
+      mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(p.nload) * (kAtom * kBK * 4) +
+                                       static_cast<uint32_t>(p.corner) * (kBK * 4));
       const int k0 = static_cast<int>((kb0 + i) * kBK);
       uint8_t* dst = smem + static_cast<size_t>(s) * stage_bytes;
       for (int j = 0; j < p.nload; ++j) tma_load_2d(dst + j * (kAtom * kBK * 4), &tmY, &full_bar[s], j * kAtom, k0);
+      if (p.corner)   // columns 128 .. l-1 of the same rows, row-major 32 x corner
+        tma_load_2d(smem + static_cast<size_t>(p.stages) * stage_bytes + static_cast<size_t>(s) * p.cstride, &tmC,
+                    &full_bar[s], kBM, k0);
       ++issued;
     }
     if (!ok) {
@@ -744,60 +754,50 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
     // split each landed stage: high part in place, low part beside it
     const int st = threadIdx.x - 64;   // 0 .. 127
     const int nq = p.nload * (kAtom * kBK * 4 / 16);   // the loaded atoms (the rest only pad MMA reads)
-    // the corner block (corner x corner, l - 128 <= 32): thread st owns
-    // elements st + 128 u, accumulated over the stage's 32 rows in FP32
-    const int ncorner = p.corner * p.corner;
+    // the corner block: warp g = warp - 2 takes rows 8 g .. 8 g + 7 of each
+    // stage, lane (bi, bj) = (lane / 8, lane mod 8) the 4 x 2 block at
+    // corner rows 4 bi .., columns 2 bj .. (FP32 FMAs in row order)
+    const int g = warp - 2, ci = 4 * (lane >> 3), cj = 2 * (lane & 7);
+    const bool cown = ci < p.corner && cj < p.corner;
+    const float* cbase = reinterpret_cast<const float*>(smem + static_cast<size_t>(p.stages) * stage_bytes);
     float cacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    bool live = true;
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
-      float cv[8];
-      if (p.corner) {   // this stage's corner columns, loaded before waiting for the tile
-        const int64_t r0 = (kb0 + i) * kBK;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int idx = st + 128 * u, r = idx >> 5, c = idx & 31;
-          cv[u] = (c < p.corner && r0 + r < p.rows) ? p.Y[(r0 + r) * p.l + kBM + c] : 0.f;
-        }
-      }
-      // after an expired wait the warp stops splitting but keeps taking the
-      // corner's named barriers (no converter warp waits on one that left)
-      if (live && !mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
+      if (!mbar_wait(&full_bar[s], (i / p.stages) & 1, abort_flag)) {
         set_status(p.status, LRAMM_ERR_TIMEOUT);
         abort_sh = 1;
-        live = false;
+        break;
       }
-      if (live) {
-        float4* h4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes);
-        float4* l4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes + p.part_bytes);
-        for (int e = st; e < nq; e += 128) {
-          const float4 y = h4[e];
-          float4 h;
-          h.x = __uint_as_float(__float_as_uint(y.x) & 0xFFFFE000u);
-          h.y = __uint_as_float(__float_as_uint(y.y) & 0xFFFFE000u);
-          h.z = __uint_as_float(__float_as_uint(y.z) & 0xFFFFE000u);
-          h.w = __uint_as_float(__float_as_uint(y.w) & 0xFFFFE000u);
-          h4[e] = h;
-          l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split_bar[s])) : "memory");
+      float4* h4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes);
+      float4* l4 = reinterpret_cast<float4*>(smem + static_cast<size_t>(s) * stage_bytes + p.part_bytes);
+      for (int e = st; e < nq; e += 128) {
+        const float4 y = h4[e];
+        float4 h;
+        h.x = __uint_as_float(__float_as_uint(y.x) & 0xFFFFE000u);
+        h.y = __uint_as_float(__float_as_uint(y.y) & 0xFFFFE000u);
+        h.z = __uint_as_float(__float_as_uint(y.z) & 0xFFFFE000u);
+        h.w = __uint_as_float(__float_as_uint(y.w) & 0xFFFFE000u);
+        h4[e] = h;
+        l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
       }
-      if (p.corner) {
-        asm volatile("bar.sync 3, 128;" ::: "memory");   // the previous stage's block is read
+      if (cown) {   // before the arrival below: the stage (and its corner copy) is refilled only after it
+        const float* cb = cbase + static_cast<size_t>(s) * (p.cstride / 4) + (8 * g) * p.corner;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) cblk[((st + 128 * u) >> 5) * 33 + ((st + 128 * u) & 31)] = cv[u];
-        asm volatile("bar.sync 3, 128;" ::: "memory");
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int e = st + 128 * u;
-          if (e < ncorner) {
-            const int ci = e / p.corner, cj = e - ci * p.corner;
-#pragma unroll 8
-            for (int r = 0; r < kBK; ++r) cacc[u] = fmaf(cblk[r * 33 + ci], cblk[r * 33 + cj], cacc[u]);
-          }
+        for (int r = 0; r < 8; ++r) {
+          const float4 a = *reinterpret_cast<const float4*>(cb + r * p.corner + ci);
+          const float2 b = *reinterpret_cast<const float2*>(cb + r * p.corner + cj);
+          cacc[0] = fmaf(a.x, b.x, cacc[0]);
+          cacc[1] = fmaf(a.x, b.y, cacc[1]);
+          cacc[2] = fmaf(a.y, b.x, cacc[2]);
+          cacc[3] = fmaf(a.y, b.y, cacc[3]);
+          cacc[4] = fmaf(a.z, b.x, cacc[4]);
+          cacc[5] = fmaf(a.z, b.y, cacc[5]);
+          cacc[6] = fmaf(a.w, b.x, cacc[6]);
+          cacc[7] = fmaf(a.w, b.y, cacc[7]);
         }
       }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&split_bar[s])) : "memory");
     }
     const int q = warp & 3;
     volatile int zero = 0;
@@ -827,15 +827,25 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, GramTcParams p, const in
         }
       }
     }
-    if (ok && p.corner)
+    if (p.corner) {
+      // the four row groups' partial blocks, added in group order by warp 2
+      // (every converter warp takes both barriers, also after an expired wait)
+      float* red = reinterpret_cast<float*>(smem + static_cast<size_t>(p.stages) * (stage_bytes + p.cstride));
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = st + 128 * u;
-        if (e < ncorner) {
-          const int ci = e / p.corner, cj = e - ci * p.corner;
-          gbase[static_cast<int64_t>(kBM + ci) * p.l + kBM + cj] = cacc[u];
+      for (int u = 0; u < 8; ++u) red[(g * 32 + lane) * 8 + u] = cacc[u];
+      asm volatile("bar.sync 3, 128;" ::: "memory");
+      if (g == 0 && ok && cown) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          float v = red[lane * 8 + u];
+          v += red[(32 + lane) * 8 + u];
+          v += red[(64 + lane) * 8 + u];
+          v += red[(96 + lane) * 8 + u];
+          const int a = ci + (u >> 1), b = cj + (u & 1);
+          if (a < p.corner && b < p.corner) gbase[static_cast<int64_t>(kBM + a) * p.l + kBM + b] = v;
         }
       }
+    }
     if (!ok) set_status(p.status, LRAMM_ERR_TIMEOUT);
   }
   tc_fence_before();
@@ -877,29 +887,31 @@ __global__ void split_reduce_kernel(const float4* __restrict__ part, int splits,
   }
 }
 
-// The same sum for many splits and few outputs (the Gram partials): four
-// threads per float4 of out, each adding a quarter of the splits in split
-// order, then the four partial sums added in a fixed order ((q0 + q1) + q2)
-// + q3 (deterministic, four times the loads in flight).  64 outputs per
-// 256-thread CTA.
+// The same sum for many splits and few outputs (the Gram partials): kRG
+// threads per float4 of out, each adding its share of the splits in split
+// order, then the kRG partial sums added in group order (deterministic, kRG
+// times the loads in flight, and 256 / kRG outputs per CTA so that the grid
+// covers the SMs).
+constexpr int kRG = 16;
 __global__ void __launch_bounds__(256) split_reduce4_kernel(const float4* __restrict__ part, int splits, int64_t n4,
                                                            float4* __restrict__ out, const int* __restrict__ cond) {
   if (cond && *cond == 0) return;
-  __shared__ float4 red[4][64];
-  const int o = threadIdx.x & 63, g = threadIdx.x >> 6;
-  const int64_t i = blockIdx.x * static_cast<int64_t>(64) + o;
-  const int per = (splits + 3) / 4;
+  constexpr int kOut = 256 / kRG;
+  __shared__ float4 red[kRG][kOut];
+  const int o = threadIdx.x % kOut, g = threadIdx.x / kOut;
+  const int64_t i = blockIdx.x * static_cast<int64_t>(kOut) + o;
+  const int per = (splits + kRG - 1) / kRG;
   const int s0 = g * per, s1 = min(splits, s0 + per);
   float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
   if (i < n4 && s0 < s1) {
     a = part[static_cast<int64_t>(s0) * n4 + i];
     int s = s0 + 1;
-    for (; s + 8 <= s1; s += 8) {
-      float4 b[8];
+    for (; s + 4 <= s1; s += 4) {
+      float4 b[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) b[u] = part[static_cast<int64_t>(s + u) * n4 + i];
+      for (int u = 0; u < 4; ++u) b[u] = part[static_cast<int64_t>(s + u) * n4 + i];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 4; ++u) {
         a.x += b[u].x;
         a.y += b[u].y;
         a.z += b[u].z;
@@ -918,7 +930,7 @@ __global__ void __launch_bounds__(256) split_reduce4_kernel(const float4* __rest
   __syncthreads();
   if (g == 0 && i < n4) {
     float4 t = red[0][o];
-    for (int q = 1; q < 4; ++q) {
+    for (int q = 1; q < kRG; ++q) {
       if (q * per >= splits) break;   // groups past the last split are empty
       t.x += red[q][o].x;
       t.y += red[q][o].y;
@@ -1111,30 +1123,30 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   p.W = gram_tc_width(l);
   p.n1 = l <= 256 ? static_cast<int>(round_up(l, 16)) : 256;
   p.n2 = l <= 256 ? 0 : static_cast<int>(round_up(l - 256, 16));
-  p.part_bytes = static_cast<uint32_t>(p.W) * kBK * 4;
-  // (the kernel's static shared memory holds the corner block, 4.2 KB)
-  p.stages = static_cast<int>((kSmemBudget - 1024 - kBK * 33 * sizeof(float)) / (2 * p.part_bytes));
-  if (p.stages > kMaxStages) p.stages = kMaxStages;
-  if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
   const int mtiles = static_cast<int>(ceil_div(l, kBM));
   // l <= 256: one CTA issues both M tiles' MMAs from each staged tile (the
-  // tile is loaded and split once), accumulators at TMEM columns 0 and 256
+  // tile is loaded and split once), accumulators at TMEM columns 0 and 256;
+  // l <= 144: the second tile's only new block is the corner, in FP32 SIMT
   p.mpc = (mtiles == 2 && p.n2 == 0) ? 2 : 1;
-  // (a SIMT corner block in place of the second tile's MMAs was measured
-  // slower: its global loads sat on the converter warps' path)
-  p.corner = 0;
+  p.corner = (p.mpc == 2 && l - kBM <= 16) ? l - kBM : 0;
   p.nload = static_cast<int>(ceil_div(l, kAtom));
+  if (p.corner) p.W = p.nload * kAtom;   // tile 0's A (atoms 0..3) and B (n1 columns) lie within the loaded atoms
+  p.part_bytes = static_cast<uint32_t>(p.W) * kBK * 4;
+  p.cstride = p.corner ? static_cast<uint32_t>(round_up(static_cast<size_t>(kBK) * p.corner * 4, 128)) : 0u;
+  const size_t red_bytes = p.corner ? 4 * 32 * 8 * sizeof(float) : 0;
+  p.stages = static_cast<int>((kSmemBudget - 1024 - red_bytes) / (2 * p.part_bytes + p.cstride));
+  if (p.stages > kMaxStages) p.stages = kMaxStages;
+  if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
   uint32_t tc = 32;
   while (tc < static_cast<uint32_t>(p.n1 + p.n2)) tc <<= 1;
-  p.tmem_cols = p.mpc == 2 ? 512u : tc;
+  p.tmem_cols = (p.mpc == 2 && !p.corner) ? 512u : tc;
   p.status = status;
   const int gx = mtiles / p.mpc;
-  const size_t smem = 1024 + static_cast<size_t>(p.stages) * 2 * p.part_bytes;
+  const size_t smem = 1024 + static_cast<size_t>(p.stages) * (2 * p.part_bytes + p.cstride) + red_bytes;
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   for (int i = 0; i < n; ++i) {
     if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
     p.rows = rows[i];
-    p.Y = Y[i];
     p.kblocks = ceil_div(rows[i], kBK);
     int64_t splits = num_sms() / (p.mpc == 2 ? 1 : mtiles);
     if (splits > p.kblocks / 2) splits = p.kblocks / 2;   // at least two K blocks per CTA
@@ -1147,15 +1159,23 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     // the FP32 rows of Y (l % 4 == 0: 16-byte row pitch); tile atoms beyond
     // l and rows beyond the end are loaded out of range (x a multiple of 32)
     // and arrive as zeros
-    CUtensorMap my;
+    CUtensorMap my, mc;
     if (!make_map_f32(&my, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, kAtom, kBK,
                       CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
       return LRAMM_ERR_CUDA;
-    gram_tc_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, p, cond);
+    if (p.corner) {   // the corner columns 128 .. l-1, a dense 32 x corner box (corner * 4 bytes: a multiple of 16)
+      if (!make_map_f32(&mc, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, static_cast<uint32_t>(p.corner), kBK,
+                        CU_TENSOR_MAP_SWIZZLE_NONE))
+        return LRAMM_ERR_CUDA;
+    } else {
+      mc = my;   // not read
+    }
+    gram_tc_kernel<<<dim3(static_cast<unsigned>(gx), static_cast<unsigned>(splits)), kThreads, smem, s>>>(my, mc, p,
+                                                                                                        cond);
     LRAMM_TRY(last_launch());
     if (splits > 1) {
       const int64_t n4 = static_cast<int64_t>(l) * l / 4;
-      split_reduce4_kernel<<<static_cast<unsigned>(ceil_div(n4, 64)), 256, 0, s>>>(
+      split_reduce4_kernel<<<static_cast<unsigned>(ceil_div(n4, 256 / kRG)), 256, 0, s>>>(
           reinterpret_cast<const float4*>(part), static_cast<int>(splits), n4, reinterpret_cast<float4*>(G[i]), cond);
       LRAMM_TRY(last_launch());
     }
