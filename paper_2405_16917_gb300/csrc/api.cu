@@ -1,3 +1,5 @@
+#include <map>
+#include <mutex>
 #include <atomic>
 // C ABI of the LRAMM library: plan, workspace layout and the pipeline
 //   RSVD(A), RSVD(B)  (Sec. 2.2 range finder + Algorithm 1)
@@ -36,6 +38,28 @@ int num_sms() {
   if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) v = 152;
   cache[dev].store(v, std::memory_order_relaxed);
   return v;
+}
+
+cudaError_t smem_cap_fn(const void* fn, size_t need) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> caps;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = caps.find({fn, dev});
+  if (it == caps.end()) {
+    cudaFuncAttributes fa{};
+    int optin = 0;
+    if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    const size_t cap = static_cast<size_t>(optin) > fa.sharedSizeBytes ? optin - fa.sharedSizeBytes : 0;
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(cap))) !=
+        cudaSuccess)
+      return e;
+    it = caps.emplace(std::make_pair(fn, dev), cap).first;
+  }
+  return need <= it->second ? cudaSuccess : cudaErrorInvalidValue;
 }
 }  // namespace lramm
 

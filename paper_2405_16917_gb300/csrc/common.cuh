@@ -65,6 +65,21 @@ void note_cuda_error(cudaError_t e, const char* where);
 // once per device): grids and split-K counts are sized from it.
 int num_sms();
 
+// The dynamic shared-memory cap of a kernel (cudaFuncAttributeMax-
+// DynamicSharedMemorySize) belongs to the function, not to a launch.  A
+// captured CUDA graph's kernel node keeps its own size, but a node that is
+// launched again on its own (as a profiler replaying the graph does) is
+// checked against the function's current cap -- the last value any launch
+// set, possibly a smaller one from another shape.  So the cap is raised
+// once per kernel and device to the device's opt-in maximum (less the
+// kernel's static shared memory), and only a launch needing more than that
+// is refused (cudaErrorInvalidValue).
+cudaError_t smem_cap_fn(const void* fn, size_t need);
+template <typename F>
+inline cudaError_t smem_cap(F* fn, size_t need) {
+  return smem_cap_fn(reinterpret_cast<const void*>(fn), need);
+}
+
 // Every kernel launch of the library is followed by exactly one check;
 // the check also counts the launch (lramm_launch_count).
 void count_launch();

@@ -1168,7 +1168,7 @@ static const int kSmemMaxO = 232448 - 1024;
 lramm_status launch_chol2(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s) {
   const size_t smem = sizeof(float) * static_cast<size_t>(l) * (l + 1) / 2;
   if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  LRAMM_CUDA_TRY(smem_cap(chol2_kernel, static_cast<int>(smem)));
   chol2_kernel<<<bt.n, 1024, smem, s>>>(bt, l, shift_rel, status);
   return last_launch();
 }
@@ -1179,7 +1179,7 @@ lramm_status launch_trsm_panel(SmallBatch bt, int l, cudaStream_t s) {
                                        static_cast<size_t>(kTP) * (kTP + 1));
   if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
   LRAMM_CUDA_TRY(
-      cudaFuncSetAttribute(trsm_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+      smem_cap(trsm_panel_kernel, static_cast<int>(smem)));
   int64_t rows = 0;
   for (int i = 0; i < bt.n; ++i) rows = bt.p[i].rows > rows ? bt.p[i].rows : rows;
   trsm_panel_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kTR)), bt.n), 256, smem, s>>>(bt, l, lq);
@@ -1206,8 +1206,7 @@ lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cud
   if (!chol3_supported(l)) return LRAMM_ERR_UNSUPPORTED;
   if (chol3_tc_smem(l) <= static_cast<size_t>(kSmemMaxO)) {
     const size_t smem = chol3_tc_smem(l);
-    LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(smem)));
+    LRAMM_CUDA_TRY(smem_cap(chol3_kernel<true>, static_cast<int>(smem)));
     // Without the diagonal-block inversions (eight warps of their own) 384
     // threads do the rest: three quarters of the SM's registers, so that the
     // CTA finds room beside a concurrent range-finder product's CTA on its SM
@@ -1219,8 +1218,7 @@ lramm_status launch_chol3(CholBatch cb, int l, float shift_rel, int* status, cud
     return last_launch();
   }
   const size_t smem = chol3_smem(l);
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(smem)));
+  LRAMM_CUDA_TRY(smem_cap(chol3_kernel<false>, static_cast<int>(smem)));
   chol3_kernel<false><<<cb.n, 512, smem, s>>>(cb, l, shift_rel, shift_big_rel, status, cond);
   return last_launch();
 }
@@ -1236,7 +1234,7 @@ lramm_status launch_trsm3(TrsmBatch tb, int l, cudaStream_t s, const int* cond) 
   const int lqL = static_cast<int>(round_up(l > kCB ? l - kCB : 4, kCB)) + 4;
   const size_t smem = sizeof(float) * (static_cast<size_t>(kR3) * lqQ + static_cast<size_t>(kCB) * lqL + 2 * kCB * kLC);
   if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(trsm3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  LRAMM_CUDA_TRY(smem_cap(trsm3_kernel, static_cast<int>(smem)));
   int64_t rows = 0;
   for (int i = 0; i < tb.n; ++i) rows = tb.p[i].rows > rows ? tb.p[i].rows : rows;
   trsm3_kernel<<<dim3(static_cast<unsigned>(ceil_div(rows, kR3)), tb.n), 256, smem, s>>>(tb, l, lqQ, lqL, cond);
@@ -1257,7 +1255,7 @@ lramm_status launch_linv(LinvBatch lb, int l, cudaStream_t s, const int* cond) {
   const int whole = whole_smem <= static_cast<size_t>(kSmemMaxO) ? 1 : 0;
   const size_t smem = whole ? whole_smem : step_smem;
   if (smem > static_cast<size_t>(kSmemMaxO)) return LRAMM_ERR_UNSUPPORTED;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(linv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+  LRAMM_CUDA_TRY(smem_cap(linv_kernel, static_cast<int>(smem)));
   linv_kernel<<<dim3(static_cast<unsigned>(nbk), lb.n), 1024, smem, s>>>(lb, l, whole, cond);
   return last_launch();
 }

@@ -913,7 +913,7 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
     const bool a1 = p.alpha == 1.f;
 #define LRAMM_TCP(K, A)                                                                                      \
   do {                                                                                                       \
-    LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tcp_kernel<K, A>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+    LRAMM_CUDA_TRY(smem_cap(qgemm_tcp_kernel<K, A>, \
                                         (int)psmem));                                                        \
     qgemm_tcp_kernel<K, A><<<gp, kPThreads, psmem, s>>>(mL, mR, mD, p, nt, ntl);                              \
   } while (0)
@@ -931,18 +931,15 @@ lramm_status launch_tc(int kind, const void* L, const void* R, int64_t M, int64_
   const dim3 grid(static_cast<unsigned>(sh.ntiles), static_cast<unsigned>(sh.mtiles), static_cast<unsigned>(sh.chunks));
   switch (kind) {
     case kKindBF16:
-      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+      LRAMM_CUDA_TRY(smem_cap(qgemm_tc_kernel<kKindBF16>, (int)smem));
       qgemm_tc_kernel<kKindBF16><<<grid, kQThreads, smem, s>>>(mL, mR, mD, p);
       break;
     case kKindFP8:
-      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindFP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+      LRAMM_CUDA_TRY(smem_cap(qgemm_tc_kernel<kKindFP8>, (int)smem));
       qgemm_tc_kernel<kKindFP8><<<grid, kQThreads, smem, s>>>(mL, mR, mD, p);
       break;
     default:
-      LRAMM_CUDA_TRY(cudaFuncSetAttribute(qgemm_tc_kernel<kKindTF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
+      LRAMM_CUDA_TRY(smem_cap(qgemm_tc_kernel<kKindTF32>, (int)smem));
       qgemm_tc_kernel<kKindTF32><<<grid, kQThreads, smem, s>>>(mL, mR, mD, p);
       break;
   }
@@ -1080,7 +1077,7 @@ lramm_status qterms_tc(int nterms, const void* const* L, const void* const* R, c
                 make_map_2d(&mD, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, D, N, M, ldd * 4, 32, 32, CU_TENSOR_MAP_SWIZZLE_128B);
   if (!p.tma_store) mD = mL[0];   // unused
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(qterms_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(qterms_tc_kernel, (int)smem));
   const dim3 grid(static_cast<unsigned>(ceil_div(N, kTermBN)), static_cast<unsigned>(ceil_div(M, kQM)));
   qterms_tc_kernel<<<grid, kQThreads, smem, s>>>(mL[0], mL[1], mL[2], mL[3], mR[0], mR[1], mR[2], mR[3], mD, p);
   return last_launch();

@@ -1026,7 +1026,7 @@ lramm_status sketch_bf(int a_mn, const void* X, int64_t rows, int64_t cols, int6
                    static_cast<uint64_t>(p.npad) * 2, kFAtom, kFK, CU_TENSOR_MAP_SWIZZLE_128B))
     return LRAMM_ERR_CUDA;
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(sketch_bf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(sketch_bf_kernel, (int)smem));
   sketch_bf_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits), static_cast<unsigned>(nslices)),
                      kThreads, smem, s>>>(mX, mBh, mBl, p);
   LRAMM_TRY(last_launch());
@@ -1094,7 +1094,7 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
   if (!make_map_f32(&mB, B, l, K, static_cast<uint64_t>(l) * 4, kAtom, kBK, CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
     return LRAMM_ERR_CUDA;
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (p.a_bytes + p.b_bytes);
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(sketch_tc_kernel, (int)smem));
   sketch_tc_kernel<<<dim3(static_cast<unsigned>(mtiles), static_cast<unsigned>(splits)), kThreads, smem, s>>>(mX, mB, p);
   LRAMM_TRY(last_launch());
   if (splits > 1) {
@@ -1143,7 +1143,7 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   p.status = status;
   const int gx = mtiles / p.mpc;
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * (2 * p.part_bytes + p.cstride) + red_bytes;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(gram_tc_kernel, (int)smem));
   for (int i = 0; i < n; ++i) {
     if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
     p.rows = rows[i];
@@ -1222,7 +1222,7 @@ lramm_status basis_tc(const float* Y, int64_t rows, const float* Lh, const float
       !make_map_f32(&mQ, Q, l, rows, pitch, kAtom, 32, CU_TENSOR_MAP_SWIZZLE_128B))
     return LRAMM_ERR_CUDA;
   const size_t smem = 1024 + static_cast<size_t>(p.stages) * stage;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(basis_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(basis_tc_kernel, (int)smem));
   basis_tc_kernel<<<static_cast<unsigned>(ceil_div(rows, kBM)), kThreads, smem, s>>>(mY, mLh, mLl, mQ, p, cond);
   return last_launch();
 }

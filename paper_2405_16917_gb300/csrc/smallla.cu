@@ -1071,7 +1071,7 @@ static const int kJacobiWarpsPerPair = 1;
 lramm_status launch_chol(SmallBatch bt, int l, float shift_rel, int* status, cudaStream_t s) {
   const size_t smem = sizeof(float) * (size_t)l * (l + 1) / 2;
   if (smem > (size_t)kSmemMax) return LRAMM_ERR_UNSUPPORTED;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(chol_kernel, (int)smem));
   chol_kernel<<<bt.n, 1024, smem, s>>>(bt, l, shift_rel, status);
   return last_launch();
 }
@@ -1080,7 +1080,7 @@ lramm_status launch_trsm_rows(SmallBatch bt, int l, cudaStream_t s) {
   const int threads = 1024, nw = threads / 32;
   const size_t smem = sizeof(float) * ((size_t)l * (l + 1) / 2 + l + (size_t)nw * l);
   if (smem > (size_t)kSmemMax) return LRAMM_ERR_UNSUPPORTED;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(trsm_rows_kernel, (int)smem));
   int64_t rows = 0;
   for (int i = 0; i < bt.n; ++i) rows = bt.p[i].rows > rows ? bt.p[i].rows : rows;
   int64_t grid = ceil_div(rows, nw);
@@ -1133,7 +1133,7 @@ static lramm_status launch_jacobi2_rp(JacobiBatch jb, int l, int ls, int C, int 
                                       float tol, int* status, cudaStream_t s, bool& launched) {
   launched = false;
   auto kern = jacobi_pair2_kernel<RP, GW>;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(kern, (int)smem));
   if (C > 8) LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
@@ -1189,7 +1189,7 @@ static lramm_status launch_pair3_rp(JacobiBatch jb, int l, int b, int max_sweeps
   const size_t smem = sizeof(float) * 3 * (size_t)b * 2 * ls;
   if (smem > (size_t)kSmemMax || 32 * b > 576) return LRAMM_OK;
   auto kern = jacobi_pair3_kernel<RP>;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(kern, (int)smem));
   LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
@@ -1237,7 +1237,7 @@ static lramm_status launch_uonly_rp(JacobiBatch jb, int l, int C, int b, size_t 
   ok = false;
   const int ls = 32 * RP;
   auto kern = jacobi_pair2_kernel<RP, 1, false>;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(kern, (int)smem));
   if (C > 8) LRAMM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(C * jb.n), 1, 1);
@@ -1300,7 +1300,7 @@ lramm_status launch_jacobi(JacobiBatch jb, int l, int max_sweeps, int* status, c
   size_t smem;
   if (!jacobi_shape(l, C, b, ls, smem)) return LRAMM_ERR_UNSUPPORTED;
   const float tol = 4.0f * sqrtf((float)l) * 0x1p-24f;
-  LRAMM_CUDA_TRY(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LRAMM_CUDA_TRY(smem_cap(jacobi_cluster_kernel, (int)smem));
   if (C > 8)
     LRAMM_CUDA_TRY(cudaFuncSetAttribute(jacobi_cluster_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg = {};
