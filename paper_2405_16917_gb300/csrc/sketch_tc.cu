@@ -628,6 +628,9 @@ __global__ void split_bf16_kernel(const float* __restrict__ B, int64_t K, int l,
 // which the converter warps accumulate in FP32 from a second, unswizzled TMA
 // copy of those columns: one M tile of MMAs instead of two (the MMA issue
 // is the kernel's clock), and a staged tile of ceil(l / 32) atoms.
+constexpr int kGK = 16;   // rows of Y per Gram stage (16-row atoms: LBO 2 KB)
+__device__ __forceinline__ uint64_t mnmajor_g_desc(uint32_t saddr) { return smem_desc(saddr, kAtom * kGK * 4, 512, 1); }
+
 struct GramTcParams {
   int l, W, n1, n2;
   int mpc;       // M tiles per CTA: 2 when l <= 256 (both from one staged tile), else 1 (grid x = M tile)
@@ -691,11 +694,11 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ 
         ok = false;
         break;
       }
-      mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(p.nload) * (kAtom * kBK * 4) +
-                                       static_cast<uint32_t>(p.corner) * (kBK * 4));
-      const int k0 = static_cast<int>((kb0 + i) * kBK);
+      mbar_expect_tx(&full_bar[s], static_cast<uint32_t>(p.nload) * (kAtom * kGK * 4) +
+                                       static_cast<uint32_t>(p.corner) * (kGK * 4));
+      const int k0 = static_cast<int>((kb0 + i) * kGK);
       uint8_t* dst = smem + static_cast<size_t>(s) * stage_bytes;
-      for (int j = 0; j < p.nload; ++j) tma_load_2d(dst + j * (kAtom * kBK * 4), &tmY, &full_bar[s], j * kAtom, k0);
+      for (int j = 0; j < p.nload; ++j) tma_load_2d(dst + j * (kAtom * kGK * 4), &tmY, &full_bar[s], j * kAtom, k0);
       if (p.corner)   // columns 128 .. l-1 of the same rows, row-major 32 x corner
         tma_load_2d(smem + static_cast<size_t>(p.stages) * stage_bytes + static_cast<size_t>(s) * p.cstride, &tmC,
                     &full_bar[s], kBM, k0);
@@ -714,7 +717,7 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ 
     const uint32_t id1 = idesc_tf32(kBM, p.n1, 1, 1);
     const uint32_t id1b = idesc_tf32(kBM, p.mpc == 2 ? ((p.l - kBM + 15) / 16) * 16 : 16, 1, 1);
     const uint32_t id2 = p.n2 ? idesc_tf32(kBM, p.n2, 1, 1) : 0u;
-    const uint32_t seg2 = static_cast<uint32_t>(256 / kAtom) * (kAtom * kBK * 4);
+    const uint32_t seg2 = static_cast<uint32_t>(256 / kAtom) * (kAtom * kGK * 4);
     for (int i = 0; i < nkb; ++i) {
       const int s = i % p.stages;
       if (!mbar_wait(&split_bar[s], (i / p.stages) & 1, abort_flag)) {
@@ -726,24 +729,24 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ 
       const uint32_t hi = smem_u32(smem + static_cast<size_t>(s) * stage_bytes);
       const uint32_t lo = hi + p.part_bytes;
       for (int t = 0; t < (p.corner ? 1 : p.mpc); ++t) {   // M tile mt + t into TMEM columns 256 t (n2 = 0 when mpc = 2)
-        const uint32_t aoff = static_cast<uint32_t>((mt + t) * (kBM / kAtom)) * (kAtom * kBK * 4);
+        const uint32_t aoff = static_cast<uint32_t>((mt + t) * (kBM / kAtom)) * (kAtom * kGK * 4);
         const uint32_t d = tmem + static_cast<uint32_t>(t * 256);
         // with two tiles per CTA the second needs only columns 128 .. l-1
         // (its rows' columns 0 .. 127 are the first tile's, transposed)
-        const uint32_t boff = t == 1 ? static_cast<uint32_t>(kBM / kAtom) * (kAtom * kBK * 4) : 0u;
+        const uint32_t boff = t == 1 ? static_cast<uint32_t>(kBM / kAtom) * (kAtom * kGK * 4) : 0u;
         const uint32_t idt = t == 1 ? id1b : id1;
 #pragma unroll
-        for (int kk = 0; kk < kBK / 8; ++kk) {
+        for (int kk = 0; kk < kGK / 8; ++kk) {
           const uint32_t ko = kk * 1024;
           const uint32_t acc0 = (i > 0 || kk > 0) ? 1u : 0u;
           // (A, B) = (hi, hi), (hi, lo), (lo, hi)
-          mma_tf32(d, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + boff + ko), idt, acc0);
-          mma_tf32(d, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + boff + ko), idt, 1u);
-          mma_tf32(d, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + boff + ko), idt, 1u);
+          mma_tf32(d, mnmajor_g_desc(hi + aoff + ko), mnmajor_g_desc(hi + boff + ko), idt, acc0);
+          mma_tf32(d, mnmajor_g_desc(hi + aoff + ko), mnmajor_g_desc(lo + boff + ko), idt, 1u);
+          mma_tf32(d, mnmajor_g_desc(lo + aoff + ko), mnmajor_g_desc(hi + boff + ko), idt, 1u);
           if (p.n2) {
-            mma_tf32(d + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, acc0);
-            mma_tf32(d + 256, mnmajor_desc(hi + aoff + ko), mnmajor_desc(lo + seg2 + ko), id2, 1u);
-            mma_tf32(d + 256, mnmajor_desc(lo + aoff + ko), mnmajor_desc(hi + seg2 + ko), id2, 1u);
+            mma_tf32(d + 256, mnmajor_g_desc(hi + aoff + ko), mnmajor_g_desc(hi + seg2 + ko), id2, acc0);
+            mma_tf32(d + 256, mnmajor_g_desc(hi + aoff + ko), mnmajor_g_desc(lo + seg2 + ko), id2, 1u);
+            mma_tf32(d + 256, mnmajor_g_desc(lo + aoff + ko), mnmajor_g_desc(hi + seg2 + ko), id2, 1u);
           }
         }
       }
@@ -753,8 +756,8 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ 
   } else if (warp >= 2) {
     // split each landed stage: high part in place, low part beside it
     const int st = threadIdx.x - 64;   // 0 .. 127
-    const int nq = p.nload * (kAtom * kBK * 4 / 16);   // the loaded atoms (the rest only pad MMA reads)
-    // the corner block: warp g = warp - 2 takes rows 8 g .. 8 g + 7 of each
+    const int nq = p.nload * (kAtom * kGK * 4 / 16);   // the loaded atoms (the rest only pad MMA reads)
+    // the corner block: warp g = warp - 2 takes rows 4 g .. 4 g + 3 of each
     // stage, lane (bi, bj) = (lane / 8, lane mod 8) the 4 x 2 block at
     // corner rows 4 bi .., columns 2 bj .. (FP32 FMAs in row order)
     const int g = warp - 2, ci = 4 * (lane >> 3), cj = 2 * (lane & 7);
@@ -781,9 +784,9 @@ gram_tc_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ 
         l4[e] = make_float4(y.x - h.x, y.y - h.y, y.z - h.z, y.w - h.w);
       }
       if (cown) {   // before the arrival below: the stage (and its corner copy) is refilled only after it
-        const float* cb = cbase + static_cast<size_t>(s) * (p.cstride / 4) + (8 * g) * p.corner;
+        const float* cb = cbase + static_cast<size_t>(s) * (p.cstride / 4) + (kGK / 4 * g) * p.corner;
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
+        for (int r = 0; r < kGK / 4; ++r) {
           const float4 a = *reinterpret_cast<const float4*>(cb + r * p.corner + ci);
           const float2 b = *reinterpret_cast<const float2*>(cb + r * p.corner + cj);
           cacc[0] = fmaf(a.x, b.x, cacc[0]);
@@ -1110,6 +1113,7 @@ lramm_status sketch_tc(int a_mn, const void* X, int64_t rows, int64_t cols, int6
 }
 
 // Gram on the tensor cores (split TF32) for one or two problems.
+constexpr size_t kGramCoSmem = 112 * 1024;
 static int gram_tc_width(int l) { return static_cast<int>(round_up(l, kBM)); }   // staged tile width
 size_t gram_tc_part_floats(int l) { return kPartSlots * l * l; }
 
@@ -1131,10 +1135,14 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   p.corner = (p.mpc == 2 && l - kBM <= 16) ? l - kBM : 0;
   p.nload = static_cast<int>(ceil_div(l, kAtom));
   if (p.corner) p.W = p.nload * kAtom;   // tile 0's A (atoms 0..3) and B (n1 columns) lie within the loaded atoms
-  p.part_bytes = static_cast<uint32_t>(p.W) * kBK * 4;
-  p.cstride = p.corner ? static_cast<uint32_t>(round_up(static_cast<size_t>(kBK) * p.corner * 4, 128)) : 0u;
+  p.part_bytes = static_cast<uint32_t>(p.W) * kGK * 4;
+  p.cstride = p.corner ? static_cast<uint32_t>(round_up(static_cast<size_t>(kGK) * p.corner * 4, 128)) : 0u;
   const size_t red_bytes = p.corner ? 4 * 32 * 8 * sizeof(float) : 0;
-  p.stages = static_cast<int>((kSmemBudget - 1024 - red_bytes) / (2 * p.part_bytes + p.cstride));
+  // at most ~110 KB when that still holds four stages: the CTA then fits
+  // beside one CTA of a concurrent range-finder product on its SM
+  const size_t gstage = 2 * static_cast<size_t>(p.part_bytes) + p.cstride;
+  p.stages = static_cast<int>((kGramCoSmem - 1024 - red_bytes) / gstage);
+  if (p.stages < 4) p.stages = static_cast<int>((kSmemBudget - 1024 - red_bytes) / gstage);
   if (p.stages > kMaxStages) p.stages = kMaxStages;
   if (p.stages < 2) return LRAMM_ERR_UNSUPPORTED;
   uint32_t tc = 32;
@@ -1147,7 +1155,7 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
   for (int i = 0; i < n; ++i) {
     if (rows[i] < 1) return LRAMM_ERR_INVALID_ARG;
     p.rows = rows[i];
-    p.kblocks = ceil_div(rows[i], kBK);
+    p.kblocks = ceil_div(rows[i], kGK);
     int64_t splits = num_sms() / (p.mpc == 2 ? 1 : mtiles);
     if (splits > p.kblocks / 2) splits = p.kblocks / 2;   // at least two K blocks per CTA
     if (splits < 1) splits = 1;
@@ -1160,11 +1168,11 @@ lramm_status gram_tc(int n, const float* const* Y, const int64_t* rows, float* c
     // l and rows beyond the end are loaded out of range (x a multiple of 32)
     // and arrive as zeros
     CUtensorMap my, mc;
-    if (!make_map_f32(&my, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, kAtom, kBK,
+    if (!make_map_f32(&my, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, kAtom, kGK,
                       CU_TENSOR_MAP_SWIZZLE_128B_ATOM_32B))
       return LRAMM_ERR_CUDA;
     if (p.corner) {   // the corner columns 128 .. l-1, a dense 32 x corner box (corner * 4 bytes: a multiple of 16)
-      if (!make_map_f32(&mc, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, static_cast<uint32_t>(p.corner), kBK,
+      if (!make_map_f32(&mc, Y[i], l, rows[i], static_cast<uint64_t>(l) * 4, static_cast<uint32_t>(p.corner), kGK,
                         CU_TENSOR_MAP_SWIZZLE_NONE))
         return LRAMM_ERR_CUDA;
     } else {
