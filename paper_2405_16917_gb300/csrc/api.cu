@@ -117,7 +117,7 @@ struct lramm_plan_s {
   size_t Ut, Vt, Wt, Zt, E1, E2t;
   size_t cV, cW, cE1, cZ, cU, cE2;
   size_t sV, sW, sE1, sZ, sU, sE2;
-  size_t amax;
+  size_t amax, amax2;   // per-tensor amax words: the call's stream, and the second operand's stream
   size_t qpart;
   size_t bsplit_bytes;           // BF16 parts of the l-column operand (BF16 A or B), per side
   // second stream and fork / join events: the two operands' RSVDs overlap
@@ -242,6 +242,7 @@ void layout(lramm_plan_s* P) {
   P->sU = b.take(sizeof(float) * d.m);
   P->sE2 = b.take(sizeof(float) * d.n);
   P->amax = b.take(kAlign);
+  P->amax2 = b.take(kAlign);
   P->xV = b.take(r * (P->kp / 32));
   P->xW = b.take(r * (P->kp / 32));
   P->xE1 = b.take(r * (P->rp / 32));
@@ -879,10 +880,25 @@ struct QOp {
 };
 
 lramm_status quant_op(lramm_plan_s* P, void* ws, const float* X, int64_t rows, int64_t cols, int64_t ldx, int prec,
-                      const QOp& op, int64_t ldq, cudaStream_t s) {
+                      const QOp& op, int64_t ldq, cudaStream_t s, bool second_stream = false) {
   if (prec == LRAMM_P_MXFP4) return quantize_mx(X, rows, cols, ldx, static_cast<int8_t*>(op.c), ldq, op.x, s);
   return quantize_rows(X, rows, cols, ldx, prec, P->d.scale == LRAMM_S_ROWCOL, op.c, ldq, op.s,
-                       at<unsigned int>(ws, P->amax), s);
+                       at<unsigned int>(ws, second_stream ? P->amax2 : P->amax), s);
+}
+
+// Which factor codes of the chain lramm_matmul forms on the operands' own
+// streams, before they join (each factor is quantised as soon as its
+// operand's randomized SVD is assembled; the chain then starts from E1).
+struct PreQuant {
+  bool vw, z, u;
+};
+PreQuant pre_quant(const lramm_desc& d, bool on) {
+  PreQuant q{false, false, false};
+  if (!on) return q;
+  q.vw = d.prec[0] != LRAMM_P_F32;
+  q.z = d.prec[1] != LRAMM_P_F32;
+  q.u = d.lead == 0 && d.prec[2] != LRAMM_P_F32 && d.prec[2] != LRAMM_P_MXFP4;
+  return q;
 }
 
 lramm_status qm_op(lramm_plan_s* P, void* ws, const QOp& L, const QOp& R, int64_t M, int64_t N, int64_t Kq, int prec,
@@ -1003,8 +1019,9 @@ lramm_status e3_lead_tail(lramm_plan_s* P, const float* Ut, const float* E2t, co
 }
 
 lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const float* Wt,
-                        const float* Zt, const float* C, float* D, void* ws, cudaStream_t s) {
+                        const float* Zt, const float* C, float* D, void* ws, cudaStream_t s, bool prequantised = false) {
   const lramm_desc& d = P->d;
+  const PreQuant pq = pre_quant(d, prequantised);
   const int64_t r = d.r, kp = P->kp, rp = P->rp;
   float* E1 = at<float>(ws, P->E1);
   float* E2t = at<float>(ws, P->E2t);
@@ -1014,8 +1031,10 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
   } else {
     const QOp v{at<void>(ws, P->cV), at<float>(ws, P->sV), at<int8_t>(ws, P->xV)};
     const QOp w{at<void>(ws, P->cW), at<float>(ws, P->sW), at<int8_t>(ws, P->xW)};
-    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Vt, r, d.k, d.k, d.prec[0], v, kp, s));
-    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Wt, r, d.k, d.k, d.prec[0], w, kp, s));
+    if (!pq.vw) {
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Vt, r, d.k, d.k, d.prec[0], v, kp, s));
+      TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Wt, r, d.k, d.k, d.prec[0], w, kp, s));
+    }
     TIMED(P, LRAMM_K_E1, s, qm_op(P, ws, v, w, r, r, kp, d.prec[0], 1.f, 0.f, nullptr, 0, E1, r, s));
   }
   // E2 = QM(E1 Z~, d2), computed transposed: E2^T = Z~^T E1^T (n x r, K = r)
@@ -1024,7 +1043,7 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
   } else {
     const QOp z{at<void>(ws, P->cZ), at<float>(ws, P->sZ), at<int8_t>(ws, P->xZ)};
     const QOp e1{at<void>(ws, P->cE1), at<float>(ws, P->sE1), at<int8_t>(ws, P->xE1)};
-    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Zt, d.n, r, r, d.prec[1], z, rp, s));
+    if (!pq.z) TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Zt, d.n, r, r, d.prec[1], z, rp, s));
     TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E1, r, r, r, d.prec[1], e1, rp, s));
     TIMED(P, LRAMM_K_E2, s, qm_op(P, ws, z, e1, d.n, r, rp, d.prec[1], 1.f, 0.f, nullptr, 0, E2t, r, s));
   }
@@ -1053,7 +1072,7 @@ lramm_status chain_core(lramm_plan_s* P, const float* Ut, const float* Vt, const
     }
     const QOp u{at<void>(ws, P->cU), at<float>(ws, P->sU), at<int8_t>(ws, P->xU)};
     const QOp e2{at<void>(ws, P->cE2), at<float>(ws, P->sE2), at<int8_t>(ws, P->xE2)};
-    TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut, d.m, r, r, d.prec[2], u, rp, s));
+    if (!pq.u) TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, Ut, d.m, r, r, d.prec[2], u, rp, s));
     TIMED(P, LRAMM_K_QUANT, s, quant_op(P, ws, E2t, d.n, r, r, d.prec[2], e2, rp, s));
     TIMED(P, LRAMM_K_E3, s, qm_op(P, ws, u, e2, d.m, d.n, rp, d.prec[2], d.alpha, beta, C, d.ldc, D, d.ldc, s));
   }
@@ -1368,6 +1387,14 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   cudaStream_t s2 = plan->s2;
   LRAMM_CUDA_TRY(cudaEventRecord(plan->ev_fork, s));
   LRAMM_CUDA_TRY(cudaStreamWaitEvent(s2, plan->ev_fork, 0));
+  // each operand's factors are quantised on its own stream once assembled,
+  // so that the first operand's codes form while the second's randomized SVD
+  // still runs (the per-tensor amax word of the second stream is its own)
+  const PreQuant pq = pre_quant(d, true);
+  const QOp qv{at<void>(ws, plan->cV), at<float>(ws, plan->sV), at<int8_t>(ws, plan->xV)};
+  const QOp qw{at<void>(ws, plan->cW), at<float>(ws, plan->sW), at<int8_t>(ws, plan->xW)};
+  const QOp qz{at<void>(ws, plan->cZ), at<float>(ws, plan->sZ), at<int8_t>(ws, plan->xZ)};
+  const QOp qu{at<void>(ws, plan->cU), at<float>(ws, plan->sU), at<int8_t>(ws, plan->xU)};
   auto side_a = [&]() -> lramm_status {
     bool mo = false;
     LRAMM_TRY(rsvd_sides(plan, &sd[0], &which[0], 1, ws, &s1s[0], &s2s[0], s, stopq, m_only, &mo, plan->ev_stag));
@@ -1382,6 +1409,8 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
       TIMED(plan, LRAMM_K_ASSEMBLE, s,
             assemble(plan, ws, SA, r, d.k, at<float>(ws, SA.S2T), at<float>(ws, SA.C0), Vt, d.k, 1,
                      at<float>(ws, SA.S2), r, 1, at<float>(ws, SA.C0), l, s, true));
+    if (pq.vw) TIMED(plan, LRAMM_K_QUANT, s, quant_op(plan, ws, Vt, r, d.k, d.k, d.prec[0], qv, plan->kp, s));
+    if (pq.u) TIMED(plan, LRAMM_K_QUANT, s, quant_op(plan, ws, Ut, d.m, r, r, d.prec[2], qu, plan->rp, s));
     return LRAMM_OK;
   };
   // B: W^T = U_s^T Q_B^T (r x k);  Z~^T = P_B (V_s Gamma) (n x r)  (M-only
@@ -1401,6 +1430,9 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
       TIMED(plan, LRAMM_K_ASSEMBLE, s2,
             assemble(plan, ws, SB, d.n, r, at<float>(ws, SB.C0), at<float>(ws, SB.S2T), Zt, r, 0,
                      at<float>(ws, SB.C0), l, 0, at<float>(ws, SB.S2), r, s2, true));
+    if (pq.vw)
+      TIMED(plan, LRAMM_K_QUANT, s2, quant_op(plan, ws, Wt, r, d.k, d.k, d.prec[0], qw, plan->kp, s2, true));
+    if (pq.z) TIMED(plan, LRAMM_K_QUANT, s2, quant_op(plan, ws, Zt, d.n, r, r, d.prec[1], qz, plan->rp, s2, true));
     return LRAMM_OK;
   };
   const lramm_status st_a = side_a();
@@ -1410,7 +1442,7 @@ lramm_status matmul_body(lramm_plan_t plan, const void* A, const void* B, const 
   LRAMM_CUDA_TRY(cudaStreamWaitEvent(s, plan->ev_join, 0));
   LRAMM_TRY(st_a);
   LRAMM_TRY(st_b);
-  return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s);
+  return chain_core(plan, Ut, Vt, Wt, Zt, C, D, ws, s, true);
 }
 
 lramm_status lramm_info_read(const void* ws, int32_t* info, int32_t n, void* stream) {
