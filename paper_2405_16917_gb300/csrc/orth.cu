@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
   __shared__ float s_red[32];
   __shared__ float s_rinv[kCB];
   __shared__ float s_rl[kCB];   // 1 / L_tt of the diagonal block being inverted
+  __shared__ __align__(16) float s_dcol[2 * kCB];   // the current pivot's column, two buffers
   __shared__ int s_bad;   // a pivot of this attempt was not positive
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ uint32_t s_tmem;
@@ -631,6 +632,10 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
         // remaining updates of this pivot issue.  A non-positive pivot is
         // replaced without a branch and latched once after the block, so the
         // unrolled pivots form straight-line code.
+        // The column l_ck of each pivot reaches the lanes through shared
+        // memory (one store a lane, float4 broadcast reads, two buffers so
+        // that one __syncwarp a pivot suffices) instead of a shuffle per
+        // column: the same FMAs in the same order.
         bool bad = false;
         float piv = __shfl_sync(0xffffffffu, a[0], 0);
   #pragma unroll
@@ -643,8 +648,17 @@ __global__ void __launch_bounds__(512, 1) chol3_kernel(CholBatch cb, int l, floa
           if (lane == k) s_rinv[k] = inv;
           float piv_next = 0.f;
           if (k + 1 < kCB) piv_next = __shfl_sync(0xffffffffu, fmaf(-lk, lk, a[k + 1]), k + 1);
+          float* dcol = s_dcol + (k & 1) * kCB;
+          dcol[lane] = lk;
+          __syncwarp();
   #pragma unroll
-          for (int c = k + 1; c < kCB; ++c) a[c] = fmaf(-lk, __shfl_sync(0xffffffffu, lk, c), a[c]);
+          for (int c4 = ((k + 1) / 4) * 4; c4 < kCB; c4 += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(dcol + c4);
+            if (c4 + 0 > k) a[c4 + 0] = fmaf(-lk, v.x, a[c4 + 0]);
+            if (c4 + 1 > k) a[c4 + 1] = fmaf(-lk, v.y, a[c4 + 1]);
+            if (c4 + 2 > k) a[c4 + 2] = fmaf(-lk, v.z, a[c4 + 2]);
+            if (c4 + 3 > k) a[c4 + 3] = fmaf(-lk, v.w, a[c4 + 3]);
+          }
           piv = piv_next;
         }
         if (bad && lane == 0) s_bad = 1;

@@ -1265,7 +1265,10 @@ lramm_status launch_jacobi_uonly(JacobiBatch jb, int l, int max_sweeps, int* sta
                                  bool& ok) {
   ok = false;
   if (l < 2 || l > kJUMaxL || jb.r <= 0 || jb.n < 1) return LRAMM_OK;
-  int C = (int)ceil_div(l, 16);
+  // up to l = 192 wider blocks on fewer CTAs (fewer block moves per sweep;
+  // l = 144: 6 CTAs of 12 columns, measured ahead of 9 of 8), beyond that
+  // 16-column pairs per CTA (l = 272: 9 and 12 CTAs measured slower than 16)
+  int C = (int)ceil_div(l, l <= 192 ? 24 : 16);
   if (C > 16) C = 16;
   const int b = (int)ceil_div(l, 2 * C), rp = (int)ceil_div(l, 32);
   const size_t smem = sizeof(float) * 4 * (size_t)b * 32 * rp;
