@@ -362,6 +362,29 @@ def quantised_agreement(D, ref_q, ref_f, exact):
     assert abs(err_gpu - err_orc) <= 0.10 * err_orc
 
 
+def test_matmul_per_tensor_scales_lramm_512(L):
+    """Per-tensor scales through lramm_matmul: each operand's factors are
+    quantised on its own stream (the second stream with its own amax word)
+    before the chain; the result against the oracle's per-tensor chain by
+    the same noise criterion as the per-row case."""
+    c = workloads.CONFIGS["lramm_512"]
+    A, B = workloads.operands("lramm_512")
+    A32, B32 = A.astype(np.float32), B.astype(np.float32)
+    m, k = A32.shape
+    n = B32.shape[1]
+    prec = (1, 1, 1)
+    plan = L.Plan(m, n, k, c["r"], c["p"], c["q"], seed=workloads.SEED_SKETCH, prec=prec, scale=L.S_TENSOR)
+    ws = plan.workspace()
+    D1 = np_(L.matmul(plan, dev(A32), dev(B32), ws=ws)).astype(np.float64)
+    D2 = np_(L.matmul(plan, dev(A32), dev(B32), ws=ws)).astype(np.float64)
+    assert L.status_read(ws) == 0
+    assert np.array_equal(D1, D2)   # the per-tensor amax words start from zero on every call
+    ref = oracle.lramm.lramm(A32, B32, c["r"], c["p"], c["q"], workloads.SEED_SKETCH, prec,
+                             scale=oracle.quant.SCALE_TENSOR)
+    ref_f = oracle.lramm.lramm(A32, B32, c["r"], c["p"], c["q"], workloads.SEED_SKETCH, (0, 0, 0))
+    quantised_agreement(D1, ref, ref_f, oracle.lramm.exact_product(A32, B32))
+
+
 @pytest.mark.parametrize("prec", [(1, 1, 1), (1, 1, 2), (3, 3, 3)])
 def test_matmul_quantised_lramm_512(L, prec):
     D, ref, A, B = _e2e(L, "lramm_512", prec)
